@@ -1,0 +1,35 @@
+"""Build the FP64 CPU oracle (test infrastructure) into oracle/liboracle.so.
+
+Only tests/, __graft_entry__ (build, smoke) and bench.py's CPU-baseline legs
+use the oracle; the product path never loads it.
+"""
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SOURCES = ["dynamics.c", "world.c", "mppi.c"]
+LIB = os.path.join(HERE, "liboracle.so")
+
+# -ffp-contract=off: no implicit fused multiply-add, so the FP32 sampling
+# sequence is exactly the one written (explicit fmaf) on every host.
+CFLAGS = ["-O2", "-std=gnu11", "-fPIC", "-shared", "-pthread", "-fno-fast-math",
+          "-ffp-contract=off", "-Wall", "-Wno-unused-function"]
+
+
+def build(force: bool = False) -> str:
+    srcs = [os.path.join(HERE, s) for s in SOURCES]
+    deps = srcs + [os.path.join(HERE, "oracle.h")]
+    if not force and os.path.exists(LIB):
+        t = os.path.getmtime(LIB)
+        if all(os.path.getmtime(d) <= t for d in deps):
+            return LIB
+    tmp = LIB + ".tmp%d" % os.getpid()
+    cmd = ["gcc"] + CFLAGS + srcs + ["-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv))
