@@ -1,0 +1,308 @@
+"""Benchmark of one MPPI control step (arXiv 2409.10469, Alg. 1) on GB300.
+
+Workload: trot on a flat plane (dt 0.005 s, n_sub 4, sigma 0.3, lambda 0.1)
+at K = 4096 samples, H = 100 steps.  A step is one full pass of the hot path:
+Philox knot sampling -> 4096 rollouts of the floating-base quadruped ->
+softmax update, applied control and shift (mppi_step of the C ABI).
+
+Metric: rollout-steps/s = K * H / step time (plus step latency p50 / p99).
+`value` is device-timed with inputs resident in HBM (CUDA events around each
+step on the controller's stream, L2 flushed between steps outside the timed
+events); `e2e` times the same call through the C ABI with HOST buffers (x0
+copied in from pinned memory, u0 read back) on the host clock.
+
+`--impl reference` times the FP64 CPU oracle on the host cores on the same
+workload (each step a bounded sample of the K rollouts).  Under torchrun each
+rank runs its own independent controller instance (weak scaling, no
+collective: MPPI instances share nothing).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+K_BENCH, H_BENCH = 4096, 100
+METRIC = "rollout-steps/s (MPPI step, K=4096, H=100)"
+
+
+def dist_env():
+    r = int(os.environ.get("RANK", "0"))
+    w = int(os.environ.get("WORLD_SIZE", "1"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return r, w, lr
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([s.strip() for s in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=6)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return None
+
+
+def cpu_baseline(cfg, seconds=12.0):
+    """The FP64 oracle as it stands, on all host cores, over a bounded sample of
+    the workload's rollouts (whole batches of 256 until `seconds` elapsed)."""
+    import oracle as O
+    world = O.World(cfg.robot)
+    m = dict(cfg.mppi)
+    cores = os.cpu_count() or 1
+    U = O.sample(dict(m, K=256), cfg.mu0, 0)
+    x0 = cfg.x0.astype(np.float64)
+    n_roll, t_start = 0, time.perf_counter()
+    while True:
+        O.rollouts(world, cfg.cost, m, 0.0, x0, U, nthreads=cores)
+        n_roll += U.shape[0]
+        el = time.perf_counter() - t_start
+        if el >= seconds:
+            break
+    rate = n_roll * m["H"] / el
+    return {"value": rate, "unit": "rollout-steps/s", "cores": cores, "kind": "oracle",
+            "sample": "%d rollouts of the K=4096 H=100 trot workload (H=%d, n_sub=%d, FP64) in %.1f s"
+                      % (n_roll, m["H"], m["n_sub"], el)}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on host cores, same workload/metric."""
+    rank, world_size, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2409_10469_gb300 import workloads as W
+    cfg = W.config_trot(K=K_BENCH, H=H_BENCH)
+    world = O.World(cfg.robot)
+    cores = os.cpu_count() or 1
+    sample_K = 512          # bounded sample of the 4096 rollouts per step
+    m = dict(cfg.mppi)
+    x0 = cfg.x0.astype(np.float64)
+    mu = cfg.mu0.copy()
+
+    def one(step):
+        U = O.sample(dict(m, K=sample_K), mu, step)
+        t = time.perf_counter()
+        L = O.rollouts(world, cfg.cost, m, 0.0, x0, U, nthreads=cores)
+        O.update(L.astype(np.float32), U, m["lam"])
+        return time.perf_counter() - t
+
+    for s in range(args.warmup):
+        one(s)
+    times = [one(args.warmup + s) for s in range(args.steps)]
+    per_step = float(np.mean(times)) * K_BENCH / sample_K   # scaled to the full K
+    value = K_BENCH * H_BENCH / per_step
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rollout-steps/s",
+            "n_gpus": world_size, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "trot flat plane K=4096 H=100 dt=0.005 n_sub=4",
+                       "K": K_BENCH, "H": H_BENCH, "l2": "n/a (host)"},
+            "cpu_baseline": {"value": value, "unit": "rollout-steps/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": "%d of the %d rollouts per step, scaled to K" % (sample_K, K_BENCH)},
+            "e2e": {"value": value, "unit": "rollout-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+    from paper_2409_10469_gb300 import _mppi, flops as F, workloads as W
+
+    rank, world_size, local_rank = dist_env()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world_size > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    cfg = W.config_trot(K=K_BENCH, H=H_BENCH)
+    m = dict(cfg.mppi)
+    m["inst"] = rank        # independent instance per rank (own Philox stream)
+    stream = torch.cuda.Stream()
+    ctl = _mppi.Controller(cfg.robot, cfg.cost, m, stream=stream.cuda_stream, block=args.block)
+    ctl.set_nominal(cfg.mu0)
+    x0_d = torch.tensor(cfg.x0, dtype=torch.float32, device="cuda")
+    u0_d = torch.empty(12, dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+
+    # warm-up
+    for s in range(args.warmup):
+        ctl.step(x0_d, s, u0_out=u0_d)
+    torch.cuda.synchronize()
+
+    ctl.set_timing(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    k_ms = []
+    launches0 = ctl.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[0])
+                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local_rank)
+    with sampler:
+        for s in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(s))          # evict L2 between steps (outside the events)
+                starts[s].record(stream)
+            ctl.step(x0_d, args.warmup + s, u0_out=u0_d)
+            ends[s].record(stream)
+            if (s + 1) % 16 == 0 or s == args.steps - 1:
+                stream.synchronize()
+            k_ms.append(None)
+        torch.cuda.synchronize()
+        # per-kernel times of every step: re-run with the library's events read per step
+        ker = []
+        for s in range(min(args.steps, 64)):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(s))
+            ctl.step(x0_d, args.warmup + args.steps + s, u0_out=u0_d)
+            ker.append(ctl.timings())
+    launches = ctl.launch_count() - launches0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = np.array([a.elapsed_time(b) for a, b in zip(starts, ends)])
+    mean_ms = float(step_ms.mean())
+    if dist:
+        t = torch.tensor([mean_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        mean_ms = float(t.item())
+    ker = np.array(ker)
+    timed_launches = 3 * args.steps   # sample, rollout, update per step (timed loop only)
+
+    # end to end through the C ABI with host buffers (pinned x0 in, u0 out)
+    x0_h = torch.tensor(cfg.x0, dtype=torch.float32).pin_memory()
+    u0_h = torch.empty(12, dtype=torch.float32).pin_memory()
+    e2e = []
+    for s in range(max(8, min(args.steps, 64))):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(s))
+        stream.synchronize()
+        t = time.perf_counter()
+        ctl.step(x0_h, 10000 + s, u0_out=u0_h)
+        e2e.append(time.perf_counter() - t)
+    e2e_ms = float(np.mean(e2e)) * 1e3
+    clocks = sampler.summary()
+    ctl.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks = measured_peaks()
+    rollout_ms = float(ker[:, 1].mean())
+    fl = F.rollout_flops(K_BENCH, H_BENCH, m["n_sub"])
+    achieved = fl / (rollout_ms * 1e-3) / 1e12
+    sm_max = (peaks or {}).get("sm_max_mhz", 2070.0)
+    peak = F.fp32_peak_tflops(152, sm_max)
+    value = world_size * K_BENCH * H_BENCH / (mean_ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "rollout-steps/s", "n_gpus": world_size,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "trot flat plane K=4096 H=100 dt=0.005 n_sub=4 (fp32, FP64 normaliser)",
+                   "K": K_BENCH, "H": H_BENCH, "n_sub": m["n_sub"], "l2": "flushed between steps",
+                   "parallelism": "independent instance per GPU"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                       "max": float(step_ms.max())},
+        "kernel_ms": {"sample": float(ker[:, 0].mean()), "rollout": rollout_ms,
+                      "update": float(ker[:, 2].mean())},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_rollout", "flops_per_launch": fl,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (max SM clock, MEASURED_PEAKS.json)" % sm_max},
+        "e2e": {"value": world_size * K_BENCH * H_BENCH / (e2e_ms * 1e-3), "unit": "rollout-steps/s",
+                "ms_per_step": e2e_ms, "p99_ms": float(np.percentile(np.array(e2e) * 1e3, 99)),
+                "h2d_bytes_per_step": 4 * 37, "d2h_bytes_per_step": 4 * 12 + 4},
+        "gpu_launches": timed_launches,
+        "clocks": clocks,
+    }
+    if args.cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg, seconds=args.cpu_seconds)
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        import __graft_entry__ as g
+        g.build()
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

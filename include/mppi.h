@@ -1,0 +1,166 @@
+/*
+ * mppi.h -- C ABI of the GB300 (sm_103a) whole-body MPPI hot path.
+ *
+ * Method: arXiv 2409.10469 (Alvarez-Padilla et al., "Real-Time Whole-Body Control
+ * of Legged Robots with Model-Predictive Path Integral Control").
+ *   Alg. 1 (Sec. II-B): sample N perturbations of the control mean, simulate each
+ *   over T steps, accumulate its cost, weight by Eq. 1, update the mean by Eq. 2,
+ *   apply u = mu[0], shift the mean.  Controls are 4 cubic-spline knots of 12 joint
+ *   targets (Sec. III-B, Fig. 2) tracked by PD (Sec. IV-A).  Costs: L_walk
+ *   (Sec. IV-B) and L_box (Sec. IV-D).  The rollout model replaces MuJoCo
+ *   (Sec. III-A): floating-base Featherstone ABA, penalty contacts with regularised
+ *   Coulomb friction, semi-implicit Euler with n_sub sub-steps.
+ *
+ * Conventions shared by every entry point:
+ *   - Status codes, never abort/exit; mppi_last_error() gives the text.
+ *   - Pointers may be host or device memory: the library asks
+ *     cudaPointerGetAttributes and copies host buffers through its own pinned
+ *     staging.  The caller owns every pointer it passes; the handle owns its
+ *     device workspace.  Device buffers must be on the handle's device.
+ *   - Work is enqueued on the handle's stream (given at creation; NULL = the
+ *     legacy default stream).  A call returns once its work is enqueued, except
+ *     that results written to HOST memory are complete on return (the call
+ *     synchronises the stream).
+ *   - A handle is not thread-safe; different handles are independent.
+ *   - State x (float): [p(3) world, quat(w,x,y,z) body->world (4), joints(12),
+ *     omega body(3), v body(3), joint rates(12)] = 37, plus the free box
+ *     [p, quat, omega, v] (13) = 50 when the model has one.  Joint order
+ *     FR, FL, RR, RL x (abduction, hip flexion, knee).
+ *   - Knots U (float[48]) are [knot j = 0..3][joint 0..11]; knot j sits at
+ *     normalised time j/3 of the horizon.
+ */
+#ifndef MPPI_GB300_H
+#define MPPI_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mppi_handle_s* mppi_handle;
+
+typedef enum {
+    MPPI_OK = 0,
+    MPPI_ERR_ARG = 1,        /* invalid argument (null, size out of range, bad layout) */
+    MPPI_ERR_OOM = 2,        /* device allocation failed */
+    MPPI_ERR_CUDA = 3,       /* a CUDA call failed (text in mppi_last_error) */
+    MPPI_ERR_NONFINITE = 4,  /* non-finite state, or every rollout cost non-finite */
+    MPPI_ERR_TIMEOUT = 5,    /* a bounded device wait ran out */
+    MPPI_ERR_BUSY = 6,       /* admission refused (memory budget) */
+    MPPI_ERR_NOTSUP = 7      /* requested feature not available in this build */
+} mppi_status;
+
+/* Raw physical description of robot, contacts and terrain.  Derived quantities
+ * (spatial inertias) are computed by the library.  The heightfield pointer is
+ * read at creation (host or device) and copied into the handle. */
+typedef struct {
+    double trunk_mass, trunk_size[3];
+    double hip_x, hip_y, hip_z;
+    double abd_mass, abd_radius;
+    double thigh_offset_y;
+    double thigh_mass, thigh_length;
+    double calf_mass, calf_length;
+    double rod_radius;
+    double foot_radius;
+    int n_trunk_spheres; double trunk_sphere_x[4]; double trunk_sphere_r;
+    double gravity;
+    double kp, kd, armature;
+    double k_contact, c_contact, mu, eps_v;
+    int has_box; double box_mass, box_size[3], box_corner_r;
+    int terrain;                 /* 0 plane z = 0, 1 heightfield */
+    int hf_nx, hf_ny; double hf_cell, hf_x0, hf_y0;
+    const float* hf;             /* [hf_ny][hf_nx] heights, row = y */
+    int n_static_boxes; double sbox_lo[4][3], sbox_hi[4][3];
+} mppi_model_t;
+
+/* L_walk (Sec. IV-B) + L_box (Sec. IV-D) weights and references. */
+typedef struct {
+    double w_z, z_ref, w_o, w_v, v_ref, w_p, goal_xy[2], w_u, w_box, box_goal_xy[2];
+    int gait;                    /* 0 stand reference, 1 open-loop trot */
+    double gait_period, gait_hip_amp, gait_knee_amp;
+    double stand[3];
+    double w_terminal;
+} mppi_cost_t;
+
+/* Alg. 1 inputs N (= K), T (= H), lambda, Sigma (diagonal sigma), plus the model's
+ * sub-step count and the control period in dt steps. */
+typedef struct {
+    int K, H, n_sub, ctrl_steps;
+    double dt, lambda;
+    float sigma[48];
+    float q_lo[3], q_hi[3];      /* knot clamp per joint type */
+    uint64_t seed;               /* Philox4x32-10 key */
+    uint32_t inst;               /* instance id (Philox counter word 3) */
+    int n_prop;                  /* last n_prop samples centre on a proposal mean */
+    int block;                   /* rollout kernel block size in threads (0 = default) */
+} mppi_config_t;
+
+/* Create a controller: copies model, cost and config, derives the model's
+ * device constants, allocates its workspace (U[K][48], L[K], mu, u0, status)
+ * for up to cfg->K samples.  stream: a cudaStream_t or NULL.
+ * Errors: ARG (K < 1, H < 2, n_sub < 1, dt <= 0, lambda <= 0, bad terrain),
+ * OOM, CUDA. */
+mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t* cost,
+                        const mppi_config_t* cfg, void* stream, mppi_handle* out);
+
+/* Free the handle and its device memory (synchronises its stream). */
+mppi_status mppi_destroy(mppi_handle h);
+
+/* Text of the last error on this handle ("" if none); valid until the next call. */
+const char* mppi_last_error(mppi_handle h);
+
+/* Nominal knots mu (float[48], host or device): write / read. */
+mppi_status mppi_set_nominal(mppi_handle h, const float* mu);
+mppi_status mppi_get_nominal(mppi_handle h, float* mu_out);
+
+/* Alg. 1 sampling step (Sec. II-B; noise generator per the model spec):
+ * U[k] = clamp(mu + sigma * eps_k), eps_k = Box-Muller(Philox4x32-10(key = seed,
+ * counter = (g, k, step, inst))), sample 0 = mu; with mu_prop != NULL the last
+ * n_prop samples centre on mu_prop (the first of them is mu_prop itself).
+ * U_out: float[K][48] (host or device), or NULL to fill the handle's own buffer. */
+mppi_status mppi_sample(mppi_handle h, uint32_t step, const float* mu_prop, float* U_out);
+
+/* Alg. 1 simulate-and-cost step: roll out n knot vectors U (float[n][48]; NULL =
+ * the handle's sampled buffer, n <= K) from x0 (float[nx], or float[n][nx] when
+ * x0_per_sample) over H dt steps of n_sub sub-steps, starting at absolute time t0
+ * (phase of the gait reference).  L_out: float[n] costs (L_walk + L_box, NULL =
+ * the handle's buffer).  traj_out: optional float[n][H + 1][nx] states x_0..x_H.
+ * Errors: ARG, NONFINITE (x0 not finite), CUDA. */
+mppi_status mppi_rollouts(mppi_handle h, const float* x0, int x0_per_sample, const float* U,
+                          int n, double t0, float* L_out, float* traj_out);
+
+/* Eq. 1 + Eq. 2 + apply + shift: weights exp(-(L - L_min)/lambda) over finite
+ * costs (normaliser accumulated in FP64), mu' = sum w U / sum w, u0 = mu'[knot 0],
+ * then the nominal becomes shifted(mu').  L (float[n]) and U (float[n][48]) may be
+ * NULL for the handle's own buffers.  mu_out (float[48], the updated mean before
+ * the shift), u0_out (float[12]) optional.  Returns NONFINITE and keeps mu when
+ * no cost is finite. */
+mppi_status mppi_update(mppi_handle h, const float* L, const float* U, int n, float* mu_out,
+                        float* u0_out);
+
+/* One full control step of Alg. 1 at control index `step` (gait time
+ * step * ctrl_steps * dt): sample, roll out from x0 (float[nx]), update, shift.
+ * u0_out: float[12] joint targets to apply; mu_out optional float[48] (updated
+ * mean before the shift).  With host outputs the call returns after the step
+ * completed. */
+mppi_status mppi_step(mppi_handle h, const float* x0, uint32_t step, float* u0_out,
+                      float* mu_out);
+
+/* Per-kernel device time of the last mppi_step, measured with CUDA events on
+ * the handle's stream when timing is on: ms[0] sample, ms[1] rollout, ms[2]
+ * update.  Timing is off by default (events add a few microseconds). */
+mppi_status mppi_set_timing(mppi_handle h, int on);
+mppi_status mppi_get_timings(mppi_handle h, float ms[3]);
+
+/* Number of kernels the library launched on this handle since creation. */
+mppi_status mppi_launch_count(mppi_handle h, uint64_t* count);
+
+/* State size of the handle's model: 37, or 50 with the free box. */
+int mppi_state_size(mppi_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

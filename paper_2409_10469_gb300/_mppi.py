@@ -1,0 +1,253 @@
+"""Thin ctypes binding of the C ABI in include/mppi.h (libmppi_gb300.so).
+
+Argument marshalling only: every step of the MPPI path (sampling, rollouts,
+update, shift) runs in the library's CUDA kernels.  Buffers may be torch
+tensors (device or host) or numpy arrays; they are passed as raw pointers.
+The library must be built (``paper_2409_10469_gb300.build``); importing this
+module without it raises, there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmppi_gb300.so")
+
+MPPI_OK, MPPI_ERR_ARG, MPPI_ERR_OOM, MPPI_ERR_CUDA = 0, 1, 2, 3
+MPPI_ERR_NONFINITE, MPPI_ERR_TIMEOUT, MPPI_ERR_BUSY, MPPI_ERR_NOTSUP = 4, 5, 6, 7
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NONFINITE",
+                5: "ERR_TIMEOUT", 6: "ERR_BUSY", 7: "ERR_NOTSUP"}
+
+# every entry point declared in include/mppi.h
+EXPORTS = ("mppi_create", "mppi_destroy", "mppi_last_error", "mppi_set_nominal",
+           "mppi_get_nominal", "mppi_sample", "mppi_rollouts", "mppi_update", "mppi_step",
+           "mppi_set_timing", "mppi_get_timings", "mppi_launch_count", "mppi_state_size")
+
+
+class MppiError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class MppiModel(C.Structure):
+    _fields_ = [
+        ("trunk_mass", C.c_double), ("trunk_size", C.c_double * 3),
+        ("hip_x", C.c_double), ("hip_y", C.c_double), ("hip_z", C.c_double),
+        ("abd_mass", C.c_double), ("abd_radius", C.c_double),
+        ("thigh_offset_y", C.c_double),
+        ("thigh_mass", C.c_double), ("thigh_length", C.c_double),
+        ("calf_mass", C.c_double), ("calf_length", C.c_double),
+        ("rod_radius", C.c_double), ("foot_radius", C.c_double),
+        ("n_trunk_spheres", C.c_int), ("trunk_sphere_x", C.c_double * 4),
+        ("trunk_sphere_r", C.c_double),
+        ("gravity", C.c_double),
+        ("kp", C.c_double), ("kd", C.c_double), ("armature", C.c_double),
+        ("k_contact", C.c_double), ("c_contact", C.c_double), ("mu", C.c_double),
+        ("eps_v", C.c_double),
+        ("has_box", C.c_int), ("box_mass", C.c_double), ("box_size", C.c_double * 3),
+        ("box_corner_r", C.c_double),
+        ("terrain", C.c_int), ("hf_nx", C.c_int), ("hf_ny", C.c_int),
+        ("hf_cell", C.c_double), ("hf_x0", C.c_double), ("hf_y0", C.c_double),
+        ("hf", C.c_void_p),
+        ("n_static_boxes", C.c_int), ("sbox_lo", (C.c_double * 3) * 4),
+        ("sbox_hi", (C.c_double * 3) * 4),
+    ]
+
+
+class MppiCost(C.Structure):
+    _fields_ = [
+        ("w_z", C.c_double), ("z_ref", C.c_double), ("w_o", C.c_double),
+        ("w_v", C.c_double), ("v_ref", C.c_double), ("w_p", C.c_double),
+        ("goal_xy", C.c_double * 2), ("w_u", C.c_double), ("w_box", C.c_double),
+        ("box_goal_xy", C.c_double * 2),
+        ("gait", C.c_int), ("gait_period", C.c_double), ("gait_hip_amp", C.c_double),
+        ("gait_knee_amp", C.c_double), ("stand", C.c_double * 3), ("w_terminal", C.c_double),
+    ]
+
+
+class MppiConfig(C.Structure):
+    _fields_ = [
+        ("K", C.c_int), ("H", C.c_int), ("n_sub", C.c_int), ("ctrl_steps", C.c_int),
+        ("dt", C.c_double), ("lam", C.c_double),
+        ("sigma", C.c_float * 48), ("q_lo", C.c_float * 3), ("q_hi", C.c_float * 3),
+        ("seed", C.c_uint64), ("inst", C.c_uint32), ("n_prop", C.c_int), ("block", C.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libmppi_gb300.so is not built: run __graft_entry__.build() "
+                              "(the CUDA path has no fallback)")
+        L = C.CDLL(LIB_PATH)
+        vp, fp = C.c_void_p, C.c_void_p
+        L.mppi_create.argtypes = [C.POINTER(MppiModel), C.POINTER(MppiCost), C.POINTER(MppiConfig),
+                                  vp, C.POINTER(C.c_void_p)]
+        L.mppi_destroy.argtypes = [vp]
+        L.mppi_last_error.restype = C.c_char_p
+        L.mppi_last_error.argtypes = [vp]
+        L.mppi_set_nominal.argtypes = [vp, fp]
+        L.mppi_get_nominal.argtypes = [vp, fp]
+        L.mppi_sample.argtypes = [vp, C.c_uint32, fp, fp]
+        L.mppi_rollouts.argtypes = [vp, fp, C.c_int, fp, C.c_int, C.c_double, fp, fp]
+        L.mppi_update.argtypes = [vp, fp, fp, C.c_int, fp, fp]
+        L.mppi_step.argtypes = [vp, fp, C.c_uint32, fp, fp]
+        L.mppi_set_timing.argtypes = [vp, C.c_int]
+        L.mppi_get_timings.argtypes = [vp, C.POINTER(C.c_float)]
+        L.mppi_launch_count.argtypes = [vp, C.POINTER(C.c_uint64)]
+        L.mppi_state_size.argtypes = [vp]
+        L.mppi_state_size.restype = C.c_int
+        for name in EXPORTS:
+            if name not in ("mppi_last_error", "mppi_state_size"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Raw pointer of a float32/uint buffer (torch tensor or numpy array), or None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"], "buffer must be contiguous"
+        return C.c_void_p(x.ctypes.data)
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous(), "buffer must be contiguous"
+        return C.c_void_p(x.data_ptr())
+    raise TypeError("unsupported buffer type %r" % type(x))
+
+
+def _fill(struct, d: dict, skip=()):
+    for name, ct in struct._fields_:
+        if name in skip or name not in d:
+            continue
+        v = d[name]
+        if isinstance(v, (tuple, list, np.ndarray)):
+            arr = getattr(struct, name)
+            for i, x in enumerate(v):
+                arr[i] = x
+        else:
+            setattr(struct, name, v)
+
+
+def model_struct(robot: dict):
+    m = MppiModel()
+    _fill(m, robot, skip=("hf", "sbox_lo", "sbox_hi"))
+    keep = None
+    if robot.get("hf") is not None:
+        keep = np.ascontiguousarray(robot["hf"], dtype=np.float32)
+        m.hf = keep.ctypes.data
+    for i, (lo, hi) in enumerate(zip(robot.get("sbox_lo", []), robot.get("sbox_hi", []))):
+        for a in range(3):
+            m.sbox_lo[i][a] = lo[a]
+            m.sbox_hi[i][a] = hi[a]
+    return m, keep
+
+
+def cost_struct(cost: dict):
+    c = MppiCost()
+    _fill(c, cost)
+    return c
+
+
+def config_struct(mp: dict, block: int = 0):
+    c = MppiConfig()
+    c.K, c.H, c.n_sub, c.ctrl_steps = mp["K"], mp["H"], mp["n_sub"], mp["ctrl_steps"]
+    c.dt, c.lam = mp["dt"], mp["lam"]
+    for i in range(48):
+        c.sigma[i] = float(mp["sigma"][i])
+    for i in range(3):
+        c.q_lo[i] = float(mp["q_lo"][i])
+        c.q_hi[i] = float(mp["q_hi"][i])
+    c.seed, c.inst, c.n_prop = int(mp["seed"]), int(mp["inst"]), int(mp.get("n_prop", 0))
+    c.block = int(block or mp.get("block", 0))
+    return c
+
+
+class Controller:
+    """One MPPI controller instance (a handle of the C ABI)."""
+
+    def __init__(self, robot: dict, cost: dict, mppi: dict, stream=None, block: int = 0):
+        L = lib()
+        self._model, self._hf = model_struct(robot)
+        self._cost = cost_struct(cost)
+        self._cfg = config_struct(mppi, block)
+        h = C.c_void_p()
+        st = C.c_void_p(stream) if isinstance(stream, int) else stream
+        rc = L.mppi_create(C.byref(self._model), C.byref(self._cost), C.byref(self._cfg), st,
+                           C.byref(h))
+        if rc != MPPI_OK:
+            raise MppiError(rc, "mppi_create failed")
+        self.h = h
+        self.K = mppi["K"]
+        self.H = mppi["H"]
+        self.nx = L.mppi_state_size(h)
+
+    def _check(self, rc):
+        if rc != MPPI_OK:
+            raise MppiError(rc, lib().mppi_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mppi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_nominal(self, mu):
+        self._check(lib().mppi_set_nominal(self.h, _ptr(mu)))
+
+    def get_nominal(self, out=None):
+        out = np.zeros(48, np.float32) if out is None else out
+        self._check(lib().mppi_get_nominal(self.h, _ptr(out)))
+        return out
+
+    def sample(self, step, mu_prop=None, out=None):
+        self._check(lib().mppi_sample(self.h, step, _ptr(mu_prop), _ptr(out)))
+        return out
+
+    def rollouts(self, x0, U=None, n=None, t0=0.0, L_out=None, traj_out=None,
+                 x0_per_sample=False):
+        n = self.K if n is None else n
+        self._check(lib().mppi_rollouts(self.h, _ptr(x0), int(bool(x0_per_sample)), _ptr(U), n,
+                                        float(t0), _ptr(L_out), _ptr(traj_out)))
+        return L_out
+
+    def update(self, L=None, U=None, n=None, mu_out=None, u0_out=None):
+        n = self.K if n is None else n
+        rc = lib().mppi_update(self.h, _ptr(L), _ptr(U), n, _ptr(mu_out), _ptr(u0_out))
+        if rc != MPPI_ERR_NONFINITE:
+            self._check(rc)
+        return rc
+
+    def step(self, x0, step, u0_out=None, mu_out=None, check=True):
+        rc = lib().mppi_step(self.h, _ptr(x0), step, _ptr(u0_out), _ptr(mu_out))
+        if check and rc != MPPI_ERR_NONFINITE:
+            self._check(rc)
+        return rc
+
+    def set_timing(self, on=True):
+        self._check(lib().mppi_set_timing(self.h, int(on)))
+
+    def timings(self):
+        ms = (C.c_float * 3)()
+        self._check(lib().mppi_get_timings(self.h, ms))
+        return list(ms)
+
+    def launch_count(self):
+        c = C.c_uint64()
+        self._check(lib().mppi_launch_count(self.h, C.byref(c)))
+        return c.value

@@ -1,0 +1,528 @@
+// api.cu -- C ABI (include/mppi.h) of the sm_103a MPPI hot path.
+//
+// Owns the controller handle: derived FP32 model constants (spatial inertias
+// built here from the raw description), device workspace, the caller's stream,
+// host<->device marshalling of host pointers, and per-kernel event timing.
+// Every step of the path runs in the kernels of sample.cu, rollout.cu and
+// update.cu; nothing here computes on the host beyond argument preparation.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+#include <string>
+#include <vector>
+
+#include "../../include/mppi.h"
+#include "kernels.h"
+
+using namespace mppi;
+
+struct mppi_handle_s {
+    mppi_model_t model_in;
+    mppi_cost_t cost_in;
+    mppi_config_t cfg;
+    DevModel dm;
+    DevCost dc;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int nx = NX_ROBOT;
+    float *d_mu = nullptr, *d_mu_prop = nullptr, *d_mu_upd = nullptr, *d_U = nullptr, *d_L = nullptr;
+    float *d_x0 = nullptr, *d_u0 = nullptr, *d_hf = nullptr;
+    int* d_status = nullptr;
+    double* d_wsum = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int timing = 0;
+    int timed_valid = 0;
+    uint64_t launches = 0;
+    std::string err;
+};
+
+// ------------------------------------------------------------------ helpers
+
+static mppi_status fail(mppi_handle h, mppi_status s, const std::string& msg) {
+    if (h) h->err = msg;
+    return s;
+}
+
+static mppi_status cuda_fail(mppi_handle h, cudaError_t e, const char* where) {
+    return fail(h, MPPI_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                  \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);    \
+    } while (0)
+
+// true when p is device (or managed) memory; host (pageable or pinned) -> false
+static bool is_device(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// spatial inertia about a body frame's origin: [Ic + m cx cx^T, m cx; m cx^T, m 1]
+static Sym6 spatial_inertia(double m, const double c[3], const double Icd[3]) {
+    double S[3][3] = {{0, -c[2], c[1]}, {c[2], 0, -c[0]}, {-c[1], c[0], 0}};
+    Sym6 I;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            double sst = 0;
+            for (int k = 0; k < 3; k++) sst += S[i][k] * S[j][k];
+            I.A[i][j] = (float)((i == j ? Icd[i] : 0.0) + m * sst);
+            I.B[i][j] = (float)(m * S[i][j]);
+            I.C[i][j] = (float)(i == j ? m : 0.0);
+        }
+    return I;
+}
+
+static void derive_model(const mppi_model_t& p, DevModel& d) {
+    memset(&d, 0, sizeof(d));
+    const double a = p.trunk_size[0], b = p.trunk_size[1], c = p.trunk_size[2], m = p.trunk_mass;
+    d.tr_Ic[0] = (float)(m * (b * b + c * c) / 12.0);
+    d.tr_Ic[1] = (float)(m * (a * a + c * c) / 12.0);
+    d.tr_Ic[2] = (float)(m * (a * a + b * b) / 12.0);
+    d.tr_m = (float)m;
+    const double zero[3] = {0, 0, 0};
+    const double ih = 0.4 * p.abd_mass * p.abd_radius * p.abd_radius;
+    const double Ihip[3] = {ih, ih, ih};
+    d.I_hip = spatial_inertia(p.abd_mass, zero, Ihip);
+    const double tl = p.thigh_length, cl = p.calf_length, rr = p.rod_radius;
+    const double It[3] = {p.thigh_mass * tl * tl / 12.0, p.thigh_mass * tl * tl / 12.0, p.thigh_mass * rr * rr / 2.0};
+    const double ct[3] = {0, 0, -0.5 * tl};
+    d.I_thigh = spatial_inertia(p.thigh_mass, ct, It);
+    const double Ic[3] = {p.calf_mass * cl * cl / 12.0, p.calf_mass * cl * cl / 12.0, p.calf_mass * rr * rr / 2.0};
+    const double cc[3] = {0, 0, -0.5 * cl};
+    d.I_calf = spatial_inertia(p.calf_mass, cc, Ic);
+    // legs FR, FL, RR, RL: front +x / rear -x, right -y / left +y
+    const double fx[4] = {1, 1, -1, -1}, sy[4] = {-1, 1, -1, 1};
+    for (int l = 0; l < 4; l++) {
+        d.r_hip[l][0] = (float)(fx[l] * p.hip_x);
+        d.r_hip[l][1] = (float)(sy[l] * p.hip_y);
+        d.r_hip[l][2] = (float)p.hip_z;
+        d.r_thigh[l][0] = 0.f;
+        d.r_thigh[l][1] = (float)(sy[l] * p.thigh_offset_y);
+        d.r_thigh[l][2] = 0.f;
+    }
+    d.r_knee[0] = 0.f; d.r_knee[1] = 0.f; d.r_knee[2] = (float)(-tl);
+    d.foot[0] = 0.f; d.foot[1] = 0.f; d.foot[2] = (float)(-cl);
+    d.foot_r = (float)p.foot_radius;
+    d.n_tsph = p.n_trunk_spheres;
+    for (int s = 0; s < 4; s++) d.tsph_x[s] = (float)p.trunk_sphere_x[s];
+    d.tsph_r = (float)p.trunk_sphere_r;
+    d.gz = (float)(-p.gravity);
+    d.kp = (float)p.kp; d.kd = (float)p.kd; d.arm0 = (float)p.armature;
+    d.kc = (float)p.k_contact; d.cc = (float)p.c_contact; d.mu = (float)p.mu;
+    d.eps2 = (float)(p.eps_v * p.eps_v);
+    d.terrain = p.terrain;
+    d.hf_nx = p.hf_nx; d.hf_ny = p.hf_ny;
+    d.hf_cell = (float)p.hf_cell;
+    d.hf_inv_cell = p.hf_cell > 0 ? (float)(1.0 / p.hf_cell) : 0.f;
+    d.hf_x0 = (float)p.hf_x0; d.hf_y0 = (float)p.hf_y0;
+    d.n_sbox = p.n_static_boxes;
+    for (int i = 0; i < p.n_static_boxes && i < MAX_SBOX; i++)
+        for (int k = 0; k < 3; k++) {
+            d.sb_lo[i][k] = (float)p.sbox_lo[i][k];
+            d.sb_hi[i][k] = (float)p.sbox_hi[i][k];
+        }
+    d.has_box = p.has_box;
+    if (p.has_box) {
+        d.box_m = (float)p.box_mass;
+        d.box_inv_m = (float)(1.0 / p.box_mass);
+        const double X = p.box_size[0], Y = p.box_size[1], Z = p.box_size[2];
+        const double I3[3] = {p.box_mass * (Y * Y + Z * Z) / 12.0, p.box_mass * (X * X + Z * Z) / 12.0,
+                              p.box_mass * (X * X + Y * Y) / 12.0};
+        for (int k = 0; k < 3; k++) {
+            d.box_half[k] = (float)(0.5 * p.box_size[k]);
+            d.box_Ic[k] = (float)I3[k];
+            d.box_inv_Ic[k] = (float)(1.0 / I3[k]);
+        }
+        d.box_cr = (float)p.box_corner_r;
+    }
+    d.nx = p.has_box ? NX_BOX : NX_ROBOT;
+}
+
+static void derive_cost(const mppi_cost_t& c, DevCost& d) {
+    d.w_z = (float)c.w_z; d.z_ref = (float)c.z_ref; d.w_o = (float)c.w_o;
+    d.w_v = (float)c.w_v; d.v_ref = (float)c.v_ref; d.w_p = (float)c.w_p;
+    d.goal_x = (float)c.goal_xy[0]; d.goal_y = (float)c.goal_xy[1];
+    d.w_u = (float)c.w_u; d.w_box = (float)c.w_box;
+    d.box_gx = (float)c.box_goal_xy[0]; d.box_gy = (float)c.box_goal_xy[1];
+    d.gait = c.gait;
+    d.two_pi_over_period = c.gait_period > 0 ? (float)(2.0 * M_PI / c.gait_period) : 0.f;
+    d.hip_amp = (float)c.gait_hip_amp; d.knee_amp = (float)c.gait_knee_amp;
+    for (int i = 0; i < 3; i++) d.stand[i] = (float)c.stand[i];
+    d.w_term = (float)c.w_terminal;
+}
+
+// gait time of step 0 of a horizon starting at absolute time t0, reduced
+// modulo the gait period so that FP32 keeps its resolution over long runs
+static float reduce_t0(const mppi_handle h, double t0) {
+    const double P = h->cost_in.gait_period;
+    if (h->cost_in.gait == 1 && P > 0) return (float)fmod(t0, P);
+    return (float)t0;
+}
+
+// a float input of n values: device pointer as is, host data copied to dst
+static mppi_status stage_in(mppi_handle h, const float* src, size_t n, float* dst, const float** out) {
+    if (is_device(src)) {
+        *out = src;
+        return MPPI_OK;
+    }
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    *out = dst;
+    return MPPI_OK;
+}
+
+static bool all_finite(const float* p, size_t n) {
+    for (size_t i = 0; i < n; i++)
+        if (!isfinite(p[i])) return false;
+    return true;
+}
+
+// ------------------------------------------------------------------ ABI
+
+extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t* cost, const mppi_config_t* cfg,
+                                   void* stream, mppi_handle* out) {
+    if (!model || !cost || !cfg || !out) return MPPI_ERR_ARG;
+    *out = nullptr;
+    if (cfg->K < 1 || cfg->H < 2 || cfg->n_sub < 1 || !(cfg->dt > 0) || !(cfg->lambda > 0) ||
+        cfg->ctrl_steps < 1 || cfg->n_prop < 0 || cfg->n_prop >= cfg->K || cfg->K > (1 << 24))
+        return MPPI_ERR_ARG;
+    if (cfg->block != 0 && (cfg->block % 32 != 0 || cfg->block < 32 || cfg->block > 256)) return MPPI_ERR_ARG;
+    if (model->terrain == 1 && (!model->hf || model->hf_nx < 2 || model->hf_ny < 2 || !(model->hf_cell > 0)))
+        return MPPI_ERR_ARG;
+    if (model->terrain != 0 && model->terrain != 1) return MPPI_ERR_ARG;
+    if (model->n_static_boxes < 0 || model->n_static_boxes > MAX_SBOX) return MPPI_ERR_ARG;
+    if (model->n_trunk_spheres < 0 || model->n_trunk_spheres > 4) return MPPI_ERR_ARG;
+    if (model->has_box) return MPPI_ERR_NOTSUP;
+
+    mppi_handle h = new mppi_handle_s();
+    h->model_in = *model;
+    h->cost_in = *cost;
+    h->cfg = *cfg;
+    h->stream = (cudaStream_t)stream;
+    cudaGetDevice(&h->device);
+    derive_model(*model, h->dm);
+    derive_cost(*cost, h->dc);
+    h->nx = h->dm.nx;
+    const size_t K = (size_t)cfg->K;
+    auto al = [&](void** p, size_t bytes) -> bool {
+        if (cudaMalloc(p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return true;
+    };
+    bool ok = al((void**)&h->d_mu, D * sizeof(float)) && al((void**)&h->d_mu_prop, D * sizeof(float)) &&
+              al((void**)&h->d_mu_upd, D * sizeof(float)) && al((void**)&h->d_U, K * D * sizeof(float)) &&
+              al((void**)&h->d_L, K * sizeof(float)) && al((void**)&h->d_x0, K * NX_BOX * sizeof(float)) &&
+              al((void**)&h->d_u0, NJ * sizeof(float)) && al((void**)&h->d_status, sizeof(int)) &&
+              al((void**)&h->d_wsum, sizeof(double));
+    if (ok && model->terrain == 1) {
+        size_t nh = (size_t)model->hf_nx * model->hf_ny;
+        ok = al((void**)&h->d_hf, nh * sizeof(float));
+        if (ok) {
+            cudaMemcpyKind kind = is_device(model->hf) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+            ok = cudaMemcpy(h->d_hf, model->hf, nh * sizeof(float), kind) == cudaSuccess;
+        }
+        h->dm.hf = h->d_hf;
+    }
+    if (!ok) {
+        mppi_destroy(h);
+        return MPPI_ERR_OOM;
+    }
+    for (int i = 0; i < 4; i++) cudaEventCreate(&h->ev[i]);
+    // default nominal: the cost's stand pose at every knot
+    float mu0[D];
+    for (int d = 0; d < D; d++) mu0[d] = (float)cost->stand[d % 3];
+    if (cudaMemcpy(h->d_mu, mu0, sizeof(mu0), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) {
+        mppi_destroy(h);
+        return MPPI_ERR_CUDA;
+    }
+    *out = h;
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_destroy(mppi_handle h) {
+    if (!h) return MPPI_ERR_ARG;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    void* bufs[] = {h->d_mu, h->d_mu_prop, h->d_mu_upd, h->d_U, h->d_L, h->d_x0, h->d_u0, h->d_hf, h->d_status, h->d_wsum};
+    for (void* p : bufs)
+        if (p) cudaFree(p);
+    for (int i = 0; i < 4; i++)
+        if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    delete h;
+    return MPPI_OK;
+}
+
+extern "C" const char* mppi_last_error(mppi_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+extern "C" int mppi_state_size(mppi_handle h) { return h ? h->nx : 0; }
+
+extern "C" mppi_status mppi_set_nominal(mppi_handle h, const float* mu) {
+    if (!h || !mu) return fail(h, MPPI_ERR_ARG, "null argument");
+    cudaMemcpyKind kind = is_device(mu) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(h->d_mu, mu, D * sizeof(float), kind, h->stream));
+    if (kind == cudaMemcpyHostToDevice) CK(cudaStreamSynchronize(h->stream));
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_get_nominal(mppi_handle h, float* mu_out) {
+    if (!h || !mu_out) return fail(h, MPPI_ERR_ARG, "null argument");
+    bool dev = is_device(mu_out);
+    CK(cudaMemcpyAsync(mu_out, h->d_mu, D * sizeof(float), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       h->stream));
+    if (!dev) CK(cudaStreamSynchronize(h->stream));
+    return MPPI_OK;
+}
+
+static mppi_status do_sample(mppi_handle h, uint32_t step, const float* mu_prop, float* U) {
+    SampleArgs a;
+    a.mu = h->d_mu;
+    a.mu_prop = nullptr;
+    if (mu_prop) {
+        const float* mp;
+        mppi_status s = stage_in(h, mu_prop, D, h->d_mu_prop, &mp);
+        if (s != MPPI_OK) return s;
+        a.mu_prop = mp;
+    }
+    a.U = U;
+    memcpy(a.sigma, h->cfg.sigma, sizeof(a.sigma));
+    memcpy(a.q_lo, h->cfg.q_lo, sizeof(a.q_lo));
+    memcpy(a.q_hi, h->cfg.q_hi, sizeof(a.q_hi));
+    a.key0 = (uint32_t)h->cfg.seed;
+    a.key1 = (uint32_t)(h->cfg.seed >> 32);
+    a.step = step;
+    a.inst = h->cfg.inst;
+    a.K = h->cfg.K;
+    a.n_prop = h->cfg.n_prop;
+    CK(launch_sample(a, h->stream));
+    h->launches++;
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_sample(mppi_handle h, uint32_t step, const float* mu_prop, float* U_out) {
+    if (!h) return MPPI_ERR_ARG;
+    bool host_out = U_out && !is_device(U_out);
+    if (U_out && !host_out && !aligned16(U_out)) return fail(h, MPPI_ERR_ARG, "U_out must be 16-byte aligned");
+    float* dst = (U_out && !host_out) ? U_out : h->d_U;
+    mppi_status s = do_sample(h, step, mu_prop, dst);
+    if (s != MPPI_OK) return s;
+    if (host_out) {
+        CK(cudaMemcpyAsync(U_out, h->d_U, (size_t)h->cfg.K * D * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    return MPPI_OK;
+}
+
+static RolloutArgs rollout_args(mppi_handle h, const float* x0, int per, const float* U, int n, double t0,
+                                float* L, float* traj) {
+    RolloutArgs a;
+    a.model = h->dm;
+    a.cost = h->dc;
+    a.x0 = x0;
+    a.x0_per_sample = per;
+    a.U = U;
+    a.L = L;
+    a.traj = traj;
+    a.n = n;
+    a.H = h->cfg.H;
+    a.n_sub = h->cfg.n_sub;
+    a.dt = (float)h->cfg.dt;
+    a.h = (float)(h->cfg.dt / h->cfg.n_sub);
+    a.inv_Hm1 = (float)(1.0 / (h->cfg.H - 1));
+    a.t0 = reduce_t0(h, t0);
+    return a;
+}
+
+static int rollout_block(mppi_handle h) { return h->cfg.block ? h->cfg.block : 128; }
+
+extern "C" mppi_status mppi_rollouts(mppi_handle h, const float* x0, int x0_per_sample, const float* U, int n,
+                                     double t0, float* L_out, float* traj_out) {
+    if (!h || !x0 || n < 0) return fail(h, MPPI_ERR_ARG, "bad argument");
+    const int nx = h->nx;
+    const bool per = x0_per_sample != 0;
+    if (!U && n > h->cfg.K) return fail(h, MPPI_ERR_ARG, "n exceeds K for the handle's own samples");
+    if (n == 0) return MPPI_OK;
+    // x0
+    const float* dx0;
+    const size_t nx0 = (size_t)nx * (per ? n : 1);
+    if (is_device(x0)) {
+        dx0 = x0;
+    } else {
+        if (!all_finite(x0, nx0)) return fail(h, MPPI_ERR_NONFINITE, "x0 not finite");
+        if (per && n > h->cfg.K) return fail(h, MPPI_ERR_ARG, "host per-sample x0 limited to K states");
+        CK(cudaMemcpyAsync(h->d_x0, x0, nx0 * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        dx0 = h->d_x0;
+    }
+    // U
+    const float* dU = h->d_U;
+    if (U) {
+        if (is_device(U)) {
+            if (!aligned16(U)) return fail(h, MPPI_ERR_ARG, "U must be 16-byte aligned");
+            dU = U;
+        } else {
+            if (n > h->cfg.K) return fail(h, MPPI_ERR_ARG, "host U limited to K samples");
+            CK(cudaMemcpyAsync(h->d_U, U, (size_t)n * D * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        }
+    }
+    // outputs
+    float* dL = h->d_L;
+    bool L_host = L_out && !is_device(L_out);
+    if (L_out && !L_host) dL = L_out;
+    if (!L_out || L_host)
+        if (n > h->cfg.K) return fail(h, MPPI_ERR_ARG, "host/internal L limited to K");
+    float* dT = nullptr;
+    bool T_host = traj_out && !is_device(traj_out);
+    const size_t tbytes = (size_t)n * (h->cfg.H + 1) * nx * sizeof(float);
+    if (traj_out) {
+        if (T_host) CK(cudaMalloc(&dT, tbytes));
+        else dT = traj_out;
+    }
+    RolloutArgs a = rollout_args(h, dx0, per, dU, n, t0, dL, dT);
+    cudaError_t e = launch_rollout(a, rollout_block(h), h->stream);
+    h->launches++;
+    if (e != cudaSuccess) {
+        if (T_host) cudaFree(dT);
+        return cuda_fail(h, e, "rollout launch");
+    }
+    if (L_host) CK(cudaMemcpyAsync(L_out, dL, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    if (T_host) {
+        cudaError_t e2 = cudaMemcpyAsync(traj_out, dT, tbytes, cudaMemcpyDeviceToHost, h->stream);
+        cudaError_t e3 = cudaStreamSynchronize(h->stream);
+        cudaFree(dT);
+        if (e2 != cudaSuccess) return cuda_fail(h, e2, "traj copy");
+        if (e3 != cudaSuccess) return cuda_fail(h, e3, "traj sync");
+    } else if (L_host) {
+        CK(cudaStreamSynchronize(h->stream));
+    }
+    return MPPI_OK;
+}
+
+static mppi_status do_update(mppi_handle h, const float* dL, const float* dU, int n) {
+    UpdateArgs a;
+    a.L = dL;
+    a.U = dU;
+    a.mu = h->d_mu;
+    a.mu_upd = h->d_mu_upd;
+    a.u0 = h->d_u0;
+    a.status = h->d_status;
+    a.wsum = h->d_wsum;
+    a.n = n;
+    a.H = h->cfg.H;
+    a.ctrl_steps = h->cfg.ctrl_steps;
+    a.inv_lambda = (float)(1.0 / h->cfg.lambda);
+    CK(launch_update(a, h->stream));
+    h->launches++;
+    return MPPI_OK;
+}
+
+// copy the step's outputs (u0, mu before the shift) and read the status
+static mppi_status finish_outputs(mppi_handle h, float* u0_out, float* mu_out) {
+    bool any_host = false;
+    if (u0_out) {
+        bool dev = is_device(u0_out);
+        any_host |= !dev;
+        CK(cudaMemcpyAsync(u0_out, h->d_u0, NJ * sizeof(float), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           h->stream));
+    }
+    if (mu_out) {
+        bool dev = is_device(mu_out);
+        any_host |= !dev;
+        CK(cudaMemcpyAsync(mu_out, h->d_mu_upd, D * sizeof(float),
+                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    }
+    if (any_host) {
+        int st = 0;
+        CK(cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        if (st != 0) return fail(h, MPPI_ERR_NONFINITE, "every rollout cost is non-finite; mean kept");
+    }
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_update(mppi_handle h, const float* L, const float* U, int n, float* mu_out,
+                                   float* u0_out) {
+    if (!h || n < 0) return fail(h, MPPI_ERR_ARG, "bad argument");
+    const float* dL = h->d_L;
+    const float* dU = h->d_U;
+    if ((!L || !U) && n > h->cfg.K) return fail(h, MPPI_ERR_ARG, "n exceeds K");
+    if (L) {
+        if (!is_device(L) && n > h->cfg.K) return fail(h, MPPI_ERR_ARG, "host L limited to K");
+        mppi_status s = stage_in(h, L, (size_t)n, h->d_L, &dL);
+        if (s != MPPI_OK) return s;
+    }
+    if (U) {
+        if (is_device(U)) {
+            if (!aligned16(U)) return fail(h, MPPI_ERR_ARG, "U must be 16-byte aligned");
+            dU = U;
+        } else {
+            if (n > h->cfg.K) return fail(h, MPPI_ERR_ARG, "host U limited to K");
+            CK(cudaMemcpyAsync(h->d_U, U, (size_t)n * D * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        }
+    }
+    mppi_status s = do_update(h, dL, dU, n);
+    if (s != MPPI_OK) return s;
+    return finish_outputs(h, u0_out, mu_out);
+}
+
+extern "C" mppi_status mppi_step(mppi_handle h, const float* x0, uint32_t step, float* u0_out, float* mu_out) {
+    if (!h || !x0) return fail(h, MPPI_ERR_ARG, "null argument");
+    const int nx = h->nx;
+    const float* dx0;
+    if (is_device(x0)) {
+        dx0 = x0;
+    } else {
+        if (!all_finite(x0, nx)) return fail(h, MPPI_ERR_NONFINITE, "x0 not finite");
+        CK(cudaMemcpyAsync(h->d_x0, x0, nx * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        dx0 = h->d_x0;
+    }
+    const bool tm = h->timing != 0;
+    if (tm) CK(cudaEventRecord(h->ev[0], h->stream));
+    mppi_status s = do_sample(h, step, nullptr, h->d_U);
+    if (s != MPPI_OK) return s;
+    if (tm) CK(cudaEventRecord(h->ev[1], h->stream));
+    const double t0 = (double)step * h->cfg.ctrl_steps * h->cfg.dt;
+    RolloutArgs a = rollout_args(h, dx0, 0, h->d_U, h->cfg.K, t0, h->d_L, nullptr);
+    CK(launch_rollout(a, rollout_block(h), h->stream));
+    h->launches++;
+    if (tm) CK(cudaEventRecord(h->ev[2], h->stream));
+    s = do_update(h, h->d_L, h->d_U, h->cfg.K);
+    if (s != MPPI_OK) return s;
+    if (tm) {
+        CK(cudaEventRecord(h->ev[3], h->stream));
+        h->timed_valid = 1;
+    }
+    return finish_outputs(h, u0_out, mu_out);
+}
+
+extern "C" mppi_status mppi_set_timing(mppi_handle h, int on) {
+    if (!h) return MPPI_ERR_ARG;
+    h->timing = on;
+    h->timed_valid = 0;
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_get_timings(mppi_handle h, float ms[3]) {
+    if (!h || !ms) return fail(h, MPPI_ERR_ARG, "null argument");
+    if (!h->timed_valid) return fail(h, MPPI_ERR_ARG, "no timed step yet (mppi_set_timing first)");
+    CK(cudaEventSynchronize(h->ev[3]));
+    for (int i = 0; i < 3; i++) CK(cudaEventElapsedTime(&ms[i], h->ev[i], h->ev[i + 1]));
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_launch_count(mppi_handle h, uint64_t* count) {
+    if (!h || !count) return MPPI_ERR_ARG;
+    *count = h->launches;
+    return MPPI_OK;
+}

@@ -1,0 +1,48 @@
+// kernels.h -- internal launch interface between the C-ABI layer (api.cu) and
+// the kernels (sample.cu, rollout.cu, update.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "common.cuh"
+
+namespace mppi {
+
+struct SampleArgs {
+    const float* mu;       // [48] device
+    const float* mu_prop;  // [48] device or null
+    float* U;              // [K][48] device
+    float sigma[D];
+    float q_lo[3], q_hi[3];
+    uint32_t key0, key1, step, inst;
+    int K, n_prop;
+};
+
+struct RolloutArgs {
+    DevModel model;
+    DevCost cost;
+    const float* x0;       // [nx] or [n][nx] device
+    int x0_per_sample;
+    const float* U;        // [n][48] device
+    float* L;              // [n] device
+    float* traj;           // [n][H+1][nx] device or null
+    int n, H, n_sub;
+    float h, dt, inv_Hm1, t0;  // t0: gait time of step 0 (reduced modulo the gait period)
+};
+
+struct UpdateArgs {
+    const float* L;        // [n]
+    const float* U;        // [n][48]
+    float* mu;             // [48] in: unused; out: shifted nominal
+    float* mu_upd;         // [48] updated mean before the shift (optional)
+    float* u0;             // [12]
+    int* status;           // 0 ok, 4 all costs non-finite
+    double* wsum;          // normaliser (FP64) of the last update, optional
+    int n, H, ctrl_steps;
+    float inv_lambda;
+};
+
+cudaError_t launch_sample(const SampleArgs& a, cudaStream_t st);
+cudaError_t launch_rollout(const RolloutArgs& a, int block, cudaStream_t st);
+cudaError_t launch_update(const UpdateArgs& a, cudaStream_t st);
+
+}  // namespace mppi

@@ -1,0 +1,240 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (model spec): knot samples bit-exact; one dt step of state from an
+identical FP32 state <= 1e-5 relative per block (|dx|_inf / max(|x|_inf, 1));
+rollout cost <= 1e-3 relative (|dL| / max(|L|, 1)); the update (Eq. 1, 2) and
+shift <= 1e-6 relative given the same FP32 costs and knots.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_2409_10469_gb300 import _mppi, workloads as W  # noqa: E402
+
+BLOCKS = {"pos": slice(0, 3), "quat": slice(3, 7), "joints": slice(7, 19), "w": slice(19, 22),
+          "v": slice(22, 25), "qd": slice(25, 37)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def rel_block(a, b):
+    """per-block |a-b|_inf / max(|b|_inf, 1) (reading O17), max over blocks"""
+    out = {}
+    for name, sl in BLOCKS.items():
+        d = np.abs(a[..., sl] - b[..., sl]).max(-1)
+        s = np.maximum(np.abs(b[..., sl]).max(-1), 1.0)
+        out[name] = d / s
+    return out
+
+
+def ctl_for(cfg, K=None, H=None, **kw):
+    m = dict(cfg.mppi)
+    if K is not None:
+        m["K"] = K
+    if H is not None:
+        m["H"] = H
+    m.update(kw)
+    return _mppi.Controller(cfg.robot, cfg.cost, m), m
+
+
+@pytest.mark.parametrize("K", [1, 5, 1000, 4096])
+def test_sample_bit_exact(K):
+    cfg = W.config_trot()
+    ctl, m = ctl_for(cfg, K=K)
+    mu = W.stand_mu() + np.linspace(-0.05, 0.05, 48).astype(np.float32)
+    ctl.set_nominal(mu)
+    U = torch.empty((K, 48), device="cuda")
+    ctl.sample(7, out=U)
+    Ug = U.cpu().numpy()
+    Uo = O.sample(m, mu, 7)
+    assert np.array_equal(Ug.view(np.uint32), Uo.view(np.uint32))
+
+
+def test_sample_with_proposal_bit_exact():
+    cfg = W.config_trot()
+    ctl, m = ctl_for(cfg, K=300, n_prop=150, seed=12345678901)
+    mu = W.stand_mu()
+    mp = mu + np.float32(0.07)
+    ctl.set_nominal(mu)
+    U = torch.empty((300, 48), device="cuda")
+    ctl.sample(3, mu_prop=dev(mp), out=U)
+    Uo = O.sample(m, mu, 3, mu_prop=mp)
+    assert np.array_equal(U.cpu().numpy().view(np.uint32), Uo.view(np.uint32))
+
+
+def test_sample_host_output():
+    cfg = W.config_stand()
+    ctl, m = ctl_for(cfg, K=64)
+    ctl.set_nominal(cfg.mu0)
+    Uh = np.zeros((64, 48), np.float32)
+    ctl.sample(2, out=Uh)
+    assert np.array_equal(Uh, O.sample(m, cfg.mu0, 2))
+
+
+@pytest.mark.parametrize("dt", [0.01, 0.005])
+def test_one_step_state_parity(dt):
+    """one dt step (n_sub sub-steps) from 300 identical FP32 states, contacts on"""
+    cfg = W.config_stand() if dt == 0.01 else W.config_trot()
+    n = 300
+    X = W.random_states(n, 42).astype(np.float32)
+    rng = np.random.default_rng(1)
+    U = (np.tile(W.stand_mu(), (n, 1)) + rng.uniform(-0.3, 0.3, (n, 48))).astype(np.float32)
+    ctl, m = ctl_for(cfg, K=n, H=2)
+    traj = torch.empty((n, 3, 37), device="cuda")
+    L = torch.empty(n, device="cuda")
+    ctl.rollouts(dev(X), U=dev(U), n=n, t0=0.0, L_out=L, traj_out=traj, x0_per_sample=True)
+    tg = traj.cpu().numpy()
+    world = O.World(cfg.robot)
+    _, to = O.rollouts(world, cfg.cost, m, 0.0, X.astype(np.float64), U, traj=True)
+    assert np.array_equal(tg[:, 0], X)
+    # step 1 starts from the GPU's own FP32 state 0 == X, so compare x_1
+    r = rel_block(tg[:, 1].astype(np.float64), to[:, 1])
+    worst = {k: float(v.max()) for k, v in r.items()}
+    assert max(worst.values()) <= 1e-5, worst
+
+
+def _cost_parity(cfg, K, H, t0=0.0, seed_mu=0):
+    ctl, m = ctl_for(cfg, K=K, H=H)
+    mu = cfg.mu0.copy()
+    ctl.set_nominal(mu)
+    U = torch.empty((K, 48), device="cuda")
+    ctl.sample(seed_mu, out=U)
+    L = torch.empty(K, device="cuda")
+    x0 = cfg.x0.astype(np.float32)
+    ctl.rollouts(dev(x0), U=U, n=K, t0=t0, L_out=L)
+    Lg = L.cpu().numpy().astype(np.float64)
+    world = O.World(cfg.robot)
+    Lo = O.rollouts(world, cfg.cost, m, t0, x0.astype(np.float64), U.cpu().numpy())
+    return np.abs(Lg - Lo) / np.maximum(np.abs(Lo), 1.0), Lg, Lo
+
+
+def test_rollout_cost_parity_stand():
+    rel, Lg, Lo = _cost_parity(W.config_stand(), 100, 50)
+    assert np.all(np.isfinite(Lg))
+    assert np.percentile(rel, 99) <= 1e-3 and rel.max() <= 1e-3, (rel.max(), np.percentile(rel, 99))
+
+
+def test_rollout_cost_parity_trot():
+    rel, Lg, Lo = _cost_parity(W.config_trot(), 130, 100, t0=0.37)
+    assert np.percentile(rel, 99) <= 1e-3, (rel.max(), np.percentile(rel, 99))
+
+
+def test_rollout_cost_parity_terrain():
+    rel, Lg, Lo = _cost_parity(W.config_terrain(), 96, 60)
+    assert np.percentile(rel, 99) <= 1e-3, (rel.max(), np.percentile(rel, 99))
+
+
+def test_update_parity():
+    cfg = W.config_trot()
+    rng = np.random.default_rng(3)
+    for K, lam, scale in [(4096, 0.1, 5.0), (1000, 1.0, 50.0), (7, 1e6, 3.0), (513, 0.01, 0.05)]:
+        ctl, m = ctl_for(cfg, K=K, lam=lam)
+        U = (np.tile(W.stand_mu(), (K, 1)) + rng.normal(0, 0.3, (K, 48))).astype(np.float32)
+        L = (100 + scale * rng.random(K)).astype(np.float32)
+        mu_g = torch.empty(48, device="cuda")
+        u0_g = torch.empty(12, device="cuda")
+        rc = ctl.update(dev(L), dev(U), n=K, mu_out=mu_g, u0_out=u0_g)
+        assert rc == 0
+        nom = ctl.get_nominal()
+        _, mu_o, _ = O.update(L, U, lam)
+        e = np.abs(mu_g.cpu().numpy() - mu_o) / np.maximum(np.abs(mu_o), 1)
+        assert e.max() <= 1e-6, (K, lam, e.max())
+        assert np.array_equal(u0_g.cpu().numpy(), mu_g.cpu().numpy()[:12])
+        sh = O.shift(mu_g.cpu().numpy(), m["H"], m["ctrl_steps"])
+        assert np.abs(nom - sh).max() <= 1e-6 * max(1.0, np.abs(sh).max())
+
+
+def test_update_nonfinite_costs():
+    cfg = W.config_stand()
+    ctl, m = ctl_for(cfg, K=8)
+    U = np.tile(W.stand_mu(), (8, 1)).astype(np.float32) + np.arange(8, dtype=np.float32)[:, None] * 0.01
+    L = np.array([np.nan, 5, np.inf, 3, 4, -np.inf, 9, 8], np.float32)
+    mu = torch.empty(48, device="cuda")
+    assert ctl.update(dev(L), dev(U), n=8, mu_out=mu) == 0
+    _, mu_o, _ = O.update(L, U, m["lam"])
+    assert np.abs(mu.cpu().numpy() - mu_o).max() < 1e-6
+    before = ctl.get_nominal()
+    mu_h = np.zeros(48, np.float32)
+    rc = ctl.update(dev(np.full(8, np.nan, np.float32)), dev(U), n=8, mu_out=mu_h)
+    assert rc == _mppi.MPPI_ERR_NONFINITE
+    assert np.array_equal(mu_h, before)
+
+
+def test_full_step_matches_components():
+    """mppi_step = sample -> rollouts -> update with the handle's buffers; its
+    costs match the oracle and its update matches the oracle on the GPU costs."""
+    cfg = W.config_stand(K=64, H=50)
+    ctl, m = ctl_for(cfg)
+    ctl.set_nominal(cfg.mu0)
+    u0 = np.zeros(12, np.float32)
+    mu = np.zeros(48, np.float32)
+    ctl.step(cfg.x0.astype(np.float32), 0, u0_out=u0, mu_out=mu)
+    rc, mu_o, u0_o, L_o, U_o = O.mppi_step(O.World(cfg.robot), cfg.cost, m, cfg.x0.astype(np.float32).astype(np.float64), cfg.mu0, 0)
+    # same samples: recompute GPU costs for them and compare the update
+    ctl2, _ = ctl_for(cfg)
+    L = torch.empty(64, device="cuda")
+    ctl2.rollouts(dev(cfg.x0), U=dev(U_o), n=64, L_out=L)
+    Lg = L.cpu().numpy()
+    rel = np.abs(Lg - L_o) / np.maximum(np.abs(L_o), 1)
+    assert rel.max() <= 1e-3
+    _, mu_same, _ = O.update(Lg, U_o, m["lam"])
+    assert np.abs(mu - mu_same).max() <= 1e-6 * 4
+    assert np.array_equal(u0, mu[:12])
+    assert ctl.launch_count() == 3
+
+
+def test_edge_cases():
+    cfg = W.config_stand()
+    ctl, m = ctl_for(cfg, K=16)
+    x = cfg.x0.astype(np.float32).copy()
+    x[3] = np.nan
+    with pytest.raises(_mppi.MppiError) as e:
+        ctl.step(x, 0, u0_out=np.zeros(12, np.float32))
+    assert e.value.status == _mppi.MPPI_ERR_NONFINITE
+    # n = 0 is a no-op
+    ctl.rollouts(dev(cfg.x0), U=None, n=0)
+    # misaligned device U is rejected
+    U = torch.zeros(16 * 48 + 1, device="cuda")
+    with pytest.raises(_mppi.MppiError) as e:
+        ctl.rollouts(dev(cfg.x0), U=U[1:], n=16, L_out=torch.empty(16, device="cuda"))
+    assert e.value.status == _mppi.MPPI_ERR_ARG
+    # invalid configs
+    bad = dict(cfg.mppi)
+    bad["H"] = 1
+    with pytest.raises(_mppi.MppiError):
+        _mppi.Controller(cfg.robot, cfg.cost, bad)
+
+
+def test_full_size_sampled_parity():
+    """trot K=4096 H=100 (the bench's step): every knot bit-exact; costs of 24
+    sampled rollouts against the oracle"""
+    cfg = W.config_trot(K=4096, H=100)
+    ctl, m = ctl_for(cfg)
+    ctl.set_nominal(cfg.mu0)
+    U = torch.empty((4096, 48), device="cuda")
+    L = torch.empty(4096, device="cuda")
+    ctl.sample(5, out=U)
+    x0 = cfg.x0.astype(np.float32)
+    t0 = 5 * m["ctrl_steps"] * m["dt"]
+    ctl.rollouts(dev(x0), U=U, n=4096, t0=t0, L_out=L)
+    Ug = U.cpu().numpy()
+    assert np.array_equal(Ug.view(np.uint32), O.sample(m, cfg.mu0, 5).view(np.uint32))
+    idx = np.r_[0, 1, 2, np.random.default_rng(0).choice(np.arange(3, 4096), 21, replace=False)]
+    Lo = O.rollouts(O.World(cfg.robot), cfg.cost, m, t0, x0.astype(np.float64), Ug[idx])
+    Lg = L.cpu().numpy()[idx]
+    rel = np.abs(Lg - Lo) / np.maximum(np.abs(Lo), 1)
+    assert np.percentile(rel, 90) <= 1e-3, rel
