@@ -112,6 +112,8 @@ def lib():
         L.or_mppi_step.restype = C.c_int
         L.or_mppi_step.argtypes = [C.c_void_p, C.POINTER(OrCost), C.POINTER(OrMppi), dp, fp, fp,
                                    C.c_uint32, fp, fp, fp, C.c_int]
+        L.or_dt_steps.argtypes = [C.c_void_p, dp, dp, C.c_long, C.c_int, C.c_double, dp, C.c_int]
+        L.or_stage_costs.argtypes = [C.c_void_p, C.POINTER(OrCost), dp, dp, dp, C.c_long, dp]
         L.or_tree_init.argtypes = [C.c_void_p, C.c_int, C.c_double]
         L.or_tree_add.restype = C.c_int
         L.or_tree_add.argtypes = [C.c_void_p, C.c_int, C.c_int, dp, C.c_double, dp, dp]
@@ -247,6 +249,33 @@ def rollouts(world: World, cost: dict, m: dict, t0, x0, U, traj=False, nthreads=
                       _p(U, C.c_float), n, _p(L, C.c_double),
                       _p(tr, C.c_double) if traj else None, nthreads)
     return (L, tr) if traj else L
+
+
+def dt_steps(world: World, X, Ut, n_sub, h, nthreads=None):
+    """One dt step (n_sub sub-steps) from each state X[m][nx] with targets Ut[m][12]."""
+    X = _f64(X).reshape(-1, world.nx)
+    Ut = _f64(Ut).reshape(-1, NJ)
+    out = np.zeros_like(X)
+    lib().or_dt_steps(world.ptr, _p(X, C.c_double), _p(Ut, C.c_double), X.shape[0], n_sub, h,
+                      _p(out, C.c_double), nthreads or os.cpu_count() or 1)
+    return out
+
+
+def stage_costs(world: World, cost: dict, X, Ut=None, t_abs=None):
+    """Stage costs of (X[m], Ut[m], t_abs[m]); terminal costs when t_abs is None."""
+    X = _f64(X).reshape(-1, world.nx)
+    m = X.shape[0]
+    out = np.zeros(m)
+    c = make_cost(cost)
+    if t_abs is None:
+        lib().or_stage_costs(world.ptr, C.byref(c), _p(X, C.c_double), None, None, m,
+                             _p(out, C.c_double))
+    else:
+        Ut = _f64(Ut).reshape(-1, NJ)
+        ta = _f64(t_abs).reshape(-1)
+        lib().or_stage_costs(world.ptr, C.byref(c), _p(X, C.c_double), _p(Ut, C.c_double),
+                             _p(ta, C.c_double), m, _p(out, C.c_double))
+    return out
 
 
 def stage_cost(world: World, cost: dict, x, u, t_abs):

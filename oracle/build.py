@@ -33,3 +33,16 @@ def build(force: bool = False) -> str:
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv))
+
+
+def build_variant(real: str = "float") -> str:
+    """The same oracle source with `real` = float (an FP32 reference for
+    measuring how much FP32 rounding alone moves a result)."""
+    out = os.path.join(HERE, "liboracle_%s.so" % real)
+    srcs = [os.path.join(HERE, s) for s in SOURCES]
+    deps = srcs + [os.path.join(HERE, "oracle.h")]
+    if os.path.exists(out) and all(os.path.getmtime(d) <= os.path.getmtime(out) for d in deps):
+        return out
+    cmd = ["gcc"] + CFLAGS + ["-DOR_REAL=" + real, "-Wno-double-promotion"] + srcs + ["-o", out, "-lm"]
+    subprocess.run(cmd, check=True)
+    return out

@@ -163,6 +163,11 @@ void or_rollouts(const or_world* w, const or_cost* c, const or_mppi* m, double t
                  const double* x0, int x0_per_sample, const float* U, int n,
                  double* L_out, double* traj, int nthreads);
 
+void or_dt_steps(const or_world* w, const double* X, const double* Ut, long m, int n_sub,
+                 double h, double* out, int nthreads);
+void or_stage_costs(const or_world* w, const or_cost* c, const double* X, const double* Ut,
+                    const double* t_abs, long m, double* out);
+
 /* sampling (FP32 by specification) */
 void  or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 float or_lnf(float x);

@@ -475,12 +475,18 @@ typedef struct {
 static void* rollout_worker(void* arg) {
     rollout_job* j = (rollout_job*)arg;
     int nx = j->w->nx, H = j->m->H;
+    real x0r[64];
+    real* tr = j->traj ? (real*)malloc(sizeof(real) * (size_t)(H + 1) * nx) : NULL;
     for (int k = j->tid; k < j->n; k += j->nthreads) {
         const double* x0 = j->x0 + (j->x0_per_sample ? (size_t)k * nx : 0);
-        double* tr = j->traj ? j->traj + (size_t)k * (H + 1) * nx : NULL;
-        j->L[k] = or_rollout(j->w, j->c, H, j->m->n_sub, j->m->dt, j->t0, x0,
-                             j->U + (size_t)k * OR_D, tr);
+        for (int i = 0; i < nx; i++) x0r[i] = (real)x0[i];
+        j->L[k] = (double)or_rollout(j->w, j->c, H, j->m->n_sub, (real)j->m->dt, (real)j->t0, x0r,
+                                     j->U + (size_t)k * OR_D, tr);
+        if (tr)
+            for (size_t i = 0; i < (size_t)(H + 1) * nx; i++)
+                j->traj[(size_t)k * (H + 1) * nx + i] = (double)tr[i];
     }
+    free(tr);
     return NULL;
 }
 
@@ -498,4 +504,57 @@ void or_rollouts(const or_world* w, const or_cost* c, const or_mppi* m, double t
     if (nthreads == 1) { rollout_worker(&jobs[0]); return; }
     for (int i = 0; i < nthreads; i++) pthread_create(&th[i], NULL, rollout_worker, &jobs[i]);
     for (int i = 0; i < nthreads; i++) pthread_join(th[i], NULL);
+}
+
+/* ---------------- batched helpers for the parity harness ---------------- */
+
+typedef struct {
+    const or_world* w; const double* X; const double* Ut; long m; int n_sub; double h;
+    double* out; int tid, nthreads;
+} dtstep_job;
+
+static void* dtstep_worker(void* arg) {
+    dtstep_job* j = (dtstep_job*)arg;
+    int nx = j->w->nx;
+    real x[64], u[OR_NJ];
+    for (long i = j->tid; i < j->m; i += j->nthreads) {
+        for (int a = 0; a < nx; a++) x[a] = (real)j->X[i * nx + a];
+        for (int a = 0; a < OR_NJ; a++) u[a] = (real)j->Ut[i * OR_NJ + a];
+        for (int s = 0; s < j->n_sub; s++) or_substep(j->w, x, u, (real)j->h);
+        for (int a = 0; a < nx; a++) j->out[i * nx + a] = (double)x[a];
+    }
+    return NULL;
+}
+
+/* m independent dt steps (n_sub sub-steps of h) from states X[m][nx] with
+ * targets Ut[m][12]; out[m][nx] */
+void or_dt_steps(const or_world* w, const double* X, const double* Ut, long m, int n_sub,
+                 double h, double* out, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    dtstep_job jobs[256];
+    pthread_t th[256];
+    for (int i = 0; i < nthreads; i++) {
+        dtstep_job jb = {w, X, Ut, m, n_sub, h, out, i, nthreads};
+        jobs[i] = jb;
+    }
+    if (nthreads == 1) { dtstep_worker(&jobs[0]); return; }
+    for (int i = 0; i < nthreads; i++) pthread_create(&th[i], NULL, dtstep_worker, &jobs[i]);
+    for (int i = 0; i < nthreads; i++) pthread_join(th[i], NULL);
+}
+
+/* stage costs of m (state, targets, time) triples, or terminal costs when t_abs is NULL */
+void or_stage_costs(const or_world* w, const or_cost* c, const double* X, const double* Ut,
+                    const double* t_abs, long m, double* out) {
+    int nx = w->nx;
+    real x[64], u[OR_NJ];
+    for (long i = 0; i < m; i++) {
+        for (int a = 0; a < nx; a++) x[a] = (real)X[i * nx + a];
+        if (t_abs) {
+            for (int a = 0; a < OR_NJ; a++) u[a] = (real)Ut[i * OR_NJ + a];
+            out[i] = (double)or_stage_cost(w, c, x, u, (real)t_abs[i]);
+        } else {
+            out[i] = (double)or_terminal_cost(w, c, x);
+        }
+    }
 }

@@ -27,9 +27,11 @@ struct mppi_handle_s {
     int device = 0;
     int nx = NX_ROBOT;
     float *d_mu = nullptr, *d_mu_prop = nullptr, *d_mu_upd = nullptr, *d_U = nullptr, *d_L = nullptr;
-    float *d_x0 = nullptr, *d_u0 = nullptr, *d_hf = nullptr;
+    float *d_x0 = nullptr, *d_u0 = nullptr, *d_hf = nullptr, *d_sbox = nullptr;
     int* d_status = nullptr;
     double* d_wsum = nullptr;
+    double* d_part = nullptr;      // update scratch: per-CTA partial sums
+    unsigned* d_counter = nullptr;  // update scratch: finished-CTA counter
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int timing = 0;
     int timed_valid = 0;
@@ -68,49 +70,67 @@ static bool is_device(const void* p) {
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-// spatial inertia about a body frame's origin: [Ic + m cx cx^T, m cx; m cx^T, m 1]
-static Sym6 spatial_inertia(double m, const double c[3], const double Icd[3]) {
-    double S[3][3] = {{0, -c[2], c[1]}, {c[2], 0, -c[0]}, {-c[1], c[0], 0}};
-    Sym6 I;
-    for (int i = 0; i < 3; i++)
-        for (int j = 0; j < 3; j++) {
-            double sst = 0;
-            for (int k = 0; k < 3; k++) sst += S[i][k] * S[j][k];
-            I.A[i][j] = (float)((i == j ? Icd[i] : 0.0) + m * sst);
-            I.B[i][j] = (float)(m * S[i][j]);
-            I.C[i][j] = (float)(i == j ? m : 0.0);
-        }
+// inertia of a body with its centre of mass on the frame's z axis at cz and a
+// diagonal rotational inertia Icd there, about the frame origin
+static BodyI body_inertia(double m, double cz, const double Icd[3]) {
+    BodyI I;
+    I.ax = (float)(Icd[0] + m * cz * cz);
+    I.ay = (float)(Icd[1] + m * cz * cz);
+    I.az = (float)Icd[2];
+    I.m = (float)m;
+    I.mcz = (float)(m * cz);
     return I;
 }
 
-static void derive_model(const mppi_model_t& p, DevModel& d) {
+// implicit-PD armature of one sub-step: h (kd + h kp) + a0
+static double armature(const mppi_model_t& p, double h) { return h * (p.kd + h * p.kp) + p.armature; }
+
+static void derive_model(const mppi_model_t& p, double h, DevModel& d) {
     memset(&d, 0, sizeof(d));
     const double a = p.trunk_size[0], b = p.trunk_size[1], c = p.trunk_size[2], m = p.trunk_mass;
     d.tr_Ic[0] = (float)(m * (b * b + c * c) / 12.0);
     d.tr_Ic[1] = (float)(m * (a * a + c * c) / 12.0);
     d.tr_Ic[2] = (float)(m * (a * a + b * b) / 12.0);
     d.tr_m = (float)m;
-    const double zero[3] = {0, 0, 0};
     const double ih = 0.4 * p.abd_mass * p.abd_radius * p.abd_radius;
     const double Ihip[3] = {ih, ih, ih};
-    d.I_hip = spatial_inertia(p.abd_mass, zero, Ihip);
+    d.I_hip = body_inertia(p.abd_mass, 0.0, Ihip);
     const double tl = p.thigh_length, cl = p.calf_length, rr = p.rod_radius;
     const double It[3] = {p.thigh_mass * tl * tl / 12.0, p.thigh_mass * tl * tl / 12.0, p.thigh_mass * rr * rr / 2.0};
-    const double ct[3] = {0, 0, -0.5 * tl};
-    d.I_thigh = spatial_inertia(p.thigh_mass, ct, It);
+    d.I_thigh = body_inertia(p.thigh_mass, -0.5 * tl, It);
     const double Ic[3] = {p.calf_mass * cl * cl / 12.0, p.calf_mass * cl * cl / 12.0, p.calf_mass * rr * rr / 2.0};
-    const double cc[3] = {0, 0, -0.5 * cl};
-    d.I_calf = spatial_inertia(p.calf_mass, cc, Ic);
-    // legs FR, FL, RR, RL: front +x / rear -x, right -y / left +y
-    const double fx[4] = {1, 1, -1, -1}, sy[4] = {-1, 1, -1, 1};
-    for (int l = 0; l < 4; l++) {
-        d.r_hip[l][0] = (float)(fx[l] * p.hip_x);
-        d.r_hip[l][1] = (float)(sy[l] * p.hip_y);
-        d.r_hip[l][2] = (float)p.hip_z;
-        d.r_thigh[l][0] = 0.f;
-        d.r_thigh[l][1] = (float)(sy[l] * p.thigh_offset_y);
-        d.r_thigh[l][2] = 0.f;
+    d.I_calf = body_inertia(p.calf_mass, -0.5 * cl, Ic);
+    {
+        // the calf has no children: its articulated inertia is its rigid inertia
+        // and its projection I - U U^T / D (U = I e_y, D = U_y + armature) is a
+        // constant of the model and the sub-step
+        const double mc = p.calf_mass, cz = -0.5 * cl;
+        const double ax = Ic[0] + mc * cz * cz, ay = Ic[1] + mc * cz * cz, az = Ic[2], mcz = mc * cz;
+        double A[3][3] = {{ax, 0, 0}, {0, ay, 0}, {0, 0, az}};
+        double B[3][3] = {{0, -mcz, 0}, {mcz, 0, 0}, {0, 0, 0}};
+        double C[3][3] = {{mc, 0, 0}, {0, mc, 0}, {0, 0, mc}};
+        const double U[6] = {A[0][1], A[1][1], A[2][1], B[1][0], B[1][1], B[1][2]};
+        const double D = U[1] + armature(p, h);
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                A[i][j] -= U[i] * U[j] / D;
+                B[i][j] -= U[i] * U[3 + j] / D;
+                C[i][j] -= U[3 + i] * U[3 + j] / D;
+            }
+        for (int i = 0; i < 3; i++)
+            for (int j = i; j < 3; j++) {
+                d.Ia_calf.A[sidx(i, j)] = (float)A[i][j];
+                d.Ia_calf.C[sidx(i, j)] = (float)C[i][j];
+            }
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) d.Ia_calf.B[i][j] = (float)B[i][j];
+        d.calf_D_inv = (float)(1.0 / D);
     }
+    // legs FR, FL, RR, RL: front +x / rear -x, right -y / left +y (signs in the kernel)
+    d.hip_x = (float)p.hip_x;
+    d.hip_y = (float)p.hip_y;
+    d.hip_z = (float)p.hip_z;
+    d.thigh_y = (float)p.thigh_offset_y;
     d.r_knee[0] = 0.f; d.r_knee[1] = 0.f; d.r_knee[2] = (float)(-tl);
     d.foot[0] = 0.f; d.foot[1] = 0.f; d.foot[2] = (float)(-cl);
     d.foot_r = (float)p.foot_radius;
@@ -126,12 +146,7 @@ static void derive_model(const mppi_model_t& p, DevModel& d) {
     d.hf_cell = (float)p.hf_cell;
     d.hf_inv_cell = p.hf_cell > 0 ? (float)(1.0 / p.hf_cell) : 0.f;
     d.hf_x0 = (float)p.hf_x0; d.hf_y0 = (float)p.hf_y0;
-    d.n_sbox = p.n_static_boxes;
-    for (int i = 0; i < p.n_static_boxes && i < MAX_SBOX; i++)
-        for (int k = 0; k < 3; k++) {
-            d.sb_lo[i][k] = (float)p.sbox_lo[i][k];
-            d.sb_hi[i][k] = (float)p.sbox_hi[i][k];
-        }
+    d.n_sbox = p.n_static_boxes;  // boxes themselves go to a device buffer (mppi_create)
     d.has_box = p.has_box;
     if (p.has_box) {
         d.box_m = (float)p.box_mass;
@@ -210,7 +225,7 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
     h->cfg = *cfg;
     h->stream = (cudaStream_t)stream;
     cudaGetDevice(&h->device);
-    derive_model(*model, h->dm);
+    derive_model(*model, cfg->dt / cfg->n_sub, h->dm);
     derive_cost(*cost, h->dc);
     h->nx = h->dm.nx;
     const size_t K = (size_t)cfg->K;
@@ -225,7 +240,9 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
               al((void**)&h->d_mu_upd, D * sizeof(float)) && al((void**)&h->d_U, K * D * sizeof(float)) &&
               al((void**)&h->d_L, K * sizeof(float)) && al((void**)&h->d_x0, K * NX_BOX * sizeof(float)) &&
               al((void**)&h->d_u0, NJ * sizeof(float)) && al((void**)&h->d_status, sizeof(int)) &&
-              al((void**)&h->d_wsum, sizeof(double));
+              al((void**)&h->d_wsum, sizeof(double)) &&
+              al((void**)&h->d_part, (size_t)UPDATE_MAX_CTAS * (D + 1) * sizeof(double)) &&
+              al((void**)&h->d_counter, sizeof(unsigned));
     if (ok && model->terrain == 1) {
         size_t nh = (size_t)model->hf_nx * model->hf_ny;
         ok = al((void**)&h->d_hf, nh * sizeof(float));
@@ -234,6 +251,17 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
             ok = cudaMemcpy(h->d_hf, model->hf, nh * sizeof(float), kind) == cudaSuccess;
         }
         h->dm.hf = h->d_hf;
+    }
+    if (ok) {
+        float boxes[MAX_SBOX * 6] = {0};
+        for (int i = 0; i < model->n_static_boxes; i++)
+            for (int k = 0; k < 3; k++) {
+                boxes[6 * i + k] = (float)model->sbox_lo[i][k];
+                boxes[6 * i + 3 + k] = (float)model->sbox_hi[i][k];
+            }
+        ok = al((void**)&h->d_sbox, sizeof(boxes)) &&
+             cudaMemcpy(h->d_sbox, boxes, sizeof(boxes), cudaMemcpyHostToDevice) == cudaSuccess;
+        h->dm.sbox = h->d_sbox;
     }
     if (!ok) {
         mppi_destroy(h);
@@ -244,7 +272,8 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
     float mu0[D];
     for (int d = 0; d < D; d++) mu0[d] = (float)cost->stand[d % 3];
     if (cudaMemcpy(h->d_mu, mu0, sizeof(mu0), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) {
+        cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(h->d_counter, 0, sizeof(unsigned)) != cudaSuccess) {
         mppi_destroy(h);
         return MPPI_ERR_CUDA;
     }
@@ -256,7 +285,9 @@ extern "C" mppi_status mppi_destroy(mppi_handle h) {
     if (!h) return MPPI_ERR_ARG;
     if (h->stream) cudaStreamSynchronize(h->stream);
     else cudaDeviceSynchronize();
-    void* bufs[] = {h->d_mu, h->d_mu_prop, h->d_mu_upd, h->d_U, h->d_L, h->d_x0, h->d_u0, h->d_hf, h->d_status, h->d_wsum};
+    void* bufs[] = {h->d_mu,  h->d_mu_prop, h->d_mu_upd, h->d_U,    h->d_L,    h->d_x0,
+                    h->d_u0,  h->d_hf,      h->d_status, h->d_wsum, h->d_part, h->d_counter,
+                    h->d_sbox};
     for (void* p : bufs)
         if (p) cudaFree(p);
     for (int i = 0; i < 4; i++)
@@ -342,6 +373,7 @@ static RolloutArgs rollout_args(mppi_handle h, const float* x0, int per, const f
     a.h = (float)(h->cfg.dt / h->cfg.n_sub);
     a.inv_Hm1 = (float)(1.0 / (h->cfg.H - 1));
     a.t0 = reduce_t0(h, t0);
+    a.arm = (float)armature(h->model_in, h->cfg.dt / h->cfg.n_sub);
     return a;
 }
 
@@ -418,6 +450,8 @@ static mppi_status do_update(mppi_handle h, const float* dL, const float* dU, in
     a.u0 = h->d_u0;
     a.status = h->d_status;
     a.wsum = h->d_wsum;
+    a.part = h->d_part;
+    a.counter = h->d_counter;
     a.n = n;
     a.H = h->cfg.H;
     a.ctrl_steps = h->cfg.ctrl_steps;

@@ -18,18 +18,34 @@ constexpr int NX_ROBOT = 37;
 constexpr int NX_BOX = 50;
 constexpr int MAX_SBOX = 4;
 
+// Symmetric 6x6 [[A, B], [B^T, C]]: A and C by their 6 unique entries
+// (order 00 01 02 11 12 22), B in full.
 struct Sym6 {
-    float A[3][3];  // symmetric
+    float A[6];
     float B[3][3];
-    float C[3][3];  // symmetric
+    float C[6];
+};
+
+__host__ __device__ __forceinline__ constexpr int sidx(int i, int j) {
+    return i <= j ? (i * (5 - i)) / 2 + j : (j * (5 - j)) / 2 + i;
+}
+
+// Spatial inertia of a body whose centre of mass lies on its frame's z axis at
+// cz and whose rotational inertia is diagonal there (the hip sphere, the thigh
+// and calf rods): about the frame origin A = diag(ax, ay, az) (parallel axis
+// included), B = m [c x], C = m 1.
+struct BodyI {
+    float ax, ay, az, m, mcz;
 };
 
 // All derived, FP32 model constants (computed on the host from mppi_model_t).
 struct DevModel {
     float tr_Ic[3], tr_m;             // trunk: principal inertia about its centre, mass
-    Sym6 I_hip, I_thigh, I_calf;      // leg bodies: spatial inertia about the joint origin
-    float r_hip[4][3];                // abduction joint in the trunk frame
-    float r_thigh[4][3];              // flexion joint in the hip frame
+    BodyI I_hip, I_thigh, I_calf;     // leg bodies: spatial inertia about the joint origin
+    Sym6 Ia_calf;                     // calf articulated inertia after its joint's projection
+    float calf_D_inv;                 // 1 / (S^T I_calf S + armature) (the calf's D is constant)
+    float hip_x, hip_y, hip_z;        // abduction joint at (+-hip_x, +-hip_y, hip_z) in the trunk frame
+    float thigh_y;                    // flexion joint at (0, +-thigh_y, 0) in the hip frame
     float r_knee[3];                  // knee in the thigh frame
     float foot[3], foot_r;            // foot sphere centre in the calf frame, radius
     int n_tsph;
@@ -42,7 +58,7 @@ struct DevModel {
     float hf_cell, hf_inv_cell, hf_x0, hf_y0;
     const float* hf;                  // device heights [ny][nx]
     int n_sbox;
-    float sb_lo[MAX_SBOX][3], sb_hi[MAX_SBOX][3];
+    const float* sbox;                // device [n_sbox][6]: lo xyz, hi xyz
     int has_box;
     float box_m, box_inv_m, box_half[3], box_Ic[3], box_inv_Ic[3], box_cr;
     int nx;
@@ -82,84 +98,157 @@ template <int AX> __device__ __forceinline__ float3 ErotT(float c, float s, floa
     return AX == 0 ? ExT(c, s, v) : EyT(c, s, v);
 }
 
-// M <- R M R^T with R = E^T (child -> parent rotation), for a general 3x3 M.
-template <int AX> __device__ __forceinline__ void rot3(float M[3][3], float c, float s) {
-    // rows then columns; AX 0 mixes (1, 2), AX 1 mixes (0, 2)
-    constexpr int i0 = AX == 0 ? 1 : 0;
-    constexpr int i1 = 2;
-    // R for AX 0: row1 = c e1 - s e2, row2 = s e1 + c e2 ; AX 1: row0 = c e0 + s e2, row2 = -s e0 + c e2
-    const float sg = AX == 0 ? -1.f : 1.f;  // sign of the s term in the first mixed row
+// ---------------------------------------------------------------- congruence
+// R = E^T (child -> parent) for a joint about AX mixes indices p, q and keeps o:
+// AX 0 (x): (p, q) = (1, 2), R = [1 0 0; 0 c -s; 0 s c] -> sigma = -1
+// AX 1 (y): (p, q) = (0, 2), R = [c 0 s; 0 1 0; -s 0 c] -> sigma = +1
+template <int AX> struct RotIdx {
+    static constexpr int o = AX == 0 ? 0 : 1, p = AX == 0 ? 1 : 0, q = 2;
+    static constexpr float sg = AX == 0 ? -1.f : 1.f;
+};
+
+// S <- R S R^T for a symmetric 3x3 in unique storage
+template <int AX> __device__ __forceinline__ void rot_sym(float S[6], float c, float s) {
+    using I = RotIdx<AX>;
+    const float cs = I::sg * c * s, cc = c * c, ss = s * s;
+    const float Sop = S[sidx(I::o, I::p)], Soq = S[sidx(I::o, I::q)];
+    const float Spp = S[sidx(I::p, I::p)], Sqq = S[sidx(I::q, I::q)], Spq = S[sidx(I::p, I::q)];
+    S[sidx(I::o, I::p)] = c * Sop + I::sg * s * Soq;
+    S[sidx(I::o, I::q)] = c * Soq - I::sg * s * Sop;
+    const float t = 2.f * cs * Spq;
+    S[sidx(I::p, I::p)] = cc * Spp + ss * Sqq + t;
+    S[sidx(I::q, I::q)] = cc * Sqq + ss * Spp - t;
+    S[sidx(I::p, I::q)] = (cc - ss) * Spq + cs * (Sqq - Spp);
+}
+
+// B <- R B R^T for a general 3x3
+template <int AX> __device__ __forceinline__ void rot_gen(float B[3][3], float c, float s) {
+    using I = RotIdx<AX>;
 #pragma unroll
     for (int j = 0; j < 3; j++) {
-        float a = M[i0][j], b = M[i1][j];
-        M[i0][j] = c * a + sg * s * b;
-        M[i1][j] = c * b - sg * s * a;
+        float a = B[I::p][j], b = B[I::q][j];
+        B[I::p][j] = c * a + I::sg * s * b;
+        B[I::q][j] = c * b - I::sg * s * a;
     }
 #pragma unroll
     for (int i = 0; i < 3; i++) {
-        float a = M[i][i0], b = M[i][i1];
-        M[i][i0] = c * a + sg * s * b;
-        M[i][i1] = c * b - sg * s * a;
+        float a = B[i][I::p], b = B[i][I::q];
+        B[i][I::p] = c * a + I::sg * s * b;
+        B[i][I::q] = c * b - I::sg * s * a;
     }
 }
 
-// Congruence of a spatial inertia into the parent frame: X^T M X with
-// X = rot(E) xlt(r) (joint rotation about AX, then the joint origin r):
+// entry (l, j) of [r x] with structurally-zero entries known at compile time;
+// MASK bit 0/1/2 = r.x/r.y/r.z may be non-zero
+template <int MASK>
+__device__ __forceinline__ bool skew_nz(int l, int j) {
+    return (l == 0 && j == 1 && (MASK & 4)) || (l == 0 && j == 2 && (MASK & 2)) ||
+           (l == 1 && j == 0 && (MASK & 4)) || (l == 1 && j == 2 && (MASK & 1)) ||
+           (l == 2 && j == 0 && (MASK & 2)) || (l == 2 && j == 1 && (MASK & 1));
+}
+__device__ __forceinline__ float skew_at(float3 r, int l, int j) {
+    return l == 0 ? (j == 1 ? -r.z : r.y) : (l == 1 ? (j == 0 ? r.z : -r.x) : (j == 0 ? -r.y : r.x));
+}
+
+// Congruence of a spatial inertia into the parent frame, X^T M X with
+// X = rot(E) xlt(r) (joint about AX, then the joint origin r):
 //   rotate every block by E^T, then
-//   A'' = A' - (P + P^T) - Q,  B'' = B' + r x C',  C'' = C',
-//   P = B' [r x],  Q = [r x] C' [r x].
-template <int AX>
+//   A'' = A' - (P + P^T) - Q,  B'' = B' + T,  C'' = C',
+//   P = B' [r x],  T = [r x] C',  Q = T [r x].
+template <int AX, int MASK>
 __device__ __forceinline__ void congruence(Sym6& M, float c, float s, float3 r) {
-    rot3<AX>(M.A, c, s);
-    rot3<AX>(M.B, c, s);
-    rot3<AX>(M.C, c, s);
-    float P[3][3], T[3][3], Q[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        P[i][0] = M.B[i][1] * r.z - M.B[i][2] * r.y;
-        P[i][1] = M.B[i][2] * r.x - M.B[i][0] * r.z;
-        P[i][2] = M.B[i][0] * r.y - M.B[i][1] * r.x;
-    }
-#pragma unroll
-    for (int j = 0; j < 3; j++) {
-        T[0][j] = r.y * M.C[2][j] - r.z * M.C[1][j];
-        T[1][j] = r.z * M.C[0][j] - r.x * M.C[2][j];
-        T[2][j] = r.x * M.C[1][j] - r.y * M.C[0][j];
-    }
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        Q[i][0] = T[i][1] * r.z - T[i][2] * r.y;
-        Q[i][1] = T[i][2] * r.x - T[i][0] * r.z;
-        Q[i][2] = T[i][0] * r.y - T[i][1] * r.x;
-    }
+    rot_sym<AX>(M.A, c, s);
+    rot_gen<AX>(M.B, c, s);
+    rot_sym<AX>(M.C, c, s);
+    float P[3][3], T[3][3];
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            M.A[i][j] = M.A[i][j] - (P[i][j] + P[j][i]) - Q[i][j];
-            M.B[i][j] = M.B[i][j] + T[i][j];
+            float p = 0.f, t = 0.f;
+#pragma unroll
+            for (int l = 0; l < 3; l++) {
+                if (skew_nz<MASK>(l, j)) p = fmaf(M.B[i][l], skew_at(r, l, j), p);
+                if (skew_nz<MASK>(i, l)) t = fmaf(skew_at(r, i, l), M.C[sidx(l, j)], t);
+            }
+            P[i][j] = p;
+            T[i][j] = t;
         }
-}
-
-__device__ __forceinline__ void sym6_add(Sym6& a, const Sym6& b) {
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) {
-            a.A[i][j] += b.A[i][j];
-            a.B[i][j] += b.B[i][j];
-            a.C[i][j] += b.C[i][j];
+        for (int j = i; j < 3; j++) {
+            float qv = 0.f;
+#pragma unroll
+            for (int l = 0; l < 3; l++)
+                if (skew_nz<MASK>(l, j)) qv = fmaf(T[i][l], skew_at(r, l, j), qv);
+            M.A[sidx(i, j)] = M.A[sidx(i, j)] - (P[i][j] + P[j][i]) - qv;
         }
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) M.B[i][j] += T[i][j];
 }
 
-// I [w; v]
+// M [w; v] for a full symmetric spatial matrix
 __device__ __forceinline__ void sym6_mv(const Sym6& M, float3 w, float3 v, float3& ha, float3& hl) {
-    ha = f3(M.A[0][0] * w.x + M.A[0][1] * w.y + M.A[0][2] * w.z + M.B[0][0] * v.x + M.B[0][1] * v.y + M.B[0][2] * v.z,
-            M.A[1][0] * w.x + M.A[1][1] * w.y + M.A[1][2] * w.z + M.B[1][0] * v.x + M.B[1][1] * v.y + M.B[1][2] * v.z,
-            M.A[2][0] * w.x + M.A[2][1] * w.y + M.A[2][2] * w.z + M.B[2][0] * v.x + M.B[2][1] * v.y + M.B[2][2] * v.z);
-    hl = f3(M.B[0][0] * w.x + M.B[1][0] * w.y + M.B[2][0] * w.z + M.C[0][0] * v.x + M.C[0][1] * v.y + M.C[0][2] * v.z,
-            M.B[0][1] * w.x + M.B[1][1] * w.y + M.B[2][1] * w.z + M.C[1][0] * v.x + M.C[1][1] * v.y + M.C[1][2] * v.z,
-            M.B[0][2] * w.x + M.B[1][2] * w.y + M.B[2][2] * w.z + M.C[2][0] * v.x + M.C[2][1] * v.y + M.C[2][2] * v.z);
+    const float* A = M.A;
+    const float* C = M.C;
+    ha = f3(A[0] * w.x + A[1] * w.y + A[2] * w.z + M.B[0][0] * v.x + M.B[0][1] * v.y + M.B[0][2] * v.z,
+            A[1] * w.x + A[3] * w.y + A[4] * w.z + M.B[1][0] * v.x + M.B[1][1] * v.y + M.B[1][2] * v.z,
+            A[2] * w.x + A[4] * w.y + A[5] * w.z + M.B[2][0] * v.x + M.B[2][1] * v.y + M.B[2][2] * v.z);
+    hl = f3(M.B[0][0] * w.x + M.B[1][0] * w.y + M.B[2][0] * w.z + C[0] * v.x + C[1] * v.y + C[2] * v.z,
+            M.B[0][1] * w.x + M.B[1][1] * w.y + M.B[2][1] * w.z + C[1] * v.x + C[3] * v.y + C[4] * v.z,
+            M.B[0][2] * w.x + M.B[1][2] * w.y + M.B[2][2] * w.z + C[2] * v.x + C[4] * v.y + C[5] * v.z);
+}
+
+// I [w; v] for a body inertia with its centre of mass on the frame's z axis
+__device__ __forceinline__ void bodyI_mv(const BodyI& I, float3 w, float3 v, float3& ha, float3& hl) {
+    ha = f3(I.ax * w.x - I.mcz * v.y, I.ay * w.y + I.mcz * v.x, I.az * w.z);
+    hl = f3(I.mcz * w.y + I.m * v.x, I.m * v.y - I.mcz * w.x, I.m * v.z);
+}
+
+// M += I (structured body inertia)
+__device__ __forceinline__ void add_bodyI(Sym6& M, const BodyI& I) {
+    M.A[0] += I.ax; M.A[3] += I.ay; M.A[5] += I.az;
+    M.B[0][1] -= I.mcz; M.B[1][0] += I.mcz;
+    M.C[0] += I.m; M.C[3] += I.m; M.C[5] += I.m;
+}
+
+// Sym6 from a structured body inertia
+__device__ __forceinline__ Sym6 sym6_of(const BodyI& I) {
+    Sym6 M;
+#pragma unroll
+    for (int i = 0; i < 6; i++) { M.A[i] = 0.f; M.C[i] = 0.f; }
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) M.B[i][j] = 0.f;
+    add_bodyI(M, I);
+    return M;
+}
+
+// sin and cos of a bounded angle (|x| < 100): x = k pi/2 + r with a two-term
+// Cody-Waite reduction, |r| <= pi/4, Taylor polynomials to r^9 / r^10.
+__device__ __forceinline__ void sincos_r(float x, float& s, float& c) {
+    const float k = rintf(x * 0.636619772f);
+    float r = fmaf(k, -1.57079637f, x);
+    r = fmaf(k, 4.37113883e-08f, r);
+    const float r2 = r * r;
+    float ps = fmaf(r2, 2.75573188e-06f, -1.98412701e-04f);
+    ps = fmaf(r2, ps, 8.33333377e-03f);
+    ps = fmaf(r2, ps, -1.66666672e-01f);
+    const float sn = fmaf(r * r2, ps, r);
+    float pc = fmaf(r2, -2.75573200e-07f, 2.48015876e-05f);
+    pc = fmaf(r2, pc, -1.38888892e-03f);
+    pc = fmaf(r2, pc, 4.16666679e-02f);
+    pc = fmaf(r2, pc, -0.5f);
+    const float cs = fmaf(r2, pc, 1.f);
+    const int q = ((int)k) & 3;
+    s = (q & 1) ? cs : sn;
+    c = (q & 1) ? sn : cs;
+    if (q == 1 || q == 2) c = -c;
+    if (q >= 2) s = -s;
 }
 
 // rotation matrix (body -> world) of a unit quaternion (w, x, y, z)
@@ -183,7 +272,7 @@ __device__ __forceinline__ void quat_integrate(float q[4], float3 w, float h) {
     float wn = sqrtf(dot3(w, w));
     float th = wn * h;
     float sh, ch;
-    sincosf(0.5f * th, &sh, &ch);
+    sincos_r(0.5f * th, sh, ch);
     float sk = (th > 1e-4f) ? sh / wn : 0.5f * h * (1.f - th * th * (1.f / 24.f));
     float d0 = ch, d1 = sk * w.x, d2 = sk * w.y, d3 = sk * w.z;
     float r0 = q[0] * d0 - q[1] * d1 - q[2] * d2 - q[3] * d3;

@@ -27,6 +27,7 @@ struct RolloutArgs {
     float* traj;           // [n][H+1][nx] device or null
     int n, H, n_sub;
     float h, dt, inv_Hm1, t0;  // t0: gait time of step 0 (reduced modulo the gait period)
+    float arm;             // implicit-PD armature h (kd + h kp) + a0
 };
 
 struct UpdateArgs {
@@ -37,9 +38,14 @@ struct UpdateArgs {
     float* u0;             // [12]
     int* status;           // 0 ok, 4 all costs non-finite
     double* wsum;          // normaliser (FP64) of the last update, optional
+    double* part;          // scratch [UPDATE_MAX_CTAS][D + 1] per-CTA partial sums
+    unsigned* counter;     // scratch: CTAs finished (0 between launches)
     int n, H, ctrl_steps;
     float inv_lambda;
 };
+
+constexpr int UPDATE_MAX_CTAS = 128;
+int update_grid(int n);
 
 cudaError_t launch_sample(const SampleArgs& a, cudaStream_t st);
 cudaError_t launch_rollout(const RolloutArgs& a, int block, cudaStream_t st);

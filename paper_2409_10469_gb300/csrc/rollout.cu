@@ -102,7 +102,7 @@ __device__ __forceinline__ void contact_wrench(const DevModel& m, float pen, flo
 // RT(world) maps a world vector into the body's coordinates
 template <int TERR, typename ToBody>
 __device__ __forceinline__ void sphere_env(const DevModel& m, float3 xw, float r, float3 cb, float3 w, float3 v,
-                                           ToBody toBody, float3& torque, float3& force) {
+                                           const ToBody& toBody, float3& torque, float3& force) {
     float h, hx, hy;
     ground<TERR>(m, xw.x, xw.y, h, hx, hy);
     float inv = 1.f / sqrtf(hx * hx + hy * hy + 1.f);
@@ -111,10 +111,31 @@ __device__ __forceinline__ void sphere_env(const DevModel& m, float3 xw, float r
     if (pen > 0.f) contact_wrench(m, pen, toBody(n), cb, r, w, v, torque, force);
     for (int b = 0; b < m.n_sbox; b++) {
         float3 nn; float pb;
-        if (sphere_aabb(xw, r, ld3(m.sb_lo[b]), ld3(m.sb_hi[b]), nn, pb))
+        const float* bx = m.sbox + 6 * b;
+        const float3 lo = f3(__ldg(bx), __ldg(bx + 1), __ldg(bx + 2));
+        const float3 hi = f3(__ldg(bx + 3), __ldg(bx + 4), __ldg(bx + 5));
+        if (sphere_aabb(xw, r, lo, hi, nn, pb))
             contact_wrench(m, pb, toBody(nn), cb, r, w, v, torque, force);
     }
 }
+
+// world -> body coordinate maps of the two kinds of contact-sphere bodies
+struct TrunkFrame {
+    float r00, r01, r02, r10, r11, r12, r20, r21, r22;  // R0 (body -> world)
+    __device__ __forceinline__ float3 operator()(float3 n) const {
+        return f3(r00 * n.x + r10 * n.y + r20 * n.z, r01 * n.x + r11 * n.y + r21 * n.z,
+                  r02 * n.x + r12 * n.y + r22 * n.z);
+    }
+};
+struct CalfFrame {
+    float r00, r01, r02, r10, r11, r12, r20, r21, r22;
+    float c0, s0, c1, s1, c2, s2;
+    __device__ __forceinline__ float3 operator()(float3 n) const {
+        float3 t = f3(r00 * n.x + r10 * n.y + r20 * n.z, r01 * n.x + r11 * n.y + r21 * n.z,
+                      r02 * n.x + r12 * n.y + r22 * n.z);
+        return Ey(c2, s2, Ey(c1, s1, Ex(c0, s0, t)));
+    }
+};
 
 // ---------------------------------------------------------------- cost
 
@@ -133,134 +154,176 @@ __device__ __forceinline__ float trunk_state_cost(const DevCost& c, const Trunk&
 
 // ---------------------------------------------------------------- one sub-step
 
+// velocity-product term c = v x (e_AX qd) of a joint about AX, from the body's
+// velocity before its own joint rate is added (the joint's own part drops out)
+template <int AX> __device__ __forceinline__ float3 vprod(float3 a, float qd) {
+    return AX == 0 ? f3(0.f, a.z * qd, -a.y * qd) : f3(-a.z * qd, 0.f, a.x * qd);
+}
+
+// Ia = IA - U U^T / D  and  pa = pA + Ia c + U u / D for a joint about AX
+// (U = IA e_AX); c has zero entries on the joint axis (structure of vprod).
+template <int AX>
+__device__ __forceinline__ void project(Sym6& M, float3& pn, float3& pf, float Dinv, float uu, float3 cw, float3 cv) {
+    float Ua[3], Ul[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        Ua[i] = M.A[sidx(i, AX)];
+        Ul[i] = M.B[AX][i];
+    }
+    float Uas[3], Uls[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) { Uas[i] = Ua[i] * Dinv; Uls[i] = Ul[i] * Dinv; }
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = i; j < 3; j++) {
+            M.A[sidx(i, j)] = fmaf(-Uas[i], Ua[j], M.A[sidx(i, j)]);
+            M.C[sidx(i, j)] = fmaf(-Uls[i], Ul[j], M.C[sidx(i, j)]);
+        }
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) M.B[i][j] = fmaf(-Uas[i], Ul[j], M.B[i][j]);
+    // Ia c with c zero on component AX of both halves
+    const float cw_[3] = {cw.x, cw.y, cw.z}, cv_[3] = {cv.x, cv.y, cv.z};
+    float n[3] = {pn.x, pn.y, pn.z}, f[3] = {pf.x, pf.y, pf.z};
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int l = 0; l < 3; l++) {
+            if (l == AX) continue;
+            n[i] = fmaf(M.A[sidx(i, l)], cw_[l], n[i]);
+            n[i] = fmaf(M.B[i][l], cv_[l], n[i]);
+            f[i] = fmaf(M.B[l][i], cw_[l], f[i]);
+            f[i] = fmaf(M.C[sidx(i, l)], cv_[l], f[i]);
+        }
+    const float k = uu * Dinv;
+    pn = f3(fmaf(k, Ua[0], n[0]), fmaf(k, Ua[1], n[1]), fmaf(k, Ua[2], n[2]));
+    pf = f3(fmaf(k, Ul[0], f[0]), fmaf(k, Ul[1], f[1]), fmaf(k, Ul[2], f[2]));
+}
+
+// bias force v x* I v of a body with a structured inertia
+__device__ __forceinline__ void body_bias(const BodyI& I, float3 w, float3 v, float3& bn, float3& bf) {
+    float3 ha, hl;
+    bodyI_mv(I, w, v, ha, hl);
+    bn = cross3(w, ha) + cross3(v, hl);
+    bf = cross3(w, hl);
+}
+
 template <int TERR>
 __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, LegState& S, const float u[3],
-                                        float h) {
+                                        float h, float arm) {
     const float g = m.gz;
     float R0[3][3];
     quat_R(T.quat, R0);
 
     // ---- leg kinematics: joint transforms, body velocities, velocity products
     float c0, s0, c1, s1, c2, s2;
-    sincosf(S.q[0], &s0, &c0);
-    sincosf(S.q[1], &s1, &c1);
-    sincosf(S.q[2], &s2, &c2);
-    const float3 rh = ld3(m.r_hip[leg]), rt = ld3(m.r_thigh[leg]), rk = ld3(m.r_knee);
-    // hip (axis x)
+    sincos_r(S.q[0], s0, c0);
+    sincos_r(S.q[1], s1, c1);
+    sincos_r(S.q[2], s2, c2);
+    // legs FR, FL, RR, RL: front (+x) for legs 0, 1; left (+y) for odd legs
+    const float fx = leg < 2 ? 1.f : -1.f, sy = (leg & 1) ? 1.f : -1.f;
+    const float3 rh = f3(fx * m.hip_x, sy * m.hip_y, m.hip_z);
+    const float3 rt = f3(0.f, sy * m.thigh_y, 0.f);
+    const float3 rk = f3(0.f, 0.f, m.r_knee[2]);
     float3 wh = Ex(c0, s0, T.w);
     float3 vh = Ex(c0, s0, T.v + cross3(T.w, rh));
-    float3 ch_w = f3(0.f, wh.z * S.qd[0], -wh.y * S.qd[0]);   // w x (e_x qd)
-    float3 ch_v = f3(0.f, vh.z * S.qd[0], -vh.y * S.qd[0]);
+    const float3 ch_w = vprod<0>(wh, S.qd[0]), ch_v = vprod<0>(vh, S.qd[0]);
     wh.x += S.qd[0];
-    // thigh (axis y)
     float3 wt = Ey(c1, s1, wh);
     float3 vt = Ey(c1, s1, vh + cross3(wh, rt));
-    float3 ct_w = f3(-wt.z * S.qd[1], 0.f, wt.x * S.qd[1]);   // w x (e_y qd)
-    float3 ct_v = f3(-vt.z * S.qd[1], 0.f, vt.x * S.qd[1]);
+    const float3 ct_w = vprod<1>(wt, S.qd[1]), ct_v = vprod<1>(vt, S.qd[1]);
     wt.y += S.qd[1];
-    // calf (axis y)
     float3 wc = Ey(c2, s2, wt);
     float3 vc = Ey(c2, s2, vt + cross3(wt, rk));
-    float3 cc_w = f3(-wc.z * S.qd[2], 0.f, wc.x * S.qd[2]);
-    float3 cc_v = f3(-vc.z * S.qd[2], 0.f, vc.x * S.qd[2]);
+    const float3 cc_w = vprod<1>(wc, S.qd[2]), cc_v = vprod<1>(vc, S.qd[2]);
     wc.y += S.qd[2];
 
     // ---- contacts: the foot sphere on the calf
     float3 fc_n = f3(0.f, 0.f, 0.f), fc_f = f3(0.f, 0.f, 0.f);
     {
-        const float3 foot = ld3(m.foot);
+        const float3 foot = f3(0.f, 0.f, m.foot[2]);
         float3 ptr = rh + ExT(c0, s0, rt + EyT(c1, s1, rk + EyT(c2, s2, foot)));   // trunk frame
         float3 xw = f3(T.p[0], T.p[1], T.p[2]) + mulR(R0, ptr);
-        auto toCalf = [&](float3 nw) { return Ey(c2, s2, Ey(c1, s1, Ex(c0, s0, mulRT(R0, nw)))); };
+        const CalfFrame toCalf = {R0[0][0], R0[0][1], R0[0][2], R0[1][0], R0[1][1], R0[1][2],
+                                  R0[2][0], R0[2][1], R0[2][2], c0, s0, c1, s1, c2, s2};
         sphere_env<TERR>(m, xw, m.foot_r, foot, wc, vc, toCalf, fc_n, fc_f);
     }
-    // ---- contacts: trunk spheres, one per lane, summed over the 4 lanes
+    // ---- contacts: trunk spheres, one per lane, summed over the 4 lanes below
     float3 f0_n = f3(0.f, 0.f, 0.f), f0_f = f3(0.f, 0.f, 0.f);
     if (leg < m.n_tsph) {
-        float3 cb = f3(m.tsph_x[leg], 0.f, 0.f);
+        const float tx = leg == 0 ? m.tsph_x[0] : (leg == 1 ? m.tsph_x[1] : (leg == 2 ? m.tsph_x[2] : m.tsph_x[3]));
+        float3 cb = f3(tx, 0.f, 0.f);
         float3 xw = f3(T.p[0], T.p[1], T.p[2]) + mulR(R0, cb);
-        auto toTrunk = [&](float3 nw) { return mulRT(R0, nw); };
+        const TrunkFrame toTrunk = {R0[0][0], R0[0][1], R0[0][2], R0[1][0], R0[1][1], R0[1][2],
+                                    R0[2][0], R0[2][1], R0[2][2]};
         sphere_env<TERR>(m, xw, m.tsph_r, cb, T.w, T.v, toTrunk, f0_n, f0_f);
     }
 
     // ---- PD with implicit damping: tau = kp (u - q - h qd) - kd qd, armature h (kd + h kp)
-    const float arm = h * (m.kd + h * m.kp) + m.arm0;
     float tau[3];
 #pragma unroll
     for (int i = 0; i < 3; i++) tau[i] = m.kp * (u[i] - S.q[i] - h * S.qd[i]) - m.kd * S.qd[i];
 
-    // ---- pass 2 (tip to root), bias forces pA = v x* I v - f_ext
+    // ---- pass 2 (tip to root)
+    // calf: its articulated inertia after projection is a model constant
+    Sym6 IA = m.Ia_calf;
     float3 pa_n, pa_f;
-    Sym6 IA;
-    float U2[6], D2inv, u2, U1[6], D1inv, u1, U0[6], D0inv, u0;
-    {   // calf
-        IA = m.I_calf;
-        float3 ha, hl;
-        sym6_mv(IA, wc, vc, ha, hl);
-        pa_n = cross3(wc, ha) + cross3(vc, hl) - fc_n;
-        pa_f = cross3(wc, hl) - fc_f;
-        U2[0] = IA.A[0][1]; U2[1] = IA.A[1][1]; U2[2] = IA.A[2][1];
-        U2[3] = IA.B[1][0]; U2[4] = IA.B[1][1]; U2[5] = IA.B[1][2];
-        D2inv = 1.f / (U2[1] + arm);
-        u2 = tau[2] - pa_n.y;
-    }
-    // articulated quantities passed to the thigh
-    auto project = [&](Sym6& M, float3& pn, float3& pf, const float U[6], float Dinv, float uu, float3 cw,
-                       float3 cv) {
-        // Ia = IA - U U^T / D ; pa = pA + Ia c + U u / D
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int j = 0; j < 3; j++) {
-                M.A[i][j] -= U[i] * U[j] * Dinv;
-                M.B[i][j] -= U[i] * U[3 + j] * Dinv;
-                M.C[i][j] -= U[3 + i] * U[3 + j] * Dinv;
-            }
+    body_bias(m.I_calf, wc, vc, pa_n, pa_f);
+    pa_n = pa_n - fc_n;
+    pa_f = pa_f - fc_f;
+    const float D2inv = m.calf_D_inv;
+    const float u2 = tau[2] - pa_n.y;
+    // U2 = I_calf e_y = (0, ay, 0 | mcz, 0, 0)
+    const float U2a = m.I_calf.ay, U2l = m.I_calf.mcz;
+    {
         float3 ia, il;
-        sym6_mv(M, cw, cv, ia, il);
-        float k = uu * Dinv;
-        pn = pn + ia + k * f3(U[0], U[1], U[2]);
-        pf = pf + il + k * f3(U[3], U[4], U[5]);
-    };
-    project(IA, pa_n, pa_f, U2, D2inv, u2, cc_w, cc_v);
+        sym6_mv(IA, cc_w, cc_v, ia, il);
+        const float k = u2 * D2inv;
+        pa_n = pa_n + ia + f3(0.f, k * U2a, 0.f);
+        pa_f = pa_f + il + f3(k * U2l, 0.f, 0.f);
+    }
     // to the thigh frame: X^T pa = [E^T n + r x E^T f; E^T f]
+    float U1a[3], U1l[3], D1inv, u1;
     {
         float3 fn = EyT(c2, s2, pa_n), ff = EyT(c2, s2, pa_f);
         pa_n = fn + cross3(rk, ff);
         pa_f = ff;
-        congruence<1>(IA, c2, s2, rk);
-        sym6_add(IA, m.I_thigh);
-        float3 ha, hl;
-        sym6_mv(m.I_thigh, wt, vt, ha, hl);
-        pa_n = pa_n + cross3(wt, ha) + cross3(vt, hl);
-        pa_f = pa_f + cross3(wt, hl);
-        U1[0] = IA.A[0][1]; U1[1] = IA.A[1][1]; U1[2] = IA.A[2][1];
-        U1[3] = IA.B[1][0]; U1[4] = IA.B[1][1]; U1[5] = IA.B[1][2];
-        D1inv = 1.f / (U1[1] + arm);
+        congruence<1, 4>(IA, c2, s2, rk);
+        add_bodyI(IA, m.I_thigh);
+        float3 bn, bf;
+        body_bias(m.I_thigh, wt, vt, bn, bf);
+        pa_n = pa_n + bn;
+        pa_f = pa_f + bf;
+#pragma unroll
+        for (int i = 0; i < 3; i++) { U1a[i] = IA.A[sidx(i, 1)]; U1l[i] = IA.B[1][i]; }
+        D1inv = 1.f / (U1a[1] + arm);
         u1 = tau[1] - pa_n.y;
     }
-    project(IA, pa_n, pa_f, U1, D1inv, u1, ct_w, ct_v);
+    project<1>(IA, pa_n, pa_f, D1inv, u1, ct_w, ct_v);
+    float U0a[3], U0l[3], D0inv, u0;
     {   // to the hip frame
         float3 fn = EyT(c1, s1, pa_n), ff = EyT(c1, s1, pa_f);
         pa_n = fn + cross3(rt, ff);
         pa_f = ff;
-        congruence<1>(IA, c1, s1, rt);
-        sym6_add(IA, m.I_hip);
-        float3 ha, hl;
-        sym6_mv(m.I_hip, wh, vh, ha, hl);
-        pa_n = pa_n + cross3(wh, ha) + cross3(vh, hl);
-        pa_f = pa_f + cross3(wh, hl);
-        U0[0] = IA.A[0][0]; U0[1] = IA.A[1][0]; U0[2] = IA.A[2][0];
-        U0[3] = IA.B[0][0]; U0[4] = IA.B[0][1]; U0[5] = IA.B[0][2];
-        D0inv = 1.f / (U0[0] + arm);
+        congruence<1, 2>(IA, c1, s1, rt);
+        add_bodyI(IA, m.I_hip);
+        float3 bn, bf;
+        body_bias(m.I_hip, wh, vh, bn, bf);
+        pa_n = pa_n + bn;
+        pa_f = pa_f + bf;
+#pragma unroll
+        for (int i = 0; i < 3; i++) { U0a[i] = IA.A[sidx(i, 0)]; U0l[i] = IA.B[0][i]; }
+        D0inv = 1.f / (U0a[0] + arm);
         u0 = tau[0] - pa_n.x;
     }
-    project(IA, pa_n, pa_f, U0, D0inv, u0, ch_w, ch_v);
+    project<0>(IA, pa_n, pa_f, D0inv, u0, ch_w, ch_v);
     {   // to the trunk frame
         float3 fn = ExT(c0, s0, pa_n), ff = ExT(c0, s0, pa_f);
         pa_n = fn + cross3(rh, ff);
         pa_f = ff;
-        congruence<0>(IA, c0, s0, rh);
+        congruence<0, 7>(IA, c0, s0, rh);
     }
 
     // ---- trunk: sum the 4 legs' contributions, add the trunk's own terms
@@ -269,8 +332,8 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = i; j < 3; j++) {
-            Mt[i][j] = xsum4(IA.A[i][j]);
-            Mt[3 + i][3 + j] = xsum4(IA.C[i][j]);
+            Mt[i][j] = xsum4(IA.A[sidx(i, j)]);
+            Mt[3 + i][3 + j] = xsum4(IA.C[sidx(i, j)]);
         }
 #pragma unroll
     for (int i = 0; i < 3; i++)
@@ -293,21 +356,20 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
         bt[4] = xsum4(pa_f.y - f0_f.y) + bf.y;
         bt[5] = xsum4(pa_f.z - f0_f.z) + bf.z;
     }
-    // ---- solve Mt a' = -bt (Cholesky, 6x6 SPD)
-    float Lc[6][6];
+    // ---- solve Mt a' = -bt (Cholesky, 6x6 SPD, upper storage)
+    float Lc[6][6], Linv[6];
 #pragma unroll
     for (int j = 0; j < 6; j++) {
         float d = Mt[j][j];
 #pragma unroll
-        for (int k = 0; k < j; k++) d -= Lc[j][k] * Lc[j][k];
-        float ljj = sqrtf(d);
-        float inv = 1.f / ljj;
-        Lc[j][j] = ljj;
+        for (int k = 0; k < j; k++) d = fmaf(-Lc[j][k], Lc[j][k], d);
+        const float inv = rsqrtf(d);
+        Linv[j] = inv;
 #pragma unroll
         for (int i = j + 1; i < 6; i++) {
-            float sum = Mt[j][i];  // symmetric: (i, j) = (j, i), upper storage
+            float sum = Mt[j][i];
 #pragma unroll
-            for (int k = 0; k < j; k++) sum -= Lc[i][k] * Lc[j][k];
+            for (int k = 0; k < j; k++) sum = fmaf(-Lc[i][k], Lc[j][k], sum);
             Lc[i][j] = sum * inv;
         }
     }
@@ -316,49 +378,66 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
     for (int i = 0; i < 6; i++) {
         float sum = -bt[i];
 #pragma unroll
-        for (int k = 0; k < i; k++) sum -= Lc[i][k] * y[k];
-        y[i] = sum / Lc[i][i];
+        for (int k = 0; k < i; k++) sum = fmaf(-Lc[i][k], y[k], sum);
+        y[i] = sum * Linv[i];
     }
 #pragma unroll
     for (int i = 5; i >= 0; i--) {
         float sum = y[i];
 #pragma unroll
-        for (int k = i + 1; k < 6; k++) sum -= Lc[k][i] * a0[k];
-        a0[i] = sum / Lc[i][i];
+        for (int k = i + 1; k < 6; k++) sum = fmaf(-Lc[k][i], a0[k], sum);
+        a0[i] = sum * Linv[i];
     }
 
     // ---- pass 3 (root to tip): a' = X a'_parent + c ; qdd = (u - U . a') / D
     float qdd[3];
-    float3 aw = f3(a0[0], a0[1], a0[2]), av = f3(a0[3], a0[4], a0[5]);
+    const float3 aw = f3(a0[0], a0[1], a0[2]), av = f3(a0[3], a0[4], a0[5]);
     {
-        float3 nw = Ex(c0, s0, aw), nv = Ex(c0, s0, av + cross3(aw, rh));
-        nw = nw + ch_w; nv = nv + ch_v;
-        qdd[0] = (u0 - (U0[0] * nw.x + U0[1] * nw.y + U0[2] * nw.z + U0[3] * nv.x + U0[4] * nv.y + U0[5] * nv.z)) * D0inv;
+        float3 nw = Ex(c0, s0, aw) + ch_w, nv = Ex(c0, s0, av + cross3(aw, rh)) + ch_v;
+        qdd[0] = (u0 - (U0a[0] * nw.x + U0a[1] * nw.y + U0a[2] * nw.z + U0l[0] * nv.x + U0l[1] * nv.y + U0l[2] * nv.z)) * D0inv;
         nw.x += qdd[0];
-        float3 tw = Ey(c1, s1, nw), tv = Ey(c1, s1, nv + cross3(nw, rt));
-        tw = tw + ct_w; tv = tv + ct_v;
-        qdd[1] = (u1 - (U1[0] * tw.x + U1[1] * tw.y + U1[2] * tw.z + U1[3] * tv.x + U1[4] * tv.y + U1[5] * tv.z)) * D1inv;
+        float3 tw = Ey(c1, s1, nw) + ct_w, tv = Ey(c1, s1, nv + cross3(nw, rt)) + ct_v;
+        qdd[1] = (u1 - (U1a[0] * tw.x + U1a[1] * tw.y + U1a[2] * tw.z + U1l[0] * tv.x + U1l[1] * tv.y + U1l[2] * tv.z)) * D1inv;
         tw.y += qdd[1];
-        float3 kw = Ey(c2, s2, tw), kv = Ey(c2, s2, tv + cross3(tw, rk));
-        kw = kw + cc_w; kv = kv + cc_v;
-        qdd[2] = (u2 - (U2[0] * kw.x + U2[1] * kw.y + U2[2] * kw.z + U2[3] * kv.x + U2[4] * kv.y + U2[5] * kv.z)) * D2inv;
+        float3 kw = Ey(c2, s2, tw) + cc_w, kv = Ey(c2, s2, tv + cross3(tw, rk)) + cc_v;
+        qdd[2] = (u2 - (U2a * kw.y + U2l * kv.x)) * D2inv;
     }
 
     // ---- semi-implicit Euler
 #pragma unroll
     for (int i = 0; i < 3; i++) {
-        S.qd[i] += h * qdd[i];
-        S.q[i] += h * S.qd[i];
+        S.qd[i] = fmaf(h, qdd[i], S.qd[i]);
+        S.q[i] = fmaf(h, S.qd[i], S.q[i]);
     }
-    float3 gb = f3(R0[2][0] * g, R0[2][1] * g, R0[2][2] * g);  // R0^T (0, 0, g)
+    const float3 gb = f3(R0[2][0] * g, R0[2][1] * g, R0[2][2] * g);  // R0^T (0, 0, g)
     T.w = T.w + h * aw;
     T.v = T.v + h * (av + gb);
-    float3 dp = mulR(R0, T.v);
-    T.p[0] += h * dp.x; T.p[1] += h * dp.y; T.p[2] += h * dp.z;
+    const float3 dp = mulR(R0, T.v);
+    T.p[0] = fmaf(h, dp.x, T.p[0]);
+    T.p[1] = fmaf(h, dp.y, T.p[1]);
+    T.p[2] = fmaf(h, dp.z, T.p[2]);
     quat_integrate(T.quat, T.w, h);
 }
 
 // ---------------------------------------------------------------- kernel
+
+// x_t of rollout k: lane 0 writes the trunk, every lane its leg's joints
+__device__ __forceinline__ void store_state(const RolloutArgs& a, int k, int t, int leg, bool valid, const Trunk& T,
+                                            const LegState& S) {
+    if (!valid) return;
+    float* o = a.traj + ((size_t)k * (a.H + 1) + t) * a.model.nx;
+    if (leg == 0) {
+        o[0] = T.p[0]; o[1] = T.p[1]; o[2] = T.p[2];
+        o[3] = T.quat[0]; o[4] = T.quat[1]; o[5] = T.quat[2]; o[6] = T.quat[3];
+        o[19] = T.w.x; o[20] = T.w.y; o[21] = T.w.z;
+        o[22] = T.v.x; o[23] = T.v.y; o[24] = T.v.z;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        o[7 + 3 * leg + i] = S.q[i];
+        o[25 + 3 * leg + i] = S.qd[i];
+    }
+}
 
 template <int TERR, bool TRAJ>
 __global__ void __launch_bounds__(256) k_rollout(RolloutArgs a) {
@@ -392,22 +471,7 @@ __global__ void __launch_bounds__(256) k_rollout(RolloutArgs a) {
     const float h = a.h;
     const float ph0 = (leg == 1 || leg == 2) ? 3.14159265358979f : 0.f;
     float L = 0.f;
-    auto store = [&](int t) {
-        if (!TRAJ || !valid) return;
-        float* o = a.traj + ((size_t)k * (a.H + 1) + t) * nx;
-        if (leg == 0) {
-            o[0] = T.p[0]; o[1] = T.p[1]; o[2] = T.p[2];
-            o[3] = T.quat[0]; o[4] = T.quat[1]; o[5] = T.quat[2]; o[6] = T.quat[3];
-            o[19] = T.w.x; o[20] = T.w.y; o[21] = T.w.z;
-            o[22] = T.v.x; o[23] = T.v.y; o[24] = T.v.z;
-        }
-#pragma unroll
-        for (int i = 0; i < 3; i++) {
-            o[7 + 3 * leg + i] = S.q[i];
-            o[25 + 3 * leg + i] = S.qd[i];
-        }
-    };
-    store(0);
+    if (TRAJ) store_state(a, k, 0, leg, valid, T, S);
     for (int t = 0; t < a.H; t++) {
         // cubic through 4 knots at tau_j = j / 3 (Lagrange basis)
         const float tau = (float)t * a.inv_Hm1;
@@ -421,7 +485,8 @@ __global__ void __launch_bounds__(256) k_rollout(RolloutArgs a) {
         {
             float ds = 0.f, dk = 0.f;
             if (c.gait == 1) {
-                float s = sinf(c.two_pi_over_period * (a.t0 + (float)t * a.dt) + ph0);
+                float s, cq;
+                sincos_r(c.two_pi_over_period * (a.t0 + (float)t * a.dt) + ph0, s, cq);
                 ds = c.hip_amp * s;
                 dk = -c.knee_amp * fmaxf(s, 0.f);
             }
@@ -429,8 +494,8 @@ __global__ void __launch_bounds__(256) k_rollout(RolloutArgs a) {
             L += c.w_u * (e0 * e0 + e1 * e1 + e2 * e2);
             if (leg == 0) L += trunk_state_cost(c, T);
         }
-        for (int sidx = 0; sidx < a.n_sub; sidx++) substep<TERR>(m, leg, T, S, u, h);
-        store(t + 1);
+        for (int sb = 0; sb < a.n_sub; sb++) substep<TERR>(m, leg, T, S, u, h, a.arm);
+        if (TRAJ) store_state(a, k, t + 1, leg, valid, T, S);
     }
     if (leg == 0) L += c.w_term * trunk_state_cost(c, T);
     L = xsum4(L);

