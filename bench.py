@@ -152,7 +152,7 @@ def run_reference(args):
             "n_gpus": world_size, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "trot flat plane K=4096 H=100 dt=0.005 n_sub=4",
+            "config": {"workload": "trot flat plane K=4096 H=100 dt=0.005 n_sub=8",
                        "K": K_BENCH, "H": H_BENCH, "l2": "n/a (host)"},
             "cpu_baseline": {"value": value, "unit": "rollout-steps/s", "cores": cores,
                              "kind": "oracle",
@@ -260,7 +260,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "trot flat plane K=4096 H=100 dt=0.005 n_sub=4 (fp32, FP64 normaliser)",
+        "config": {"workload": "trot flat plane K=4096 H=100 dt=0.005 n_sub=8 (fp32, FP64 normaliser)",
                    "K": K_BENCH, "H": H_BENCH, "n_sub": m["n_sub"], "l2": "flushed between steps",
                    "parallelism": "independent instance per GPU"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),

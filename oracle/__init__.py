@@ -457,3 +457,21 @@ def world_tree(world: World) -> Tree:
     t = Tree.__new__(Tree)
     t.buf = world.buf
     return t
+
+
+class use_float:
+    """Context: the same oracle source compiled with `real` = float, as the
+    reference for what plain FP32 arithmetic achieves on the same inputs (the
+    "FP32 floor").  Worlds must be created inside the context."""
+
+    def __enter__(self):
+        global _lib
+        self._saved = (_lib, _build.build)
+        path = _build.build_variant("float")
+        _lib = None
+        _build.build = lambda force=False: path
+        return self
+
+    def __exit__(self, *a):
+        global _lib
+        _lib, _build.build = self._saved

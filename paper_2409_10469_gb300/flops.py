@@ -1,47 +1,49 @@
 """Algorithmic work of the MPPI hot path, for the roofline.
 
-FLOPs are counted per structured operation of the algorithm as formulated in
-the kernels (FMA = 2, add/sub/mul = 1, divide/sqrt = 1; sin/cos are listed
-separately and not counted), once per rollout: work a kernel replicates across
-lanes (the trunk solve runs on all 4 lanes of a rollout) counts once, and
-symmetric 3x3 blocks count their 6 unique entries.  Bytes are the unique
+FLOPs are counted per operation of the algorithm as formulated in the rollout
+kernel (FMA = 2, add / sub / mul = 1, divide / sqrt / rsqrt = 1), once per
+rollout: work a kernel replicates across the 4 lanes of a rollout (the trunk
+solve) counts once, symmetric 3x3 blocks count their 6 unique entries, and
+structurally-zero operands (joint offsets along one axis, centres of mass on
+the joint axis, the plane's normal) count nothing.  Bytes are the unique
 global-memory bytes an ideal kernel moves.
 """
 
-# ---- per structured op
-ROT3_VEC = 6          # coordinate rotation of a 3-vector about x or y
-CROSS = 9
-ADD3 = 3
-SYM6_MV = 72          # dense 6x6 times 6-vector
-BIAS = SYM6_MV + 3 * CROSS + 2 * ADD3 + 6          # v x* I v - f_ext
-PROJECT = (6 + 21 * 2) + (SYM6_MV + 1 + 12 + 6)     # Ia = IA - U U^T/D ; pa = pA + Ia c + U u/D
-UDU = 3                                            # D = U_k + a, 1/D, u = tau - pA_k
-FORCE_XFORM = 2 * ROT3_VEC + CROSS + ADD3          # X^T f
-CONGRUENCE = (30 + 36 + 30) + (27 + 27 + 18 + 18 + 9)   # rotate blocks; translate (P, T, Q, A'', B'')
-ADD_I = 21
-KIN_BODY = ROT3_VEC + (CROSS + ADD3) + ROT3_VEC + 1 + 4   # v = X v_p + S qd ; c = v x S qd
-PASS3_BODY = 24 + 6 + 11 + 2 + 1
-PD_JOINT = 6
-INT_JOINT = 4
-FOOT_FK = 3 * (ROT3_VEC + ADD3) + 15 + 3
-NORMAL_TO_BODY = 15 + 3 * ROT3_VEC
-GROUND_PLANE = 7
-CONTACT = 65
+# ---------------------------------------------------------------- one leg
+SINCOS = 25                       # bounded sin/cos pair (reduction + 2 polynomials)
+JOINT_SINCOS = 3 * SINCOS
+KIN = 25 + 21 + 21                # body velocities + velocity products, hip/thigh/calf
+FOOT_POS = 19 + 18                # foot in the trunk frame, then world
+NORMAL_TO_CALF = 18               # plane normal into calf coordinates
+GROUND_PLANE = 1
+CONTACT = 64                      # spring-damper + regularised Coulomb + wrench
+FOOT = FOOT_POS + NORMAL_TO_CALF + GROUND_PLANE + CONTACT
+PD = 3 * 6
+BIAS = 50                         # v x* I v - f_ext, structured body inertia
+ROTATE_SYM6 = 20 + 36 + 20        # A, B, C blocks turned about one axis
+CONG_KNEE = ROTATE_SYM6 + 33      # translation along z only
+CONG_THIGH = ROTATE_SYM6 + 33     # translation along y only
+CONG_HIP = ROTATE_SYM6 + 72       # translation in x and y
+PROJECT = 6 + 24 + 18 + 48 + 1 + 12   # Ia = IA - U U^T / D ; pa = pA + Ia c + U u / D
+FXFORM_1AX = 16                   # X^T f with a one-axis joint offset
+FXFORM_HIP = 20
+PASS2 = ((BIAS + 1 + 24 + FXFORM_1AX + CONG_KNEE)                       # calf (constant Ia)
+         + (8 + BIAS + 6 + 3 + PROJECT + FXFORM_1AX + CONG_THIGH)        # thigh
+         + (6 + 36 + 3 + PROJECT + FXFORM_HIP + CONG_HIP))               # hip
+PASS3 = 40 + 34 + 25
+INTEGRATE_LEG = 12
+LEG = JOINT_SINCOS + KIN + FOOT + PD + PASS2 + PASS3 + INTEGRATE_LEG
 
-LEG = (3 * KIN_BODY + 3 * PD_JOINT
-       + (BIAS + UDU + PROJECT + FORCE_XFORM + CONGRUENCE)            # calf
-       + 2 * (ADD_I + BIAS + UDU + PROJECT + FORCE_XFORM + CONGRUENCE)  # thigh, hip
-       + 3 * PASS3_BODY + 3 * INT_JOINT
-       + FOOT_FK + NORMAL_TO_BODY + GROUND_PLANE + CONTACT)
-TRUNK_SPHERE = 15 + 3 + 15 + GROUND_PLANE + 10     # typical: out of contact
-TRUNK = (24                    # R from the quaternion
-         + 27 * 3 + 6 * 3 + 6  # sum of the 4 legs' (IA, pA) and sphere wrenches
-         + 30                  # the trunk's own bias and inertia
-         + 82 + 72             # 6x6 Cholesky and two triangular solves
-         + 90                  # semi-implicit Euler of the free base incl. quaternion
-         + 3 * TRUNK_SPHERE)
-SUBSTEP = 4 * LEG + TRUNK      # one rollout advanced by one sub-step
-PER_DT_STEP = 4 * 22 + 12 * 3 * 2 + 60   # spline basis + targets + stage cost
+# ---------------------------------------------------------------- trunk
+TRUNK = (30          # rotation matrix of the quaternion
+         + 99        # sums of the 4 legs' articulated inertias (21) and bias forces (6)
+         + 30        # the trunk's own inertia and bias
+         + 91 + 72   # 6x6 Cholesky and two triangular solves
+         + 120       # semi-implicit Euler of the free base incl. quaternion
+         + 3 * 7)    # trunk spheres against the plane (out of contact)
+
+SUBSTEP = 4 * LEG + TRUNK          # one rollout advanced by one sub-step
+PER_DT_STEP = 112 + 180 + 25       # spline targets, per-leg control cost, trunk state cost
 
 
 def rollout_flops(K: int, H: int, n_sub: int) -> float:
