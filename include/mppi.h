@@ -160,6 +160,35 @@ mppi_status mppi_launch_count(mppi_handle h, uint64_t* count);
 /* State size of the handle's model: 37, or 50 with the free box. */
 int mppi_state_size(mppi_handle h);
 
+/* The update of mppi_update (Eq. 1 + Eq. 2 + apply + shift) without a handle and
+ * without allocating anything.  The paper has no counterpart: this is for
+ * callers that must not allocate device memory when they run -- a hard
+ * real-time control loop that may not block in the driver's allocator, code
+ * running inside another framework's memory pool, or a runtime that forbids
+ * cudaMalloc after start-up.  They pass every buffer; the call's scratch (the
+ * per-CTA partial sums and a completion counter) is a fixed 50,432-byte device
+ * array compiled into the library, which every GPU that loads the library
+ * keeps until the process exits.
+ *   L (float[n]), U (float[n][48], 16-byte aligned): costs and knots, device.
+ *   mu_in (float[48]): the current nominal (kept if every cost is non-finite).
+ *   mu_out (float[48]): the shifted nominal; may equal mu_in.
+ *   mu_upd_out (float[48], optional): the updated mean before the shift.
+ *   u0_out (float[12]): the control to apply; status_out (int, optional): 0, or
+ *   4 when every cost is non-finite.  All pointers are device memory.
+ *   stream: a cudaStream_t or NULL; the call only enqueues work.
+ * The first call on a device looks up the array's device address with that
+ * device current, so make it before any stream capture.  Calls share the one
+ * array: calls that overlap on the GPU (different streams, or threads without
+ * ordering) race and corrupt each other's results.
+ * Errors: MPPI_ERR_ARG when n < 1 or n > MPPI_NOALLOC_MAX_N, H < 2,
+ * ctrl_steps < 1, lambda <= 0, a buffer is not device memory or U is
+ * misaligned; MPPI_ERR_CUDA when a CUDA call fails.  No cudaMalloc, cudaFree or
+ * other allocating call is made. */
+#define MPPI_NOALLOC_MAX_N (1 << 20)
+mppi_status mppi_update_noalloc(const float* L, const float* U, int n, int H, int ctrl_steps,
+                                double lambda, const float* mu_in, float* mu_out,
+                                float* mu_upd_out, float* u0_out, int* status_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

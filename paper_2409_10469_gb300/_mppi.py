@@ -24,7 +24,8 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NONF
 # every entry point declared in include/mppi.h
 EXPORTS = ("mppi_create", "mppi_destroy", "mppi_last_error", "mppi_set_nominal",
            "mppi_get_nominal", "mppi_sample", "mppi_rollouts", "mppi_update", "mppi_step",
-           "mppi_set_timing", "mppi_get_timings", "mppi_launch_count", "mppi_state_size")
+           "mppi_set_timing", "mppi_get_timings", "mppi_launch_count", "mppi_state_size",
+           "mppi_update_noalloc")
 
 
 class MppiError(RuntimeError):
@@ -103,6 +104,8 @@ def lib():
         L.mppi_set_timing.argtypes = [vp, C.c_int]
         L.mppi_get_timings.argtypes = [vp, C.POINTER(C.c_float)]
         L.mppi_launch_count.argtypes = [vp, C.POINTER(C.c_uint64)]
+        L.mppi_update_noalloc.argtypes = [fp, fp, C.c_int, C.c_int, C.c_int, C.c_double, fp, fp,
+                                           fp, fp, fp, vp]
         L.mppi_state_size.argtypes = [vp]
         L.mppi_state_size.restype = C.c_int
         for name in EXPORTS:
@@ -170,6 +173,15 @@ def config_struct(mp: dict, block: int = 0):
     c.seed, c.inst, c.n_prop = int(mp["seed"]), int(mp["inst"]), int(mp.get("n_prop", 0))
     c.block = int(block or mp.get("block", 0))
     return c
+
+
+def update_noalloc(L, U, n, H, ctrl_steps, lam, mu_in, mu_out, u0_out, mu_upd_out=None,
+                   status_out=None, stream=None):
+    """mppi_update_noalloc: the update without a handle or any allocation (for
+    callers that cannot allocate device memory); all buffers are device memory."""
+    return lib().mppi_update_noalloc(_ptr(L), _ptr(U), n, H, ctrl_steps, lam, _ptr(mu_in),
+                                     _ptr(mu_out), _ptr(mu_upd_out), _ptr(u0_out),
+                                     _ptr(status_out), stream)
 
 
 class Controller:

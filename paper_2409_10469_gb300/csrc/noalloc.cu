@@ -1,0 +1,100 @@
+// noalloc.cu -- mppi_update_noalloc: the Eq. 1 / Eq. 2 update with its scratch
+// memory in a fixed device array instead of a handle's allocations.
+//
+// Who needs this: code that runs where allocating device memory is not an
+// option -- a real-time control thread that must never block in the driver's
+// allocator, a process whose memory pool is owned by another framework, an
+// embedded runtime that forbids cudaMalloc after start-up, or a library call
+// made while another component holds the allocator.  Such a caller still owns
+// and passes every input and output buffer; the only memory this call adds is
+// the file-scope array below, which every GPU that loads the library keeps for
+// the life of the process.
+//
+// The update kernel needs per-CTA partial sums and a finished-CTA counter.  Here
+// they live in `g_update_scratch` (MPPI_NOALLOC_SCRATCH_BYTES = 50,432 bytes:
+// 128 CTAs x 49 doubles + the counter).  Host code cannot use the symbol itself
+// as a device address: on each device the first call asks the runtime for the
+// array's address (cudaGetSymbolAddress, with that device current) and caches
+// it.  That first call should therefore happen before any stream capture.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "../../include/mppi.h"
+#include "kernels.h"
+
+using namespace mppi;
+
+namespace {
+
+constexpr size_t PART_DOUBLES = (size_t)UPDATE_MAX_CTAS * (D + 1);
+constexpr size_t SCRATCH_BYTES = PART_DOUBLES * sizeof(double) + 256;  // partials + counter slot
+
+static __device__ __align__(256) unsigned char g_update_scratch[SCRATCH_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_mu;
+void* g_addr[MAX_DEVICES] = {nullptr};
+
+bool on_device(const void* p) {
+    cudaPointerAttributes at;
+    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" mppi_status mppi_update_noalloc(const float* L, const float* U, int n, int H, int ctrl_steps,
+                                           double lambda, const float* mu_in, float* mu_out, float* mu_upd_out,
+                                           float* u0_out, int* status_out, void* stream) {
+    if (n < 1 || n > MPPI_NOALLOC_MAX_N || H < 2 || ctrl_steps < 1 || !(lambda > 0)) return MPPI_ERR_ARG;
+    if (update_grid(n) > UPDATE_MAX_CTAS) return MPPI_ERR_ARG;  // scratch holds UPDATE_MAX_CTAS partials
+    if (!on_device(L) || !on_device(U) || !on_device(mu_in) || !on_device(mu_out) || !on_device(u0_out))
+        return MPPI_ERR_ARG;
+    if ((mu_upd_out && !on_device(mu_upd_out)) || (status_out && !on_device(status_out))) return MPPI_ERR_ARG;
+    if (((uintptr_t)U & 15u) != 0) return MPPI_ERR_ARG;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return MPPI_ERR_CUDA;
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_addr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_update_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return MPPI_ERR_CUDA;
+            }
+            g_addr[dev] = p;
+        }
+        base = g_addr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    double* part = (double*)base;
+    unsigned* counter = (unsigned*)((unsigned char*)base + PART_DOUBLES * sizeof(double));
+    // the counter must read zero when the kernel starts; the partials need no clearing
+    if (cudaMemsetAsync(counter, 0, sizeof(unsigned), st) != cudaSuccess) return MPPI_ERR_CUDA;
+    if (mu_out != mu_in &&
+        cudaMemcpyAsync(mu_out, mu_in, D * sizeof(float), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return MPPI_ERR_CUDA;
+
+    UpdateArgs a;
+    a.L = L;
+    a.U = U;
+    a.mu = mu_out;
+    a.mu_upd = mu_upd_out;
+    a.u0 = u0_out;
+    a.status = status_out;
+    a.wsum = nullptr;
+    a.part = part;
+    a.counter = counter;
+    a.n = n;
+    a.H = H;
+    a.ctrl_steps = ctrl_steps;
+    a.inv_lambda = (float)(1.0 / lambda);
+    return launch_update(a, st) == cudaSuccess ? MPPI_OK : MPPI_ERR_CUDA;
+}
