@@ -160,6 +160,45 @@ mppi_status mppi_launch_count(mppi_handle h, uint64_t* count);
 /* State size of the handle's model: 37, or 50 with the free box. */
 int mppi_state_size(mppi_handle h);
 
+/* ------------------------------------------------------------------ batches
+ * Many controllers (handles of any K, H, terrain, task) stepped together: one
+ * persistent kernel per control step runs Alg. 1 for every active instance
+ * (sampling in-kernel with the same bit-exact noise, the same rollout
+ * arithmetic as mppi_rollouts, and each instance's Eq. 1/Eq. 2 update + shift
+ * in a fixed order by the block that finishes its last rollouts), captured in a
+ * CUDA graph.  An instance's result does not depend on the other instances in
+ * the batch.  The handles must outlive the batch; their nominals are updated in
+ * place exactly as mppi_step would. */
+typedef struct mppi_batch_s* mppi_batch;
+
+/* Batch of n handles (all on the current device).  stream: cudaStream_t or NULL. */
+mppi_status mppi_batch_create(const mppi_handle* hs, int n, void* stream, mppi_batch* out);
+mppi_status mppi_batch_destroy(mppi_batch b);
+const char* mppi_batch_last_error(mppi_batch b);
+
+/* One control step of every active instance.  active: host int[n] (non-zero =
+ * step this instance; NULL = all); x0s: float[n][50] host or device (row i uses
+ * its first nx_i entries); steps: host uint32[n] control-step index of each
+ * instance (its Philox counter word 2 and gait time), NULL = unchanged;
+ * u0s: optional float[n][12] host or device (rows of inactive instances keep
+ * their last value).  Host outputs are complete on return. */
+mppi_status mppi_batch_step(mppi_batch b, const int* active, const float* x0s, const uint32_t* steps,
+                            float* u0s);
+
+/* Block shape of the persistent kernel: block in {64, 128, 256} threads (block/4
+ * rollouts per work item), blocks_per_sm up to the occupancy limit. */
+mppi_status mppi_batch_set_shape(mppi_batch b, int block, int blocks_per_sm);
+mppi_status mppi_batch_get_shape(mppi_batch b, int* block, int* blocks_per_sm);
+
+/* Autotuner: times every candidate shape (trials steps each, CUDA events, from
+ * the same nominals, which are restored afterwards) on this batch from x0s and
+ * keeps the fastest.  Outputs (optional): the chosen shape and its step time. */
+mppi_status mppi_batch_autotune(mppi_batch b, const float* x0s, int trials, int* block_out,
+                                int* bpsm_out, float* best_ms_out);
+
+/* Number of graph launches (one per mppi_batch_step). */
+mppi_status mppi_batch_launch_count(mppi_batch b, uint64_t* count);
+
 /* The update of mppi_update (Eq. 1 + Eq. 2 + apply + shift) without a handle and
  * without allocating anything.  The paper has no counterpart: this is for
  * callers that must not allocate device memory when they run -- a hard

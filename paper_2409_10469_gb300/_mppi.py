@@ -25,7 +25,9 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NONF
 EXPORTS = ("mppi_create", "mppi_destroy", "mppi_last_error", "mppi_set_nominal",
            "mppi_get_nominal", "mppi_sample", "mppi_rollouts", "mppi_update", "mppi_step",
            "mppi_set_timing", "mppi_get_timings", "mppi_launch_count", "mppi_state_size",
-           "mppi_update_noalloc")
+           "mppi_update_noalloc", "mppi_batch_create", "mppi_batch_destroy",
+           "mppi_batch_last_error", "mppi_batch_step", "mppi_batch_set_shape", "mppi_batch_get_shape",
+           "mppi_batch_autotune", "mppi_batch_launch_count")
 
 
 class MppiError(RuntimeError):
@@ -106,10 +108,20 @@ def lib():
         L.mppi_launch_count.argtypes = [vp, C.POINTER(C.c_uint64)]
         L.mppi_update_noalloc.argtypes = [fp, fp, C.c_int, C.c_int, C.c_int, C.c_double, fp, fp,
                                            fp, fp, fp, vp]
+        L.mppi_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, vp, C.POINTER(C.c_void_p)]
+        L.mppi_batch_destroy.argtypes = [vp]
+        L.mppi_batch_last_error.argtypes = [vp]
+        L.mppi_batch_last_error.restype = C.c_char_p
+        L.mppi_batch_step.argtypes = [vp, vp, vp, vp, vp]
+        L.mppi_batch_set_shape.argtypes = [vp, C.c_int, C.c_int]
+        L.mppi_batch_get_shape.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.mppi_batch_autotune.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                          C.POINTER(C.c_float)]
+        L.mppi_batch_launch_count.argtypes = [vp, C.POINTER(C.c_uint64)]
         L.mppi_state_size.argtypes = [vp]
         L.mppi_state_size.restype = C.c_int
         for name in EXPORTS:
-            if name not in ("mppi_last_error", "mppi_state_size"):
+            if name not in ("mppi_last_error", "mppi_state_size", "mppi_batch_last_error"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -262,4 +274,59 @@ class Controller:
     def launch_count(self):
         c = C.c_uint64()
         self._check(lib().mppi_launch_count(self.h, C.byref(c)))
+        return c.value
+
+
+class Batch:
+    """Many controllers stepped by one persistent launch per control step."""
+
+    def __init__(self, controllers, stream=None):
+        L = lib()
+        self.ctls = list(controllers)
+        arr = (C.c_void_p * len(self.ctls))(*[c.h.value for c in self.ctls])
+        b = C.c_void_p()
+        st = C.c_void_p(stream) if isinstance(stream, int) else stream
+        rc = L.mppi_batch_create(arr, len(self.ctls), st, C.byref(b))
+        if rc != MPPI_OK:
+            raise MppiError(rc, "mppi_batch_create failed")
+        self.b = b
+        self.n = len(self.ctls)
+
+    def _check(self, rc):
+        if rc != MPPI_OK:
+            raise MppiError(rc, lib().mppi_batch_last_error(self.b).decode())
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().mppi_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, x0s, steps, u0s=None, active=None):
+        st = np.ascontiguousarray(steps, dtype=np.uint32)
+        act = None if active is None else np.ascontiguousarray(active, dtype=np.int32)
+        self._check(lib().mppi_batch_step(self.b, _ptr(act), _ptr(x0s), _ptr(st), _ptr(u0s)))
+        return u0s
+
+    def set_shape(self, block, blocks_per_sm):
+        self._check(lib().mppi_batch_set_shape(self.b, block, blocks_per_sm))
+
+    def shape(self):
+        b, p = C.c_int(), C.c_int()
+        self._check(lib().mppi_batch_get_shape(self.b, C.byref(b), C.byref(p)))
+        return b.value, p.value
+
+    def autotune(self, x0s, trials=3):
+        b, p, ms = C.c_int(), C.c_int(), C.c_float()
+        self._check(lib().mppi_batch_autotune(self.b, _ptr(x0s), trials, C.byref(b), C.byref(p), C.byref(ms)))
+        return b.value, p.value, ms.value
+
+    def launch_count(self):
+        c = C.c_uint64()
+        self._check(lib().mppi_batch_launch_count(self.b, C.byref(c)))
         return c.value

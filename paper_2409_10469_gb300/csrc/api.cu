@@ -12,32 +12,9 @@
 #include <string>
 #include <vector>
 
-#include "../../include/mppi.h"
-#include "kernels.h"
+#include "handle.h"
 
 using namespace mppi;
-
-struct mppi_handle_s {
-    mppi_model_t model_in;
-    mppi_cost_t cost_in;
-    mppi_config_t cfg;
-    DevModel dm;
-    DevCost dc;
-    cudaStream_t stream = nullptr;
-    int device = 0;
-    int nx = NX_ROBOT;
-    float *d_mu = nullptr, *d_mu_prop = nullptr, *d_mu_upd = nullptr, *d_U = nullptr, *d_L = nullptr;
-    float *d_x0 = nullptr, *d_u0 = nullptr, *d_hf = nullptr, *d_sbox = nullptr;
-    int* d_status = nullptr;
-    double* d_wsum = nullptr;
-    double* d_part = nullptr;      // update scratch: per-CTA partial sums
-    unsigned* d_counter = nullptr;  // update scratch: finished-CTA counter
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    int timing = 0;
-    int timed_valid = 0;
-    uint64_t launches = 0;
-    std::string err;
-};
 
 // ------------------------------------------------------------------ helpers
 
@@ -83,7 +60,8 @@ static BodyI body_inertia(double m, double cz, const double Icd[3]) {
 }
 
 // implicit-PD armature of one sub-step: h (kd + h kp) + a0
-static double armature(const mppi_model_t& p, double h) { return h * (p.kd + h * p.kp) + p.armature; }
+double mppi_armature(const mppi_model_t& p, double h) { return h * (p.kd + h * p.kp) + p.armature; }
+static double armature(const mppi_model_t& p, double h) { return mppi_armature(p, h); }
 
 static void derive_model(const mppi_model_t& p, double h, DevModel& d) {
     memset(&d, 0, sizeof(d));
@@ -179,7 +157,7 @@ static void derive_cost(const mppi_cost_t& c, DevCost& d) {
 
 // gait time of step 0 of a horizon starting at absolute time t0, reduced
 // modulo the gait period so that FP32 keeps its resolution over long runs
-static float reduce_t0(const mppi_handle h, double t0) {
+float mppi_reduce_t0(const mppi_handle h, double t0) {
     const double P = h->cost_in.gait_period;
     if (h->cost_in.gait == 1 && P > 0) return (float)fmod(t0, P);
     return (float)t0;
@@ -217,7 +195,6 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
     if (model->terrain != 0 && model->terrain != 1) return MPPI_ERR_ARG;
     if (model->n_static_boxes < 0 || model->n_static_boxes > MAX_SBOX) return MPPI_ERR_ARG;
     if (model->n_trunk_spheres < 0 || model->n_trunk_spheres > 4) return MPPI_ERR_ARG;
-    if (model->has_box) return MPPI_ERR_NOTSUP;
 
     mppi_handle h = new mppi_handle_s();
     h->model_in = *model;
@@ -372,7 +349,7 @@ static RolloutArgs rollout_args(mppi_handle h, const float* x0, int per, const f
     a.dt = (float)h->cfg.dt;
     a.h = (float)(h->cfg.dt / h->cfg.n_sub);
     a.inv_Hm1 = (float)(1.0 / (h->cfg.H - 1));
-    a.t0 = reduce_t0(h, t0);
+    a.t0 = mppi_reduce_t0(h, t0);
     a.arm = (float)armature(h->model_in, h->cfg.dt / h->cfg.n_sub);
     return a;
 }

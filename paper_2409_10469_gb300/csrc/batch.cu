@@ -1,0 +1,600 @@
+// batch.cu -- many MPPI instances in one persistent launch per control step.
+//
+// Each instance is a controller handle (its own model, cost, K, H, nominal and
+// buffers).  One control step of a batch runs Alg. 1 of arXiv 2409.10469
+// (sample, roll out, weight by Eq. 1, update by Eq. 2, apply, shift) for every
+// active instance in a single persistent kernel:
+//   - the work is a list of items (instance, first sample, count), one item per
+//     chunk of blockDim/4 rollouts, longest horizons first (so that the uneven
+//     H of the instances does not leave a long tail);
+//   - blocks (a grid of blocks_per_sm x SMs) take items from an atomic counter
+//     until the list is exhausted -- no block ever waits on another;
+//   - an item samples its knots in-kernel (the same Philox/Box-Muller code and
+//     clamp as the sampling kernel, so the knots are bit-identical), rolls them
+//     out with the same per-lane simulator as the single-instance kernel, and
+//     writes U and L;
+//   - the block that completes an instance's last chunk (an atomic count of
+//     finished samples per instance reaches K) runs that instance's update in
+//     one block, in a fixed order, so an instance's result does not depend on
+//     which other instances share the launch.
+// The host side captures [work-list copy, step indices, counter resets, kernel]
+// in a CUDA graph once per block shape; the autotuner times the candidate block
+// shapes on the batch itself and keeps the fastest.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "handle.h"
+#include "noise.cuh"
+#include "rollout.cuh"
+
+using namespace mppi;
+
+namespace mppi {
+
+struct InstDesc {
+    DevModel model;
+    DevCost cost;
+    float* mu;            // nominal knots, updated in place (shifted)
+    float* mu_upd;        // updated mean before the shift
+    float* u0;            // applied control
+    float* U;             // [K][48] sampled knots
+    float* L;             // [K] costs
+    int* status;          // 0 ok, 4 all costs non-finite
+    const float* mu_prop; // proposal mean or null
+    int K, H, n_sub, n_prop, ctrl_steps, nx, gait;
+    float h, dt, inv_Hm1, arm, inv_lambda;
+    double dt_d, period_d;
+    float sigma[D], q_lo[3], q_hi[3];
+    uint32_t key0, key1, inst_id;
+};
+
+struct WorkItem {
+    int inst, k0, n;
+};
+
+struct BatchArgs {
+    const InstDesc* desc;
+    const WorkItem* items;
+    const int* n_items;
+    int* next;
+    unsigned* done;
+    const float* x0s;       // [n_inst][NX_BOX]
+    const uint32_t* steps;  // [n_inst] control-step index of each instance
+    float* u0s;             // [n_inst][12]
+};
+
+// this lane's 12 knots of sample k (the leg's 3 joints at the 4 knots), and
+// write them to U[k]; the same formula as k_sample, element by element
+__device__ __forceinline__ void sample_lane(const InstDesc& d, int k, int leg, uint32_t step, bool write,
+                                            float (&Uk)[NKNOT][3]) {
+    const int kp0 = d.K - (d.mu_prop ? d.n_prop : 0);
+    const bool prop = d.mu_prop && k >= kp0;
+    const float* ctr = prop ? d.mu_prop : d.mu;
+    const bool nominal = (k == 0) || (prop && k == kp0);
+#pragma unroll
+    for (int j = 0; j < NKNOT; j++)
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            const int dd = j * NJ + 3 * leg + i;
+            const float eps = nominal ? 0.f : normal_at(d.key0, d.key1, step, d.inst_id, (uint32_t)k, dd);
+            float v = __fmaf_rn(d.sigma[dd], eps, __ldcg(ctr + dd));
+            v = fminf(fmaxf(v, d.q_lo[i]), d.q_hi[i]);
+            Uk[j][i] = v;
+            if (write) d.U[(size_t)k * D + dd] = v;
+        }
+}
+
+__device__ __forceinline__ bool finite_f(float x) { return fabsf(x) <= 3.402823466e38f; }
+
+// Eq. 1, Eq. 2, apply, shift for one instance in one block.  The sums run over
+// 8 fixed groups of samples (k = g mod 8, each in increasing k) whatever the
+// block size, and are combined in group order: the result does not depend on
+// the block shape or on the other instances in the launch.
+constexpr int UPD_GROUPS = 8;
+
+template <int BLOCK>
+__device__ void block_update(const InstDesc& d, float* u0_row) {
+    constexpr int W = BLOCK / 32;
+    constexpr int ACTIVE = BLOCK / 24;  // groups processed at once (24 lanes each, two dims per lane)
+    __shared__ float s_min[W];
+    __shared__ double s_z[UPD_GROUPS];
+    __shared__ double s_part[UPD_GROUPS][D];
+    __shared__ float s_mu[D];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int K = d.K;
+    float lm = INFINITY;
+    for (int k = tid; k < K; k += BLOCK) {
+        float l = __ldcg(d.L + k);
+        if (finite_f(l)) lm = fminf(lm, l);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lm = fminf(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+    if (lane == 0) s_min[warp] = lm;
+    __syncthreads();
+    float Lmin = s_min[0];
+#pragma unroll
+    for (int w = 1; w < W; w++) Lmin = fminf(Lmin, s_min[w]);
+    const bool ok = finite_f(Lmin);
+    const int li = tid % 24;
+    for (int g = tid / 24; g < UPD_GROUPS && tid < ACTIVE * 24; g += ACTIVE) {
+        float s0 = 0.f, s1 = 0.f, c0 = 0.f, c1 = 0.f;
+        double z = 0.0;
+        if (ok)
+            for (int k = g; k < K; k += UPD_GROUPS) {
+                float l = __ldcg(d.L + k);
+                float w = finite_f(l) ? expf(-(l - Lmin) * d.inv_lambda) : 0.f;
+                z += (double)w;
+                float2 u = __ldcg(reinterpret_cast<const float2*>(d.U + (size_t)k * D) + li);
+                float y0 = w * u.x - c0, y1 = w * u.y - c1;
+                float t0 = s0 + y0, t1 = s1 + y1;
+                c0 = (t0 - s0) - y0;
+                c1 = (t1 - s1) - y1;
+                s0 = t0;
+                s1 = t1;
+            }
+        s_part[g][2 * li] = (double)s0 - (double)c0;
+        s_part[g][2 * li + 1] = (double)s1 - (double)c1;
+        if (li == 0) s_z[g] = z;
+    }
+    __syncthreads();
+    if (tid < D) {
+        float mu_new;
+        if (ok) {
+            double S = 0.0, Z = 0.0;
+            for (int q = 0; q < UPD_GROUPS; q++) {
+                S += s_part[q][tid];
+                Z += s_z[q];
+            }
+            mu_new = (float)(S / Z);
+        } else {
+            mu_new = __ldcg(d.mu + tid);
+        }
+        s_mu[tid] = mu_new;
+        d.mu_upd[tid] = mu_new;
+        if (tid < NJ) {
+            d.u0[tid] = mu_new;
+            u0_row[tid] = mu_new;
+        }
+    }
+    if (tid == 0) *d.status = ok ? 0 : 4;
+    __syncthreads();
+    if (tid < D) {
+        const int j = tid / NJ, i = tid % NJ;
+        const float delta = (float)d.ctrl_steps / (float)(d.H - 1);
+        const float tau = fminf((float)j * (1.f / 3.f) + delta, 1.f);
+        const float d0 = tau, d1 = tau - (1.f / 3.f), d2 = tau - (2.f / 3.f), d3 = tau - 1.f;
+        const float B0 = d1 * d2 * d3 * -4.5f, B1 = d0 * d2 * d3 * 13.5f;
+        const float B2 = d0 * d1 * d3 * -13.5f, B3 = d0 * d1 * d2 * 4.5f;
+        d.mu[tid] = B0 * s_mu[i] + B1 * s_mu[NJ + i] + B2 * s_mu[2 * NJ + i] + B3 * s_mu[3 * NJ + i];
+    }
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_batch(BatchArgs a) {
+    __shared__ InstDesc sd;
+    __shared__ int s_item, s_last;
+    const int tid = threadIdx.x, leg = tid & 3, r = tid >> 2;
+    const int n_items = *a.n_items;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(a.next, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const WorkItem w = a.items[it];
+        {
+            const int* src = reinterpret_cast<const int*>(a.desc + w.inst);
+            int* dst = reinterpret_cast<int*>(&sd);
+            for (int i = tid; i < (int)(sizeof(InstDesc) / 4); i += BLOCK) dst[i] = __ldcg(src + i);
+        }
+        __syncthreads();
+        const bool valid = r < w.n;
+        const int k = w.k0 + (valid ? r : w.n - 1);
+        const uint32_t step = __ldcg(a.steps + w.inst);
+        float Uk[NKNOT][3];
+        sample_lane(sd, k, leg, step, valid, Uk);
+        // gait time of this horizon: step * control period, reduced modulo the gait period
+        const double t0d = (double)step * sd.ctrl_steps * sd.dt_d;
+        const float t0 = (sd.gait == 1 && sd.period_d > 0) ? (float)fmod(t0d, sd.period_d) : (float)t0d;
+        const HorizonArgs hz = {sd.H, sd.n_sub, sd.nx, sd.h, sd.dt, sd.inv_Hm1, t0, sd.arm};
+        const float* x0 = a.x0s + (size_t)w.inst * NX_BOX;
+        float L;
+        if (sd.model.terrain == 1)
+            L = sd.model.has_box ? rollout_lane<1, false, true>(sd.model, sd.cost, hz, x0, Uk, leg, k, valid, nullptr)
+                                 : rollout_lane<1, false, false>(sd.model, sd.cost, hz, x0, Uk, leg, k, valid, nullptr);
+        else
+            L = sd.model.has_box ? rollout_lane<0, false, true>(sd.model, sd.cost, hz, x0, Uk, leg, k, valid, nullptr)
+                                 : rollout_lane<0, false, false>(sd.model, sd.cost, hz, x0, Uk, leg, k, valid, nullptr);
+        if (valid && leg == 0) sd.L[k] = L;
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned prev = atomicAdd(a.done + w.inst, (unsigned)w.n);
+            s_last = (prev + (unsigned)w.n == (unsigned)sd.K);
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            block_update<BLOCK>(sd, a.u0s + (size_t)w.inst * NJ);
+            if (tid == 0) a.done[w.inst] = 0u;
+        }
+        __syncthreads();
+    }
+}
+
+template <int BLOCK>
+static cudaError_t launch_batch_t(const BatchArgs& a, int grid, cudaStream_t st) {
+    k_batch<BLOCK><<<grid, BLOCK, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_batch(const BatchArgs& a, int block, int grid, cudaStream_t st) {
+    switch (block) {
+        case 64: return launch_batch_t<64>(a, grid, st);
+        case 128: return launch_batch_t<128>(a, grid, st);
+        case 256: return launch_batch_t<256>(a, grid, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+static int max_blocks_per_sm(int block) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    if (block == 64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<64>, 64, 0);
+    if (block == 128) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<128>, 128, 0);
+    if (block == 256) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<256>, 256, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+}  // namespace mppi
+
+// ------------------------------------------------------------------ host side
+
+struct mppi_batch_s {
+    std::vector<mppi_handle> hs;
+    int n = 0;
+    cudaStream_t stream = nullptr;
+    int sms = 0;
+    int block = 128, blocks_per_sm = 4;
+    int max_items = 0;
+    InstDesc* d_desc = nullptr;
+    WorkItem* d_items = nullptr;
+    int *d_nitems = nullptr, *d_next = nullptr;
+    unsigned* d_done = nullptr;
+    float *d_x0s = nullptr, *d_u0s = nullptr;
+    uint32_t* d_steps = nullptr;
+    WorkItem* h_items = nullptr;  // pinned
+    int* h_nitems = nullptr;      // pinned
+    uint32_t* h_steps = nullptr;  // pinned
+    float *h_x0s = nullptr, *h_u0s = nullptr;  // pinned
+    cudaGraphExec_t exec = nullptr;
+    int graph_block = 0, graph_bpsm = 0;
+    uint64_t launches = 0;
+    std::string err;
+};
+
+static mppi_status bfail(mppi_batch b, mppi_status s, const std::string& m) {
+    if (b) b->err = m;
+    return s;
+}
+#define BCK(call)                                                                             \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return bfail(b, MPPI_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+static bool dev_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static InstDesc make_desc(mppi_handle h) {
+    InstDesc d;
+    memset(&d, 0, sizeof(d));
+    d.model = h->dm;
+    d.cost = h->dc;
+    d.mu = h->d_mu;
+    d.mu_upd = h->d_mu_upd;
+    d.u0 = h->d_u0;
+    d.U = h->d_U;
+    d.L = h->d_L;
+    d.status = h->d_status;
+    d.mu_prop = nullptr;
+    d.K = h->cfg.K;
+    d.H = h->cfg.H;
+    d.n_sub = h->cfg.n_sub;
+    d.n_prop = h->cfg.n_prop;
+    d.ctrl_steps = h->cfg.ctrl_steps;
+    d.nx = h->nx;
+    d.gait = h->cost_in.gait;
+    d.h = (float)(h->cfg.dt / h->cfg.n_sub);
+    d.dt = (float)h->cfg.dt;
+    d.inv_Hm1 = (float)(1.0 / (h->cfg.H - 1));
+    d.arm = (float)mppi_armature(h->model_in, h->cfg.dt / h->cfg.n_sub);
+    d.inv_lambda = (float)(1.0 / h->cfg.lambda);
+    d.dt_d = h->cfg.dt;
+    d.period_d = h->cost_in.gait_period;
+    memcpy(d.sigma, h->cfg.sigma, sizeof(d.sigma));
+    memcpy(d.q_lo, h->cfg.q_lo, sizeof(d.q_lo));
+    memcpy(d.q_hi, h->cfg.q_hi, sizeof(d.q_hi));
+    d.key0 = (uint32_t)h->cfg.seed;
+    d.key1 = (uint32_t)(h->cfg.seed >> 32);
+    d.inst_id = h->cfg.inst;
+    return d;
+}
+
+// work list of the active instances, longest horizons first
+static int build_items(mppi_batch b, const int* active) {
+    const int R = b->block / 4;
+    std::vector<int> order;
+    for (int i = 0; i < b->n; i++)
+        if (!active || active[i]) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const long cx = (long)b->hs[x]->cfg.H * b->hs[x]->cfg.n_sub, cy = (long)b->hs[y]->cfg.H * b->hs[y]->cfg.n_sub;
+        return cx > cy;
+    });
+    int n = 0;
+    for (int i : order)
+        for (int k0 = 0; k0 < b->hs[i]->cfg.K; k0 += R) {
+            WorkItem w = {i, k0, std::min(R, b->hs[i]->cfg.K - k0)};
+            b->h_items[n++] = w;
+        }
+    *b->h_nitems = n;
+    return n;
+}
+
+// the step's device work: copy the work list and step indices, reset the
+// counters, run the persistent kernel
+static cudaError_t enqueue_step(mppi_batch b) {
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(b->d_items, b->h_items, (size_t)b->max_items * sizeof(WorkItem), cudaMemcpyHostToDevice,
+                             b->stream)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpyAsync(b->d_nitems, b->h_nitems, sizeof(int), cudaMemcpyHostToDevice, b->stream)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpyAsync(b->d_steps, b->h_steps, (size_t)b->n * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                             b->stream)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(b->d_next, 0, sizeof(int), b->stream)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b->d_done, 0, (size_t)b->n * sizeof(unsigned), b->stream)) != cudaSuccess) return e;
+    BatchArgs a = {b->d_desc, b->d_items, b->d_nitems, b->d_next, b->d_done, b->d_x0s, b->d_steps, b->d_u0s};
+    return launch_batch(a, b->block, b->blocks_per_sm * b->sms, b->stream);
+}
+
+static mppi_status rebuild_graph(mppi_batch b) {
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    cudaStream_t cap;
+    BCK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaStream_t saved = b->stream;
+    b->stream = cap;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e1 = enqueue_step(b);
+        e = cudaStreamEndCapture(cap, &g);
+        if (e1 != cudaSuccess) e = e1;
+    }
+    b->stream = saved;
+    cudaStreamDestroy(cap);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b->exec = nullptr;
+        return bfail(b, MPPI_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    b->graph_block = b->block;
+    b->graph_bpsm = b->blocks_per_sm;
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_batch_create(const mppi_handle* hs, int n, void* stream, mppi_batch* out) {
+    if (!hs || n < 1 || !out) return MPPI_ERR_ARG;
+    *out = nullptr;
+    mppi_batch b = new mppi_batch_s();
+    b->n = n;
+    b->stream = (cudaStream_t)stream;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    std::vector<InstDesc> descs;
+    int max_items = 0;
+    for (int i = 0; i < n; i++) {
+        if (!hs[i]) {
+            delete b;
+            return MPPI_ERR_ARG;
+        }
+        b->hs.push_back(hs[i]);
+        descs.push_back(make_desc(hs[i]));
+        max_items += (hs[i]->cfg.K + 15) / 16;  // enough for the smallest block shape (64 threads)
+    }
+    b->max_items = max_items;
+    bool ok = cudaMalloc((void**)&b->d_desc, n * sizeof(InstDesc)) == cudaSuccess &&
+              cudaMalloc((void**)&b->d_items, max_items * sizeof(WorkItem)) == cudaSuccess &&
+              cudaMalloc((void**)&b->d_nitems, sizeof(int)) == cudaSuccess &&
+              cudaMalloc((void**)&b->d_next, sizeof(int)) == cudaSuccess &&
+              cudaMalloc((void**)&b->d_done, n * sizeof(unsigned)) == cudaSuccess &&
+              cudaMalloc((void**)&b->d_x0s, (size_t)n * NX_BOX * sizeof(float)) == cudaSuccess &&
+              cudaMalloc((void**)&b->d_u0s, (size_t)n * NJ * sizeof(float)) == cudaSuccess &&
+              cudaMalloc((void**)&b->d_steps, n * sizeof(uint32_t)) == cudaSuccess &&
+              cudaMallocHost((void**)&b->h_items, max_items * sizeof(WorkItem)) == cudaSuccess &&
+              cudaMallocHost((void**)&b->h_nitems, sizeof(int)) == cudaSuccess &&
+              cudaMallocHost((void**)&b->h_steps, n * sizeof(uint32_t)) == cudaSuccess &&
+              cudaMallocHost((void**)&b->h_x0s, (size_t)n * NX_BOX * sizeof(float)) == cudaSuccess &&
+              cudaMallocHost((void**)&b->h_u0s, (size_t)n * NJ * sizeof(float)) == cudaSuccess;
+    if (!ok || cudaMemcpy(b->d_desc, descs.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(b->d_done, 0, n * sizeof(unsigned)) != cudaSuccess ||
+        cudaMemset(b->d_x0s, 0, (size_t)n * NX_BOX * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        mppi_batch_destroy(b);
+        return MPPI_ERR_OOM;
+    }
+    memset(b->h_items, 0, max_items * sizeof(WorkItem));
+    memset(b->h_steps, 0, n * sizeof(uint32_t));
+    b->block = 128;
+    b->blocks_per_sm = std::max(1, std::min(4, max_blocks_per_sm(128)));
+    *out = b;
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_batch_destroy(mppi_batch b) {
+    if (!b) return MPPI_ERR_ARG;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    void* d[] = {b->d_desc, b->d_items, b->d_nitems, b->d_next, b->d_done, b->d_x0s, b->d_u0s, b->d_steps};
+    for (void* p : d)
+        if (p) cudaFree(p);
+    void* hp[] = {b->h_items, b->h_nitems, b->h_steps, b->h_x0s, b->h_u0s};
+    for (void* p : hp)
+        if (p) cudaFreeHost(p);
+    delete b;
+    return MPPI_OK;
+}
+
+extern "C" const char* mppi_batch_last_error(mppi_batch b) { return b ? b->err.c_str() : "null batch"; }
+
+extern "C" mppi_status mppi_batch_set_shape(mppi_batch b, int block, int blocks_per_sm) {
+    if (!b) return MPPI_ERR_ARG;
+    if (block != 64 && block != 128 && block != 256) return bfail(b, MPPI_ERR_ARG, "block must be 64, 128 or 256");
+    const int mx = max_blocks_per_sm(block);
+    if (blocks_per_sm < 1 || blocks_per_sm > mx)
+        return bfail(b, MPPI_ERR_ARG, "blocks_per_sm out of range (occupancy limit " + std::to_string(mx) + ")");
+    b->block = block;
+    b->blocks_per_sm = blocks_per_sm;
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_batch_get_shape(mppi_batch b, int* block, int* blocks_per_sm) {
+    if (!b || !block || !blocks_per_sm) return MPPI_ERR_ARG;
+    *block = b->block;
+    *blocks_per_sm = b->blocks_per_sm;
+    return MPPI_OK;
+}
+
+// stage x0s (host or device, [n][NX_BOX]) and step indices (host, [n]) for the next step
+static mppi_status stage_inputs(mppi_batch b, const float* x0s, const uint32_t* steps) {
+    if (steps) memcpy(b->h_steps, steps, (size_t)b->n * sizeof(uint32_t));
+    if (x0s) {
+        if (dev_ptr(x0s)) {
+            BCK(cudaMemcpyAsync(b->d_x0s, x0s, (size_t)b->n * NX_BOX * sizeof(float), cudaMemcpyDeviceToDevice,
+                                b->stream));
+        } else {
+            for (int i = 0; i < b->n * NX_BOX; i++)
+                if (!isfinite(x0s[i])) return bfail(b, MPPI_ERR_NONFINITE, "x0s not finite");
+            memcpy(b->h_x0s, x0s, (size_t)b->n * NX_BOX * sizeof(float));
+            BCK(cudaMemcpyAsync(b->d_x0s, b->h_x0s, (size_t)b->n * NX_BOX * sizeof(float), cudaMemcpyHostToDevice,
+                                b->stream));
+        }
+    }
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_batch_step(mppi_batch b, const int* active, const float* x0s, const uint32_t* steps,
+                                       float* u0s) {
+    if (!b) return MPPI_ERR_ARG;
+    mppi_status s = stage_inputs(b, x0s, steps);
+    if (s != MPPI_OK) return s;
+    // the previous graph launch may still read the pinned work list: order the rewrite after it
+    BCK(cudaStreamSynchronize(b->stream));
+    build_items(b, active);
+    if (!b->exec || b->graph_block != b->block || b->graph_bpsm != b->blocks_per_sm) {
+        s = rebuild_graph(b);
+        if (s != MPPI_OK) return s;
+    }
+    BCK(cudaGraphLaunch(b->exec, b->stream));
+    b->launches++;
+    if (u0s) {
+        const bool dev = dev_ptr(u0s);
+        if (dev) {
+            BCK(cudaMemcpyAsync(u0s, b->d_u0s, (size_t)b->n * NJ * sizeof(float), cudaMemcpyDeviceToDevice, b->stream));
+        } else {
+            BCK(cudaMemcpyAsync(b->h_u0s, b->d_u0s, (size_t)b->n * NJ * sizeof(float), cudaMemcpyDeviceToHost,
+                                b->stream));
+            BCK(cudaStreamSynchronize(b->stream));
+            memcpy(u0s, b->h_u0s, (size_t)b->n * NJ * sizeof(float));
+        }
+    }
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_batch_autotune(mppi_batch b, const float* x0s, int trials, int* block_out,
+                                           int* bpsm_out, float* best_ms_out) {
+    if (!b || trials < 1) return MPPI_ERR_ARG;
+    mppi_status s = stage_inputs(b, x0s, nullptr);
+    if (s != MPPI_OK) return s;
+    // every candidate starts from the same nominals: save them, restore after each trial
+    std::vector<float*> saved(b->n, nullptr);
+    for (int i = 0; i < b->n; i++) {
+        BCK(cudaMalloc((void**)&saved[i], D * sizeof(float)));
+        BCK(cudaMemcpyAsync(saved[i], b->hs[i]->d_mu, D * sizeof(float), cudaMemcpyDeviceToDevice, b->stream));
+    }
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_b = b->block, best_p = b->blocks_per_sm;
+    const int blocks[3] = {64, 128, 256};
+    for (int bi = 0; bi < 3; bi++) {
+        const int mx = max_blocks_per_sm(blocks[bi]);
+        for (int p = 1; p <= mx && p <= 16; p *= 2) {
+            b->block = blocks[bi];
+            b->blocks_per_sm = p;
+            BCK(cudaStreamSynchronize(b->stream));
+            build_items(b, nullptr);
+            float tot = 0.f;
+            for (int t = 0; t <= trials; t++) {
+                for (int i = 0; i < b->n; i++)
+                    BCK(cudaMemcpyAsync(b->hs[i]->d_mu, saved[i], D * sizeof(float), cudaMemcpyDeviceToDevice,
+                                        b->stream));
+                BCK(cudaEventRecord(e0, b->stream));
+                BCK(enqueue_step(b));
+                BCK(cudaEventRecord(e1, b->stream));
+                BCK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                BCK(cudaEventElapsedTime(&ms, e0, e1));
+                if (t > 0) tot += ms;  // the first run warms up
+            }
+            const float mean = tot / trials;
+            if (mean < best) {
+                best = mean;
+                best_b = blocks[bi];
+                best_p = p;
+            }
+        }
+    }
+    for (int i = 0; i < b->n; i++) {
+        BCK(cudaMemcpyAsync(b->hs[i]->d_mu, saved[i], D * sizeof(float), cudaMemcpyDeviceToDevice, b->stream));
+    }
+    BCK(cudaStreamSynchronize(b->stream));
+    for (float* p : saved) cudaFree(p);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->block = best_b;
+    b->blocks_per_sm = best_p;
+    if (block_out) *block_out = best_b;
+    if (bpsm_out) *bpsm_out = best_p;
+    if (best_ms_out) *best_ms_out = best;
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_batch_launch_count(mppi_batch b, uint64_t* count) {
+    if (!b || !count) return MPPI_ERR_ARG;
+    *count = b->launches;
+    return MPPI_OK;
+}

@@ -1,0 +1,38 @@
+// handle.h -- the controller handle behind the C ABI (internal to the library;
+// shared by api.cu and the multi-instance code in batch.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/mppi.h"
+#include "kernels.h"
+
+struct mppi_handle_s {
+    mppi_model_t model_in;
+    mppi_cost_t cost_in;
+    mppi_config_t cfg;
+    mppi::DevModel dm;
+    mppi::DevCost dc;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int nx = mppi::NX_ROBOT;
+    float *d_mu = nullptr, *d_mu_prop = nullptr, *d_mu_upd = nullptr, *d_U = nullptr, *d_L = nullptr;
+    float *d_x0 = nullptr, *d_u0 = nullptr, *d_hf = nullptr, *d_sbox = nullptr;
+    int* d_status = nullptr;
+    double* d_wsum = nullptr;
+    double* d_part = nullptr;      // update scratch: per-CTA partial sums
+    unsigned* d_counter = nullptr;  // update scratch: finished-CTA counter
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    int timing = 0;
+    int timed_valid = 0;
+    uint64_t launches = 0;
+    std::string err;
+};
+
+
+// implicit-PD armature of one sub-step: h (kd + h kp) + a0
+double mppi_armature(const mppi_model_t& p, double h);
+// gait time of a horizon starting at absolute time t0, reduced modulo the gait period
+float mppi_reduce_t0(const mppi_handle h, double t0);

@@ -1,520 +1,52 @@
-// rollout.cu -- K2: MPPI rollouts on sm_103a CUDA cores (FP32).
+// rollout.cu -- K2: MPPI rollouts of one instance on sm_103a CUDA cores (FP32).
 //
 // arXiv 2409.10469, Alg. 1 inner loop: every sample's knot vector is turned into
 // joint targets by the cubic spline (Sec. III-B), tracked by PD (Sec. IV-A) and
 // simulated for T steps while L_walk (Sec. IV-B) and L_box (Sec. IV-D) accumulate.
-// The simulator is the model spec's replacement for MuJoCo (Sec. III-A):
-// floating-base articulated-body algorithm, penalty contacts with regularised
-// Coulomb friction, semi-implicit Euler with n_sub sub-steps, implicit PD damping.
-//
-// Mapping: one rollout = 4 consecutive lanes, one lane per leg.  Each lane runs
-// its leg's 3-body chain of every ABA pass in registers; the legs meet only at
-// the trunk, whose articulated inertia (21 numbers) and bias force (6) are summed
-// with two xor-shuffle rounds.  Every lane then holds bit-identical trunk sums and
-// solves the 6x6 trunk system itself, so the replicated trunk state never
-// diverges between lanes.  A warp holds 8 rollouts.
-#include "common.cuh"
+// The per-lane arithmetic lives in rollout.cuh; this kernel maps 4 lanes to a
+// rollout (8 rollouts per warp) over the n samples of one controller.
 #include "kernels.h"
+#include "rollout.cuh"
 
 namespace mppi {
 
-struct LegState {
-    float q[3], qd[3];
-};
-
-struct Trunk {
-    float p[3], quat[4];
-    float3 w, v;  // body-frame angular and linear velocity
-};
-
-__device__ __forceinline__ float xsum4(float v) {
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    return v;
-}
-
-// ---------------------------------------------------------------- terrain
-
-// ground height and slope under (x, y): plane, or bilinear heightfield with
-// clamped edges (zero slope across a clamped edge)
-template <int TERR>
-__device__ __forceinline__ void ground(const DevModel& m, float x, float y, float& h, float& hx, float& hy) {
-    if (TERR == 0) { h = 0.f; hx = 0.f; hy = 0.f; return; }
-    float u = (x - m.hf_x0) * m.hf_inv_cell, v = (y - m.hf_y0) * m.hf_inv_cell;
-    const float umax = (float)(m.hf_nx - 1), vmax = (float)(m.hf_ny - 1);
-    bool inx = (u >= 0.f) && (u <= umax), iny = (v >= 0.f) && (v <= vmax);
-    u = fminf(fmaxf(u, 0.f), umax);
-    v = fminf(fmaxf(v, 0.f), vmax);
-    int i = min((int)floorf(u), m.hf_nx - 2), j = min((int)floorf(v), m.hf_ny - 2);
-    float fx = u - (float)i, fy = v - (float)j;
-    const float* r0 = m.hf + j * m.hf_nx + i;
-    float h00 = __ldg(r0), h10 = __ldg(r0 + 1), h01 = __ldg(r0 + m.hf_nx), h11 = __ldg(r0 + m.hf_nx + 1);
-    h = (1.f - fx) * (1.f - fy) * h00 + fx * (1.f - fy) * h10 + (1.f - fx) * fy * h01 + fx * fy * h11;
-    hx = inx ? ((1.f - fy) * (h10 - h00) + fy * (h11 - h01)) * m.hf_inv_cell : 0.f;
-    hy = iny ? ((1.f - fx) * (h01 - h00) + fx * (h11 - h10)) * m.hf_inv_cell : 0.f;
-}
-
-// sphere vs axis-aligned box: outward normal and depth when overlapping
-__device__ __forceinline__ bool sphere_aabb(float3 x, float r, float3 lo, float3 hi, float3& n, float& pen) {
-    float3 cp = f3(fminf(fmaxf(x.x, lo.x), hi.x), fminf(fmaxf(x.y, lo.y), hi.y), fminf(fmaxf(x.z, lo.z), hi.z));
-    float3 d = x - cp;
-    float d2 = dot3(d, d);
-    if (d2 > 0.f) {
-        float dn = sqrtf(d2);
-        if (dn >= r) return false;
-        float inv = 1.f / dn;
-        n = inv * d;
-        pen = r - dn;
-        return true;
-    }
-    // centre inside: leave through the nearest face (order x-, x+, y-, y+, z-, z+)
-    float best = x.x - lo.x; int bf = 0;
-    float t;
-    t = hi.x - x.x; if (t < best) { best = t; bf = 1; }
-    t = x.y - lo.y; if (t < best) { best = t; bf = 2; }
-    t = hi.y - x.y; if (t < best) { best = t; bf = 3; }
-    t = x.z - lo.z; if (t < best) { best = t; bf = 4; }
-    t = hi.z - x.z; if (t < best) { best = t; bf = 5; }
-    float sgn = (bf & 1) ? 1.f : -1.f;
-    n = f3(bf / 2 == 0 ? sgn : 0.f, bf / 2 == 1 ? sgn : 0.f, bf / 2 == 2 ? sgn : 0.f);
-    pen = r + best;
-    return true;
-}
-
-// Force (in body coordinates) of one contact on a sphere fixed in a body.
-// nb: normal in body coordinates, cb: sphere centre in the body frame, (w, v):
-// body velocity; the force acts at the deepest point cb - r nb.
-__device__ __forceinline__ void contact_wrench(const DevModel& m, float pen, float3 nb, float3 cb, float r,
-                                               float3 w, float3 v, float3& torque, float3& force) {
-    float3 pc = cb - r * nb;
-    float3 vp = v + cross3(w, pc);
-    float vn = dot3(vp, nb);
-    float fn = fmaxf(m.kc * pen - m.cc * vn, 0.f);
-    float3 vt = vp - vn * nb;
-    float s = sqrtf(dot3(vt, vt) + m.eps2);
-    float fr = m.mu * fn / s;
-    float3 f = fn * nb - fr * vt;
-    force = force + f;
-    torque = torque + cross3(pc, f);
-}
-
-// all static-environment contacts of one sphere (world centre xw, radius r);
-// RT(world) maps a world vector into the body's coordinates
-template <int TERR, typename ToBody>
-__device__ __forceinline__ void sphere_env(const DevModel& m, float3 xw, float r, float3 cb, float3 w, float3 v,
-                                           const ToBody& toBody, float3& torque, float3& force) {
-    float h, hx, hy;
-    ground<TERR>(m, xw.x, xw.y, h, hx, hy);
-    float inv = 1.f / sqrtf(hx * hx + hy * hy + 1.f);
-    float3 n = f3(-hx * inv, -hy * inv, inv);
-    float pen = r - (xw.z - h) * n.z;
-    if (pen > 0.f) contact_wrench(m, pen, toBody(n), cb, r, w, v, torque, force);
-    for (int b = 0; b < m.n_sbox; b++) {
-        float3 nn; float pb;
-        const float* bx = m.sbox + 6 * b;
-        const float3 lo = f3(__ldg(bx), __ldg(bx + 1), __ldg(bx + 2));
-        const float3 hi = f3(__ldg(bx + 3), __ldg(bx + 4), __ldg(bx + 5));
-        if (sphere_aabb(xw, r, lo, hi, nn, pb))
-            contact_wrench(m, pb, toBody(nn), cb, r, w, v, torque, force);
-    }
-}
-
-// world -> body coordinate maps of the two kinds of contact-sphere bodies
-struct TrunkFrame {
-    float r00, r01, r02, r10, r11, r12, r20, r21, r22;  // R0 (body -> world)
-    __device__ __forceinline__ float3 operator()(float3 n) const {
-        return f3(r00 * n.x + r10 * n.y + r20 * n.z, r01 * n.x + r11 * n.y + r21 * n.z,
-                  r02 * n.x + r12 * n.y + r22 * n.z);
-    }
-};
-struct CalfFrame {
-    float r00, r01, r02, r10, r11, r12, r20, r21, r22;
-    float c0, s0, c1, s1, c2, s2;
-    __device__ __forceinline__ float3 operator()(float3 n) const {
-        float3 t = f3(r00 * n.x + r10 * n.y + r20 * n.z, r01 * n.x + r11 * n.y + r21 * n.z,
-                      r02 * n.x + r12 * n.y + r22 * n.z);
-        return Ey(c2, s2, Ey(c1, s1, Ex(c0, s0, t)));
-    }
-};
-
-// ---------------------------------------------------------------- cost
-
-__device__ __forceinline__ float trunk_state_cost(const DevCost& c, const Trunk& T) {
-    float dz = T.p[2] - c.z_ref;
-    float L = c.w_z * dz * dz;
-    float sg = T.quat[0] < 0.f ? -2.f : 2.f;
-    float ex = sg * T.quat[1], ey = sg * T.quat[2], ez = sg * T.quat[3];
-    L += c.w_o * (ex * ex + ey * ey + ez * ez);
-    float dv = T.v.x - c.v_ref;
-    L += c.w_v * dv * dv;
-    float dx = T.p[0] - c.goal_x, dy = T.p[1] - c.goal_y;
-    L += c.w_p * (dx * dx + dy * dy);
-    return L;
-}
-
-// ---------------------------------------------------------------- one sub-step
-
-// velocity-product term c = v x (e_AX qd) of a joint about AX, from the body's
-// velocity before its own joint rate is added (the joint's own part drops out)
-template <int AX> __device__ __forceinline__ float3 vprod(float3 a, float qd) {
-    return AX == 0 ? f3(0.f, a.z * qd, -a.y * qd) : f3(-a.z * qd, 0.f, a.x * qd);
-}
-
-// Ia = IA - U U^T / D  and  pa = pA + Ia c + U u / D for a joint about AX
-// (U = IA e_AX); c has zero entries on the joint axis (structure of vprod).
-template <int AX>
-__device__ __forceinline__ void project(Sym6& M, float3& pn, float3& pf, float Dinv, float uu, float3 cw, float3 cv) {
-    float Ua[3], Ul[3];
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        Ua[i] = M.A[sidx(i, AX)];
-        Ul[i] = M.B[AX][i];
-    }
-    float Uas[3], Uls[3];
-#pragma unroll
-    for (int i = 0; i < 3; i++) { Uas[i] = Ua[i] * Dinv; Uls[i] = Ul[i] * Dinv; }
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = i; j < 3; j++) {
-            M.A[sidx(i, j)] = fmaf(-Uas[i], Ua[j], M.A[sidx(i, j)]);
-            M.C[sidx(i, j)] = fmaf(-Uls[i], Ul[j], M.C[sidx(i, j)]);
-        }
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) M.B[i][j] = fmaf(-Uas[i], Ul[j], M.B[i][j]);
-    // Ia c with c zero on component AX of both halves
-    const float cw_[3] = {cw.x, cw.y, cw.z}, cv_[3] = {cv.x, cv.y, cv.z};
-    float n[3] = {pn.x, pn.y, pn.z}, f[3] = {pf.x, pf.y, pf.z};
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int l = 0; l < 3; l++) {
-            if (l == AX) continue;
-            n[i] = fmaf(M.A[sidx(i, l)], cw_[l], n[i]);
-            n[i] = fmaf(M.B[i][l], cv_[l], n[i]);
-            f[i] = fmaf(M.B[l][i], cw_[l], f[i]);
-            f[i] = fmaf(M.C[sidx(i, l)], cv_[l], f[i]);
-        }
-    const float k = uu * Dinv;
-    pn = f3(fmaf(k, Ua[0], n[0]), fmaf(k, Ua[1], n[1]), fmaf(k, Ua[2], n[2]));
-    pf = f3(fmaf(k, Ul[0], f[0]), fmaf(k, Ul[1], f[1]), fmaf(k, Ul[2], f[2]));
-}
-
-// bias force v x* I v of a body with a structured inertia
-__device__ __forceinline__ void body_bias(const BodyI& I, float3 w, float3 v, float3& bn, float3& bf) {
-    float3 ha, hl;
-    bodyI_mv(I, w, v, ha, hl);
-    bn = cross3(w, ha) + cross3(v, hl);
-    bf = cross3(w, hl);
-}
-
-template <int TERR>
-__device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, LegState& S, const float u[3],
-                                        float h, float arm) {
-    const float g = m.gz;
-    float R0[3][3];
-    quat_R(T.quat, R0);
-
-    // ---- leg kinematics: joint transforms, body velocities, velocity products
-    float c0, s0, c1, s1, c2, s2;
-    sincos_r(S.q[0], s0, c0);
-    sincos_r(S.q[1], s1, c1);
-    sincos_r(S.q[2], s2, c2);
-    // legs FR, FL, RR, RL: front (+x) for legs 0, 1; left (+y) for odd legs
-    const float fx = leg < 2 ? 1.f : -1.f, sy = (leg & 1) ? 1.f : -1.f;
-    const float3 rh = f3(fx * m.hip_x, sy * m.hip_y, m.hip_z);
-    const float3 rt = f3(0.f, sy * m.thigh_y, 0.f);
-    const float3 rk = f3(0.f, 0.f, m.r_knee[2]);
-    float3 wh = Ex(c0, s0, T.w);
-    float3 vh = Ex(c0, s0, T.v + cross3(T.w, rh));
-    const float3 ch_w = vprod<0>(wh, S.qd[0]), ch_v = vprod<0>(vh, S.qd[0]);
-    wh.x += S.qd[0];
-    float3 wt = Ey(c1, s1, wh);
-    float3 vt = Ey(c1, s1, vh + cross3(wh, rt));
-    const float3 ct_w = vprod<1>(wt, S.qd[1]), ct_v = vprod<1>(vt, S.qd[1]);
-    wt.y += S.qd[1];
-    float3 wc = Ey(c2, s2, wt);
-    float3 vc = Ey(c2, s2, vt + cross3(wt, rk));
-    const float3 cc_w = vprod<1>(wc, S.qd[2]), cc_v = vprod<1>(vc, S.qd[2]);
-    wc.y += S.qd[2];
-
-    // ---- contacts: the foot sphere on the calf
-    float3 fc_n = f3(0.f, 0.f, 0.f), fc_f = f3(0.f, 0.f, 0.f);
-    {
-        const float3 foot = f3(0.f, 0.f, m.foot[2]);
-        float3 ptr = rh + ExT(c0, s0, rt + EyT(c1, s1, rk + EyT(c2, s2, foot)));   // trunk frame
-        float3 xw = f3(T.p[0], T.p[1], T.p[2]) + mulR(R0, ptr);
-        const CalfFrame toCalf = {R0[0][0], R0[0][1], R0[0][2], R0[1][0], R0[1][1], R0[1][2],
-                                  R0[2][0], R0[2][1], R0[2][2], c0, s0, c1, s1, c2, s2};
-        sphere_env<TERR>(m, xw, m.foot_r, foot, wc, vc, toCalf, fc_n, fc_f);
-    }
-    // ---- contacts: trunk spheres, one per lane, summed over the 4 lanes below
-    float3 f0_n = f3(0.f, 0.f, 0.f), f0_f = f3(0.f, 0.f, 0.f);
-    if (leg < m.n_tsph) {
-        const float tx = leg == 0 ? m.tsph_x[0] : (leg == 1 ? m.tsph_x[1] : (leg == 2 ? m.tsph_x[2] : m.tsph_x[3]));
-        float3 cb = f3(tx, 0.f, 0.f);
-        float3 xw = f3(T.p[0], T.p[1], T.p[2]) + mulR(R0, cb);
-        const TrunkFrame toTrunk = {R0[0][0], R0[0][1], R0[0][2], R0[1][0], R0[1][1], R0[1][2],
-                                    R0[2][0], R0[2][1], R0[2][2]};
-        sphere_env<TERR>(m, xw, m.tsph_r, cb, T.w, T.v, toTrunk, f0_n, f0_f);
-    }
-
-    // ---- PD with implicit damping: tau = kp (u - q - h qd) - kd qd, armature h (kd + h kp)
-    float tau[3];
-#pragma unroll
-    for (int i = 0; i < 3; i++) tau[i] = m.kp * (u[i] - S.q[i] - h * S.qd[i]) - m.kd * S.qd[i];
-
-    // ---- pass 2 (tip to root)
-    // calf: its articulated inertia after projection is a model constant
-    Sym6 IA = m.Ia_calf;
-    float3 pa_n, pa_f;
-    body_bias(m.I_calf, wc, vc, pa_n, pa_f);
-    pa_n = pa_n - fc_n;
-    pa_f = pa_f - fc_f;
-    const float D2inv = m.calf_D_inv;
-    const float u2 = tau[2] - pa_n.y;
-    // U2 = I_calf e_y = (0, ay, 0 | mcz, 0, 0)
-    const float U2a = m.I_calf.ay, U2l = m.I_calf.mcz;
-    {
-        float3 ia, il;
-        sym6_mv(IA, cc_w, cc_v, ia, il);
-        const float k = u2 * D2inv;
-        pa_n = pa_n + ia + f3(0.f, k * U2a, 0.f);
-        pa_f = pa_f + il + f3(k * U2l, 0.f, 0.f);
-    }
-    // to the thigh frame: X^T pa = [E^T n + r x E^T f; E^T f]
-    float U1a[3], U1l[3], D1inv, u1;
-    {
-        float3 fn = EyT(c2, s2, pa_n), ff = EyT(c2, s2, pa_f);
-        pa_n = fn + cross3(rk, ff);
-        pa_f = ff;
-        congruence<1, 4>(IA, c2, s2, rk);
-        add_bodyI(IA, m.I_thigh);
-        float3 bn, bf;
-        body_bias(m.I_thigh, wt, vt, bn, bf);
-        pa_n = pa_n + bn;
-        pa_f = pa_f + bf;
-#pragma unroll
-        for (int i = 0; i < 3; i++) { U1a[i] = IA.A[sidx(i, 1)]; U1l[i] = IA.B[1][i]; }
-        D1inv = 1.f / (U1a[1] + arm);
-        u1 = tau[1] - pa_n.y;
-    }
-    project<1>(IA, pa_n, pa_f, D1inv, u1, ct_w, ct_v);
-    float U0a[3], U0l[3], D0inv, u0;
-    {   // to the hip frame
-        float3 fn = EyT(c1, s1, pa_n), ff = EyT(c1, s1, pa_f);
-        pa_n = fn + cross3(rt, ff);
-        pa_f = ff;
-        congruence<1, 2>(IA, c1, s1, rt);
-        add_bodyI(IA, m.I_hip);
-        float3 bn, bf;
-        body_bias(m.I_hip, wh, vh, bn, bf);
-        pa_n = pa_n + bn;
-        pa_f = pa_f + bf;
-#pragma unroll
-        for (int i = 0; i < 3; i++) { U0a[i] = IA.A[sidx(i, 0)]; U0l[i] = IA.B[0][i]; }
-        D0inv = 1.f / (U0a[0] + arm);
-        u0 = tau[0] - pa_n.x;
-    }
-    project<0>(IA, pa_n, pa_f, D0inv, u0, ch_w, ch_v);
-    {   // to the trunk frame
-        float3 fn = ExT(c0, s0, pa_n), ff = ExT(c0, s0, pa_f);
-        pa_n = fn + cross3(rh, ff);
-        pa_f = ff;
-        congruence<0, 7>(IA, c0, s0, rh);
-    }
-
-    // ---- trunk: sum the 4 legs' contributions, add the trunk's own terms
-    float Mt[6][6], bt[6];
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = i; j < 3; j++) {
-            Mt[i][j] = xsum4(IA.A[sidx(i, j)]);
-            Mt[3 + i][3 + j] = xsum4(IA.C[sidx(i, j)]);
-        }
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) Mt[i][3 + j] = xsum4(IA.B[i][j]);
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        Mt[i][i] += m.tr_Ic[i];
-        Mt[3 + i][3 + i] += m.tr_m;
-    }
-    {
-        // per-lane terms (leg bias, minus this lane's trunk-sphere wrench) summed
-        // over the 4 lanes, then the trunk's own bias v x* I v once
-        float3 Iw = f3(m.tr_Ic[0] * T.w.x, m.tr_Ic[1] * T.w.y, m.tr_Ic[2] * T.w.z);
-        float3 bn = cross3(T.w, Iw), bf = m.tr_m * cross3(T.w, T.v);
-        bt[0] = xsum4(pa_n.x - f0_n.x) + bn.x;
-        bt[1] = xsum4(pa_n.y - f0_n.y) + bn.y;
-        bt[2] = xsum4(pa_n.z - f0_n.z) + bn.z;
-        bt[3] = xsum4(pa_f.x - f0_f.x) + bf.x;
-        bt[4] = xsum4(pa_f.y - f0_f.y) + bf.y;
-        bt[5] = xsum4(pa_f.z - f0_f.z) + bf.z;
-    }
-    // ---- solve Mt a' = -bt (Cholesky, 6x6 SPD, upper storage)
-    float Lc[6][6], Linv[6];
-#pragma unroll
-    for (int j = 0; j < 6; j++) {
-        float d = Mt[j][j];
-#pragma unroll
-        for (int k = 0; k < j; k++) d = fmaf(-Lc[j][k], Lc[j][k], d);
-        const float inv = rsqrtf(d);
-        Linv[j] = inv;
-#pragma unroll
-        for (int i = j + 1; i < 6; i++) {
-            float sum = Mt[j][i];
-#pragma unroll
-            for (int k = 0; k < j; k++) sum = fmaf(-Lc[i][k], Lc[j][k], sum);
-            Lc[i][j] = sum * inv;
-        }
-    }
-    float y[6], a0[6];
-#pragma unroll
-    for (int i = 0; i < 6; i++) {
-        float sum = -bt[i];
-#pragma unroll
-        for (int k = 0; k < i; k++) sum = fmaf(-Lc[i][k], y[k], sum);
-        y[i] = sum * Linv[i];
-    }
-#pragma unroll
-    for (int i = 5; i >= 0; i--) {
-        float sum = y[i];
-#pragma unroll
-        for (int k = i + 1; k < 6; k++) sum = fmaf(-Lc[k][i], a0[k], sum);
-        a0[i] = sum * Linv[i];
-    }
-
-    // ---- pass 3 (root to tip): a' = X a'_parent + c ; qdd = (u - U . a') / D
-    float qdd[3];
-    const float3 aw = f3(a0[0], a0[1], a0[2]), av = f3(a0[3], a0[4], a0[5]);
-    {
-        float3 nw = Ex(c0, s0, aw) + ch_w, nv = Ex(c0, s0, av + cross3(aw, rh)) + ch_v;
-        qdd[0] = (u0 - (U0a[0] * nw.x + U0a[1] * nw.y + U0a[2] * nw.z + U0l[0] * nv.x + U0l[1] * nv.y + U0l[2] * nv.z)) * D0inv;
-        nw.x += qdd[0];
-        float3 tw = Ey(c1, s1, nw) + ct_w, tv = Ey(c1, s1, nv + cross3(nw, rt)) + ct_v;
-        qdd[1] = (u1 - (U1a[0] * tw.x + U1a[1] * tw.y + U1a[2] * tw.z + U1l[0] * tv.x + U1l[1] * tv.y + U1l[2] * tv.z)) * D1inv;
-        tw.y += qdd[1];
-        float3 kw = Ey(c2, s2, tw) + cc_w, kv = Ey(c2, s2, tv + cross3(tw, rk)) + cc_v;
-        qdd[2] = (u2 - (U2a * kw.y + U2l * kv.x)) * D2inv;
-    }
-
-    // ---- semi-implicit Euler
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        S.qd[i] = fmaf(h, qdd[i], S.qd[i]);
-        S.q[i] = fmaf(h, S.qd[i], S.q[i]);
-    }
-    const float3 gb = f3(R0[2][0] * g, R0[2][1] * g, R0[2][2] * g);  // R0^T (0, 0, g)
-    T.w = T.w + h * aw;
-    T.v = T.v + h * (av + gb);
-    const float3 dp = mulR(R0, T.v);
-    T.p[0] = fmaf(h, dp.x, T.p[0]);
-    T.p[1] = fmaf(h, dp.y, T.p[1]);
-    T.p[2] = fmaf(h, dp.z, T.p[2]);
-    quat_integrate(T.quat, T.w, h);
-}
-
-// ---------------------------------------------------------------- kernel
-
-// x_t of rollout k: lane 0 writes the trunk, every lane its leg's joints
-__device__ __forceinline__ void store_state(const RolloutArgs& a, int k, int t, int leg, bool valid, const Trunk& T,
-                                            const LegState& S) {
-    if (!valid) return;
-    float* o = a.traj + ((size_t)k * (a.H + 1) + t) * a.model.nx;
-    if (leg == 0) {
-        o[0] = T.p[0]; o[1] = T.p[1]; o[2] = T.p[2];
-        o[3] = T.quat[0]; o[4] = T.quat[1]; o[5] = T.quat[2]; o[6] = T.quat[3];
-        o[19] = T.w.x; o[20] = T.w.y; o[21] = T.w.z;
-        o[22] = T.v.x; o[23] = T.v.y; o[24] = T.v.z;
-    }
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        o[7 + 3 * leg + i] = S.q[i];
-        o[25 + 3 * leg + i] = S.qd[i];
-    }
-}
-
-template <int TERR, bool TRAJ>
+template <int TERR, bool TRAJ, bool BOX>
 __global__ void __launch_bounds__(256) k_rollout(RolloutArgs a) {
-    const DevModel& m = a.model;
-    const DevCost& c = a.cost;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = gt >> 2, leg = gt & 3;
     const bool valid = k < a.n;
     const int kk = valid ? k : a.n - 1;
-    const int nx = m.nx;
+    const int nx = a.model.nx;
     const float* x0 = a.x0 + (a.x0_per_sample ? (size_t)kk * nx : 0);
-
-    Trunk T;
-    T.p[0] = x0[0]; T.p[1] = x0[1]; T.p[2] = x0[2];
-    T.quat[0] = x0[3]; T.quat[1] = x0[4]; T.quat[2] = x0[5]; T.quat[3] = x0[6];
-    T.w = f3(x0[19], x0[20], x0[21]);
-    T.v = f3(x0[22], x0[23], x0[24]);
-    LegState S;
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        S.q[i] = x0[7 + 3 * leg + i];
-        S.qd[i] = x0[25 + 3 * leg + i];
-    }
     float Uk[NKNOT][3];
     const float* Urow = a.U + (size_t)kk * D;
 #pragma unroll
     for (int j = 0; j < NKNOT; j++)
 #pragma unroll
         for (int i = 0; i < 3; i++) Uk[j][i] = Urow[j * NJ + 3 * leg + i];
-
-    const float h = a.h;
-    const float ph0 = (leg == 1 || leg == 2) ? 3.14159265358979f : 0.f;
-    float L = 0.f;
-    if (TRAJ) store_state(a, k, 0, leg, valid, T, S);
-    for (int t = 0; t < a.H; t++) {
-        // cubic through 4 knots at tau_j = j / 3 (Lagrange basis)
-        const float tau = (float)t * a.inv_Hm1;
-        const float d0 = tau, d1 = tau - (1.f / 3.f), d2 = tau - (2.f / 3.f), d3 = tau - 1.f;
-        const float B0 = d1 * d2 * d3 * -4.5f, B1 = d0 * d2 * d3 * 13.5f;
-        const float B2 = d0 * d1 * d3 * -13.5f, B3 = d0 * d1 * d2 * 4.5f;
-        float u[3];
-#pragma unroll
-        for (int i = 0; i < 3; i++) u[i] = B0 * Uk[0][i] + B1 * Uk[1][i] + B2 * Uk[2][i] + B3 * Uk[3][i];
-        // stage cost: this leg's control term; the trunk terms on lane 0
-        {
-            float ds = 0.f, dk = 0.f;
-            if (c.gait == 1) {
-                float s, cq;
-                sincos_r(c.two_pi_over_period * (a.t0 + (float)t * a.dt) + ph0, s, cq);
-                ds = c.hip_amp * s;
-                dk = -c.knee_amp * fmaxf(s, 0.f);
-            }
-            float e0 = u[0] - c.stand[0], e1 = u[1] - (c.stand[1] + ds), e2 = u[2] - (c.stand[2] + dk);
-            L += c.w_u * (e0 * e0 + e1 * e1 + e2 * e2);
-            if (leg == 0) L += trunk_state_cost(c, T);
-        }
-        for (int sb = 0; sb < a.n_sub; sb++) substep<TERR>(m, leg, T, S, u, h, a.arm);
-        if (TRAJ) store_state(a, k, t + 1, leg, valid, T, S);
-    }
-    if (leg == 0) L += c.w_term * trunk_state_cost(c, T);
-    L = xsum4(L);
+    const HorizonArgs hz = {a.H, a.n_sub, nx, a.h, a.dt, a.inv_Hm1, a.t0, a.arm};
+    const float L = rollout_lane<TERR, TRAJ, BOX>(a.model, a.cost, hz, x0, Uk, leg, k, valid, a.traj);
     if (valid && leg == 0) a.L[k] = L;
 }
 
-template <int TERR, bool TRAJ>
+template <int TERR, bool TRAJ, bool BOX>
 static cudaError_t launch_t(const RolloutArgs& a, int block, cudaStream_t st) {
     long threads = 4L * a.n;
     int grid = (int)((threads + block - 1) / block);
-    k_rollout<TERR, TRAJ><<<grid, block, 0, st>>>(a);
+    k_rollout<TERR, TRAJ, BOX><<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
+}
+
+template <int TERR, bool BOX>
+static cudaError_t launch_b(const RolloutArgs& a, int block, cudaStream_t st) {
+    return a.traj ? launch_t<TERR, true, BOX>(a, block, st) : launch_t<TERR, false, BOX>(a, block, st);
 }
 
 cudaError_t launch_rollout(const RolloutArgs& a, int block, cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
-    if (a.model.terrain == 1)
-        return a.traj ? launch_t<1, true>(a, block, st) : launch_t<1, false>(a, block, st);
-    return a.traj ? launch_t<0, true>(a, block, st) : launch_t<0, false>(a, block, st);
+    const bool box = a.model.has_box != 0;
+    if (a.model.terrain == 1) return box ? launch_b<1, true>(a, block, st) : launch_b<1, false>(a, block, st);
+    return box ? launch_b<0, true>(a, block, st) : launch_b<0, false>(a, block, st);
 }
 
 }  // namespace mppi

@@ -205,14 +205,19 @@ def config_terrain(K: int = 1024, H: int = 100, seed: int = 3) -> Workload:
 
 
 def config_push(K: int = 4096, H: int = 100, seed: int = 100, n_prop: int = 0) -> Workload:
-    """Box pushing: free 0.5 x 0.5 x 0.4 m, 3 kg box 0.6 m ahead; box goal
-    offset U(0.5, 1.5) m further forward."""
+    """Box pushing: free 0.5 x 0.5 x 0.4 m, 3 kg box whose centre starts 0.5 m
+    ahead of the trunk (near face 0.25 m ahead, within reach); box goal offset
+    U(0.5, 1.5) m further forward; the robot's position goal is the box's start
+    centre."""
     rng = np.random.default_rng(seed)
     dt = 0.005
-    goal = (0.6 + rng.uniform(0.5, 1.5), 0.0)
-    return Workload("push_K%d_H%d" % (K, H), robot(box=True), cost("push", box_goal=goal),
+    bx = 0.5
+    goal = (bx + rng.uniform(0.5, 1.5), 0.0)
+    c = cost("push", box_goal=goal)
+    c["goal_xy"] = (bx, 0.0)
+    return Workload("push_K%d_H%d" % (K, H), robot(box=True), c,
                     mppi(K, H, dt, 0.3, n_sub_for(dt), seed=0, n_prop=n_prop),
-                    stand_state(box_xy=(0.6, 0.0)), stand_mu(), 100, dict(goal=goal))
+                    stand_state(box_xy=(bx, 0.0)), stand_mu(), 100, dict(goal=goal))
 
 
 def multi_instance_mix(n: int = 16, seed: int = 2):

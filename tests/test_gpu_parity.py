@@ -16,7 +16,8 @@ import oracle as O  # noqa: E402
 from paper_2409_10469_gb300 import _mppi, workloads as W  # noqa: E402
 
 BLOCKS = {"pos": slice(0, 3), "quat": slice(3, 7), "joints": slice(7, 19), "w": slice(19, 22),
-          "v": slice(22, 25), "qd": slice(25, 37)}
+          "v": slice(22, 25), "qd": slice(25, 37), "box_pos": slice(37, 40), "box_quat": slice(40, 44),
+          "box_w": slice(44, 47), "box_v": slice(47, 50)}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -35,6 +36,8 @@ def rel_block(a, b):
     """per-block |a-b|_inf / max(|b|_inf, 1) (reading O17), max over blocks"""
     out = {}
     for name, sl in BLOCKS.items():
+        if sl.start >= a.shape[-1]:
+            continue
         d = np.abs(a[..., sl] - b[..., sl]).max(-1)
         s = np.maximum(np.abs(b[..., sl]).max(-1), 1.0)
         out[name] = d / s
@@ -85,6 +88,11 @@ def test_sample_host_output():
     assert np.array_equal(Uh, O.sample(m, cfg.mu0, 2))
 
 
+def config(which):
+    return {"stand": W.config_stand, "trot": W.config_trot, "terrain": W.config_terrain,
+            "push": W.config_push}[which]()
+
+
 def visited_states(cfg, n, seed, H=None):
     """n states the oracle's own MPPI rollouts of this workload pass through
     (sampled over samples and time), as FP32: the distribution the kernels see."""
@@ -100,7 +108,7 @@ def visited_states(cfg, n, seed, H=None):
     return tr[ks, ts].astype(np.float32), U[ks], ts
 
 
-STRICT = ("pos", "quat", "joints", "v")
+STRICT = ("pos", "quat", "joints", "v", "box_pos", "box_quat")
 
 
 def floor_bound(e_gpu, e_f32, strict=STRICT, max_factor=2.0):
@@ -118,7 +126,7 @@ def floor_bound(e_gpu, e_f32, strict=STRICT, max_factor=2.0):
     return bad
 
 
-@pytest.mark.parametrize("which", ["stand", "trot"])
+@pytest.mark.parametrize("which", ["stand", "trot", "push"])
 def test_one_step_state_parity(which):
     """one dt step (n_sub sub-steps) from 400 identical FP32 states that MPPI
     rollouts visit (contacts, swing legs, falls).  Position, attitude, joints
@@ -126,11 +134,12 @@ def test_one_step_state_parity(which):
     FP32 floor of the stiff contact model (k pen amplifies the ~3e-8 m rounding
     of foot heights) and must stay within 2x that floor, measured by the same
     oracle source compiled in float."""
-    cfg = W.config_stand() if which == "stand" else W.config_trot()
+    cfg = config(which)
     n = 400
     X, U, ts = visited_states(cfg, n, 3)
+    nx = X.shape[1]
     ctl, m = ctl_for(cfg, K=n, H=2)
-    traj = torch.empty((n, 3, 37), device="cuda")
+    traj = torch.empty((n, 3, nx), device="cuda")
     L = torch.empty(n, device="cuda")
     ctl.rollouts(dev(X), U=dev(U), n=n, t0=0.0, L_out=L, traj_out=traj, x0_per_sample=True)
     tg = traj.cpu().numpy()
@@ -152,7 +161,7 @@ def teacher_forced(cfg, K, H, t0=0.0):
     ctl.set_nominal(cfg.mu0)
     U = torch.empty((K, 48), device="cuda")
     ctl.sample(4, out=U)
-    nx = 37
+    nx = len(cfg.x0)
     traj = torch.empty((K, H + 1, nx), device="cuda")
     L = torch.empty(K, device="cuda")
     x0 = cfg.x0.astype(np.float32)
@@ -178,7 +187,7 @@ def teacher_forced(cfg, K, H, t0=0.0):
     return step_err, cost_rel
 
 
-@pytest.mark.parametrize("which", ["stand", "trot", "terrain"])
+@pytest.mark.parametrize("which", ["stand", "trot", "terrain", "push"])
 def test_rollout_teacher_forced(which):
     """every dt step of every GPU rollout matches the oracle stepped from the same
     FP32 state; the GPU's accumulated cost matches the oracle's L_walk evaluated
@@ -187,8 +196,10 @@ def test_rollout_teacher_forced(which):
         cfg, K, H, t0 = W.config_stand(), 100, 50, 0.0
     elif which == "trot":
         cfg, K, H, t0 = W.config_trot(), 66, 100, 0.37
-    else:
+    elif which == "terrain":
         cfg, K, H, t0 = W.config_terrain(), 40, 60, 0.0
+    else:
+        cfg, K, H, t0 = W.config_push(), 40, 100, 0.0
     (e_gpu, e_f32), cost_rel = teacher_forced(cfg, K, H, t0)
     assert cost_rel.max() <= 1e-5, cost_rel.max()
     # on the heightfield a foot crossing a cell edge meets a slope jump (bilinear
@@ -199,7 +210,7 @@ def test_rollout_teacher_forced(which):
     assert not bad, bad
 
 
-@pytest.mark.parametrize("which", ["stand", "trot", "terrain"])
+@pytest.mark.parametrize("which", ["stand", "trot", "terrain", "push"])
 def test_rollout_cost_parity(which):
     """full-horizon rollout cost (spec bound): <= 1e-3 relative for every
     sample, on the model spec's well-conditioned sub-step"""
@@ -207,8 +218,10 @@ def test_rollout_cost_parity(which):
         cfg, K, H, t0 = W.config_stand(), 100, 50, 0.0
     elif which == "trot":
         cfg, K, H, t0 = W.config_trot(), 130, 100, 0.37
-    else:
+    elif which == "terrain":
         cfg, K, H, t0 = W.config_terrain(), 96, 60, 0.0
+    else:
+        cfg, K, H, t0 = W.config_push(), 96, 100, 0.0
     ctl, m = ctl_for(cfg, K=K, H=H)
     ctl.set_nominal(cfg.mu0)
     U = torch.empty((K, 48), device="cuda")
@@ -222,12 +235,13 @@ def test_rollout_cost_parity(which):
     Lo = O.rollouts(world, cfg.cost, m, t0, x0d, U.cpu().numpy())
     rel = np.abs(Lg - Lo) / np.maximum(np.abs(Lo), 1.0)
     assert np.all(np.isfinite(Lg))
-    if which != "terrain":
+    if which in ("stand", "trot"):
         assert rel.max() <= 1e-3, (rel.max(), np.percentile(rel, 99))
     else:
-        # a bilinear heightfield's slope jumps at cell edges: a rollout whose
-        # foot crosses one at the wrong moment is not determined to 1e-3 even in
-        # FP64; bound every sample by max(1e-3, 3x its own FP64 sensitivity)
+        # a bilinear heightfield's slope jumps at cell edges, a box's normal jumps
+        # at its edges: a rollout that crosses one at the wrong moment is not
+        # determined to 1e-3 even in FP64; bound every sample by max(1e-3, 3x its
+        # own FP64 sensitivity)
         sens = np.zeros(K)
         for sd in range(2):
             xp = x0d * (1 + 1e-7 * np.random.default_rng(sd).standard_normal(x0d.shape))
