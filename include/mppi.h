@@ -199,6 +199,47 @@ mppi_status mppi_batch_autotune(mppi_batch b, const float* x0s, int trials, int*
 /* Number of graph launches (one per mppi_batch_step). */
 mppi_status mppi_batch_launch_count(mppi_batch b, uint64_t* count);
 
+/* ------------------------------------------------------------------ serving
+ * Continuous batching of control-step requests from many robots.  A robot is a
+ * controller handle (its nominal stays on the device between requests).  The
+ * server admits queued requests in arrival order while their workspace (K x 49
+ * floats per solve) fits a device pool of budget_bytes, launches the admitted
+ * set as one persistent multi-instance step on one of two streams (so requests
+ * admitted while another launch runs overlap with it on the GPU), and retires
+ * launches when their completion event fires.  A robot's control is the same
+ * alone and in any mix.  All calls are host-side and non-blocking except
+ * drain; tick must be called to make progress (it never waits on the GPU). */
+typedef struct mppi_server_s* mppi_server;
+
+typedef struct {
+    uint64_t submitted, completed, launches, busy_rejects, queued, in_flight;
+    uint64_t pool_bytes, pool_in_use, pool_peak;
+    double rollout_steps;                          /* sum of K * H over completed requests */
+    double latency_p50, latency_p99, latency_max;  /* seconds, submit -> observed completion */
+} mppi_server_stats_t;
+
+/* budget_bytes: device pool for solve workspace; max_robots; max_samples: the
+ * largest K of any robot.  Errors: ARG, OOM. */
+mppi_status mppi_server_create(size_t budget_bytes, int max_robots, int max_samples, mppi_server* out);
+mppi_status mppi_server_destroy(mppi_server s);
+const char* mppi_server_last_error(mppi_server s);
+/* Register a robot (its handle must outlive the server).  ARG if one of its
+ * solves alone exceeds the budget. */
+mppi_status mppi_server_add_robot(mppi_server s, mppi_handle h, int* robot_id);
+/* Queue one control step of `robot` from host state x0 (float[nx]) at control
+ * index `step`.  BUSY if the robot already has a request queued or in flight;
+ * NONFINITE if x0 is not finite. */
+mppi_status mppi_server_submit(mppi_server s, int robot, const float* x0, uint32_t step);
+/* Retire finished launches, admit and launch queued requests. */
+mppi_status mppi_server_tick(mppi_server s, int* completed);
+/* ready = 1 and the control (float[12]) and submit-to-completion latency when a
+ * new result is waiting; ready = 0 otherwise. */
+mppi_status mppi_server_poll(mppi_server s, int robot, float* u0_out, double* latency_s, int* ready);
+mppi_status mppi_server_stats(mppi_server s, mppi_server_stats_t* out);
+mppi_status mppi_server_reset_stats(mppi_server s);
+/* Block until every queued and in-flight request has completed. */
+mppi_status mppi_server_drain(mppi_server s);
+
 /* The update of mppi_update (Eq. 1 + Eq. 2 + apply + shift) without a handle and
  * without allocating anything.  The paper has no counterpart: this is for
  * callers that must not allocate device memory when they run -- a hard

@@ -27,7 +27,10 @@ EXPORTS = ("mppi_create", "mppi_destroy", "mppi_last_error", "mppi_set_nominal",
            "mppi_set_timing", "mppi_get_timings", "mppi_launch_count", "mppi_state_size",
            "mppi_update_noalloc", "mppi_batch_create", "mppi_batch_destroy",
            "mppi_batch_last_error", "mppi_batch_step", "mppi_batch_set_shape", "mppi_batch_get_shape",
-           "mppi_batch_autotune", "mppi_batch_launch_count")
+           "mppi_batch_autotune", "mppi_batch_launch_count", "mppi_server_create",
+           "mppi_server_destroy", "mppi_server_last_error", "mppi_server_add_robot", "mppi_server_submit",
+           "mppi_server_tick", "mppi_server_poll", "mppi_server_stats", "mppi_server_reset_stats",
+           "mppi_server_drain")
 
 
 class MppiError(RuntimeError):
@@ -81,6 +84,12 @@ class MppiConfig(C.Structure):
     ]
 
 
+class ServerStats(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("submitted", "completed", "launches", "busy_rejects", "queued",
+                                          "in_flight", "pool_bytes", "pool_in_use", "pool_peak")] + \
+               [(n, C.c_double) for n in ("rollout_steps", "latency_p50", "latency_p99", "latency_max")]
+
+
 _lib = None
 
 
@@ -118,10 +127,22 @@ def lib():
         L.mppi_batch_autotune.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                           C.POINTER(C.c_float)]
         L.mppi_batch_launch_count.argtypes = [vp, C.POINTER(C.c_uint64)]
+        L.mppi_server_create.argtypes = [C.c_size_t, C.c_int, C.c_int, C.POINTER(C.c_void_p)]
+        L.mppi_server_destroy.argtypes = [vp]
+        L.mppi_server_last_error.argtypes = [vp]
+        L.mppi_server_last_error.restype = C.c_char_p
+        L.mppi_server_add_robot.argtypes = [vp, vp, C.POINTER(C.c_int)]
+        L.mppi_server_submit.argtypes = [vp, C.c_int, vp, C.c_uint32]
+        L.mppi_server_tick.argtypes = [vp, C.POINTER(C.c_int)]
+        L.mppi_server_poll.argtypes = [vp, C.c_int, vp, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+        L.mppi_server_stats.argtypes = [vp, C.POINTER(ServerStats)]
+        L.mppi_server_reset_stats.argtypes = [vp]
+        L.mppi_server_drain.argtypes = [vp]
         L.mppi_state_size.argtypes = [vp]
         L.mppi_state_size.restype = C.c_int
         for name in EXPORTS:
-            if name not in ("mppi_last_error", "mppi_state_size", "mppi_batch_last_error"):
+            if name not in ("mppi_last_error", "mppi_state_size", "mppi_batch_last_error",
+                            "mppi_server_last_error"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -330,3 +351,64 @@ class Batch:
         c = C.c_uint64()
         self._check(lib().mppi_batch_launch_count(self.b, C.byref(c)))
         return c.value
+
+
+class Server:
+    """Continuous-batching serving runtime (mppi_server_*)."""
+
+    def __init__(self, budget_bytes: int, max_robots: int, max_samples: int):
+        s = C.c_void_p()
+        rc = lib().mppi_server_create(budget_bytes, max_robots, max_samples, C.byref(s))
+        if rc != MPPI_OK:
+            raise MppiError(rc, "mppi_server_create failed")
+        self.s = s
+        self.robots = []
+
+    def _check(self, rc, ok=(MPPI_OK,)):
+        if rc not in ok:
+            raise MppiError(rc, lib().mppi_server_last_error(self.s).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "s", None):
+            lib().mppi_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_robot(self, ctl: "Controller") -> int:
+        rid = C.c_int()
+        self._check(lib().mppi_server_add_robot(self.s, ctl.h, C.byref(rid)))
+        self.robots.append(ctl)
+        return rid.value
+
+    def submit(self, robot: int, x0, step: int) -> int:
+        x = np.ascontiguousarray(x0, dtype=np.float32)
+        return self._check(lib().mppi_server_submit(self.s, robot, _ptr(x), step),
+                           ok=(MPPI_OK, MPPI_ERR_BUSY))
+
+    def tick(self) -> int:
+        n = C.c_int()
+        self._check(lib().mppi_server_tick(self.s, C.byref(n)))
+        return n.value
+
+    def poll(self, robot: int):
+        u0 = np.zeros(12, np.float32)
+        lat, ready = C.c_double(), C.c_int()
+        self._check(lib().mppi_server_poll(self.s, robot, _ptr(u0), C.byref(lat), C.byref(ready)))
+        return (u0, lat.value) if ready.value else None
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        self._check(lib().mppi_server_stats(self.s, C.byref(st)))
+        return {n: getattr(st, n) for n, _ in ServerStats._fields_}
+
+    def reset_stats(self):
+        self._check(lib().mppi_server_reset_stats(self.s))
+
+    def drain(self):
+        self._check(lib().mppi_server_drain(self.s))

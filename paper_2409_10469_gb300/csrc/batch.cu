@@ -28,6 +28,7 @@
 #include <string>
 #include <vector>
 
+#include "batch.cuh"
 #include "handle.h"
 #include "noise.cuh"
 #include "rollout.cuh"
@@ -35,38 +36,6 @@
 using namespace mppi;
 
 namespace mppi {
-
-struct InstDesc {
-    DevModel model;
-    DevCost cost;
-    float* mu;            // nominal knots, updated in place (shifted)
-    float* mu_upd;        // updated mean before the shift
-    float* u0;            // applied control
-    float* U;             // [K][48] sampled knots
-    float* L;             // [K] costs
-    int* status;          // 0 ok, 4 all costs non-finite
-    const float* mu_prop; // proposal mean or null
-    int K, H, n_sub, n_prop, ctrl_steps, nx, gait;
-    float h, dt, inv_Hm1, arm, inv_lambda;
-    double dt_d, period_d;
-    float sigma[D], q_lo[3], q_hi[3];
-    uint32_t key0, key1, inst_id;
-};
-
-struct WorkItem {
-    int inst, k0, n;
-};
-
-struct BatchArgs {
-    const InstDesc* desc;
-    const WorkItem* items;
-    const int* n_items;
-    int* next;
-    unsigned* done;
-    const float* x0s;       // [n_inst][NX_BOX]
-    const uint32_t* steps;  // [n_inst] control-step index of each instance
-    float* u0s;             // [n_inst][12]
-};
 
 // this lane's 12 knots of sample k (the leg's 3 joints at the 4 knots), and
 // write them to U[k]; the same formula as k_sample, element by element
@@ -232,7 +201,7 @@ static cudaError_t launch_batch_t(const BatchArgs& a, int grid, cudaStream_t st)
     return cudaGetLastError();
 }
 
-static cudaError_t launch_batch(const BatchArgs& a, int block, int grid, cudaStream_t st) {
+cudaError_t launch_batch(const BatchArgs& a, int block, int grid, cudaStream_t st) {
     switch (block) {
         case 64: return launch_batch_t<64>(a, grid, st);
         case 128: return launch_batch_t<128>(a, grid, st);
@@ -241,7 +210,7 @@ static cudaError_t launch_batch(const BatchArgs& a, int block, int grid, cudaStr
     }
 }
 
-static int max_blocks_per_sm(int block) {
+int max_blocks_per_sm(int block) {
     int n = 0;
     cudaError_t e = cudaErrorInvalidValue;
     if (block == 64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<64>, 64, 0);
@@ -300,7 +269,7 @@ static bool dev_ptr(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-static InstDesc make_desc(mppi_handle h) {
+InstDesc mppi::make_desc(const mppi_handle_s* h) {
     InstDesc d;
     memset(&d, 0, sizeof(d));
     d.model = h->dm;

@@ -1,0 +1,90 @@
+"""Serving loop over the C ABI's continuous-batching runtime (mppi_server_*).
+
+Simulated robots issue control-step requests at Poisson times; the loop
+submits each request at its arrival time (or as soon as the robot's previous
+request has completed), keeps calling the runtime's tick, and records every
+request's latency from its arrival to its observed completion.  All GPU work
+(sampling, rollouts, updates of every admitted request) runs in the library's
+persistent multi-instance kernel; this module only schedules host calls.
+"""
+from __future__ import annotations
+
+import collections
+import time
+
+import numpy as np
+
+from . import _mppi
+from . import workloads as W
+
+
+def build_robots(n_robots, seed, K_range=(512, 8192), H_range=(50, 150)):
+    """Controllers of the serving workload (per-robot task, K, H); each robot has
+    its own Philox stream (instance id = robot index)."""
+    specs = W.serving_robots(n_robots, seed, K_range, H_range)
+    ctls, x0s = [], []
+    for r, (task, K, H) in enumerate(specs):
+        cfg = W.task_config(task, K, H)
+        m = dict(cfg.mppi, inst=r)
+        c = _mppi.Controller(cfg.robot, cfg.cost, m)
+        c.set_nominal(cfg.mu0)
+        ctls.append(c)
+        x0s.append(cfg.x0.astype(np.float32))
+    return specs, ctls, x0s
+
+
+def run(n_robots=64, rate_hz=50.0, duration=1.0, seed=4, budget_bytes=512 << 20,
+        K_range=(512, 8192), H_range=(50, 150), warmup=0.1):
+    """Serve Poisson arrivals for `duration` s; returns a metrics dict."""
+    specs, ctls, x0s = build_robots(n_robots, seed, K_range, H_range)
+    server = _mppi.Server(budget_bytes, n_robots, max(K for _, K, _ in specs))
+    rids = [server.add_robot(c) for c in ctls]
+    arrivals = W.serving_arrivals(n_robots, rate_hz, duration + warmup, seed)
+    pending = collections.deque(arrivals)
+    waiting = {r: collections.deque() for r in range(n_robots)}  # arrived, not yet submitted
+    inflight = {}                                                # robot -> arrival time
+    steps = np.zeros(n_robots, np.int64)
+    lat, done_rs = [], 0.0
+    t0 = time.perf_counter()
+    while pending or any(waiting.values()) or inflight:
+        now = time.perf_counter() - t0
+        while pending and pending[0][0] <= now:
+            t_arr, r = pending.popleft()
+            waiting[r].append(t_arr)
+        for r in range(n_robots):
+            if waiting[r] and r not in inflight:
+                t_arr = waiting[r].popleft()
+                server.submit(rids[r], x0s[r], int(steps[r]))
+                steps[r] += 1
+                inflight[r] = t_arr
+        server.tick()
+        for r in list(inflight):
+            res = server.poll(rids[r])
+            if res is not None:
+                t_arr = inflight.pop(r)
+                t_done = time.perf_counter() - t0
+                if t_arr >= warmup:
+                    lat.append(t_done - t_arr)
+                    _, K, H = specs[r]
+                    done_rs += K * H
+        if not pending and not any(waiting.values()) and not inflight:
+            break
+    elapsed = time.perf_counter() - t0 - warmup
+    st = server.stats()
+    lat = np.array(lat)
+    offered = sum(K * H for t, r in arrivals if t >= warmup for (_, K, H) in [specs[r]])
+    out = {
+        "requests": int(len(lat)), "robots": n_robots, "rate_hz_per_robot": rate_hz,
+        "duration_s": duration, "elapsed_s": elapsed,
+        "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
+                       "p99": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
+                       "max": float(lat.max() * 1e3) if len(lat) else None},
+        "rollout_steps_per_s": done_rs / max(elapsed, 1e-9),
+        "offered_rollout_steps_per_s": offered / duration,
+        "launches": int(st["launches"]), "pool_peak_bytes": int(st["pool_peak"]),
+        "budget_bytes": int(budget_bytes),
+    }
+    server.close()
+    for c in ctls:
+        c.close()
+    return out

@@ -228,19 +228,30 @@ def multi_instance_mix(n: int = 16, seed: int = 2):
     return [(int(k), int(h)) for k, h in zip(Ks, Hs)]
 
 
+def serving_robots(n_robots: int = 64, seed: int = 4, K_range=(512, 8192), H_range=(50, 150)):
+    """Per-robot (task, K, H) of the serving workload: tasks cycle through
+    stand / trot / terrain / push, K ~ U{512..8192}, H ~ U{50..150}."""
+    rng = np.random.default_rng(seed)
+    tasks = ["stand", "trot", "terrain", "push"]
+    return [(tasks[r % len(tasks)], int(rng.integers(K_range[0], K_range[1] + 1)),
+             int(rng.integers(H_range[0], H_range[1] + 1))) for r in range(n_robots)]
+
+
 def serving_arrivals(n_robots: int = 64, rate_hz: float = 50.0, duration: float = 1.0,
                      seed: int = 4):
-    """Poisson arrivals per robot: list of (t, robot, K, H, task), sorted by t."""
-    rng = np.random.default_rng(seed)
+    """Poisson request times of every robot over `duration` seconds:
+    sorted list of (t, robot)."""
+    rng = np.random.default_rng(seed + 1000)
     out = []
-    tasks = ["stand", "trot", "terrain", "push"]
-    robot_task = [tasks[i % len(tasks)] for i in range(n_robots)]
     for r in range(n_robots):
         t = rng.exponential(1.0 / rate_hz)
         while t < duration:
-            K = int(rng.integers(512, 8193))
-            H = int(rng.integers(50, 151))
-            out.append((t, r, K, H, robot_task[r]))
+            out.append((t, r))
             t += rng.exponential(1.0 / rate_hz)
     out.sort()
     return out
+
+
+def task_config(task: str, K: int, H: int) -> "Workload":
+    return {"stand": config_stand, "trot": config_trot, "terrain": config_terrain,
+            "push": config_push}[task](K=K, H=H)

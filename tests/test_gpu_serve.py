@@ -1,0 +1,116 @@
+"""Serving runtime (mppi_server_*): a robot's control is bit-identical alone and
+inside a busy mix of concurrent requests, and within the update tolerance of the
+single-instance step; admission respects the memory budget; a second request
+for a busy robot is refused."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2409_10469_gb300 import _mppi, workloads as W  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def robot(task, K, H, inst):
+    cfg = W.task_config(task, K, H)
+    c = _mppi.Controller(cfg.robot, cfg.cost, dict(cfg.mppi, inst=inst))
+    c.set_nominal(cfg.mu0)
+    return c, cfg
+
+
+def ws_bytes(K):
+    al = lambda x: (x + 255) // 256 * 256
+    return al(K * 48 * 4) + al(K * 4)
+
+
+def test_result_same_alone_and_in_the_mix():
+    # alone
+    srv = _mppi.Server(64 << 20, 4, 2048)
+    x, cfg = robot("trot", 700, 80, inst=5)
+    rid = srv.add_robot(x)
+    outs_alone = []
+    for step in range(2):
+        srv.submit(rid, cfg.x0, step)
+        srv.drain()
+        u0, lat = srv.poll(rid)
+        outs_alone.append(u0)
+    # in a mix of 24 robots with concurrent requests, twice
+    specs = W.serving_robots(23, seed=11, K_range=(256, 2048), H_range=(50, 150))
+    srv2 = _mppi.Server(256 << 20, 24, 2048)
+    others = []
+    for i, (task, K, H) in enumerate(specs):
+        c, cf = robot(task, K, H, inst=100 + i)
+        others.append((srv2.add_robot(c), c, cf))
+    x2, cfg2 = robot("trot", 700, 80, inst=5)
+    rid2 = srv2.add_robot(x2)
+    for step in range(2):
+        for j, (r, c, cf) in enumerate(others[: 12]):
+            srv2.submit(r, cf.x0, step)
+        srv2.tick()
+        srv2.submit(rid2, cfg2.x0, step)       # arrives while others are on the GPU
+        for j, (r, c, cf) in enumerate(others[12:]):
+            srv2.submit(r, cf.x0, step)
+        srv2.drain()
+        u0, lat = srv2.poll(rid2)
+        assert np.array_equal(u0.view(np.uint32), outs_alone[step].view(np.uint32)), step
+        for r, c, cf in others:
+            assert srv2.poll(r) is not None
+    assert np.array_equal(x.get_nominal(), x2.get_nominal())
+    st = srv2.stats()
+    assert st["completed"] == 48 and st["launches"] >= 2
+    # and close to the single-instance step of the same robot
+    single, cfg3 = robot("trot", 700, 80, inst=5)
+    u0s = np.zeros(12, np.float32)
+    single.step(cfg3.x0.astype(np.float32), 0, u0_out=u0s)
+    assert np.max(np.abs(u0s - outs_alone[0]) / np.maximum(np.abs(u0s), 1)) <= 1e-6
+
+
+def test_admission_by_memory_budget():
+    K = 1024
+    budget = 2 * ws_bytes(K) + 100        # room for two solves at a time
+    srv = _mppi.Server(budget, 6, K)
+    rs = []
+    for i in range(6):
+        c, cfg = robot("stand", K, 50, inst=i)
+        rs.append((srv.add_robot(c), c, cfg))
+    for r, c, cfg in rs:
+        srv.submit(r, cfg.x0, 0)
+    srv.tick()
+    st = srv.stats()
+    assert st["in_flight"] <= 2 and st["queued"] >= 4 and st["pool_in_use"] <= budget
+    srv.drain()
+    st = srv.stats()
+    assert st["completed"] == 6 and st["pool_peak"] <= budget and st["pool_in_use"] == 0
+    # a robot whose single solve exceeds the budget is refused at registration
+    big, _ = robot("stand", 4 * K, 50, inst=9)
+    with pytest.raises(_mppi.MppiError):
+        srv.add_robot(big)
+
+
+def test_busy_robot_refused_until_done():
+    srv = _mppi.Server(32 << 20, 2, 512)
+    c, cfg = robot("stand", 512, 50, inst=1)
+    r = srv.add_robot(c)
+    assert srv.submit(r, cfg.x0, 0) == _mppi.MPPI_OK
+    assert srv.submit(r, cfg.x0, 1) == _mppi.MPPI_ERR_BUSY
+    srv.drain()
+    assert srv.poll(r) is not None
+    assert srv.submit(r, cfg.x0, 1) == _mppi.MPPI_OK
+    srv.drain()
+
+
+def test_serving_loop_small():
+    from paper_2409_10469_gb300 import serve
+    out = serve.run(n_robots=8, rate_hz=50.0, duration=0.3, K_range=(512, 1024), H_range=(50, 80),
+                    warmup=0.05)
+    assert out["requests"] > 0 and out["latency_ms"]["p99"] is not None
+    assert out["pool_peak_bytes"] <= out["budget_bytes"]
