@@ -240,6 +240,37 @@ mppi_status mppi_server_reset_stats(mppi_server s);
 /* Block until every queued and in-flight request has completed. */
 mppi_status mppi_server_drain(mppi_server s);
 
+/* ------------------------------------------------------------------ proposal network
+ * The learned sampling distribution that the paper leaves to future work
+ * (Sec. V-B; offline-learned distributions are cited in Sec. II-B): an MLP
+ * 62 -> 256 -> 256 -> 256 -> 48 with GELU (x Phi(x)), BF16 weights and activations,
+ * FP32 accumulation, trained and run on the tcgen05 tensor cores.  Parameters
+ * are one flat FP32 array: W1 [256][62], b1 [256], W2 [256][256], b2, W3 [256][256],
+ * b3, W4 [48][256], b4 [48] (row = output unit); the network keeps FP32 master
+ * copies and refreshes BF16 copies for its GEMMs. */
+typedef struct mppi_mlp_s* mppi_mlp;
+
+mppi_status mppi_mlp_create(int max_batch, mppi_mlp* out);
+mppi_status mppi_mlp_destroy(mppi_mlp net);
+const char* mppi_mlp_last_error(mppi_mlp net);
+long mppi_mlp_param_count(mppi_mlp net);
+/* params: float[param_count], host or device; resets the optimiser state. */
+mppi_status mppi_mlp_set_params(mppi_mlp net, const float* params, void* stream);
+mppi_status mppi_mlp_get_params(mppi_mlp net, float* params, void* stream);
+/* Y[B][48] = MLP(X[B][62]) (host or device buffers; B <= max_batch). */
+mppi_status mppi_mlp_forward(mppi_mlp net, const float* X, int B, float* Y, void* stream);
+/* One training step on (X[B][62], T[B][48]): mean-squared-error loss, backward
+ * pass on the tensor cores, AdamW (beta 0.9 / 0.999, eps 1e-8) when lr > 0.
+ * loss_out (float), grad_out (float[param_count], the gradient before the
+ * update) optional.  TIMEOUT if a tensor-core wait ran out. */
+mppi_status mppi_mlp_train_step(mppi_mlp net, const float* X, const float* T, int B, float lr,
+                                float weight_decay, float* loss_out, float* grad_out, void* stream);
+/* D[M][N] = A[M][K] B[N][K]^T with BF16 inputs (raw uint16 bits) and FP32
+ * accumulation on the tcgen05 tensor cores -- the network's GEMM; device
+ * buffers, N <= 256. */
+mppi_status mppi_tc_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int K,
+                              void* stream);
+
 /* The update of mppi_update (Eq. 1 + Eq. 2 + apply + shift) without a handle and
  * without allocating anything.  The paper has no counterpart: this is for
  * callers that must not allocate device memory when they run -- a hard

@@ -30,7 +30,9 @@ EXPORTS = ("mppi_create", "mppi_destroy", "mppi_last_error", "mppi_set_nominal",
            "mppi_batch_autotune", "mppi_batch_launch_count", "mppi_server_create",
            "mppi_server_destroy", "mppi_server_last_error", "mppi_server_add_robot", "mppi_server_submit",
            "mppi_server_tick", "mppi_server_poll", "mppi_server_stats", "mppi_server_reset_stats",
-           "mppi_server_drain")
+           "mppi_server_drain", "mppi_mlp_create", "mppi_mlp_destroy", "mppi_mlp_last_error",
+           "mppi_mlp_param_count", "mppi_mlp_set_params", "mppi_mlp_get_params", "mppi_mlp_forward",
+           "mppi_mlp_train_step", "mppi_tc_gemm_bf16")
 
 
 class MppiError(RuntimeError):
@@ -138,11 +140,22 @@ def lib():
         L.mppi_server_stats.argtypes = [vp, C.POINTER(ServerStats)]
         L.mppi_server_reset_stats.argtypes = [vp]
         L.mppi_server_drain.argtypes = [vp]
+        L.mppi_mlp_create.argtypes = [C.c_int, C.POINTER(C.c_void_p)]
+        L.mppi_mlp_destroy.argtypes = [vp]
+        L.mppi_mlp_last_error.argtypes = [vp]
+        L.mppi_mlp_last_error.restype = C.c_char_p
+        L.mppi_mlp_param_count.argtypes = [vp]
+        L.mppi_mlp_param_count.restype = C.c_long
+        L.mppi_mlp_set_params.argtypes = [vp, vp, vp]
+        L.mppi_mlp_get_params.argtypes = [vp, vp, vp]
+        L.mppi_mlp_forward.argtypes = [vp, vp, C.c_int, vp, vp]
+        L.mppi_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_float, C.c_float, vp, vp, vp]
+        L.mppi_tc_gemm_bf16.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, vp]
         L.mppi_state_size.argtypes = [vp]
         L.mppi_state_size.restype = C.c_int
         for name in EXPORTS:
             if name not in ("mppi_last_error", "mppi_state_size", "mppi_batch_last_error",
-                            "mppi_server_last_error"):
+                            "mppi_server_last_error", "mppi_mlp_last_error", "mppi_mlp_param_count"):
                 getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -412,3 +425,63 @@ class Server:
 
     def drain(self):
         self._check(lib().mppi_server_drain(self.s))
+
+
+class MLP:
+    """The proposal network (mppi_mlp_*): BF16 tcgen05 forward / backward, AdamW."""
+
+    IN, HID, OUT = 62, 256, 48
+
+    def __init__(self, max_batch: int, stream=None):
+        n = C.c_void_p()
+        rc = lib().mppi_mlp_create(max_batch, C.byref(n))
+        if rc != MPPI_OK:
+            raise MppiError(rc, "mppi_mlp_create failed")
+        self.n = n
+        self.stream = C.c_void_p(stream) if isinstance(stream, int) else stream
+        self.nparam = lib().mppi_mlp_param_count(n)
+
+    def _check(self, rc):
+        if rc != MPPI_OK:
+            raise MppiError(rc, lib().mppi_mlp_last_error(self.n).decode())
+
+    def close(self):
+        if getattr(self, "n", None):
+            lib().mppi_mlp_destroy(self.n)
+            self.n = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        self._check(lib().mppi_mlp_set_params(self.n, _ptr(np.ascontiguousarray(p, np.float32)
+                                                          if isinstance(p, np.ndarray) else p), self.stream))
+
+    def get_params(self):
+        out = np.zeros(self.nparam, np.float32)
+        self._check(lib().mppi_mlp_get_params(self.n, _ptr(out), self.stream))
+        return out
+
+    def forward(self, X, out=None):
+        X = np.ascontiguousarray(X, np.float32) if isinstance(X, np.ndarray) else X
+        B = X.shape[0]
+        out = np.zeros((B, self.OUT), np.float32) if out is None else out
+        self._check(lib().mppi_mlp_forward(self.n, _ptr(X), B, _ptr(out), self.stream))
+        return out
+
+    def train_step(self, X, T, lr=1e-3, weight_decay=0.0, grad=False):
+        X = np.ascontiguousarray(X, np.float32) if isinstance(X, np.ndarray) else X
+        T = np.ascontiguousarray(T, np.float32) if isinstance(T, np.ndarray) else T
+        loss = np.zeros(1, np.float32)
+        g = np.zeros(self.nparam, np.float32) if grad else None
+        self._check(lib().mppi_mlp_train_step(self.n, _ptr(X), _ptr(T), X.shape[0], lr, weight_decay,
+                                              _ptr(loss), _ptr(g), self.stream))
+        return (float(loss[0]), g) if grad else float(loss[0])
+
+
+def tc_gemm_bf16(A_bits, B_bits, M, N, K, D):
+    """D = A B^T on the tensor cores; A_bits, B_bits: device uint16 (BF16 bits)."""
+    return lib().mppi_tc_gemm_bf16(_ptr(A_bits), _ptr(B_bits), _ptr(D), M, N, K, None)

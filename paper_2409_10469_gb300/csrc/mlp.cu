@@ -1,0 +1,566 @@
+// mlp.cu -- the learned proposal network: a 62 -> 256 -> 256 -> 256 -> 48 MLP
+// with GELU, BF16 weights and activations, FP32 accumulation, trained and run on
+// the 5th-generation tensor cores (tcgen05, TMEM accumulators).
+//
+// The paper leaves better sampling distributions to future work (arXiv
+// 2409.10469, Sec. V-B) and cites learning one offline (Sec. II-B); this
+// network maps a robot + task state to a mean for the spline knots.  It is
+// trained on (state, updated mean) pairs from the plain controller and seeds
+// half of the samples; plain MPPI's samples stay in every step.
+//
+// Every layer is one GEMM D = A B^T (A: M x K activations, B: N x K weights,
+// both BF16, K-major in shared memory) on tcgen05 with a fused epilogue; the
+// backward pass uses the same kernel with transposed staging (dW = dZ^T H,
+// dH = dZ W).  One CTA of 4 warps owns a 128-row x NT-column output tile in
+// TMEM; operands are staged by the CTA's threads 64 k-elements at a time into
+// the core-matrix layout of tc.cuh; one thread issues the MMAs and commits them
+// to an mbarrier that every thread waits on (bounded).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mppi.h"
+#include "tc.cuh"
+
+using namespace mppi;
+
+namespace mppi {
+
+enum Epi { EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_GELU = 2, EPI_GELU_BWD = 3 };
+
+struct GemmArgs {
+    const __nv_bfloat16* A;
+    long a_sm, a_sk;  // A[m][k] = A[m * a_sm + k * a_sk]
+    const __nv_bfloat16* B;
+    long b_sn, b_sk;  // B[n][k] = B[n * b_sn + k * b_sk]
+    int M, N, K;
+    int epi;
+    const float* bias;        // [N]
+    const float* aux;         // pre-activation Z [M][ldaux] for EPI_GELU_BWD
+    long ldaux;
+    float* out;               // FP32 [M][ldo]
+    long ldo;
+    __nv_bfloat16* out_b;     // BF16 [M][ldob] (optional)
+    long ldob;
+    int* err;                 // set when a wait runs out
+};
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+// d/dz of z Phi(z) = Phi(z) + z phi(z)
+__device__ __forceinline__ float gelu_grad(float z) {
+    return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g) {
+    static_assert(NT % 16 == 0 && NT >= 32 && NT <= 256, "tile width");
+    constexpr uint32_t TCOLS = NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256));
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sA = smem;                       // 128 x 64 bf16 = 16 KB
+    unsigned char* sB = smem + 128 * tc::KCHUNK * 2;  // NT x 64 bf16
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * 128, n0 = blockIdx.y * NT;
+
+    if (warp == 0) tc::tmem_alloc(&tmem_base, TCOLS);
+    if (tid == 0) {
+        tc::mbar_init(&bar, 1);
+        s_fail = 0;
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = tc::idesc_bf16_f32(128, NT);
+    uint32_t phase = 0;
+    const int nk = (g.K + tc::KCHUNK - 1) / tc::KCHUNK;
+    for (int kc = 0; kc < nk; kc++) {
+        const int k0 = kc * tc::KCHUNK;
+        // stage A (128 x 64) and B (NT x 64), zero outside the matrices
+        for (int idx = tid; idx < 128 * tc::KCHUNK; idx += 128) {
+            int r, k;
+            if (g.a_sk == 1) { r = idx >> 6; k = idx & 63; } else { k = idx >> 7; r = idx & 127; }
+            const int gm = m0 + r, gk = k0 + k;
+            __nv_bfloat16 v = __float2bfloat16(0.f);
+            if (gm < g.M && gk < g.K) v = g.A[(long)gm * g.a_sm + (long)gk * g.a_sk];
+            *reinterpret_cast<__nv_bfloat16*>(sA + tc::tile_offset(r, k)) = v;
+        }
+        for (int idx = tid; idx < NT * tc::KCHUNK; idx += 128) {
+            int r, k;
+            if (g.b_sk == 1) { r = idx >> 6; k = idx & 63; } else { k = idx / NT; r = idx % NT; }
+            const int gn = n0 + r, gk = k0 + k;
+            __nv_bfloat16 v = __float2bfloat16(0.f);
+            if (gn < g.N && gk < g.K) v = g.B[(long)gn * g.b_sn + (long)gk * g.b_sk];
+            *reinterpret_cast<__nv_bfloat16*>(sB + tc::tile_offset(r, k)) = v;
+        }
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after();
+            const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+#pragma unroll
+            for (int ks = 0; ks < tc::KCHUNK / 16; ks++) {
+                const uint64_t ad = tc::smem_desc(a0 + ks * 2 * tc::CM_BYTES, tc::LBO, tc::SBO);
+                const uint64_t bd = tc::smem_desc(b0 + ks * 2 * tc::CM_BYTES, tc::LBO, tc::SBO);
+                tc::mma_bf16(tmem, ad, bd, idesc, (kc | ks) != 0);
+            }
+            tc::mma_commit(&bar);
+        }
+        // every thread waits for the MMAs (they read the staged tiles) before restaging
+        if (!tc::mbar_wait(&bar, phase, 1u << 22)) s_fail = 1;
+        phase ^= 1u;
+        __syncthreads();
+        if (s_fail) break;
+    }
+    tc::fence_after();
+    if (s_fail) {
+        if (tid == 0 && g.err) atomicExch(g.err, 1);
+    } else {
+        // epilogue: warp w owns rows 32w .. 32w + 31 (TMEM lanes)
+        const int m = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c = 0; c < NT / 16; c++) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 16), v);
+            if (m < g.M) {
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const int n = n0 + c * 16 + j;
+                    if (n >= g.N) break;
+                    float d = v[j];
+                    if (g.epi == EPI_BIAS || g.epi == EPI_BIAS_GELU) d += g.bias[n];
+                    if (g.epi == EPI_GELU_BWD) d *= gelu_grad(g.aux[(long)m * g.ldaux + n]);
+                    g.out[(long)m * g.ldo + n] = d;
+                    if (g.out_b) g.out_b[(long)m * g.ldob + n] = __float2bfloat16(g.epi == EPI_BIAS_GELU ? gelu(d) : d);
+                }
+            }
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, TCOLS);
+}
+
+static size_t gemm_smem(int nt) { return (size_t)(128 + nt) * tc::KCHUNK * 2; }
+
+static cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t st) {
+    const int nt = g.N <= 64 ? 64 : 256;
+    dim3 grid((g.M + 127) / 128, (g.N + nt - 1) / nt);
+    if (nt == 64) {
+        k_gemm_tc<64><<<grid, 128, gemm_smem(64), st>>>(g);
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_gemm_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem(256));
+            attr = true;
+        }
+        k_gemm_tc<256><<<grid, 128, gemm_smem(256), st>>>(g);
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- elementwise kernels
+
+// FP32 [B][in] -> BF16 [B][ld] (zero padding past `in`)
+__global__ void k_to_bf16(const float* x, int B, int in, int ld, __nv_bfloat16* y) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= (long)B * ld) return;
+    const int r = (int)(i / ld), c = (int)(i % ld);
+    y[i] = __float2bfloat16(c < in ? x[(long)r * in + c] : 0.f);
+}
+
+// mean-squared error over B x O: loss and dY = 2 (Y - T) / (B O), FP32 and BF16
+__global__ void k_mse(const float* Y, const float* T, int n, float scale, float* dY, __nv_bfloat16* dYb,
+                      float* loss) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float e = 0.f;
+    if (i < n) {
+        const float d = Y[i] - T[i];
+        dY[i] = 2.f * d * scale;
+        dYb[i] = __float2bfloat16(2.f * d * scale);
+        e = d * d * scale;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, e);
+}
+
+// column sums of dZ [B][N] (bias gradients), one thread per column, fixed order
+__global__ void k_colsum(const float* dZ, int B, int N, long ld, float* db) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float s = 0.f;
+    for (int b = 0; b < B; b++) s += dZ[(long)b * ld + n];
+    db[n] = s;
+}
+
+// AdamW on FP32 master parameters, refreshing the BF16 weight copies
+__global__ void k_adamw(float* p, const float* g, float* m1, float* m2, long n, float lr, float b1, float b2,
+                        float eps, float wd, float c1, float c2, const long* wofs, const long* wlen,
+                        __nv_bfloat16* const* wb, int nw, const int* wcols, const int* wld) {
+    const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float a = b1 * m1[i] + (1.f - b1) * gi;
+    const float v = b2 * m2[i] + (1.f - b2) * gi * gi;
+    m1[i] = a;
+    m2[i] = v;
+    const float pi = p[i] - lr * ((a / c1) / (sqrtf(v / c2) + eps) + wd * p[i]);
+    p[i] = pi;
+    for (int w = 0; w < nw; w++)
+        if (i >= wofs[w] && i < wofs[w] + wlen[w]) {
+            const long j = i - wofs[w];
+            const int r = (int)(j / wcols[w]), c = (int)(j % wcols[w]);
+            wb[w][(long)r * wld[w] + c] = __float2bfloat16(pi);
+        }
+}
+
+}  // namespace mppi
+
+// ---------------------------------------------------------------- host object
+
+namespace {
+
+constexpr int IN = 62, IN_PAD = 64, HID = 256, OUT = 48;
+constexpr int NL = 4;
+const int LIN[NL] = {IN, HID, HID, HID};
+const int LOUT[NL] = {HID, HID, HID, OUT};
+const int LLD[NL] = {IN_PAD, HID, HID, HID};  // leading dimension of each layer's BF16 input / weight rows
+
+}  // namespace
+
+struct mppi_mlp_s {
+    int max_batch = 0;
+    long nparam = 0;
+    long wofs[NL], bofs[NL];
+    float *d_p = nullptr, *d_g = nullptr, *d_m1 = nullptr, *d_m2 = nullptr;
+    __nv_bfloat16* d_wb[NL] = {nullptr};      // BF16 weights [out][ld]
+    __nv_bfloat16* d_hb[NL + 1] = {nullptr};  // BF16 activations: input [B][64], hidden [B][256]
+    float* d_z[NL] = {nullptr};               // FP32 pre-activations [B][out]
+    float* d_dz = nullptr;                    // FP32 dZ scratch [B][256]
+    __nv_bfloat16* d_dzb = nullptr;           // BF16 dZ [B][256]
+    __nv_bfloat16* d_dhb = nullptr;           // BF16 next dZ [B][256]
+    float* d_dh = nullptr;                    // FP32 [B][256]
+    float *d_T = nullptr, *d_X = nullptr, *d_loss = nullptr;
+    int* d_err = nullptr;
+    long *d_wofs = nullptr, *d_wlen = nullptr;
+    int *d_wcols = nullptr, *d_wld = nullptr;
+    __nv_bfloat16** d_wbp = nullptr;
+    int step = 0;
+    std::string err;
+};
+
+static mppi_status mfail(mppi_mlp n, mppi_status s, const std::string& m) {
+    if (n) n->err = m;
+    return s;
+}
+#define MCK(call)                                                                                   \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) return mfail(net, MPPI_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+static bool mdev(const void* p) {
+    cudaPointerAttributes at;
+    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+extern "C" mppi_status mppi_mlp_create(int max_batch, mppi_mlp* out) {
+    if (!out || max_batch < 1) return MPPI_ERR_ARG;
+    mppi_mlp net = new mppi_mlp_s();
+    net->max_batch = max_batch;
+    long o = 0;
+    for (int l = 0; l < NL; l++) {
+        net->wofs[l] = o;
+        o += (long)LOUT[l] * LIN[l];
+        net->bofs[l] = o;
+        o += LOUT[l];
+    }
+    net->nparam = o;
+    const long B = max_batch;
+    bool ok = cudaMalloc((void**)&net->d_p, o * 4) == cudaSuccess && cudaMalloc((void**)&net->d_g, o * 4) == cudaSuccess &&
+              cudaMalloc((void**)&net->d_m1, o * 4) == cudaSuccess && cudaMalloc((void**)&net->d_m2, o * 4) == cudaSuccess;
+    for (int l = 0; ok && l < NL; l++) {
+        ok = cudaMalloc((void**)&net->d_wb[l], (size_t)LOUT[l] * LLD[l] * 2) == cudaSuccess &&
+             cudaMemset(net->d_wb[l], 0, (size_t)LOUT[l] * LLD[l] * 2) == cudaSuccess &&
+             cudaMalloc((void**)&net->d_z[l], (size_t)B * LOUT[l] * 4) == cudaSuccess;
+    }
+    for (int l = 0; ok && l <= NL; l++) {
+        const int w = l == 0 ? IN_PAD : (l == NL ? OUT : HID);
+        ok = cudaMalloc((void**)&net->d_hb[l], (size_t)B * w * 2) == cudaSuccess;
+    }
+    ok = ok && cudaMalloc((void**)&net->d_dz, B * HID * 4) == cudaSuccess &&
+         cudaMalloc((void**)&net->d_dzb, B * HID * 2) == cudaSuccess &&
+         cudaMalloc((void**)&net->d_dhb, B * HID * 2) == cudaSuccess &&
+         cudaMalloc((void**)&net->d_dh, B * HID * 4) == cudaSuccess &&
+         cudaMalloc((void**)&net->d_T, B * OUT * 4) == cudaSuccess &&
+         cudaMalloc((void**)&net->d_X, B * IN * 4) == cudaSuccess &&
+         cudaMalloc((void**)&net->d_loss, 4) == cudaSuccess && cudaMalloc((void**)&net->d_err, 4) == cudaSuccess &&
+         cudaMalloc((void**)&net->d_wofs, NL * 8) == cudaSuccess && cudaMalloc((void**)&net->d_wlen, NL * 8) == cudaSuccess &&
+         cudaMalloc((void**)&net->d_wcols, NL * 4) == cudaSuccess && cudaMalloc((void**)&net->d_wld, NL * 4) == cudaSuccess &&
+         cudaMalloc((void**)&net->d_wbp, NL * sizeof(void*)) == cudaSuccess;
+    if (ok) {
+        long wo[NL], wl[NL];
+        int wc[NL], wd[NL];
+        for (int l = 0; l < NL; l++) {
+            wo[l] = net->wofs[l];
+            wl[l] = (long)LOUT[l] * LIN[l];
+            wc[l] = LIN[l];
+            wd[l] = LLD[l];
+        }
+        ok = cudaMemcpy(net->d_wofs, wo, sizeof(wo), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(net->d_wlen, wl, sizeof(wl), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(net->d_wcols, wc, sizeof(wc), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(net->d_wld, wd, sizeof(wd), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(net->d_wbp, net->d_wb, sizeof(net->d_wb), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemset(net->d_m1, 0, o * 4) == cudaSuccess && cudaMemset(net->d_m2, 0, o * 4) == cudaSuccess &&
+             cudaMemset(net->d_p, 0, o * 4) == cudaSuccess && cudaMemset(net->d_err, 0, 4) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        mppi_mlp_destroy(net);
+        return MPPI_ERR_OOM;
+    }
+    *out = net;
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_mlp_destroy(mppi_mlp net) {
+    if (!net) return MPPI_ERR_ARG;
+    cudaDeviceSynchronize();
+    std::vector<void*> ps = {net->d_p, net->d_g, net->d_m1, net->d_m2, net->d_dz, net->d_dzb, net->d_dhb, net->d_dh,
+                             net->d_T, net->d_X, net->d_loss, net->d_err, net->d_wofs, net->d_wlen, net->d_wcols,
+                             net->d_wld, net->d_wbp};
+    for (int l = 0; l < NL; l++) {
+        ps.push_back(net->d_wb[l]);
+        ps.push_back(net->d_z[l]);
+    }
+    for (int l = 0; l <= NL; l++) ps.push_back(net->d_hb[l]);
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    delete net;
+    return MPPI_OK;
+}
+
+extern "C" const char* mppi_mlp_last_error(mppi_mlp net) { return net ? net->err.c_str() : "null mlp"; }
+
+extern "C" long mppi_mlp_param_count(mppi_mlp net) { return net ? net->nparam : 0; }
+
+// refresh every BF16 weight copy from the FP32 master parameters
+static mppi_status refresh_bf16(mppi_mlp net, cudaStream_t st) {
+    for (int l = 0; l < NL; l++) {
+        const int rows = LOUT[l], cols = LIN[l], ld = LLD[l];
+        // weights [rows][cols] FP32 -> [rows][ld] BF16 with zero padding
+        k_to_bf16<<<(rows * ld + 255) / 256, 256, 0, st>>>(net->d_p + net->wofs[l], rows, cols, ld, net->d_wb[l]);
+        MCK(cudaGetLastError());
+    }
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_mlp_set_params(mppi_mlp net, const float* params, void* stream) {
+    if (!net || !params) return MPPI_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    MCK(cudaMemcpyAsync(net->d_p, params, net->nparam * 4, mdev(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        st));
+    MCK(cudaMemsetAsync(net->d_m1, 0, net->nparam * 4, st));
+    MCK(cudaMemsetAsync(net->d_m2, 0, net->nparam * 4, st));
+    net->step = 0;
+    mppi_status s = refresh_bf16(net, st);
+    if (s != MPPI_OK) return s;
+    MCK(cudaStreamSynchronize(st));
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_mlp_get_params(mppi_mlp net, float* params, void* stream) {
+    if (!net || !params) return MPPI_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool dev = mdev(params);
+    MCK(cudaMemcpyAsync(params, net->d_p, net->nparam * 4, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (!dev) MCK(cudaStreamSynchronize(st));
+    return MPPI_OK;
+}
+
+// forward pass of B rows already converted to BF16 in d_hb[0]; outputs d_z[NL-1] (FP32)
+static mppi_status forward_bf16(mppi_mlp net, int B, cudaStream_t st) {
+    for (int l = 0; l < NL; l++) {
+        GemmArgs g;
+        memset(&g, 0, sizeof(g));
+        const int ldi = (l == 0) ? IN_PAD : HID;
+        g.A = net->d_hb[l];
+        g.a_sm = ldi;
+        g.a_sk = 1;
+        g.B = net->d_wb[l];
+        g.b_sn = LLD[l];
+        g.b_sk = 1;
+        g.M = B;
+        g.N = LOUT[l];
+        g.K = LLD[l];
+        g.epi = (l < NL - 1) ? EPI_BIAS_GELU : EPI_BIAS;
+        g.bias = net->d_p + net->bofs[l];
+        g.out = net->d_z[l];
+        g.ldo = LOUT[l];
+        g.out_b = (l < NL - 1) ? net->d_hb[l + 1] : nullptr;
+        g.ldob = HID;
+        g.err = net->d_err;
+        MCK(launch_gemm(g, st));
+    }
+    return MPPI_OK;
+}
+
+static mppi_status stage_x(mppi_mlp net, const float* X, int B, cudaStream_t st) {
+    const float* dX = X;
+    if (!mdev(X)) {
+        MCK(cudaMemcpyAsync(net->d_X, X, (size_t)B * IN * 4, cudaMemcpyHostToDevice, st));
+        dX = net->d_X;
+    }
+    k_to_bf16<<<(B * IN_PAD + 255) / 256, 256, 0, st>>>(dX, B, IN, IN_PAD, net->d_hb[0]);
+    MCK(cudaGetLastError());
+    return MPPI_OK;
+}
+
+static mppi_status check_err(mppi_mlp net, cudaStream_t st) {
+    int e = 0;
+    MCK(cudaMemcpyAsync(&e, net->d_err, 4, cudaMemcpyDeviceToHost, st));
+    MCK(cudaStreamSynchronize(st));
+    if (e) return mfail(net, MPPI_ERR_TIMEOUT, "a tensor-core wait ran out");
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_mlp_forward(mppi_mlp net, const float* X, int B, float* Y, void* stream) {
+    if (!net || !X || !Y || B < 1 || B > net->max_batch) return MPPI_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    mppi_status s = stage_x(net, X, B, st);
+    if (s == MPPI_OK) s = forward_bf16(net, B, st);
+    if (s != MPPI_OK) return s;
+    const bool dev = mdev(Y);
+    MCK(cudaMemcpyAsync(Y, net->d_z[NL - 1], (size_t)B * OUT * 4, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        st));
+    if (!dev) return check_err(net, st);
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_mlp_train_step(mppi_mlp net, const float* X, const float* T, int B, float lr,
+                                           float weight_decay, float* loss_out, float* grad_out, void* stream) {
+    if (!net || !X || !T || B < 1 || B > net->max_batch) return MPPI_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    mppi_status s = stage_x(net, X, B, st);
+    if (s == MPPI_OK) s = forward_bf16(net, B, st);
+    if (s != MPPI_OK) return s;
+    const float* dT = T;
+    if (!mdev(T)) {
+        MCK(cudaMemcpyAsync(net->d_T, T, (size_t)B * OUT * 4, cudaMemcpyHostToDevice, st));
+        dT = net->d_T;
+    }
+    MCK(cudaMemsetAsync(net->d_loss, 0, 4, st));
+    const int n = B * OUT;
+    k_mse<<<(n + 255) / 256, 256, 0, st>>>(net->d_z[NL - 1], dT, n, 1.f / (float)n, net->d_dz, net->d_dzb, net->d_loss);
+    MCK(cudaGetLastError());
+    // backward, layer NL-1 .. 0: dZ (FP32 in d_dz, BF16 in d_dzb, [B][out])
+    for (int l = NL - 1; l >= 0; l--) {
+        const int out = LOUT[l], in = LIN[l], ldi = (l == 0) ? IN_PAD : HID;
+        // dW[o][i] = sum_b dZ[b][o] H[b][i]: A[o][b] = dZ (stride out along b), B[i][b] = H (stride ldi)
+        GemmArgs g;
+        memset(&g, 0, sizeof(g));
+        g.A = net->d_dzb;
+        g.a_sm = 1;
+        g.a_sk = out;
+        g.B = net->d_hb[l];
+        g.b_sn = 1;
+        g.b_sk = ldi;
+        g.M = out;
+        g.N = in;
+        g.K = B;
+        g.epi = EPI_STORE;
+        g.out = net->d_g + net->wofs[l];
+        g.ldo = in;
+        g.err = net->d_err;
+        MCK(launch_gemm(g, st));
+        k_colsum<<<(out + 127) / 128, 128, 0, st>>>(net->d_dz, B, out, out, net->d_g + net->bofs[l]);
+        MCK(cudaGetLastError());
+        if (l == 0) break;
+        // dH[b][i] = sum_o dZ[b][o] W[o][i], then dZ_prev = dH * gelu'(Z_prev)
+        GemmArgs h;
+        memset(&h, 0, sizeof(h));
+        h.A = net->d_dzb;
+        h.a_sm = out;
+        h.a_sk = 1;
+        h.B = net->d_wb[l];
+        h.b_sn = 1;
+        h.b_sk = LLD[l];
+        h.M = B;
+        h.N = in;
+        h.K = out;
+        h.epi = EPI_GELU_BWD;
+        h.aux = net->d_z[l - 1];
+        h.ldaux = HID;
+        h.out = net->d_dh;
+        h.ldo = HID;
+        h.out_b = net->d_dhb;
+        h.ldob = HID;
+        h.err = net->d_err;
+        MCK(launch_gemm(h, st));
+        std::swap(net->d_dz, net->d_dh);
+        std::swap(net->d_dzb, net->d_dhb);
+    }
+    if (grad_out) {
+        const bool dev = mdev(grad_out);
+        MCK(cudaMemcpyAsync(grad_out, net->d_g, net->nparam * 4, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    }
+    if (lr > 0.f) {
+        net->step++;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f - powf(b1, (float)net->step), c2 = 1.f - powf(b2, (float)net->step);
+        k_adamw<<<(int)((net->nparam + 255) / 256), 256, 0, st>>>(net->d_p, net->d_g, net->d_m1, net->d_m2, net->nparam,
+                                                                  lr, b1, b2, 1e-8f, weight_decay, c1, c2, net->d_wofs,
+                                                                  net->d_wlen, net->d_wbp, NL, net->d_wcols, net->d_wld);
+        MCK(cudaGetLastError());
+    }
+    if (loss_out) {
+        const bool dev = mdev(loss_out);
+        MCK(cudaMemcpyAsync(loss_out, net->d_loss, 4, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+        if (!dev) return check_err(net, st);
+    }
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_tc_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int K,
+                                         void* stream) {
+    if (!A || !B || !D || M < 1 || N < 1 || N > 256 || K < 1) return MPPI_ERR_ARG;
+    if (!mdev(A) || !mdev(B) || !mdev(D)) return MPPI_ERR_ARG;
+    int* err = nullptr;
+    if (cudaMalloc((void**)&err, 4) != cudaSuccess) return MPPI_ERR_OOM;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaMemsetAsync(err, 0, 4, st);
+    GemmArgs g;
+    memset(&g, 0, sizeof(g));
+    g.A = reinterpret_cast<const __nv_bfloat16*>(A);
+    g.a_sm = K;
+    g.a_sk = 1;
+    g.B = reinterpret_cast<const __nv_bfloat16*>(B);
+    g.b_sn = K;
+    g.b_sk = 1;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.epi = EPI_STORE;
+    g.out = D;
+    g.ldo = N;
+    g.err = err;
+    cudaError_t e = launch_gemm(g, st);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(err);
+    if (e != cudaSuccess) return MPPI_ERR_CUDA;
+    return h ? MPPI_ERR_TIMEOUT : MPPI_OK;
+}
