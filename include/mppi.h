@@ -196,6 +196,11 @@ mppi_status mppi_batch_get_shape(mppi_batch b, int* block, int* blocks_per_sm);
 mppi_status mppi_batch_autotune(mppi_batch b, const float* x0s, int trials, int* block_out,
                                 int* bpsm_out, float* best_ms_out);
 
+/* After a step: every instance's updated mean before the shift (mu_upds,
+ * float[n][48]) and its shifted nominal (nominals, float[n][48]); host or
+ * device, either may be NULL. */
+mppi_status mppi_batch_get_means(mppi_batch b, float* mu_upds, float* nominals);
+
 /* Number of graph launches (one per mppi_batch_step). */
 mppi_status mppi_batch_launch_count(mppi_batch b, uint64_t* count);
 
@@ -265,6 +270,18 @@ mppi_status mppi_mlp_forward(mppi_mlp net, const float* X, int B, float* Y, void
  * update) optional.  TIMEOUT if a tensor-core wait ran out. */
 mppi_status mppi_mlp_train_step(mppi_mlp net, const float* X, const float* T, int B, float lr,
                                 float weight_decay, float* loss_out, float* grad_out, void* stream);
+/* The network's input for n states X (float[n][nx], host or device) of this
+ * handle's robot and task at control index `step`: F (float[n][62], host or
+ * device) = trunk height, attitude (w >= 0), joints, velocities, joint rates
+ * x 0.1, box pose/velocity relative to the trunk, box-goal and trunk-goal
+ * offsets, gait phase (sin, cos), gravity in the trunk frame, box heading,
+ * the two xy distances and a constant 1. */
+mppi_status mppi_features(mppi_handle h, const float* X, int n, uint32_t step, float* F);
+/* Proposal mean for the handle's next steps (float[48], host or device; NULL
+ * stops using it): mppi_step and batches then draw the last n_prop samples
+ * around it (the first of them is the proposal itself); a non-finite entry
+ * falls back to the plain mean.  ARG if the handle has n_prop = 0. */
+mppi_status mppi_set_proposal(mppi_handle h, const float* mu_prop);
 /* D[M][N] = A[M][K] B[N][K]^T with BF16 inputs (raw uint16 bits) and FP32
  * accumulation on the tcgen05 tensor cores -- the network's GEMM; device
  * buffers, N <= 256. */

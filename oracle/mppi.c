@@ -135,7 +135,9 @@ void or_sample(const or_mppi* m, const float mu[OR_D], const float* mu_prop, uin
         else or_noise(m->seed, step, m->inst, (uint32_t)k, eps);
         for (int d = 0; d < OR_D; d++) {
             int jt = d % 3;
-            float v = fmaf(m->sigma[d], eps[d], ctrv[d]);
+            float c = ctrv[d];
+            if (k >= kp0 && !isfinite(c)) c = mu[d];   /* non-finite proposal: the plain mean */
+            float v = fmaf(m->sigma[d], eps[d], c);
             v = fmaxf(v, m->q_lo[jt]);
             v = fminf(v, m->q_hi[jt]);
             U[(size_t)k * OR_D + d] = v;

@@ -32,7 +32,8 @@ EXPORTS = ("mppi_create", "mppi_destroy", "mppi_last_error", "mppi_set_nominal",
            "mppi_server_tick", "mppi_server_poll", "mppi_server_stats", "mppi_server_reset_stats",
            "mppi_server_drain", "mppi_mlp_create", "mppi_mlp_destroy", "mppi_mlp_last_error",
            "mppi_mlp_param_count", "mppi_mlp_set_params", "mppi_mlp_get_params", "mppi_mlp_forward",
-           "mppi_mlp_train_step", "mppi_tc_gemm_bf16")
+           "mppi_mlp_train_step", "mppi_tc_gemm_bf16", "mppi_features", "mppi_set_proposal",
+           "mppi_batch_get_means")
 
 
 class MppiError(RuntimeError):
@@ -151,6 +152,9 @@ def lib():
         L.mppi_mlp_forward.argtypes = [vp, vp, C.c_int, vp, vp]
         L.mppi_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_float, C.c_float, vp, vp, vp]
         L.mppi_tc_gemm_bf16.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, vp]
+        L.mppi_features.argtypes = [vp, vp, C.c_int, C.c_uint32, vp]
+        L.mppi_batch_get_means.argtypes = [vp, vp, vp]
+        L.mppi_set_proposal.argtypes = [vp, vp]
         L.mppi_state_size.argtypes = [vp]
         L.mppi_state_size.restype = C.c_int
         for name in EXPORTS:
@@ -297,6 +301,18 @@ class Controller:
             self._check(rc)
         return rc
 
+    def features(self, X, step, out=None):
+        X = np.ascontiguousarray(X, np.float32) if isinstance(X, np.ndarray) else X
+        n = X.shape[0] if X.ndim == 2 else 1
+        out = np.zeros((n, 62), np.float32) if out is None else out
+        self._check(lib().mppi_features(self.h, _ptr(X), n, step, _ptr(out)))
+        return out
+
+    def set_proposal(self, mu_prop):
+        if mu_prop is not None and isinstance(mu_prop, np.ndarray):
+            mu_prop = np.ascontiguousarray(mu_prop, np.float32)
+        self._check(lib().mppi_set_proposal(self.h, _ptr(mu_prop)))
+
     def set_timing(self, on=True):
         self._check(lib().mppi_set_timing(self.h, int(on)))
 
@@ -364,6 +380,10 @@ class Batch:
         c = C.c_uint64()
         self._check(lib().mppi_batch_launch_count(self.b, C.byref(c)))
         return c.value
+
+    def means(self, mu_upds=None, nominals=None):
+        self._check(lib().mppi_batch_get_means(self.b, _ptr(mu_upds), _ptr(nominals)))
+        return mu_upds, nominals
 
 
 class Server:

@@ -500,7 +500,7 @@ extern "C" mppi_status mppi_step(mppi_handle h, const float* x0, uint32_t step, 
     }
     const bool tm = h->timing != 0;
     if (tm) CK(cudaEventRecord(h->ev[0], h->stream));
-    mppi_status s = do_sample(h, step, nullptr, h->d_U);
+    mppi_status s = do_sample(h, step, h->has_prop ? h->d_mu_prop : nullptr, h->d_U);
     if (s != MPPI_OK) return s;
     if (tm) CK(cudaEventRecord(h->ev[1], h->stream));
     const double t0 = (double)step * h->cfg.ctrl_steps * h->cfg.dt;

@@ -51,7 +51,9 @@ __device__ __forceinline__ void sample_lane(const InstDesc& d, int k, int leg, u
         for (int i = 0; i < 3; i++) {
             const int dd = j * NJ + 3 * leg + i;
             const float eps = nominal ? 0.f : normal_at(d.key0, d.key1, step, d.inst_id, (uint32_t)k, dd);
-            float v = __fmaf_rn(d.sigma[dd], eps, __ldcg(ctr + dd));
+            float c = __ldcg(ctr + dd);
+            if (prop && !(fabsf(c) <= 3.402823466e38f)) c = __ldcg(d.mu + dd);  // non-finite proposal: plain mean
+            float v = __fmaf_rn(d.sigma[dd], eps, c);
             v = fminf(fmaxf(v, d.q_lo[i]), d.q_hi[i]);
             Uk[j][i] = v;
             if (write) d.U[(size_t)k * D + dd] = v;
@@ -280,7 +282,7 @@ InstDesc mppi::make_desc(const mppi_handle_s* h) {
     d.U = h->d_U;
     d.L = h->d_L;
     d.status = h->d_status;
-    d.mu_prop = nullptr;
+    d.mu_prop = h->cfg.n_prop > 0 ? h->d_mu_prop : nullptr;  // filled by mppi_set_proposal
     d.K = h->cfg.K;
     d.H = h->cfg.H;
     d.n_sub = h->cfg.n_sub;
@@ -565,5 +567,20 @@ extern "C" mppi_status mppi_batch_autotune(mppi_batch b, const float* x0s, int t
 extern "C" mppi_status mppi_batch_launch_count(mppi_batch b, uint64_t* count) {
     if (!b || !count) return MPPI_ERR_ARG;
     *count = b->launches;
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_batch_get_means(mppi_batch b, float* mu_upds, float* nominals) {
+    if (!b) return MPPI_ERR_ARG;
+    const bool hu = mu_upds && !dev_ptr(mu_upds), hn = nominals && !dev_ptr(nominals);
+    for (int i = 0; i < b->n; i++) {
+        if (mu_upds)
+            BCK(cudaMemcpyAsync(mu_upds + (size_t)i * D, b->hs[i]->d_mu_upd, D * sizeof(float),
+                                hu ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, b->stream));
+        if (nominals)
+            BCK(cudaMemcpyAsync(nominals + (size_t)i * D, b->hs[i]->d_mu, D * sizeof(float),
+                                hn ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, b->stream));
+    }
+    if (hu || hn) BCK(cudaStreamSynchronize(b->stream));
     return MPPI_OK;
 }

@@ -26,6 +26,7 @@ struct mppi_handle_s {
     unsigned* d_counter = nullptr;  // update scratch: finished-CTA counter
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int timing = 0;
+    int has_prop = 0;  // mppi_step samples the last n_prop samples around d_mu_prop
     int timed_valid = 0;
     uint64_t launches = 0;
     std::string err;

@@ -35,7 +35,9 @@ __global__ void __launch_bounds__(256) k_sample(SampleArgs a) {
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         const int d = 4 * g + i, jt = d % 3;
-        float v = __fmaf_rn(a.sigma[d], eps[i], __ldg(ctr + d));
+        float c = __ldg(ctr + d);
+        if (prop && !(fabsf(c) <= 3.402823466e38f)) c = __ldg(a.mu + d);  // non-finite proposal: plain mean
+        float v = __fmaf_rn(a.sigma[d], eps[i], c);
         o[i] = fminf(fmaxf(v, a.q_lo[jt]), a.q_hi[jt]);
     }
     reinterpret_cast<float4*>(a.U + (size_t)k * D)[g] = out;

@@ -255,3 +255,19 @@ def serving_arrivals(n_robots: int = 64, rate_hz: float = 50.0, duration: float 
 def task_config(task: str, K: int, H: int) -> "Workload":
     return {"stand": config_stand, "trot": config_trot, "terrain": config_terrain,
             "push": config_push}[task](K=K, H=H)
+
+
+MLP_SIZES = [(256, 62), (256, 256), (256, 256), (48, 256)]
+
+
+def mlp_init(seed: int = 0) -> np.ndarray:
+    """Seeded initial parameters of the proposal network (flat FP32, layout
+    W1 [256][62], b1, W2, b2, W3, b3, W4 [48][256], b4): weights uniform in
+    +-sqrt(6 / (fan_in + fan_out)), biases zero."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for no, ni in MLP_SIZES:
+        lim = math.sqrt(6.0 / (ni + no))
+        out.append(rng.uniform(-lim, lim, no * ni))
+        out.append(np.zeros(no))
+    return np.concatenate(out).astype(np.float32)
