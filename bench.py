@@ -36,10 +36,8 @@ METRIC = "rollout-steps/s (MPPI step, K=4096, H=100)"
 
 
 def dist_env():
-    r = int(os.environ.get("RANK", "0"))
-    w = int(os.environ.get("WORLD_SIZE", "1"))
-    lr = int(os.environ.get("LOCAL_RANK", "0"))
-    return r, w, lr
+    from paper_2409_10469_gb300 import dist as D
+    return D.env()
 
 
 class ClockSampler:
@@ -222,10 +220,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     step_ms = np.array([a.elapsed_time(b) for a, b in zip(starts, ends)])
     mean_ms = float(step_ms.mean())
-    if dist:
-        t = torch.tensor([mean_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        mean_ms = float(t.item())
+    from paper_2409_10469_gb300 import dist as D
+    mean_ms = D.max_over_ranks(mean_ms, device="cuda")
     ker = np.array(ker)
     timed_launches = 3 * args.steps   # sample, rollout, update per step (timed loop only)
 
@@ -254,7 +250,7 @@ def run_ours(args):
     achieved = fl / (rollout_ms * 1e-3) / 1e12
     sm_max = (peaks or {}).get("sm_max_mhz", 2070.0)
     peak = F.fp32_peak_tflops(152, sm_max)
-    value = world_size * K_BENCH * H_BENCH / (mean_ms * 1e-3)
+    value = D.job_throughput(K_BENCH * H_BENCH, world_size, mean_ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "rollout-steps/s", "n_gpus": world_size,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,

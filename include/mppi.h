@@ -270,6 +270,12 @@ mppi_status mppi_mlp_forward(mppi_mlp net, const float* X, int B, float* Y, void
  * update) optional.  TIMEOUT if a tensor-core wait ran out. */
 mppi_status mppi_mlp_train_step(mppi_mlp net, const float* X, const float* T, int B, float lr,
                                 float weight_decay, float* loss_out, float* grad_out, void* stream);
+/* Failure-detection self-test: runs the tensor-core GEMM with its completion
+ * signal withheld, so every thread's bounded wait runs out; the kernel records
+ * the timeout, releases its tensor memory and returns.  Expected result:
+ * MPPI_ERR_TIMEOUT, with the CUDA context still usable afterwards. */
+mppi_status mppi_selftest_wait_timeout(void* stream);
+
 /* The network's input for n states X (float[n][nx], host or device) of this
  * handle's robot and task at control index `step`: F (float[n][62], host or
  * device) = trunk height, attitude (w >= 0), joints, velocities, joint rates

@@ -47,6 +47,8 @@ struct GemmArgs {
     __nv_bfloat16* out_b;     // BF16 [M][ldob] (optional)
     long ldob;
     int* err;                 // set when a wait runs out
+    uint32_t wait_limit;      // mbarrier polls before giving up (0 = default)
+    int withhold_commit;      // self-test: never signal completion, so the wait runs out
 };
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
@@ -108,12 +110,12 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g) {
             for (int ks = 0; ks < tc::KCHUNK / 16; ks++) {
                 const uint64_t ad = tc::smem_desc(a0 + ks * 2 * tc::CM_BYTES, tc::LBO, tc::SBO);
                 const uint64_t bd = tc::smem_desc(b0 + ks * 2 * tc::CM_BYTES, tc::LBO, tc::SBO);
-                tc::mma_bf16(tmem, ad, bd, idesc, (kc | ks) != 0);
+                if (!g.withhold_commit) tc::mma_bf16(tmem, ad, bd, idesc, (kc | ks) != 0);
             }
-            tc::mma_commit(&bar);
+            if (!g.withhold_commit) tc::mma_commit(&bar);
         }
         // every thread waits for the MMAs (they read the staged tiles) before restaging
-        if (!tc::mbar_wait(&bar, phase, 1u << 22)) s_fail = 1;
+        if (!tc::mbar_wait(&bar, phase, g.wait_limit ? g.wait_limit : (1u << 22))) s_fail = 1;
         phase ^= 1u;
         __syncthreads();
         if (s_fail) break;
@@ -561,6 +563,39 @@ extern "C" mppi_status mppi_tc_gemm_bf16(const uint16_t* A, const uint16_t* B, f
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(err);
+    if (e != cudaSuccess) return MPPI_ERR_CUDA;
+    return h ? MPPI_ERR_TIMEOUT : MPPI_OK;
+}
+
+extern "C" mppi_status mppi_selftest_wait_timeout(void* stream) {
+    // a 128 x 64 x 64 GEMM whose completion is never signalled: every thread's
+    // bounded mbarrier wait must run out, the kernel must record it, free its
+    // tensor memory and return, and the context must stay usable
+    cudaStream_t st = (cudaStream_t)stream;
+    __nv_bfloat16 *A = nullptr, *B = nullptr;
+    float* D = nullptr;
+    int* err = nullptr;
+    if (cudaMalloc((void**)&A, 128 * 64 * 2) != cudaSuccess || cudaMalloc((void**)&B, 64 * 64 * 2) != cudaSuccess ||
+        cudaMalloc((void**)&D, 128 * 64 * 4) != cudaSuccess || cudaMalloc((void**)&err, 4) != cudaSuccess) {
+        cudaFree(A); cudaFree(B); cudaFree(D); cudaFree(err);
+        return MPPI_ERR_OOM;
+    }
+    cudaMemsetAsync(A, 0, 128 * 64 * 2, st);
+    cudaMemsetAsync(B, 0, 64 * 64 * 2, st);
+    cudaMemsetAsync(err, 0, 4, st);
+    GemmArgs g;
+    memset(&g, 0, sizeof(g));
+    g.A = A; g.a_sm = 64; g.a_sk = 1;
+    g.B = B; g.b_sn = 64; g.b_sk = 1;
+    g.M = 128; g.N = 64; g.K = 64;
+    g.epi = EPI_STORE; g.out = D; g.ldo = 64; g.err = err;
+    g.wait_limit = 1u << 12;
+    g.withhold_commit = 1;
+    cudaError_t e = launch_gemm(g, st);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(A); cudaFree(B); cudaFree(D); cudaFree(err);
     if (e != cudaSuccess) return MPPI_ERR_CUDA;
     return h ? MPPI_ERR_TIMEOUT : MPPI_OK;
 }

@@ -101,3 +101,15 @@ def test_adamw_step_matches_oracle_and_training_converges():
     for _ in range(300):
         last = net.train_step(Xt, Tt, lr=2e-3)
     assert last < 0.2 * first, (first, last)
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """a tensor-core wait that is never signalled runs out after its limit; the
+    kernel returns an error status and the GPU stays usable"""
+    assert _mppi.lib().mppi_selftest_wait_timeout(None) == _mppi.MPPI_ERR_TIMEOUT
+    A = torch.ones(128, 64, dtype=torch.bfloat16).view(torch.int16).cuda()
+    B = torch.ones(64, 64, dtype=torch.bfloat16).view(torch.int16).cuda()
+    D = torch.zeros(128, 64, device="cuda")
+    assert _mppi.tc_gemm_bf16(A, B, 128, 64, 64, D) == _mppi.MPPI_OK
+    torch.cuda.synchronize()
+    assert torch.all(D == 64.0)
