@@ -273,13 +273,13 @@ __device__ __forceinline__ void quat_integrate(float q[4], float3 w, float h) {
     float th = wn * h;
     float sh, ch;
     sincos_r(0.5f * th, sh, ch);
-    float sk = (th > 1e-4f) ? sh / wn : 0.5f * h * (1.f - th * th * (1.f / 24.f));
+    float sk = (th > 1e-4f) ? sh * __frcp_rn(wn) : 0.5f * h * (1.f - th * th * (1.f / 24.f));
     float d0 = ch, d1 = sk * w.x, d2 = sk * w.y, d3 = sk * w.z;
     float r0 = q[0] * d0 - q[1] * d1 - q[2] * d2 - q[3] * d3;
     float r1 = q[0] * d1 + q[1] * d0 + q[2] * d3 - q[3] * d2;
     float r2 = q[0] * d2 - q[1] * d3 + q[2] * d0 + q[3] * d1;
     float r3 = q[0] * d3 + q[1] * d2 - q[2] * d1 + q[3] * d0;
-    float inv = 1.f / sqrtf(r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
+    float inv = rsqrtf(r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
     q[0] = r0 * inv; q[1] = r1 * inv; q[2] = r2 * inv; q[3] = r3 * inv;
 }
 

@@ -85,14 +85,14 @@ __device__ __forceinline__ bool sphere_aabb(float3 x, float r, float3 lo, float3
 // nb: normal in body coordinates, cb: sphere centre in the body frame, (w, v):
 // body velocity; the force acts at the deepest point cb - r nb.
 __device__ __forceinline__ void contact_wrench(const DevModel& m, float pen, float3 nb, float3 cb, float r,
-                                               float3 w, float3 v, float3& torque, float3& force) {
+                                               float3 w, float3 v, float3& torque, float3& force,
+                                               bool active = true) {
     float3 pc = cb - r * nb;
     float3 vp = v + cross3(w, pc);
     float vn = dot3(vp, nb);
-    float fn = fmaxf(m.kc * pen - m.cc * vn, 0.f);
+    const float fn = active ? fmaxf(m.kc * pen - m.cc * vn, 0.f) : 0.f;
     float3 vt = vp - vn * nb;
-    float s = sqrtf(dot3(vt, vt) + m.eps2);
-    float fr = m.mu * fn / s;
+    const float fr = m.mu * fn * rsqrtf(dot3(vt, vt) + m.eps2);
     float3 f = fn * nb - fr * vt;
     force = force + f;
     torque = torque + cross3(pc, f);
@@ -105,10 +105,11 @@ __device__ __forceinline__ void sphere_env(const DevModel& m, float3 xw, float r
                                            const ToBody& toBody, float3& torque, float3& force) {
     float h, hx, hy;
     ground<TERR>(m, xw.x, xw.y, h, hx, hy);
-    float inv = 1.f / sqrtf(hx * hx + hy * hy + 1.f);
+    float inv = rsqrtf(hx * hx + hy * hy + 1.f);
     float3 n = f3(-hx * inv, -hy * inv, inv);
-    float pen = r - (xw.z - h) * n.z;
-    if (pen > 0.f) contact_wrench(m, pen, toBody(n), cb, r, w, v, torque, force);
+    const float pen = r - (xw.z - h) * n.z;
+    // computed unconditionally and zeroed out of contact (no branch)
+    contact_wrench(m, fmaxf(pen, 0.f), toBody(n), cb, r, w, v, torque, force, pen > 0.f);
     for (int b = 0; b < m.n_sbox; b++) {
         float3 nn; float pb;
         const float* bx = m.sbox + 6 * b;
@@ -179,7 +180,7 @@ __device__ __forceinline__ void sphere_vs_box(const DevModel& m, const BoxKin& B
     const float vn = dot3(vrel, nw);
     const float fn = fmaxf(m.kc * pen - m.cc * vn, 0.f);
     const float3 vt = vrel - vn * nw;
-    const float fr = m.mu * fn / sqrtf(dot3(vt, vt) + m.eps2);
+    const float fr = m.mu * fn * rsqrtf(dot3(vt, vt) + m.eps2);
     const float3 fw = fn * nw - fr * vt;
     const float3 fbody = F(fw);
     force = force + fbody;
@@ -378,7 +379,7 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
         pa_f = pa_f + bf;
 #pragma unroll
         for (int i = 0; i < 3; i++) { U1a[i] = IA.A[sidx(i, 1)]; U1l[i] = IA.B[1][i]; }
-        D1inv = 1.f / (U1a[1] + arm);
+        D1inv = __fdividef(1.f, U1a[1] + arm);
         u1 = tau[1] - pa_n.y;
     }
     project<1>(IA, pa_n, pa_f, D1inv, u1, ct_w, ct_v);
@@ -395,7 +396,7 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
         pa_f = pa_f + bf;
 #pragma unroll
         for (int i = 0; i < 3; i++) { U0a[i] = IA.A[sidx(i, 0)]; U0l[i] = IA.B[0][i]; }
-        D0inv = 1.f / (U0a[0] + arm);
+        D0inv = __fdividef(1.f, U0a[0] + arm);
         u0 = tau[0] - pa_n.x;
     }
     project<0>(IA, pa_n, pa_f, D0inv, u0, ch_w, ch_v);
@@ -436,37 +437,56 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
         bt[4] = xsum4(pa_f.y - f0_f.y) + bf.y;
         bt[5] = xsum4(pa_f.z - f0_f.z) + bf.z;
     }
-    // ---- solve Mt a' = -bt (Cholesky, 6x6 SPD, upper storage)
-    float Lc[6][6], Linv[6];
+    // ---- solve Mt a' = -bt by the Schur complement of the linear block:
+    // Mt = [A B; B^T C], C^-1 and S^-1 (S = A - B C^-1 B^T) by 3x3 cofactors
+    float a0[6];
+    {
+        const float C00 = Mt[3][3], C01 = Mt[3][4], C02 = Mt[3][5], C11 = Mt[4][4], C12 = Mt[4][5], C22 = Mt[5][5];
+        float ci[6];
+        ci[0] = C11 * C22 - C12 * C12;
+        ci[1] = C02 * C12 - C01 * C22;
+        ci[2] = C01 * C12 - C02 * C11;
+        ci[3] = C00 * C22 - C02 * C02;
+        ci[4] = C01 * C02 - C00 * C12;
+        ci[5] = C00 * C11 - C01 * C01;
+        const float idc = __frcp_rn(C00 * ci[0] + C01 * ci[1] + C02 * ci[2]);
 #pragma unroll
-    for (int j = 0; j < 6; j++) {
-        float d = Mt[j][j];
+        for (int i = 0; i < 6; i++) ci[i] *= idc;
+        // W = B C^-1 (3x3)
+        float W[3][3];
 #pragma unroll
-        for (int k = 0; k < j; k++) d = fmaf(-Lc[j][k], Lc[j][k], d);
-        const float inv = rsqrtf(d);
-        Linv[j] = inv;
+        for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int i = j + 1; i < 6; i++) {
-            float sum = Mt[j][i];
+            for (int j = 0; j < 3; j++)
+                W[i][j] = Mt[i][3] * ci[sidx(0, j)] + Mt[i][4] * ci[sidx(1, j)] + Mt[i][5] * ci[sidx(2, j)];
+        // S = A - W B^T (symmetric)
+        float S[6];
 #pragma unroll
-            for (int k = 0; k < j; k++) sum = fmaf(-Lc[i][k], Lc[j][k], sum);
-            Lc[i][j] = sum * inv;
-        }
-    }
-    float y[6], a0[6];
+        for (int i = 0; i < 3; i++)
 #pragma unroll
-    for (int i = 0; i < 6; i++) {
-        float sum = -bt[i];
+            for (int j = i; j < 3; j++)
+                S[sidx(i, j)] = Mt[i][j] - (W[i][0] * Mt[j][3] + W[i][1] * Mt[j][4] + W[i][2] * Mt[j][5]);
+        float si[6];
+        si[0] = S[3] * S[5] - S[4] * S[4];
+        si[1] = S[2] * S[4] - S[1] * S[5];
+        si[2] = S[1] * S[4] - S[2] * S[3];
+        si[3] = S[0] * S[5] - S[2] * S[2];
+        si[4] = S[1] * S[2] - S[0] * S[4];
+        si[5] = S[0] * S[3] - S[1] * S[1];
+        const float ids = __frcp_rn(S[0] * si[0] + S[1] * si[1] + S[2] * si[2]);
+        // [A B; B^T C] [x; y] = -[p; q]:  x = S^-1 (-p + W q),  y = C^-1 (-q - B^T x)
+        float rx[3];
 #pragma unroll
-        for (int k = 0; k < i; k++) sum = fmaf(-Lc[i][k], y[k], sum);
-        y[i] = sum * Linv[i];
-    }
+        for (int i = 0; i < 3; i++) rx[i] = -bt[i] + (W[i][0] * bt[3] + W[i][1] * bt[4] + W[i][2] * bt[5]);
 #pragma unroll
-    for (int i = 5; i >= 0; i--) {
-        float sum = y[i];
+        for (int i = 0; i < 3; i++)
+            a0[i] = ids * (si[sidx(i, 0)] * rx[0] + si[sidx(i, 1)] * rx[1] + si[sidx(i, 2)] * rx[2]);
+        float ry[3];
 #pragma unroll
-        for (int k = i + 1; k < 6; k++) sum = fmaf(-Lc[k][i], a0[k], sum);
-        a0[i] = sum * Linv[i];
+        for (int j = 0; j < 3; j++) ry[j] = -bt[3 + j] - (Mt[0][3 + j] * a0[0] + Mt[1][3 + j] * a0[1] + Mt[2][3 + j] * a0[2]);
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            a0[3 + j] = ci[sidx(j, 0)] * ry[0] + ci[sidx(j, 1)] * ry[1] + ci[sidx(j, 2)] * ry[2];
     }
 
     // ---- pass 3 (root to tip): a' = X a'_parent + c ; qdd = (u - U . a') / D
