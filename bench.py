@@ -1,6 +1,6 @@
 """Benchmark of one MPPI control step (arXiv 2409.10469, Alg. 1) on GB300.
 
-Workload: trot on a flat plane (dt 0.005 s, n_sub 4, sigma 0.3, lambda 0.1)
+Workload: trot on a flat plane (dt 0.005 s, n_sub 8, sigma 0.3, lambda 0.1)
 at K = 4096 samples, H = 100 steps.  A step is one full pass of the hot path:
 Philox knot sampling -> 4096 rollouts of the floating-base quadruped ->
 softmax update, applied control and shift (mppi_step of the C ABI).
@@ -33,6 +33,22 @@ sys.path.insert(0, ROOT)
 
 K_BENCH, H_BENCH = 4096, 100
 METRIC = "rollout-steps/s (MPPI step, K=4096, H=100)"
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture) of
+# one k_rollout launch on this workload, valid only for the kernel sources whose
+# SHA-256 prefix is given; reported as null once those sources change.
+ROLLOUT_TRAFFIC = {"bytes": 826624, "sources_sha256": "59c22fca46d063bc"}
+ROLLOUT_SOURCES = ("rollout.cu", "rollout.cuh", "common.cuh")
+
+
+def rollout_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ROLLOUT_SOURCES:
+        with open(os.path.join(ROOT, "paper_2409_10469_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    ok = h.hexdigest()[:16] == ROLLOUT_TRAFFIC["sources_sha256"]
+    return ROLLOUT_TRAFFIC["bytes"] if ok else None
 
 
 def dist_env():
@@ -264,7 +280,7 @@ def run_ours(args):
         "kernel_ms": {"sample": float(ker[:, 0].mean()), "rollout": rollout_ms,
                       "update": float(ker[:, 2].mean())},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": rollout_traffic(),
                      "kernel": "k_rollout", "flops_per_launch": fl,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (max SM clock, MEASURED_PEAKS.json)" % sm_max},
         "e2e": {"value": world_size * K_BENCH * H_BENCH / (e2e_ms * 1e-3), "unit": "rollout-steps/s",
