@@ -113,7 +113,7 @@ static void derive_model(const mppi_model_t& p, double h, DevModel& d) {
     d.foot[0] = 0.f; d.foot[1] = 0.f; d.foot[2] = (float)(-cl);
     d.foot_r = (float)p.foot_radius;
     d.n_tsph = p.n_trunk_spheres;
-    for (int s = 0; s < 4; s++) d.tsph_x[s] = (float)p.trunk_sphere_x[s];
+    for (int s = 0; s < 4; s++) d.tsph_x[s] = s < p.n_trunk_spheres ? (float)p.trunk_sphere_x[s] : 0.f;
     d.tsph_r = (float)p.trunk_sphere_r;
     d.gz = (float)(-p.gravity);
     d.kp = (float)p.kp; d.kd = (float)p.kd; d.arm0 = (float)p.armature;

@@ -146,7 +146,7 @@ __device__ void block_update(const InstDesc& d, float* u0_row) {
 }
 
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_batch(BatchArgs a) {
+__global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 1 : 384 / BLOCK) k_batch(BatchArgs a) {
     __shared__ InstDesc sd;
     __shared__ int s_item, s_last;
     const int tid = threadIdx.x, leg = tid & 3, r = tid >> 2;
@@ -174,12 +174,12 @@ __global__ void __launch_bounds__(BLOCK) k_batch(BatchArgs a) {
         const HorizonArgs hz = {sd.H, sd.n_sub, sd.nx, sd.h, sd.dt, sd.inv_Hm1, t0, sd.arm};
         const float* x0 = a.x0s + (size_t)w.inst * NX_BOX;
         float L;
-        if (sd.model.terrain == 1)
-            L = sd.model.has_box ? rollout_lane<1, false, true>(sd.model, sd.cost, hz, x0, Uk, leg, k, valid, nullptr)
-                                 : rollout_lane<1, false, false>(sd.model, sd.cost, hz, x0, Uk, leg, k, valid, nullptr);
+        if (sd.model.terrain != 0 || sd.model.n_sbox > 0)
+            L = sd.model.has_box ? rollout_lane<1, true>(sd.model, sd.cost, hz, x0, Uk, leg, k, valid, nullptr)
+                                 : rollout_lane<1, false>(sd.model, sd.cost, hz, x0, Uk, leg, k, valid, nullptr);
         else
-            L = sd.model.has_box ? rollout_lane<0, false, true>(sd.model, sd.cost, hz, x0, Uk, leg, k, valid, nullptr)
-                                 : rollout_lane<0, false, false>(sd.model, sd.cost, hz, x0, Uk, leg, k, valid, nullptr);
+            L = sd.model.has_box ? rollout_lane<0, true>(sd.model, sd.cost, hz, x0, Uk, leg, k, valid, nullptr)
+                                 : rollout_lane<0, false>(sd.model, sd.cost, hz, x0, Uk, leg, k, valid, nullptr);
         if (valid && leg == 0) sd.L[k] = L;
         __threadfence();
         __syncthreads();

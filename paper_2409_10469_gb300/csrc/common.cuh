@@ -84,6 +84,20 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
 }
 __device__ __forceinline__ float3 ld3(const float* p) { return f3(p[0], p[1], p[2]); }
 
+// c + a x b with every component one fused chain
+__device__ __forceinline__ float3 cross_acc(float3 a, float3 b, float3 c) {
+    return f3(fmaf(a.y, b.z, fmaf(-a.z, b.y, c.x)), fmaf(a.z, b.x, fmaf(-a.x, b.z, c.y)),
+              fmaf(a.x, b.y, fmaf(-a.y, b.x, c.z)));
+}
+// c + a x (0, r, 0) and c + a x (0, 0, r), the structurally-zero products left out
+// (IEEE arithmetic does not let the compiler drop x * 0 by itself)
+__device__ __forceinline__ float3 cross_y_acc(float3 a, float r, float3 c) {
+    return f3(fmaf(-a.z, r, c.x), c.y, fmaf(a.x, r, c.z));
+}
+__device__ __forceinline__ float3 cross_z_acc(float3 a, float r, float3 c) {
+    return f3(fmaf(a.y, r, c.x), fmaf(-a.x, r, c.y), c.z);
+}
+
 // Coordinate rotations (parent -> child coordinates, E) of a frame turned by +q
 // about x or y, with (c, s) = (cos q, sin q), and their transposes.
 __device__ __forceinline__ float3 Ex(float c, float s, float3 v) { return f3(v.x, c * v.y + s * v.z, c * v.z - s * v.y); }
@@ -190,16 +204,24 @@ __device__ __forceinline__ void congruence(Sym6& M, float c, float s, float3 r) 
         for (int j = 0; j < 3; j++) M.B[i][j] += T[i][j];
 }
 
-// M [w; v] for a full symmetric spatial matrix
-__device__ __forceinline__ void sym6_mv(const Sym6& M, float3 w, float3 v, float3& ha, float3& hl) {
-    const float* A = M.A;
-    const float* C = M.C;
-    ha = f3(A[0] * w.x + A[1] * w.y + A[2] * w.z + M.B[0][0] * v.x + M.B[0][1] * v.y + M.B[0][2] * v.z,
-            A[1] * w.x + A[3] * w.y + A[4] * w.z + M.B[1][0] * v.x + M.B[1][1] * v.y + M.B[1][2] * v.z,
-            A[2] * w.x + A[4] * w.y + A[5] * w.z + M.B[2][0] * v.x + M.B[2][1] * v.y + M.B[2][2] * v.z);
-    hl = f3(M.B[0][0] * w.x + M.B[1][0] * w.y + M.B[2][0] * w.z + C[0] * v.x + C[1] * v.y + C[2] * v.z,
-            M.B[0][1] * w.x + M.B[1][1] * w.y + M.B[2][1] * w.z + C[1] * v.x + C[3] * v.y + C[4] * v.z,
-            M.B[0][2] * w.x + M.B[1][2] * w.y + M.B[2][2] * w.z + C[2] * v.x + C[4] * v.y + C[5] * v.z);
+// (ha, hl) += M [w; v] for a symmetric spatial matrix M and a spatial vector
+// whose component AX (of both halves) is structurally zero
+template <int AX>
+__device__ __forceinline__ void sym6_mv_acc(const Sym6& M, float3 w, float3 v, float3& ha, float3& hl) {
+    const float w_[3] = {w.x, w.y, w.z}, v_[3] = {v.x, v.y, v.z};
+    float a[3] = {ha.x, ha.y, ha.z}, l[3] = {hl.x, hl.y, hl.z};
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            if (j == AX) continue;
+            a[i] = fmaf(M.A[sidx(i, j)], w_[j], a[i]);
+            a[i] = fmaf(M.B[i][j], v_[j], a[i]);
+            l[i] = fmaf(M.B[j][i], w_[j], l[i]);
+            l[i] = fmaf(M.C[sidx(i, j)], v_[j], l[i]);
+        }
+    ha = f3(a[0], a[1], a[2]);
+    hl = f3(l[0], l[1], l[2]);
 }
 
 // I [w; v] for a body inertia with its centre of mass on the frame's z axis
@@ -228,27 +250,31 @@ __device__ __forceinline__ Sym6 sym6_of(const BodyI& I) {
     return M;
 }
 
-// sin and cos of a bounded angle (|x| < 100): x = k pi/2 + r with a two-term
-// Cody-Waite reduction, |r| <= pi/4, Taylor polynomials to r^9 / r^10.
+// sin and cos of an angle |x| < 2^21: x = k pi + r with k the nearest integer to
+// x / pi (rounded by the 1.5 * 2^23 shift, whose low mantissa bits then hold k),
+// a two-term Cody-Waite reduction to |r| <= pi/2, Taylor polynomials to r^13 /
+// r^12 (truncation below 7e-9), and the sign (-1)^k set by flipping sign bits.
 __device__ __forceinline__ void sincos_r(float x, float& s, float& c) {
-    const float k = rintf(x * 0.636619772f);
-    float r = fmaf(k, -1.57079637f, x);
-    r = fmaf(k, 4.37113883e-08f, r);
+    const float t = fmaf(x, 0.318309886f, 12582912.f);
+    const float k = t - 12582912.f;
+    float r = fmaf(k, -3.14159274f, x);
+    r = fmaf(k, 8.74227766e-08f, r);
     const float r2 = r * r;
-    float ps = fmaf(r2, 2.75573188e-06f, -1.98412701e-04f);
-    ps = fmaf(r2, ps, 8.33333377e-03f);
-    ps = fmaf(r2, ps, -1.66666672e-01f);
+    float ps = fmaf(r2, 1.60590438e-10f, -2.50521084e-08f);
+    ps = fmaf(r2, ps, 2.75573192e-06f);
+    ps = fmaf(r2, ps, -1.98412698e-04f);
+    ps = fmaf(r2, ps, 8.33333333e-03f);
+    ps = fmaf(r2, ps, -1.66666667e-01f);
     const float sn = fmaf(r * r2, ps, r);
-    float pc = fmaf(r2, -2.75573200e-07f, 2.48015876e-05f);
-    pc = fmaf(r2, pc, -1.38888892e-03f);
-    pc = fmaf(r2, pc, 4.16666679e-02f);
+    float pc = fmaf(r2, 2.08767570e-09f, -2.75573192e-07f);
+    pc = fmaf(r2, pc, 2.48015873e-05f);
+    pc = fmaf(r2, pc, -1.38888889e-03f);
+    pc = fmaf(r2, pc, 4.16666667e-02f);
     pc = fmaf(r2, pc, -0.5f);
     const float cs = fmaf(r2, pc, 1.f);
-    const int q = ((int)k) & 3;
-    s = (q & 1) ? cs : sn;
-    c = (q & 1) ? sn : cs;
-    if (q == 1 || q == 2) c = -c;
-    if (q >= 2) s = -s;
+    const unsigned sg = (unsigned)__float_as_int(t) << 31;
+    s = __int_as_float(__float_as_int(sn) ^ (int)sg);
+    c = __int_as_float(__float_as_int(cs) ^ (int)sg);
 }
 
 // rotation matrix (body -> world) of a unit quaternion (w, x, y, z)
@@ -267,14 +293,23 @@ __device__ __forceinline__ float3 mulRT(const float R[3][3], float3 v) {
               R[0][2] * v.x + R[1][2] * v.y + R[2][2] * v.z);
 }
 
-// quaternion q <- normalise(q (x) exp(w h)), w in body coordinates
+// quaternion q <- normalise(q (x) exp(w h)), w in body coordinates.  With
+// x = (|w| h / 2)^2 the exponential's parts are power series in x, so no square
+// root, reciprocal or range reduction is needed: cos(|w| h / 2) and
+// sin(|w| h / 2) / |w| = (h / 2) sin(s) / s to x^4, truncation below 3e-10 for
+// |w| h <= 1 (a sub-step's rotation is far smaller).
 __device__ __forceinline__ void quat_integrate(float q[4], float3 w, float h) {
-    float wn = sqrtf(dot3(w, w));
-    float th = wn * h;
-    float sh, ch;
-    sincos_r(0.5f * th, sh, ch);
-    float sk = (th > 1e-4f) ? sh * __frcp_rn(wn) : 0.5f * h * (1.f - th * th * (1.f / 24.f));
-    float d0 = ch, d1 = sk * w.x, d2 = sk * w.y, d3 = sk * w.z;
+    const float hh = 0.5f * h;
+    const float x = dot3(w, w) * (hh * hh);
+    float pc = fmaf(x, 2.48015873e-05f, -1.38888889e-03f);
+    pc = fmaf(x, pc, 4.16666667e-02f);
+    pc = fmaf(x, pc, -0.5f);
+    const float d0 = fmaf(x, pc, 1.f);
+    float ps = fmaf(x, 2.75573192e-06f, -1.98412698e-04f);
+    ps = fmaf(x, ps, 8.33333333e-03f);
+    ps = fmaf(x, ps, -1.66666667e-01f);
+    const float sk = hh * fmaf(x, ps, 1.f);
+    const float d1 = sk * w.x, d2 = sk * w.y, d3 = sk * w.z;
     float r0 = q[0] * d0 - q[1] * d1 - q[2] * d2 - q[3] * d3;
     float r1 = q[0] * d1 + q[1] * d0 + q[2] * d3 - q[3] * d2;
     float r2 = q[0] * d2 - q[1] * d3 + q[2] * d0 + q[3] * d1;

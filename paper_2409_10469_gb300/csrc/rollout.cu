@@ -10,8 +10,8 @@
 
 namespace mppi {
 
-template <int TERR, bool TRAJ, bool BOX>
-__global__ void __launch_bounds__(256) k_rollout(RolloutArgs a) {
+template <int TERR, bool BOX>
+__global__ void __launch_bounds__(256, 1) k_rollout(RolloutArgs a) {
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = gt >> 2, leg = gt & 3;
     const bool valid = k < a.n;
@@ -25,28 +25,25 @@ __global__ void __launch_bounds__(256) k_rollout(RolloutArgs a) {
 #pragma unroll
         for (int i = 0; i < 3; i++) Uk[j][i] = Urow[j * NJ + 3 * leg + i];
     const HorizonArgs hz = {a.H, a.n_sub, nx, a.h, a.dt, a.inv_Hm1, a.t0, a.arm};
-    const float L = rollout_lane<TERR, TRAJ, BOX>(a.model, a.cost, hz, x0, Uk, leg, k, valid, a.traj);
+    const float L = rollout_lane<TERR, BOX>(a.model, a.cost, hz, x0, Uk, leg, k, valid, a.traj);
     if (valid && leg == 0) a.L[k] = L;
 }
 
-template <int TERR, bool TRAJ, bool BOX>
+template <int TERR, bool BOX>
 static cudaError_t launch_t(const RolloutArgs& a, int block, cudaStream_t st) {
     long threads = 4L * a.n;
     int grid = (int)((threads + block - 1) / block);
-    k_rollout<TERR, TRAJ, BOX><<<grid, block, 0, st>>>(a);
+    k_rollout<TERR, BOX><<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
-}
-
-template <int TERR, bool BOX>
-static cudaError_t launch_b(const RolloutArgs& a, int block, cudaStream_t st) {
-    return a.traj ? launch_t<TERR, true, BOX>(a, block, st) : launch_t<TERR, false, BOX>(a, block, st);
 }
 
 cudaError_t launch_rollout(const RolloutArgs& a, int block, cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
     const bool box = a.model.has_box != 0;
-    if (a.model.terrain == 1) return box ? launch_b<1, true>(a, block, st) : launch_b<1, false>(a, block, st);
-    return box ? launch_b<0, true>(a, block, st) : launch_b<0, false>(a, block, st);
+    // 0: flat plane and no static boxes (specialised); 1: plane or heightfield with static boxes
+    if (a.model.terrain != 0 || a.model.n_sbox > 0)
+        return box ? launch_t<1, true>(a, block, st) : launch_t<1, false>(a, block, st);
+    return box ? launch_t<0, true>(a, block, st) : launch_t<0, false>(a, block, st);
 }
 
 }  // namespace mppi

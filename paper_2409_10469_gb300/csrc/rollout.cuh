@@ -37,9 +37,8 @@ __device__ __forceinline__ float xsum4(float v) {
 
 // ground height and slope under (x, y): plane, or bilinear heightfield with
 // clamped edges (zero slope across a clamped edge)
-template <int TERR>
 __device__ __forceinline__ void ground(const DevModel& m, float x, float y, float& h, float& hx, float& hy) {
-    if (TERR == 0) { h = 0.f; hx = 0.f; hy = 0.f; return; }
+    if (m.terrain == 0) { h = 0.f; hx = 0.f; hy = 0.f; return; }
     float u = (x - m.hf_x0) * m.hf_inv_cell, v = (y - m.hf_y0) * m.hf_inv_cell;
     const float umax = (float)(m.hf_nx - 1), vmax = (float)(m.hf_ny - 1);
     bool inx = (u >= 0.f) && (u <= umax), iny = (v >= 0.f) && (v <= vmax);
@@ -81,43 +80,25 @@ __device__ __forceinline__ bool sphere_aabb(float3 x, float r, float3 lo, float3
     return true;
 }
 
-// Force (in body coordinates) of one contact on a sphere fixed in a body.
-// nb: normal in body coordinates, cb: sphere centre in the body frame, (w, v):
-// body velocity; the force acts at the deepest point cb - r nb.
+// Force (in body coordinates) of one contact on a sphere fixed in a body, added
+// to (torque, force) with sign SG (+1 a wrench on the body, -1 its negation as
+// it enters a bias force).  nb: normal in body coordinates, cb: sphere centre
+// in the body frame, (w, v): body velocity; the force acts at the deepest point
+// cb - r nb.  An inactive contact adds exactly zero.
+template <int SG>
 __device__ __forceinline__ void contact_wrench(const DevModel& m, float pen, float3 nb, float3 cb, float r,
                                                float3 w, float3 v, float3& torque, float3& force,
                                                bool active = true) {
-    float3 pc = cb - r * nb;
-    float3 vp = v + cross3(w, pc);
-    float vn = dot3(vp, nb);
-    const float fn = active ? fmaxf(m.kc * pen - m.cc * vn, 0.f) : 0.f;
-    float3 vt = vp - vn * nb;
+    const float3 pc = f3(fmaf(-r, nb.x, cb.x), fmaf(-r, nb.y, cb.y), fmaf(-r, nb.z, cb.z));
+    const float3 vp = cross_acc(w, pc, v);
+    const float vn = dot3(vp, nb);
+    const float fn = active ? fmaxf(fmaf(m.kc, pen, -m.cc * vn), 0.f) : 0.f;
+    const float3 vt = f3(fmaf(-vn, nb.x, vp.x), fmaf(-vn, nb.y, vp.y), fmaf(-vn, nb.z, vp.z));
     const float fr = m.mu * fn * rsqrtf(dot3(vt, vt) + m.eps2);
-    float3 f = fn * nb - fr * vt;
+    const float sn = SG > 0 ? fn : -fn, st = SG > 0 ? -fr : fr;
+    const float3 f = f3(fmaf(sn, nb.x, st * vt.x), fmaf(sn, nb.y, st * vt.y), fmaf(sn, nb.z, st * vt.z));
     force = force + f;
-    torque = torque + cross3(pc, f);
-}
-
-// all static-environment contacts of one sphere (world centre xw, radius r);
-// RT(world) maps a world vector into the body's coordinates
-template <int TERR, typename ToBody>
-__device__ __forceinline__ void sphere_env(const DevModel& m, float3 xw, float r, float3 cb, float3 w, float3 v,
-                                           const ToBody& toBody, float3& torque, float3& force) {
-    float h, hx, hy;
-    ground<TERR>(m, xw.x, xw.y, h, hx, hy);
-    float inv = rsqrtf(hx * hx + hy * hy + 1.f);
-    float3 n = f3(-hx * inv, -hy * inv, inv);
-    const float pen = r - (xw.z - h) * n.z;
-    // computed unconditionally and zeroed out of contact (no branch)
-    contact_wrench(m, fmaxf(pen, 0.f), toBody(n), cb, r, w, v, torque, force, pen > 0.f);
-    for (int b = 0; b < m.n_sbox; b++) {
-        float3 nn; float pb;
-        const float* bx = m.sbox + 6 * b;
-        const float3 lo = f3(__ldg(bx), __ldg(bx + 1), __ldg(bx + 2));
-        const float3 hi = f3(__ldg(bx + 3), __ldg(bx + 4), __ldg(bx + 5));
-        if (sphere_aabb(xw, r, lo, hi, nn, pb))
-            contact_wrench(m, pb, toBody(nn), cb, r, w, v, torque, force);
-    }
+    torque = cross_acc(pc, f, torque);
 }
 
 // world -> body coordinate maps of the two kinds of contact-sphere bodies
@@ -131,6 +112,7 @@ struct TrunkFrame {
         return f3(r00 * v.x + r01 * v.y + r02 * v.z, r10 * v.x + r11 * v.y + r12 * v.z,
                   r20 * v.x + r21 * v.y + r22 * v.z);
     }
+    __device__ __forceinline__ float3 ez() const { return f3(r20, r21, r22); }  // world e_z in body coordinates
 };
 struct CalfFrame {
     float r00, r01, r02, r10, r11, r12, r20, r21, r22;
@@ -145,6 +127,7 @@ struct CalfFrame {
         return f3(r00 * t.x + r01 * t.y + r02 * t.z, r10 * t.x + r11 * t.y + r12 * t.z,
                   r20 * t.x + r21 * t.y + r22 * t.z);
     }
+    __device__ __forceinline__ float3 ez() const { return Ey(c2, s2, Ey(c1, s1, Ex(c0, s0, f3(r20, r21, r22)))); }
 };
 
 // the free box of the push task: pose, rotation (box -> world) and body velocity
@@ -160,16 +143,17 @@ struct BoxKin {
 
 // robot sphere (world centre xw, radius r, centre cb in its body) against the
 // free box (oriented box in its own frame): equal and opposite forces at the
-// sphere's deepest point, from the relative velocity of the two body points
-template <typename Frame>
+// sphere's deepest point, from the relative velocity of the two body points.
+// The robot's share goes to (torque, force) with sign SG, the box's to (bt, bf).
+template <int SG, typename Frame>
 __device__ __forceinline__ void sphere_vs_box(const DevModel& m, const BoxKin& B, float3 xw, float r, float3 cb,
                                               float3 w, float3 v, const Frame& F, float3& torque, float3& force,
-                                              float3& bt, float3& bf) {
+                                              float3& bt, float3& bf, bool on = true) {
     const float3 xl = mulRT(B.R, xw - B.p);
     const float3 hb = f3(m.box_half[0], m.box_half[1], m.box_half[2]);
     float3 nl;
     float pen;
-    if (!sphere_aabb(xl, r, -hb, hb, nl, pen)) return;
+    if (!on || !sphere_aabb(xl, r, -hb, hb, nl, pen)) return;
     const float3 nw = mulR(B.R, nl);
     const float3 nb = F(nw);
     const float3 pc_b = cb - r * nb;                      // contact point, robot body frame
@@ -182,12 +166,42 @@ __device__ __forceinline__ void sphere_vs_box(const DevModel& m, const BoxKin& B
     const float3 vt = vrel - vn * nw;
     const float fr = m.mu * fn * rsqrtf(dot3(vt, vt) + m.eps2);
     const float3 fw = fn * nw - fr * vt;
-    const float3 fbody = F(fw);
+    const float3 fbody = SG > 0 ? F(fw) : -F(fw);
     force = force + fbody;
     torque = torque + cross3(pc_b, fbody);
     const float3 fl = -mulRT(B.R, fw);
     bf = bf + fl;
     bt = bt + cross3(pc_l, fl);
+}
+
+// All static-environment contacts of one sphere (world centre xw, radius r),
+// added with sign SG; toBody maps a world vector into the body's coordinates.
+// TERR 0: flat ground and no static boxes (normal e_z, depth r - z); TERR 1:
+// the model's plane or heightfield and its static boxes.  A sphere that is not
+// `on` adds exactly zero.
+template <int TERR, int SG, typename ToBody>
+__device__ __forceinline__ void sphere_env(const DevModel& m, float3 xw, float r, float3 cb, float3 w, float3 v,
+                                           const ToBody& toBody, float3& torque, float3& force, bool on = true) {
+    if (TERR == 0) {
+        const float pen = r - xw.z;
+        contact_wrench<SG>(m, fmaxf(pen, 0.f), toBody.ez(), cb, r, w, v, torque, force, on && pen > 0.f);
+        return;
+    }
+    float h, hx, hy;
+    ground(m, xw.x, xw.y, h, hx, hy);
+    float inv = rsqrtf(hx * hx + hy * hy + 1.f);
+    float3 n = f3(-hx * inv, -hy * inv, inv);
+    const float pen = r - (xw.z - h) * n.z;
+    // computed unconditionally and zeroed out of contact (no branch)
+    contact_wrench<SG>(m, fmaxf(pen, 0.f), toBody(n), cb, r, w, v, torque, force, on && pen > 0.f);
+    for (int b = 0; b < m.n_sbox; b++) {
+        float3 nn; float pb;
+        const float* bx = m.sbox + 6 * b;
+        const float3 lo = f3(__ldg(bx), __ldg(bx + 1), __ldg(bx + 2));
+        const float3 hi = f3(__ldg(bx + 3), __ldg(bx + 4), __ldg(bx + 5));
+        if (on && sphere_aabb(xw, r, lo, hi, nn, pb))
+            contact_wrench<SG>(m, pb, toBody(nn), cb, r, w, v, torque, force);
+    }
 }
 
 // ---------------------------------------------------------------- cost
@@ -217,6 +231,10 @@ __device__ __forceinline__ float box_cost(const DevCost& c, const BoxState& B) {
 template <int AX> __device__ __forceinline__ float3 vprod(float3 a, float qd) {
     return AX == 0 ? f3(0.f, a.z * qd, -a.y * qd) : f3(-a.z * qd, 0.f, a.x * qd);
 }
+// a + c for such a term (its component AX is structurally zero)
+template <int AX> __device__ __forceinline__ float3 add_vp(float3 a, float3 c) {
+    return AX == 0 ? f3(a.x, a.y + c.y, a.z + c.z) : f3(a.x + c.x, a.y, a.z + c.z);
+}
 
 // Ia = IA - U U^T / D  and  pa = pA + Ia c + U u / D for a joint about AX
 // (U = IA e_AX); c has zero entries on the joint axis (structure of vprod).
@@ -242,30 +260,38 @@ __device__ __forceinline__ void project(Sym6& M, float3& pn, float3& pf, float D
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) M.B[i][j] = fmaf(-Uas[i], Ul[j], M.B[i][j]);
-    // Ia c with c zero on component AX of both halves
-    const float cw_[3] = {cw.x, cw.y, cw.z}, cv_[3] = {cv.x, cv.y, cv.z};
-    float n[3] = {pn.x, pn.y, pn.z}, f[3] = {pf.x, pf.y, pf.z};
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int l = 0; l < 3; l++) {
-            if (l == AX) continue;
-            n[i] = fmaf(M.A[sidx(i, l)], cw_[l], n[i]);
-            n[i] = fmaf(M.B[i][l], cv_[l], n[i]);
-            f[i] = fmaf(M.B[l][i], cw_[l], f[i]);
-            f[i] = fmaf(M.C[sidx(i, l)], cv_[l], f[i]);
-        }
+    sym6_mv_acc<AX>(M, cw, cv, pn, pf);
     const float k = uu * Dinv;
-    pn = f3(fmaf(k, Ua[0], n[0]), fmaf(k, Ua[1], n[1]), fmaf(k, Ua[2], n[2]));
-    pf = f3(fmaf(k, Ul[0], f[0]), fmaf(k, Ul[1], f[1]), fmaf(k, Ul[2], f[2]));
+    pn = f3(fmaf(k, Ua[0], pn.x), fmaf(k, Ua[1], pn.y), fmaf(k, Ua[2], pn.z));
+    pf = f3(fmaf(k, Ul[0], pf.x), fmaf(k, Ul[1], pf.y), fmaf(k, Ul[2], pf.z));
 }
 
-// bias force v x* I v of a body with a structured inertia
-__device__ __forceinline__ void body_bias(const BodyI& I, float3 w, float3 v, float3& bn, float3& bf) {
+// bias force v x* I v of a body with a structured inertia, added to (bn, bf)
+__device__ __forceinline__ void body_bias_acc(const BodyI& I, float3 w, float3 v, float3& bn, float3& bf) {
     float3 ha, hl;
     bodyI_mv(I, w, v, ha, hl);
-    bn = cross3(w, ha) + cross3(v, hl);
-    bf = cross3(w, hl);
+    bn = cross_acc(v, hl, cross_acc(w, ha, bn));
+    bf = cross_acc(w, hl, bf);
+}
+
+// Spatial force p in a child frame (joint about AX at angle (c, s), joint
+// origin r in the parent) to the parent: X^T p = [E^T n + r x E^T f; E^T f].
+// The origins of the knee (0, 0, rz) and the flexion joint (0, ry, 0) lie on a
+// coordinate axis; the abduction joint's origin is general.
+__device__ __forceinline__ void force_up_knee(float c, float s, float rz, float3& n, float3& f) {
+    const float3 fn = EyT(c, s, n), ff = EyT(c, s, f);
+    n = cross_z_acc(ff, -rz, fn);     // fn + (0, 0, rz) x ff
+    f = ff;
+}
+__device__ __forceinline__ void force_up_flex(float c, float s, float ry, float3& n, float3& f) {
+    const float3 fn = EyT(c, s, n), ff = EyT(c, s, f);
+    n = cross_y_acc(ff, -ry, fn);     // fn + (0, ry, 0) x ff
+    f = ff;
+}
+__device__ __forceinline__ void force_up_abd(float c, float s, float3 r, float3& n, float3& f) {
+    const float3 fn = ExT(c, s, n), ff = ExT(c, s, f);
+    n = cross_acc(r, ff, fn);
+    f = ff;
 }
 
 template <int TERR, bool BOX>
@@ -290,43 +316,94 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
     sincos_r(S.q[2], s2, c2);
     // legs FR, FL, RR, RL: front (+x) for legs 0, 1; left (+y) for odd legs
     const float fx = leg < 2 ? 1.f : -1.f, sy = (leg & 1) ? 1.f : -1.f;
-    const float3 rh = f3(fx * m.hip_x, sy * m.hip_y, m.hip_z);
-    const float3 rt = f3(0.f, sy * m.thigh_y, 0.f);
-    const float3 rk = f3(0.f, 0.f, m.r_knee[2]);
+    const float3 rh = f3(fx * m.hip_x, sy * m.hip_y, m.hip_z);   // abduction joint in the trunk
+    const float ty = sy * m.thigh_y;                               // flexion joint (0, ty, 0) in the hip
+    const float kz = m.r_knee[2], fz = m.foot[2];                  // knee (0, 0, kz), foot (0, 0, fz)
     float3 wh = Ex(c0, s0, T.w);
-    float3 vh = Ex(c0, s0, T.v + cross3(T.w, rh));
+    float3 vh = Ex(c0, s0, cross_acc(T.w, rh, T.v));
     const float3 ch_w = vprod<0>(wh, S.qd[0]), ch_v = vprod<0>(vh, S.qd[0]);
     wh.x += S.qd[0];
     float3 wt = Ey(c1, s1, wh);
-    float3 vt = Ey(c1, s1, vh + cross3(wh, rt));
+    float3 vt = Ey(c1, s1, cross_y_acc(wh, ty, vh));
     const float3 ct_w = vprod<1>(wt, S.qd[1]), ct_v = vprod<1>(vt, S.qd[1]);
     wt.y += S.qd[1];
     float3 wc = Ey(c2, s2, wt);
-    float3 vc = Ey(c2, s2, vt + cross3(wt, rk));
+    float3 vc = Ey(c2, s2, cross_z_acc(wt, kz, vt));
     const float3 cc_w = vprod<1>(wc, S.qd[2]), cc_v = vprod<1>(vc, S.qd[2]);
     wc.y += S.qd[2];
 
-    // ---- contacts: the foot sphere on the calf
-    float3 fc_n = f3(0.f, 0.f, 0.f), fc_f = f3(0.f, 0.f, 0.f);
+    // ---- PD with implicit damping: tau = kp (u - q - h qd) - kd qd, armature h (kd + h kp)
+    float tau[3];
+#pragma unroll
+    for (int i = 0; i < 3; i++) tau[i] = m.kp * (u[i] - S.q[i] - h * S.qd[i]) - m.kd * S.qd[i];
+
+    // ---- pass 2 (tip to root), calf: its bias minus the foot's contact wrench
+    float3 pa_n = f3(0.f, 0.f, 0.f), pa_f = f3(0.f, 0.f, 0.f);
+    body_bias_acc(m.I_calf, wc, vc, pa_n, pa_f);
     {
-        const float3 foot = f3(0.f, 0.f, m.foot[2]);
-        float3 ptr = rh + ExT(c0, s0, rt + EyT(c1, s1, rk + EyT(c2, s2, foot)));   // trunk frame
-        float3 xw = f3(T.p[0], T.p[1], T.p[2]) + mulR(R0, ptr);
+        const float3 foot = f3(0.f, 0.f, fz);
+        // foot centre in the trunk frame: rh + E0^T ((0, ty, 0) + E1^T ((0, 0, kz) + E2^T foot))
+        const float ax = s2 * fz, az = fmaf(c2, fz, kz);
+        const float bx = fmaf(c1, ax, s1 * az), bz = fmaf(c1, az, -s1 * ax);
+        const float3 ptr = f3(rh.x + bx, rh.y + fmaf(c0, ty, -s0 * bz), rh.z + fmaf(s0, ty, c0 * bz));
+        const float3 xw = f3(T.p[0], T.p[1], T.p[2]) + mulR(R0, ptr);
         const CalfFrame toCalf = {R0[0][0], R0[0][1], R0[0][2], R0[1][0], R0[1][1], R0[1][2],
                                   R0[2][0], R0[2][1], R0[2][2], c0, s0, c1, s1, c2, s2};
-        sphere_env<TERR>(m, xw, m.foot_r, foot, wc, vc, toCalf, fc_n, fc_f);
-        if (BOX) sphere_vs_box(m, BK, xw, m.foot_r, foot, wc, vc, toCalf, fc_n, fc_f, bx_t, bx_f);
+        sphere_env<TERR, -1>(m, xw, m.foot_r, foot, wc, vc, toCalf, pa_n, pa_f);
+        if (BOX) sphere_vs_box<-1>(m, BK, xw, m.foot_r, foot, wc, vc, toCalf, pa_n, pa_f, bx_t, bx_f);
     }
-    // ---- contacts: trunk spheres, one per lane, summed over the 4 lanes below
-    float3 f0_n = f3(0.f, 0.f, 0.f), f0_f = f3(0.f, 0.f, 0.f);
-    if (leg < m.n_tsph) {
+    // the calf's articulated inertia after projection is a model constant
+    const float D2inv = m.calf_D_inv;
+    const float u2 = tau[2] - pa_n.y;
+    // U2 = I_calf e_y = (0, ay, 0 | mcz, 0, 0)
+    const float U2a = m.I_calf.ay, U2l = m.I_calf.mcz;
+    {
+        sym6_mv_acc<1>(m.Ia_calf, cc_w, cc_v, pa_n, pa_f);
+        const float k = u2 * D2inv;
+        pa_n.y = fmaf(k, U2a, pa_n.y);
+        pa_f.x = fmaf(k, U2l, pa_f.x);
+    }
+    // to the thigh frame
+    Sym6 IA = m.Ia_calf;
+    float U1a[3], U1l[3], D1inv, u1;
+    {
+        force_up_knee(c2, s2, kz, pa_n, pa_f);
+        congruence<1, 4>(IA, c2, s2, f3(0.f, 0.f, kz));
+        add_bodyI(IA, m.I_thigh);
+        body_bias_acc(m.I_thigh, wt, vt, pa_n, pa_f);
+#pragma unroll
+        for (int i = 0; i < 3; i++) { U1a[i] = IA.A[sidx(i, 1)]; U1l[i] = IA.B[1][i]; }
+        D1inv = __fdividef(1.f, U1a[1] + arm);
+        u1 = tau[1] - pa_n.y;
+    }
+    project<1>(IA, pa_n, pa_f, D1inv, u1, ct_w, ct_v);
+    float U0a[3], U0l[3], D0inv, u0;
+    {   // to the hip frame
+        force_up_flex(c1, s1, ty, pa_n, pa_f);
+        congruence<1, 2>(IA, c1, s1, f3(0.f, ty, 0.f));
+        add_bodyI(IA, m.I_hip);
+        body_bias_acc(m.I_hip, wh, vh, pa_n, pa_f);
+#pragma unroll
+        for (int i = 0; i < 3; i++) { U0a[i] = IA.A[sidx(i, 0)]; U0l[i] = IA.B[0][i]; }
+        D0inv = __fdividef(1.f, U0a[0] + arm);
+        u0 = tau[0] - pa_n.x;
+    }
+    project<0>(IA, pa_n, pa_f, D0inv, u0, ch_w, ch_v);
+    // to the trunk frame
+    force_up_abd(c0, s0, rh, pa_n, pa_f);
+    congruence<0, 7>(IA, c0, s0, rh);
+
+    // ---- contacts of the trunk spheres, one per lane (lanes past the last
+    // sphere compute a zero wrench), minus into this lane's trunk bias
+    {
+        const bool on = leg < m.n_tsph;
         const float tx = leg == 0 ? m.tsph_x[0] : (leg == 1 ? m.tsph_x[1] : (leg == 2 ? m.tsph_x[2] : m.tsph_x[3]));
-        float3 cb = f3(tx, 0.f, 0.f);
-        float3 xw = f3(T.p[0], T.p[1], T.p[2]) + mulR(R0, cb);
+        const float3 cb = f3(tx, 0.f, 0.f);
+        const float3 xw = f3(fmaf(R0[0][0], tx, T.p[0]), fmaf(R0[1][0], tx, T.p[1]), fmaf(R0[2][0], tx, T.p[2]));
         const TrunkFrame toTrunk = {R0[0][0], R0[0][1], R0[0][2], R0[1][0], R0[1][1], R0[1][2],
                                     R0[2][0], R0[2][1], R0[2][2]};
-        sphere_env<TERR>(m, xw, m.tsph_r, cb, T.w, T.v, toTrunk, f0_n, f0_f);
-        if (BOX) sphere_vs_box(m, BK, xw, m.tsph_r, cb, T.w, T.v, toTrunk, f0_n, f0_f, bx_t, bx_f);
+        sphere_env<TERR, -1>(m, xw, m.tsph_r, cb, T.w, T.v, toTrunk, pa_n, pa_f, on);
+        if (BOX) sphere_vs_box<-1>(m, BK, xw, m.tsph_r, cb, T.w, T.v, toTrunk, pa_n, pa_f, bx_t, bx_f, on);
     }
     // ---- the box's 8 corner spheres against the static environment, 2 per lane
     if (BOX) {
@@ -338,73 +415,8 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
             const float3 cl = f3((cn & 1) ? m.box_half[0] : -m.box_half[0], (cn & 2) ? m.box_half[1] : -m.box_half[1],
                                  (cn & 4) ? m.box_half[2] : -m.box_half[2]);
             const float3 xc = BK.p + mulR(BK.R, cl);
-            sphere_env<TERR>(m, xc, m.box_cr, cl, BK.w, BK.v, toBox, bx_t, bx_f);
+            sphere_env<TERR, 1>(m, xc, m.box_cr, cl, BK.w, BK.v, toBox, bx_t, bx_f);
         }
-    }
-
-    // ---- PD with implicit damping: tau = kp (u - q - h qd) - kd qd, armature h (kd + h kp)
-    float tau[3];
-#pragma unroll
-    for (int i = 0; i < 3; i++) tau[i] = m.kp * (u[i] - S.q[i] - h * S.qd[i]) - m.kd * S.qd[i];
-
-    // ---- pass 2 (tip to root)
-    // calf: its articulated inertia after projection is a model constant
-    Sym6 IA = m.Ia_calf;
-    float3 pa_n, pa_f;
-    body_bias(m.I_calf, wc, vc, pa_n, pa_f);
-    pa_n = pa_n - fc_n;
-    pa_f = pa_f - fc_f;
-    const float D2inv = m.calf_D_inv;
-    const float u2 = tau[2] - pa_n.y;
-    // U2 = I_calf e_y = (0, ay, 0 | mcz, 0, 0)
-    const float U2a = m.I_calf.ay, U2l = m.I_calf.mcz;
-    {
-        float3 ia, il;
-        sym6_mv(IA, cc_w, cc_v, ia, il);
-        const float k = u2 * D2inv;
-        pa_n = pa_n + ia + f3(0.f, k * U2a, 0.f);
-        pa_f = pa_f + il + f3(k * U2l, 0.f, 0.f);
-    }
-    // to the thigh frame: X^T pa = [E^T n + r x E^T f; E^T f]
-    float U1a[3], U1l[3], D1inv, u1;
-    {
-        float3 fn = EyT(c2, s2, pa_n), ff = EyT(c2, s2, pa_f);
-        pa_n = fn + cross3(rk, ff);
-        pa_f = ff;
-        congruence<1, 4>(IA, c2, s2, rk);
-        add_bodyI(IA, m.I_thigh);
-        float3 bn, bf;
-        body_bias(m.I_thigh, wt, vt, bn, bf);
-        pa_n = pa_n + bn;
-        pa_f = pa_f + bf;
-#pragma unroll
-        for (int i = 0; i < 3; i++) { U1a[i] = IA.A[sidx(i, 1)]; U1l[i] = IA.B[1][i]; }
-        D1inv = __fdividef(1.f, U1a[1] + arm);
-        u1 = tau[1] - pa_n.y;
-    }
-    project<1>(IA, pa_n, pa_f, D1inv, u1, ct_w, ct_v);
-    float U0a[3], U0l[3], D0inv, u0;
-    {   // to the hip frame
-        float3 fn = EyT(c1, s1, pa_n), ff = EyT(c1, s1, pa_f);
-        pa_n = fn + cross3(rt, ff);
-        pa_f = ff;
-        congruence<1, 2>(IA, c1, s1, rt);
-        add_bodyI(IA, m.I_hip);
-        float3 bn, bf;
-        body_bias(m.I_hip, wh, vh, bn, bf);
-        pa_n = pa_n + bn;
-        pa_f = pa_f + bf;
-#pragma unroll
-        for (int i = 0; i < 3; i++) { U0a[i] = IA.A[sidx(i, 0)]; U0l[i] = IA.B[0][i]; }
-        D0inv = __fdividef(1.f, U0a[0] + arm);
-        u0 = tau[0] - pa_n.x;
-    }
-    project<0>(IA, pa_n, pa_f, D0inv, u0, ch_w, ch_v);
-    {   // to the trunk frame
-        float3 fn = ExT(c0, s0, pa_n), ff = ExT(c0, s0, pa_f);
-        pa_n = fn + cross3(rh, ff);
-        pa_f = ff;
-        congruence<0, 7>(IA, c0, s0, rh);
     }
 
     // ---- trunk: sum the 4 legs' contributions, add the trunk's own terms
@@ -426,16 +438,14 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
         Mt[3 + i][3 + i] += m.tr_m;
     }
     {
-        // per-lane terms (leg bias, minus this lane's trunk-sphere wrench) summed
+        // per-lane terms (leg bias less this lane's trunk-sphere wrench) summed
         // over the 4 lanes, then the trunk's own bias v x* I v once
-        float3 Iw = f3(m.tr_Ic[0] * T.w.x, m.tr_Ic[1] * T.w.y, m.tr_Ic[2] * T.w.z);
-        float3 bn = cross3(T.w, Iw), bf = m.tr_m * cross3(T.w, T.v);
-        bt[0] = xsum4(pa_n.x - f0_n.x) + bn.x;
-        bt[1] = xsum4(pa_n.y - f0_n.y) + bn.y;
-        bt[2] = xsum4(pa_n.z - f0_n.z) + bn.z;
-        bt[3] = xsum4(pa_f.x - f0_f.x) + bf.x;
-        bt[4] = xsum4(pa_f.y - f0_f.y) + bf.y;
-        bt[5] = xsum4(pa_f.z - f0_f.z) + bf.z;
+        const float3 Iw = f3(m.tr_Ic[0] * T.w.x, m.tr_Ic[1] * T.w.y, m.tr_Ic[2] * T.w.z);
+        const float3 bn = cross_acc(T.w, Iw, f3(xsum4(pa_n.x), xsum4(pa_n.y), xsum4(pa_n.z)));
+        const float3 mv = m.tr_m * T.v;
+        const float3 bf = cross_acc(T.w, mv, f3(xsum4(pa_f.x), xsum4(pa_f.y), xsum4(pa_f.z)));
+        bt[0] = bn.x; bt[1] = bn.y; bt[2] = bn.z;
+        bt[3] = bf.x; bt[4] = bf.y; bt[5] = bf.z;
     }
     // ---- solve Mt a' = -bt by the Schur complement of the linear block:
     // Mt = [A B; B^T C], C^-1 and S^-1 (S = A - B C^-1 B^T) by 3x3 cofactors
@@ -493,13 +503,13 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
     float qdd[3];
     const float3 aw = f3(a0[0], a0[1], a0[2]), av = f3(a0[3], a0[4], a0[5]);
     {
-        float3 nw = Ex(c0, s0, aw) + ch_w, nv = Ex(c0, s0, av + cross3(aw, rh)) + ch_v;
+        float3 nw = add_vp<0>(Ex(c0, s0, aw), ch_w), nv = add_vp<0>(Ex(c0, s0, cross_acc(aw, rh, av)), ch_v);
         qdd[0] = (u0 - (U0a[0] * nw.x + U0a[1] * nw.y + U0a[2] * nw.z + U0l[0] * nv.x + U0l[1] * nv.y + U0l[2] * nv.z)) * D0inv;
         nw.x += qdd[0];
-        float3 tw = Ey(c1, s1, nw) + ct_w, tv = Ey(c1, s1, nv + cross3(nw, rt)) + ct_v;
+        float3 tw = add_vp<1>(Ey(c1, s1, nw), ct_w), tv = add_vp<1>(Ey(c1, s1, cross_y_acc(nw, ty, nv)), ct_v);
         qdd[1] = (u1 - (U1a[0] * tw.x + U1a[1] * tw.y + U1a[2] * tw.z + U1l[0] * tv.x + U1l[1] * tv.y + U1l[2] * tv.z)) * D1inv;
         tw.y += qdd[1];
-        float3 kw = Ey(c2, s2, tw) + cc_w, kv = Ey(c2, s2, tv + cross3(tw, rk)) + cc_v;
+        float3 kw = add_vp<1>(Ey(c2, s2, tw), cc_w), kv = add_vp<1>(Ey(c2, s2, cross_z_acc(tw, kz, tv)), cc_v);
         qdd[2] = (u2 - (U2a * kw.y + U2l * kv.x)) * D2inv;
     }
 
@@ -572,9 +582,20 @@ __device__ __forceinline__ void store_state(float* traj, int H, int k, int t, in
 }
 
 
+// The trajectory pointer through an opaque move inside the horizon loop, so that
+// the compiler keeps one copy of the loop (no unswitching on traj == nullptr):
+// rollouts with and without trajectory output run the same instructions and
+// give bit-identical results.
+__device__ __forceinline__ float* opaque_ptr(float* p) {
+    float* q;
+    asm volatile("mov.b64 %0, %1;" : "=l"(q) : "l"(p));
+    return q;
+}
+
 // One lane's share of rollout k: x0 (state), Uk[4][3] (this leg's knots), the
-// horizon; returns the rollout's total cost on every lane of the rollout.
-template <int TERR, bool TRAJ, bool BOX>
+// horizon, optional trajectory output traj (float[n][H + 1][nx], or nullptr);
+// returns the rollout's total cost on every lane of the rollout.
+template <int TERR, bool BOX>
 __device__ __forceinline__ float rollout_lane(const DevModel& m, const DevCost& c, const HorizonArgs& a,
                                               const float* x0, const float (&Uk)[NKNOT][3], int leg, int k,
                                               bool valid, float* traj) {
@@ -600,7 +621,7 @@ __device__ __forceinline__ float rollout_lane(const DevModel& m, const DevCost& 
     const float h = a.h;
     const float ph0 = (leg == 1 || leg == 2) ? 3.14159265358979f : 0.f;
     float L = 0.f;
-    if (TRAJ) store_state<BOX>(traj, a.H, k, 0, leg, valid, T, S, Bx, a.nx);
+    if (float* tp = opaque_ptr(traj)) store_state<BOX>(tp, a.H, k, 0, leg, valid, T, S, Bx, a.nx);
     for (int t = 0; t < a.H; t++) {
         // cubic through 4 knots at tau_j = j / 3 (Lagrange basis)
         const float tau = (float)t * a.inv_Hm1;
@@ -624,7 +645,7 @@ __device__ __forceinline__ float rollout_lane(const DevModel& m, const DevCost& 
             if (leg == 0) L += trunk_state_cost(c, T) + (BOX ? box_cost(c, Bx) : 0.f);
         }
         for (int sb = 0; sb < a.n_sub; sb++) substep<TERR, BOX>(m, leg, T, S, u, h, a.arm, Bx);
-        if (TRAJ) store_state<BOX>(traj, a.H, k, t + 1, leg, valid, T, S, Bx, a.nx);
+        if (float* tp = opaque_ptr(traj)) store_state<BOX>(tp, a.H, k, t + 1, leg, valid, T, S, Bx, a.nx);
     }
     if (leg == 0) L += c.w_term * (trunk_state_cost(c, T) + (BOX ? box_cost(c, Bx) : 0.f));
     return xsum4(L);
