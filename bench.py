@@ -37,7 +37,7 @@ METRIC = "rollout-steps/s (MPPI step, K=4096, H=100)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture) of
 # one k_rollout launch on this workload, valid only for the kernel sources whose
 # SHA-256 prefix is given; reported as null once those sources change.
-ROLLOUT_TRAFFIC = {"bytes": 826624, "sources_sha256": "59c22fca46d063bc"}
+ROLLOUT_TRAFFIC = {"bytes": 866304, "sources_sha256": "13153ca5ac889870"}
 ROLLOUT_SOURCES = ("rollout.cu", "rollout.cuh", "common.cuh")
 
 
@@ -57,52 +57,83 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every `period_ms` by one
+    `nvidia-smi -lms` process started before the warm-up; the summary keeps the
+    samples that fall inside the timed region (marked by `window()`)."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, period_ms: int = 50):
         self.idx = gpu_index
-        self.rows = []
-        self._stop = threading.Event()
+        self.period_ms = period_ms
+        self.rows = []          # (host time, fields)
+        self.t0 = self.t1 = None
+        self._p = None
         self._t = None
 
-    def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
-                                      "--format=csv,noheader,nounits"], capture_output=True,
-                                     text=True, timeout=5).stdout.strip()
-                if out:
-                    self.rows.append([s.strip() for s in out.split(",")])
-            except Exception:
-                pass
-            self._stop.wait(0.2)
+    def _read(self):
+        for line in self._p.stdout:
+            f = [x.strip() for x in line.strip().split(",")]
+            if len(f) >= 9:
+                self.rows.append((time.perf_counter(), f))
 
-    def __enter__(self):
-        self._t = threading.Thread(target=self._run, daemon=True)
+    def start(self):
+        try:
+            self._p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                        "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
+                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self._p = None
+            return self
+        self._t = threading.Thread(target=self._read, daemon=True)
         self._t.start()
         return self
 
-    def __exit__(self, *a):
-        self._stop.set()
-        self._t.join(timeout=6)
+    def stop(self):
+        if self._p is not None:
+            self._p.terminate()
+            try:
+                self._p.wait(timeout=5)
+            except Exception:
+                self._p.kill()
+            self._t.join(timeout=5)
+            self._p = None
+
+    class _Window:
+        def __init__(self, s):
+            self.s = s
+
+        def __enter__(self):
+            self.s.t0 = time.perf_counter()
+
+        def __exit__(self, *a):
+            self.s.t1 = time.perf_counter()
+
+    def window(self):
+        return ClockSampler._Window(self)
 
     def summary(self):
-        if not self.rows:
+        rows = [f for t, f in self.rows
+                if self.t0 is not None and self.t1 is not None and self.t0 - 0.06 <= t <= self.t1 + 0.06]
+        where = "timed region"
+        if not rows and self.rows:   # region shorter than the sampling period: the nearest samples
+            mid = 0.5 * (self.t0 + self.t1) if self.t0 is not None and self.t1 is not None else 0.0
+            rows = [f for t, f in sorted(self.rows, key=lambda r: abs(r[0] - mid))[:2]]
+            where = "nearest to the timed region"
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = set()
-        for r in self.rows:
+        for r in rows:
             for n, v in zip(names, r[5:9]):
                 if v.strip().lower() == "active":
                     reasons.add(n)
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(self.rows)}
+                "samples": len(rows), "sampled": where, "period_ms": self.period_ms}
 
 
 def measured_peaks():
@@ -197,6 +228,10 @@ def run_ours(args):
     u0_d = torch.empty(12, dtype=torch.float32, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
 
+    # clocks: one nvidia-smi stream from before the warm-up to the end of the run
+    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[0])
+                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local_rank).start()
+
     # warm-up
     for s in range(args.warmup):
         ctl.step(x0_d, s, u0_out=u0_d)
@@ -210,9 +245,7 @@ def run_ours(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[0])
-                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local_rank)
-    with sampler:
+    with sampler.window():
         for s in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.fill_(float(s))          # evict L2 between steps (outside the events)
@@ -223,13 +256,13 @@ def run_ours(args):
                 stream.synchronize()
             k_ms.append(None)
         torch.cuda.synchronize()
-        # per-kernel times of every step: re-run with the library's events read per step
-        ker = []
-        for s in range(min(args.steps, 64)):
-            with torch.cuda.stream(stream):
-                flush.fill_(float(s))
-            ctl.step(x0_d, args.warmup + args.steps + s, u0_out=u0_d)
-            ker.append(ctl.timings())
+    # per-kernel times of every step: re-run with the library's events read per step
+    ker = []
+    for s in range(min(args.steps, 64)):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(s))
+        ctl.step(x0_d, args.warmup + args.steps + s, u0_out=u0_d)
+        ker.append(ctl.timings())
     launches = ctl.launch_count() - launches0
     if dist:
         dist.barrier()
@@ -253,6 +286,7 @@ def run_ours(args):
         ctl.step(x0_h, 10000 + s, u0_out=u0_h)
         e2e.append(time.perf_counter() - t)
     e2e_ms = float(np.mean(e2e)) * 1e3
+    sampler.stop()
     clocks = sampler.summary()
     ctl.close()
 
