@@ -121,87 +121,114 @@ template <int AX> struct RotIdx {
     static constexpr float sg = AX == 0 ? -1.f : 1.f;
 };
 
-// S <- R S R^T for a symmetric 3x3 in unique storage
-template <int AX> __device__ __forceinline__ void rot_sym(float S[6], float c, float s) {
+// S <- R S R^T (+ diag(d) when ADD) for a symmetric 3x3 in unique storage.  The
+// rotated diagonal entries take d as the seed of their FMA chains, so only the
+// entry on the joint axis pays an addition.
+template <int AX, bool ADD>
+__device__ __forceinline__ void rot_sym(float S[6], float c, float s, float3 d) {
     using I = RotIdx<AX>;
+    const float dg[3] = {d.x, d.y, d.z};
     const float cs = I::sg * c * s, cc = c * c, ss = s * s;
     const float Sop = S[sidx(I::o, I::p)], Soq = S[sidx(I::o, I::q)];
     const float Spp = S[sidx(I::p, I::p)], Sqq = S[sidx(I::q, I::q)], Spq = S[sidx(I::p, I::q)];
-    S[sidx(I::o, I::p)] = c * Sop + I::sg * s * Soq;
-    S[sidx(I::o, I::q)] = c * Soq - I::sg * s * Sop;
-    const float t = 2.f * cs * Spq;
-    S[sidx(I::p, I::p)] = cc * Spp + ss * Sqq + t;
-    S[sidx(I::q, I::q)] = cc * Sqq + ss * Spp - t;
-    S[sidx(I::p, I::q)] = (cc - ss) * Spq + cs * (Sqq - Spp);
+    S[sidx(I::o, I::p)] = fmaf(c, Sop, I::sg * s * Soq);
+    S[sidx(I::o, I::q)] = fmaf(c, Soq, -I::sg * s * Sop);
+    const float t2 = 2.f * cs;
+    S[sidx(I::p, I::p)] = fmaf(cc, Spp, fmaf(ss, Sqq, fmaf(t2, Spq, ADD ? dg[I::p] : 0.f)));
+    S[sidx(I::q, I::q)] = fmaf(cc, Sqq, fmaf(ss, Spp, fmaf(-t2, Spq, ADD ? dg[I::q] : 0.f)));
+    S[sidx(I::p, I::q)] = fmaf(cc - ss, Spq, cs * (Sqq - Spp));
+    if (ADD) S[sidx(I::o, I::o)] += dg[I::o];
 }
 
 // B <- R B R^T for a general 3x3
-template <int AX> __device__ __forceinline__ void rot_gen(float B[3][3], float c, float s) {
+template <int AX>
+__device__ __forceinline__ void rot_gen(float B[3][3], float c, float s) {
     using I = RotIdx<AX>;
+    const float ss_ = I::sg * s;
 #pragma unroll
     for (int j = 0; j < 3; j++) {
         float a = B[I::p][j], b = B[I::q][j];
-        B[I::p][j] = c * a + I::sg * s * b;
-        B[I::q][j] = c * b - I::sg * s * a;
+        B[I::p][j] = fmaf(c, a, ss_ * b);
+        B[I::q][j] = fmaf(c, b, -ss_ * a);
     }
 #pragma unroll
     for (int i = 0; i < 3; i++) {
         float a = B[i][I::p], b = B[i][I::q];
-        B[i][I::p] = c * a + I::sg * s * b;
-        B[i][I::q] = c * b - I::sg * s * a;
+        B[i][I::p] = fmaf(c, a, ss_ * b);
+        B[i][I::q] = fmaf(c, b, -ss_ * a);
     }
 }
 
 // entry (l, j) of [r x] with structurally-zero entries known at compile time;
 // MASK bit 0/1/2 = r.x/r.y/r.z may be non-zero
 template <int MASK>
-__device__ __forceinline__ bool skew_nz(int l, int j) {
+__device__ __forceinline__ constexpr bool skew_nz(int l, int j) {
     return (l == 0 && j == 1 && (MASK & 4)) || (l == 0 && j == 2 && (MASK & 2)) ||
            (l == 1 && j == 0 && (MASK & 4)) || (l == 1 && j == 2 && (MASK & 1)) ||
            (l == 2 && j == 0 && (MASK & 2)) || (l == 2 && j == 1 && (MASK & 1));
+}
+template <int MASK>
+__device__ __forceinline__ constexpr bool skew_row_nz(int i) {
+    return skew_nz<MASK>(i, 0) || skew_nz<MASK>(i, 1) || skew_nz<MASK>(i, 2);
 }
 __device__ __forceinline__ float skew_at(float3 r, int l, int j) {
     return l == 0 ? (j == 1 ? -r.z : r.y) : (l == 1 ? (j == 0 ? r.z : -r.x) : (j == 0 ? -r.y : r.x));
 }
 
 // Congruence of a spatial inertia into the parent frame, X^T M X with
-// X = rot(E) xlt(r) (joint about AX, then the joint origin r):
+// X = rot(E) xlt(r) (joint about AX, then the joint origin r), plus, when ADD,
+// the parent body's structured inertia I (expressed in the parent frame):
 //   rotate every block by E^T, then
-//   A'' = A' - (P + P^T) - Q,  B'' = B' + T,  C'' = C',
-//   P = B' [r x],  T = [r x] C',  Q = T [r x].
-template <int AX, int MASK>
-__device__ __forceinline__ void congruence(Sym6& M, float c, float s, float3 r) {
-    rot_sym<AX>(M.A, c, s);
+//   A'' = A' - P - P^T - Q,  B'' = B' + T,  C'' = C',
+//   P = B' [r x],  T = [r x] C',  Q = T [r x],
+// each A'' entry one FMA chain over its non-zero terms.  I's rotational part
+// seeds the rotation chains of A (A' feeds only A''); its B and C parts are
+// added once the translation has used B' and C'.
+template <int AX, int MASK, bool ADD>
+__device__ __forceinline__ void congruence(Sym6& M, float c, float s, float3 r, const BodyI& I) {
+    rot_sym<AX, ADD>(M.A, c, s, f3(I.ax, I.ay, I.az));
     rot_gen<AX>(M.B, c, s);
-    rot_sym<AX>(M.C, c, s);
-    float P[3][3], T[3][3];
+    rot_sym<AX, false>(M.C, c, s, f3(0.f, 0.f, 0.f));
+    float T[3][3];
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            float p = 0.f, t = 0.f;
+            float t = 0.f;
 #pragma unroll
-            for (int l = 0; l < 3; l++) {
-                if (skew_nz<MASK>(l, j)) p = fmaf(M.B[i][l], skew_at(r, l, j), p);
+            for (int l = 0; l < 3; l++)
                 if (skew_nz<MASK>(i, l)) t = fmaf(skew_at(r, i, l), M.C[sidx(l, j)], t);
-            }
-            P[i][j] = p;
             T[i][j] = t;
         }
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = i; j < 3; j++) {
-            float qv = 0.f;
+            float acc = M.A[sidx(i, j)];
 #pragma unroll
             for (int l = 0; l < 3; l++)
-                if (skew_nz<MASK>(l, j)) qv = fmaf(T[i][l], skew_at(r, l, j), qv);
-            M.A[sidx(i, j)] = M.A[sidx(i, j)] - (P[i][j] + P[j][i]) - qv;
+                if (skew_nz<MASK>(l, j)) acc = fmaf(-M.B[i][l], skew_at(r, l, j), acc);   // - P_ij
+#pragma unroll
+            for (int l = 0; l < 3; l++)
+                if (skew_nz<MASK>(l, i)) acc = fmaf(-M.B[j][l], skew_at(r, l, i), acc);   // - P_ji
+#pragma unroll
+            for (int l = 0; l < 3; l++)
+                if (skew_row_nz<MASK>(i) && skew_nz<MASK>(l, j)) acc = fmaf(-T[i][l], skew_at(r, l, j), acc);  // - Q_ij
+            M.A[sidx(i, j)] = acc;
         }
 #pragma unroll
     for (int i = 0; i < 3; i++)
+        if (skew_row_nz<MASK>(i))
 #pragma unroll
-        for (int j = 0; j < 3; j++) M.B[i][j] += T[i][j];
+            for (int j = 0; j < 3; j++) M.B[i][j] += T[i][j];
+    if (ADD) {
+        // I = [diag(a), m [c x]; m [c x]^T, m 1] with c = (0, 0, cz)
+        M.B[0][1] -= I.mcz;
+        M.B[1][0] += I.mcz;
+        M.C[0] += I.m;
+        M.C[3] += I.m;
+        M.C[5] += I.m;
+    }
 }
 
 // (ha, hl) += M [w; v] for a symmetric spatial matrix M and a spatial vector
@@ -228,26 +255,6 @@ __device__ __forceinline__ void sym6_mv_acc(const Sym6& M, float3 w, float3 v, f
 __device__ __forceinline__ void bodyI_mv(const BodyI& I, float3 w, float3 v, float3& ha, float3& hl) {
     ha = f3(I.ax * w.x - I.mcz * v.y, I.ay * w.y + I.mcz * v.x, I.az * w.z);
     hl = f3(I.mcz * w.y + I.m * v.x, I.m * v.y - I.mcz * w.x, I.m * v.z);
-}
-
-// M += I (structured body inertia)
-__device__ __forceinline__ void add_bodyI(Sym6& M, const BodyI& I) {
-    M.A[0] += I.ax; M.A[3] += I.ay; M.A[5] += I.az;
-    M.B[0][1] -= I.mcz; M.B[1][0] += I.mcz;
-    M.C[0] += I.m; M.C[3] += I.m; M.C[5] += I.m;
-}
-
-// Sym6 from a structured body inertia
-__device__ __forceinline__ Sym6 sym6_of(const BodyI& I) {
-    Sym6 M;
-#pragma unroll
-    for (int i = 0; i < 6; i++) { M.A[i] = 0.f; M.C[i] = 0.f; }
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) M.B[i][j] = 0.f;
-    add_bodyI(M, I);
-    return M;
 }
 
 // sin and cos of an angle |x| < 2^21: x = k pi + r with k the nearest integer to
@@ -277,12 +284,21 @@ __device__ __forceinline__ void sincos_r(float x, float& s, float& c) {
     c = __int_as_float(__float_as_int(cs) ^ (int)sg);
 }
 
-// rotation matrix (body -> world) of a unit quaternion (w, x, y, z)
+// rotation matrix (body -> world) of a unit quaternion (w, x, y, z):
+// R = 1 + 2 w [v x] + 2 [v x]^2, each entry one short FMA chain
 __device__ __forceinline__ void quat_R(const float q[4], float R[3][3]) {
-    float w = q[0], x = q[1], y = q[2], z = q[3];
-    R[0][0] = 1.f - 2.f * (y * y + z * z); R[0][1] = 2.f * (x * y - w * z);       R[0][2] = 2.f * (x * z + w * y);
-    R[1][0] = 2.f * (x * y + w * z);       R[1][1] = 1.f - 2.f * (x * x + z * z); R[1][2] = 2.f * (y * z - w * x);
-    R[2][0] = 2.f * (x * z - w * y);       R[2][1] = 2.f * (y * z + w * x);       R[2][2] = 1.f - 2.f * (x * x + y * y);
+    const float w = q[0], x = q[1], y = q[2], z = q[3];
+    const float x2 = x + x, y2 = y + y, z2 = z + z;
+    const float wx = w * x2, wy = w * y2, wz = w * z2;
+    R[0][0] = fmaf(-y, y2, fmaf(-z, z2, 1.f));
+    R[1][1] = fmaf(-x, x2, fmaf(-z, z2, 1.f));
+    R[2][2] = fmaf(-x, x2, fmaf(-y, y2, 1.f));
+    R[0][1] = fmaf(x, y2, -wz);
+    R[1][0] = fmaf(x, y2, wz);
+    R[0][2] = fmaf(x, z2, wy);
+    R[2][0] = fmaf(x, z2, -wy);
+    R[1][2] = fmaf(y, z2, -wx);
+    R[2][1] = fmaf(y, z2, wx);
 }
 __device__ __forceinline__ float3 mulR(const float R[3][3], float3 v) {
     return f3(R[0][0] * v.x + R[0][1] * v.y + R[0][2] * v.z, R[1][0] * v.x + R[1][1] * v.y + R[1][2] * v.z,

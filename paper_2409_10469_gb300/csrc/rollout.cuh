@@ -94,7 +94,7 @@ __device__ __forceinline__ void contact_wrench(const DevModel& m, float pen, flo
     const float vn = dot3(vp, nb);
     const float fn = active ? fmaxf(fmaf(m.kc, pen, -m.cc * vn), 0.f) : 0.f;
     const float3 vt = f3(fmaf(-vn, nb.x, vp.x), fmaf(-vn, nb.y, vp.y), fmaf(-vn, nb.z, vp.z));
-    const float fr = m.mu * fn * rsqrtf(dot3(vt, vt) + m.eps2);
+    const float fr = m.mu * fn * rsqrtf(fmaf(vt.x, vt.x, fmaf(vt.y, vt.y, fmaf(vt.z, vt.z, m.eps2))));
     const float sn = SG > 0 ? fn : -fn, st = SG > 0 ? -fr : fr;
     const float3 f = f3(fmaf(sn, nb.x, st * vt.x), fmaf(sn, nb.y, st * vt.y), fmaf(sn, nb.z, st * vt.z));
     force = force + f;
@@ -231,9 +231,13 @@ __device__ __forceinline__ float box_cost(const DevCost& c, const BoxState& B) {
 template <int AX> __device__ __forceinline__ float3 vprod(float3 a, float qd) {
     return AX == 0 ? f3(0.f, a.z * qd, -a.y * qd) : f3(-a.z * qd, 0.f, a.x * qd);
 }
-// a + c for such a term (its component AX is structurally zero)
-template <int AX> __device__ __forceinline__ float3 add_vp(float3 a, float3 c) {
-    return AX == 0 ? f3(a.x, a.y + c.y, a.z + c.z) : f3(a.x + c.x, a.y, a.z + c.z);
+// E v + c for such a term c of the same joint (its component on the joint axis
+// is structurally zero), as two FMA chains per rotated component
+__device__ __forceinline__ float3 Ex_vp(float c, float s, float3 v, float3 cv) {
+    return f3(v.x, fmaf(c, v.y, fmaf(s, v.z, cv.y)), fmaf(c, v.z, fmaf(-s, v.y, cv.z)));
+}
+__device__ __forceinline__ float3 Ey_vp(float c, float s, float3 v, float3 cv) {
+    return f3(fmaf(c, v.x, fmaf(-s, v.z, cv.x)), v.y, fmaf(s, v.x, fmaf(c, v.z, cv.z)));
 }
 
 // Ia = IA - U U^T / D  and  pa = pA + Ia c + U u / D for a joint about AX
@@ -295,8 +299,8 @@ __device__ __forceinline__ void force_up_abd(float c, float s, float3 r, float3&
 }
 
 template <int TERR, bool BOX>
-__device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, LegState& S, const float u[3],
-                                        float h, float arm, BoxState& Bx) {
+__device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, LegState& S, const float kpu[3],
+                                        float h, float kdh, float hg, float arm, BoxState& Bx) {
     const float g = m.gz;
     float R0[3][3];
     quat_R(T.quat, R0);
@@ -332,10 +336,11 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
     const float3 cc_w = vprod<1>(wc, S.qd[2]), cc_v = vprod<1>(vc, S.qd[2]);
     wc.y += S.qd[2];
 
-    // ---- PD with implicit damping: tau = kp (u - q - h qd) - kd qd, armature h (kd + h kp)
+    // ---- PD with implicit damping: tau = kp (u - q - h qd) - kd qd, armature h (kd + h kp);
+    // kpu = kp u per dt step, kdh = kp h + kd per horizon
     float tau[3];
 #pragma unroll
-    for (int i = 0; i < 3; i++) tau[i] = m.kp * (u[i] - S.q[i] - h * S.qd[i]) - m.kd * S.qd[i];
+    for (int i = 0; i < 3; i++) tau[i] = fmaf(-kdh, S.qd[i], fmaf(-m.kp, S.q[i], kpu[i]));
 
     // ---- pass 2 (tip to root), calf: its bias minus the foot's contact wrench
     float3 pa_n = f3(0.f, 0.f, 0.f), pa_f = f3(0.f, 0.f, 0.f);
@@ -368,8 +373,7 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
     float U1a[3], U1l[3], D1inv, u1;
     {
         force_up_knee(c2, s2, kz, pa_n, pa_f);
-        congruence<1, 4>(IA, c2, s2, f3(0.f, 0.f, kz));
-        add_bodyI(IA, m.I_thigh);
+        congruence<1, 4, true>(IA, c2, s2, f3(0.f, 0.f, kz), m.I_thigh);
         body_bias_acc(m.I_thigh, wt, vt, pa_n, pa_f);
 #pragma unroll
         for (int i = 0; i < 3; i++) { U1a[i] = IA.A[sidx(i, 1)]; U1l[i] = IA.B[1][i]; }
@@ -380,8 +384,7 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
     float U0a[3], U0l[3], D0inv, u0;
     {   // to the hip frame
         force_up_flex(c1, s1, ty, pa_n, pa_f);
-        congruence<1, 2>(IA, c1, s1, f3(0.f, ty, 0.f));
-        add_bodyI(IA, m.I_hip);
+        congruence<1, 2, true>(IA, c1, s1, f3(0.f, ty, 0.f), m.I_hip);
         body_bias_acc(m.I_hip, wh, vh, pa_n, pa_f);
 #pragma unroll
         for (int i = 0; i < 3; i++) { U0a[i] = IA.A[sidx(i, 0)]; U0l[i] = IA.B[0][i]; }
@@ -391,7 +394,7 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
     project<0>(IA, pa_n, pa_f, D0inv, u0, ch_w, ch_v);
     // to the trunk frame
     force_up_abd(c0, s0, rh, pa_n, pa_f);
-    congruence<0, 7>(IA, c0, s0, rh);
+    congruence<0, 7, false>(IA, c0, s0, rh, m.I_hip);
 
     // ---- contacts of the trunk spheres, one per lane (lanes past the last
     // sphere compute a zero wrench), minus into this lane's trunk bias
@@ -475,7 +478,7 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
         for (int i = 0; i < 3; i++)
 #pragma unroll
             for (int j = i; j < 3; j++)
-                S[sidx(i, j)] = Mt[i][j] - (W[i][0] * Mt[j][3] + W[i][1] * Mt[j][4] + W[i][2] * Mt[j][5]);
+                S[sidx(i, j)] = fmaf(-W[i][0], Mt[j][3], fmaf(-W[i][1], Mt[j][4], fmaf(-W[i][2], Mt[j][5], Mt[i][j])));
         float si[6];
         si[0] = S[3] * S[5] - S[4] * S[4];
         si[1] = S[2] * S[4] - S[1] * S[5];
@@ -487,13 +490,14 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
         // [A B; B^T C] [x; y] = -[p; q]:  x = S^-1 (-p + W q),  y = C^-1 (-q - B^T x)
         float rx[3];
 #pragma unroll
-        for (int i = 0; i < 3; i++) rx[i] = -bt[i] + (W[i][0] * bt[3] + W[i][1] * bt[4] + W[i][2] * bt[5]);
+        for (int i = 0; i < 3; i++) rx[i] = fmaf(W[i][0], bt[3], fmaf(W[i][1], bt[4], fmaf(W[i][2], bt[5], -bt[i])));
 #pragma unroll
         for (int i = 0; i < 3; i++)
             a0[i] = ids * (si[sidx(i, 0)] * rx[0] + si[sidx(i, 1)] * rx[1] + si[sidx(i, 2)] * rx[2]);
         float ry[3];
 #pragma unroll
-        for (int j = 0; j < 3; j++) ry[j] = -bt[3 + j] - (Mt[0][3 + j] * a0[0] + Mt[1][3 + j] * a0[1] + Mt[2][3 + j] * a0[2]);
+        for (int j = 0; j < 3; j++)
+            ry[j] = fmaf(-Mt[0][3 + j], a0[0], fmaf(-Mt[1][3 + j], a0[1], fmaf(-Mt[2][3 + j], a0[2], -bt[3 + j])));
 #pragma unroll
         for (int j = 0; j < 3; j++)
             a0[3 + j] = ci[sidx(j, 0)] * ry[0] + ci[sidx(j, 1)] * ry[1] + ci[sidx(j, 2)] * ry[2];
@@ -503,14 +507,16 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
     float qdd[3];
     const float3 aw = f3(a0[0], a0[1], a0[2]), av = f3(a0[3], a0[4], a0[5]);
     {
-        float3 nw = add_vp<0>(Ex(c0, s0, aw), ch_w), nv = add_vp<0>(Ex(c0, s0, cross_acc(aw, rh, av)), ch_v);
-        qdd[0] = (u0 - (U0a[0] * nw.x + U0a[1] * nw.y + U0a[2] * nw.z + U0l[0] * nv.x + U0l[1] * nv.y + U0l[2] * nv.z)) * D0inv;
+        float3 nw = Ex_vp(c0, s0, aw, ch_w), nv = Ex_vp(c0, s0, cross_acc(aw, rh, av), ch_v);
+        qdd[0] = D0inv * fmaf(-U0a[0], nw.x, fmaf(-U0a[1], nw.y, fmaf(-U0a[2], nw.z,
+                         fmaf(-U0l[0], nv.x, fmaf(-U0l[1], nv.y, fmaf(-U0l[2], nv.z, u0))))));
         nw.x += qdd[0];
-        float3 tw = add_vp<1>(Ey(c1, s1, nw), ct_w), tv = add_vp<1>(Ey(c1, s1, cross_y_acc(nw, ty, nv)), ct_v);
-        qdd[1] = (u1 - (U1a[0] * tw.x + U1a[1] * tw.y + U1a[2] * tw.z + U1l[0] * tv.x + U1l[1] * tv.y + U1l[2] * tv.z)) * D1inv;
+        float3 tw = Ey_vp(c1, s1, nw, ct_w), tv = Ey_vp(c1, s1, cross_y_acc(nw, ty, nv), ct_v);
+        qdd[1] = D1inv * fmaf(-U1a[0], tw.x, fmaf(-U1a[1], tw.y, fmaf(-U1a[2], tw.z,
+                         fmaf(-U1l[0], tv.x, fmaf(-U1l[1], tv.y, fmaf(-U1l[2], tv.z, u1))))));
         tw.y += qdd[1];
-        float3 kw = add_vp<1>(Ey(c2, s2, tw), cc_w), kv = add_vp<1>(Ey(c2, s2, cross_z_acc(tw, kz, tv)), cc_v);
-        qdd[2] = (u2 - (U2a * kw.y + U2l * kv.x)) * D2inv;
+        float3 kw = Ey_vp(c2, s2, tw, cc_w), kv = Ey_vp(c2, s2, cross_z_acc(tw, kz, tv), cc_v);
+        qdd[2] = D2inv * fmaf(-U2a, kw.y, fmaf(-U2l, kv.x, u2));
     }
 
     // ---- semi-implicit Euler
@@ -519,9 +525,10 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
         S.qd[i] = fmaf(h, qdd[i], S.qd[i]);
         S.q[i] = fmaf(h, S.qd[i], S.q[i]);
     }
-    const float3 gb = f3(R0[2][0] * g, R0[2][1] * g, R0[2][2] * g);  // R0^T (0, 0, g)
-    T.w = T.w + h * aw;
-    T.v = T.v + h * (av + gb);
+    // v += h (a + R0^T (0, 0, g)), hg = h g
+    T.w = f3(fmaf(h, aw.x, T.w.x), fmaf(h, aw.y, T.w.y), fmaf(h, aw.z, T.w.z));
+    T.v = f3(fmaf(h, av.x, fmaf(hg, R0[2][0], T.v.x)), fmaf(h, av.y, fmaf(hg, R0[2][1], T.v.y)),
+             fmaf(h, av.z, fmaf(hg, R0[2][2], T.v.z)));
     const float3 dp = mulR(R0, T.v);
     T.p[0] = fmaf(h, dp.x, T.p[0]);
     T.p[1] = fmaf(h, dp.y, T.p[1]);
@@ -619,6 +626,7 @@ __device__ __forceinline__ float rollout_lane(const DevModel& m, const DevCost& 
         Bx.v = f3(x0[47], x0[48], x0[49]);
     }
     const float h = a.h;
+    const float kdh = fmaf(m.kp, h, m.kd), hg = h * m.gz;
     const float ph0 = (leg == 1 || leg == 2) ? 3.14159265358979f : 0.f;
     float L = 0.f;
     if (float* tp = opaque_ptr(traj)) store_state<BOX>(tp, a.H, k, 0, leg, valid, T, S, Bx, a.nx);
@@ -644,7 +652,8 @@ __device__ __forceinline__ float rollout_lane(const DevModel& m, const DevCost& 
             L += c.w_u * (e0 * e0 + e1 * e1 + e2 * e2);
             if (leg == 0) L += trunk_state_cost(c, T) + (BOX ? box_cost(c, Bx) : 0.f);
         }
-        for (int sb = 0; sb < a.n_sub; sb++) substep<TERR, BOX>(m, leg, T, S, u, h, a.arm, Bx);
+        const float kpu[3] = {m.kp * u[0], m.kp * u[1], m.kp * u[2]};
+        for (int sb = 0; sb < a.n_sub; sb++) substep<TERR, BOX>(m, leg, T, S, kpu, h, kdh, hg, a.arm, Bx);
         if (float* tp = opaque_ptr(traj)) store_state<BOX>(tp, a.H, k, t + 1, leg, valid, T, S, Bx, a.nx);
     }
     if (leg == 0) L += c.w_term * (trunk_state_cost(c, T) + (BOX ? box_cost(c, Bx) : 0.f));
