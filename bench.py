@@ -144,13 +144,9 @@ def measured_peaks():
     return None
 
 
-def cpu_baseline(cfg, seconds=12.0):
-    """The FP64 oracle as it stands, on all host cores, over a bounded sample of
-    the workload's rollouts (whole batches of 256 until `seconds` elapsed)."""
-    import oracle as O
+def _oracle_rate(O, cfg, seconds, cores):
     world = O.World(cfg.robot)
     m = dict(cfg.mppi)
-    cores = os.cpu_count() or 1
     U = O.sample(dict(m, K=256), cfg.mu0, 0)
     x0 = cfg.x0.astype(np.float64)
     n_roll, t_start = 0, time.perf_counter()
@@ -160,10 +156,26 @@ def cpu_baseline(cfg, seconds=12.0):
         el = time.perf_counter() - t_start
         if el >= seconds:
             break
-    rate = n_roll * m["H"] / el
+    return n_roll * m["H"] / el, n_roll, el
+
+
+def cpu_baseline(cfg, seconds=12.0):
+    """The oracle as it stands, on all host cores, over a bounded sample of the
+    workload's rollouts (whole batches of 256 until the time is used): the FP64
+    build (the reported value) for 2/3 of `seconds`, the FP32 build of the same
+    source for the rest."""
+    import oracle as O
+    cores = os.cpu_count() or 1
+    m = cfg.mppi
+    rate, n_roll, el = _oracle_rate(O, cfg, seconds * 2 / 3, cores)
+    with O.use_float():
+        rate32, n32, el32 = _oracle_rate(O, cfg, seconds / 3, cores)
     return {"value": rate, "unit": "rollout-steps/s", "cores": cores, "kind": "oracle",
             "sample": "%d rollouts of the K=4096 H=100 trot workload (H=%d, n_sub=%d, FP64) in %.1f s"
-                      % (n_roll, m["H"], m["n_sub"], el)}
+                      % (n_roll, m["H"], m["n_sub"], el),
+            "fp32_build": {"value": rate32, "unit": "rollout-steps/s",
+                           "sample": "%d rollouts, same source compiled with real = float, in %.1f s"
+                                     % (n32, el32)}}
 
 
 def run_reference(args):
@@ -176,10 +188,16 @@ def run_reference(args):
     cfg = W.config_trot(K=K_BENCH, H=H_BENCH)
     world = O.World(cfg.robot)
     cores = os.cpu_count() or 1
-    sample_K = 512          # bounded sample of the 4096 rollouts per step
     m = dict(cfg.mppi)
     x0 = cfg.x0.astype(np.float64)
     mu = cfg.mu0.copy()
+    # bounded sample of the 4096 rollouts per step: at most 512, fewer when the
+    # run would exceed ~2 minutes (rate calibrated on 64 rollouts)
+    t = time.perf_counter()
+    O.rollouts(world, cfg.cost, m, 0.0, x0, O.sample(dict(m, K=64), mu, 0), nthreads=cores)
+    per_rollout = (time.perf_counter() - t) / 64
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    sample_K = int(max(16, min(512, budget / per_rollout)))
 
     def one(step):
         U = O.sample(dict(m, K=sample_K), mu, step)
@@ -205,6 +223,16 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "rollout-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def hbm_line(nbytes, ms, peaks):
+    """An HBM roofline entry for a byte-moving kernel: algorithmic bytes over its
+    CUDA-event time against the measured copy bandwidth."""
+    peak = (peaks or {}).get("hbm_gbs", 6800.0)
+    ach = nbytes / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "bytes_per_launch": nbytes, "ms": ms,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
 
 
 def run_ours(args):
@@ -313,6 +341,9 @@ def run_ours(args):
                        "max": float(step_ms.max())},
         "kernel_ms": {"sample": float(ker[:, 0].mean()), "rollout": rollout_ms,
                       "update": float(ker[:, 2].mean())},
+        "roofline_aux": {
+            "k_sample": hbm_line(F.sample_bytes(K_BENCH), float(ker[:, 0].mean()), peaks),
+            "k_update": hbm_line(F.update_bytes(K_BENCH), float(ker[:, 2].mean()), peaks)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": rollout_traffic(),
                      "kernel": "k_rollout", "flops_per_launch": fl,
@@ -333,8 +364,8 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

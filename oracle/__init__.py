@@ -475,3 +475,28 @@ class use_float:
     def __exit__(self, *a):
         global _lib
         _lib, _build.build = self._saved
+
+
+class use_count:
+    """Context: the same oracle source compiled with `real` = an operation-counting
+    scalar; `opcounts()` reads (and clears) the operations performed since the
+    last read.  Worlds must be created inside the context; run single-threaded."""
+
+    def __enter__(self):
+        global _lib
+        self._saved = (_lib, _build.build)
+        path = _build.build_count()
+        _lib = None
+        _build.build = lambda force=False: path
+        lib().or_opcount_take.argtypes = [C.POINTER(C.c_ulonglong)]
+        self.opcounts()
+        return self
+
+    def opcounts(self) -> dict:
+        out = (C.c_ulonglong * 6)()
+        lib().or_opcount_take(out)
+        return dict(zip(("add", "mul", "div", "sqrt", "trans", "cmp"), (int(v) for v in out)))
+
+    def __exit__(self, *a):
+        global _lib
+        _lib, _build.build = self._saved

@@ -46,3 +46,21 @@ def build_variant(real: str = "float") -> str:
     cmd = ["gcc"] + CFLAGS + ["-DOR_REAL=" + real, "-Wno-double-promotion"] + srcs + ["-o", out, "-lm"]
     subprocess.run(cmd, check=True)
     return out
+
+
+def build_count() -> str:
+    """The same oracle source compiled as C++ with `real` = an operation-counting
+    scalar (opcount.h): it measures how many floating-point operations the
+    oracle's plain formulation performs."""
+    out = os.path.join(HERE, "liboracle_count.so")
+    srcs = [os.path.join(HERE, s) for s in SOURCES]
+    deps = srcs + [os.path.join(HERE, f) for f in ("oracle.h", "opcount.h", "opcount.cpp")]
+    if os.path.exists(out) and all(os.path.getmtime(d) <= os.path.getmtime(out) for d in deps):
+        return out
+    tmp = out + ".tmp%d" % os.getpid()
+    cmd = (["g++", "-std=c++17", "-O1", "-fPIC", "-shared", "-pthread", "-ffp-contract=off", "-x", "c++",
+            "-include", os.path.join(HERE, "opcount.h"), "-DOR_REAL=or_creal"] + srcs
+           + [os.path.join(HERE, "opcount.cpp"), "-o", tmp, "-lm"])
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out

@@ -31,6 +31,7 @@
 #ifndef MPPI_ORACLE_H
 #define MPPI_ORACLE_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -186,6 +187,14 @@ void or_shift(const float mu[OR_D], int H, int ctrl_steps, float mu_out[OR_D]);
 int  or_mppi_step(const or_world* w, const or_cost* c, const or_mppi* m, const double* x0,
                   float mu[OR_D], const float* mu_prop, uint32_t step, float u0[OR_NJ],
                   float* L_out, float* U_out, int nthreads);
+
+/* helpers for the Python test harness */
+size_t or_world_size(void);
+size_t or_tree_size(void);
+void or_lnf_many(const float* x, float* y, long n);
+void or_sincos_u24_many(const uint32_t* nn, float* c, float* s, long n);
+void or_noise_many(uint64_t seed, uint32_t step, uint32_t inst, const uint32_t* ks, long n,
+                   float* eps);
 
 #ifdef __cplusplus
 }

@@ -43,6 +43,13 @@ TRUNK = (30          # rotation matrix of the quaternion
          + 3 * 7)    # trunk spheres against the plane (out of contact)
 
 SUBSTEP = 4 * LEG + TRUNK          # one rollout advanced by one sub-step
+
+# The same sub-step as the FP64 oracle's plain formulation computes it (dense
+# 6x6 spatial algebra, general rotations, no structural zeros dropped), counted
+# operation by operation by the oracle's counting build (add/sub, mul, div, sqrt
+# = 1; trot model, flat ground, from the stand state).  Context for SUBSTEP, which
+# the roofline uses: the structured count is the smaller, conservative figure.
+ORACLE_PLAIN_SUBSTEP = 23200
 PER_DT_STEP = 112 + 180 + 25       # spline targets, per-leg control cost, trunk state cost
 
 
