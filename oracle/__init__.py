@@ -63,8 +63,22 @@ class OrMppi(C.Structure):
         ("K", C.c_int), ("H", C.c_int), ("n_sub", C.c_int), ("ctrl_steps", C.c_int),
         ("dt", C.c_double), ("lam", C.c_double),
         ("sigma", C.c_float * 48), ("q_lo", C.c_float * 3), ("q_hi", C.c_float * 3),
-        ("seed", C.c_uint64), ("inst", C.c_uint32), ("n_prop", C.c_int),
+        ("seed", C.c_uint64), ("inst", C.c_uint32), ("n_prop", C.c_int), ("interp", C.c_int),
     ]
+
+
+# control representations (oracle.h OR_INTERP_*)
+INTERP = {"cubic": 0, "zero": 1, "linear": 2, "direct": 3}
+
+
+def param_dim(m: dict) -> int:
+    """Parameters per sample: 48 knots, or 12 targets per dt step (direct)."""
+    return NJ * m["H"] if interp_of(m) == 3 else D
+
+
+def interp_of(m: dict) -> int:
+    v = m.get("interp", 0)
+    return INTERP[v] if isinstance(v, str) else int(v)
 
 
 def _p(a, ct):
@@ -106,6 +120,11 @@ def lib():
         L.or_sample.argtypes = [C.POINTER(OrMppi), fp, fp, C.c_uint32, fp]
         L.or_update.restype = C.c_int
         L.or_update.argtypes = [fp, fp, C.c_int, C.c_double, fp, dp]
+        L.or_update_dim.restype = C.c_int
+        L.or_update_dim.argtypes = [dp, fp, C.c_int, C.c_int, C.c_double, fp, dp]
+        L.or_shift_mode.argtypes = [fp, C.c_int, C.c_int, C.c_int, fp]
+        L.or_controls.argtypes = [C.c_int, C.c_int, C.c_int, fp, dp]
+        L.or_interp_basis.argtypes = [C.c_int, C.c_int, C.c_int, dp]
         L.or_update_d.restype = C.c_int
         L.or_update_d.argtypes = [dp, fp, C.c_int, C.c_double, fp, dp]
         L.or_shift.argtypes = [fp, C.c_int, C.c_int, fp]
@@ -201,6 +220,7 @@ def make_mppi(m: dict) -> OrMppi:
         o.q_lo[i] = float(m["q_lo"][i])
         o.q_hi[i] = float(m["q_hi"][i])
     o.seed, o.inst, o.n_prop = int(m["seed"]), int(m["inst"]), int(m.get("n_prop", 0))
+    o.interp = interp_of(m)
     return o
 
 
@@ -237,7 +257,7 @@ def rollout(world: World, cost: dict, H, n_sub, dt, t0, x0, U, traj=False):
 
 
 def rollouts(world: World, cost: dict, m: dict, t0, x0, U, traj=False, nthreads=None):
-    U = _f32(U).reshape(-1, D)
+    U = _f32(U).reshape(-1, param_dim(m))
     n = U.shape[0]
     x0 = _f64(x0)
     per = 1 if x0.ndim == 2 else 0
@@ -339,7 +359,7 @@ def noise(seed, step, inst, ks):
 
 def sample(m: dict, mu, step, mu_prop=None):
     mm = make_mppi(m)
-    U = np.zeros((m["K"], D), np.float32)
+    U = np.zeros((m["K"], param_dim(m)), np.float32)
     mp = _f32(mu_prop) if mu_prop is not None else None
     lib().or_sample(C.byref(mm), _p(_f32(mu), C.c_float),
                     _p(mp, C.c_float) if mp is not None else None, step, _p(U, C.c_float))
@@ -348,12 +368,17 @@ def sample(m: dict, mu, step, mu_prop=None):
 
 # ---------------- update ----------------
 
-def update(L, U, lam, double_costs=False):
-    U = _f32(U).reshape(-1, D)
+def update(L, U, lam, double_costs=False, dim=None):
+    """Eq. 1 + Eq. 2 over K samples of `dim` parameters (48 by default)."""
+    dim = D if dim is None else dim
+    U = _f32(U).reshape(-1, dim)
     K = U.shape[0]
-    mu = np.zeros(D, np.float32)
+    mu = np.zeros(dim, np.float32)
     w = np.zeros(K)
-    if double_costs:
+    if dim != D:
+        rc = lib().or_update_dim(_p(_f64(L), C.c_double), _p(U, C.c_float), K, dim, lam,
+                                 _p(mu, C.c_float), _p(w, C.c_double))
+    elif double_costs:
         rc = lib().or_update_d(_p(_f64(L), C.c_double), _p(U, C.c_float), K, lam,
                                _p(mu, C.c_float), _p(w, C.c_double))
     else:
@@ -362,10 +387,27 @@ def update(L, U, lam, double_costs=False):
     return rc, mu, w
 
 
-def shift(mu, H, ctrl_steps):
-    out = np.zeros(D, np.float32)
-    lib().or_shift(_p(_f32(mu), C.c_float), H, ctrl_steps, _p(out, C.c_float))
+def shift(mu, H, ctrl_steps, interp=0):
+    mu = _f32(mu)
+    out = np.zeros(mu.shape[0], np.float32)
+    lib().or_shift_mode(_p(mu, C.c_float), INTERP[interp] if isinstance(interp, str) else int(interp),
+                        H, ctrl_steps, _p(out, C.c_float))
     return out
+
+
+def controls(interp, H, t, U):
+    """Joint targets u_t[12] of dt step t for one sample's parameters U."""
+    u = np.zeros(NJ)
+    lib().or_controls(INTERP[interp] if isinstance(interp, str) else int(interp), H, t,
+                      _p(_f32(U), C.c_float), _p(u, C.c_double))
+    return u
+
+
+def interp_basis(interp, H, t):
+    B = np.zeros(4)
+    lib().or_interp_basis(INTERP[interp] if isinstance(interp, str) else int(interp), H, t,
+                          _p(B, C.c_double))
+    return B
 
 
 def mppi_step(world: World, cost: dict, m: dict, x0, mu, step, mu_prop=None, nthreads=None):
@@ -373,7 +415,7 @@ def mppi_step(world: World, cost: dict, m: dict, x0, mu, step, mu_prop=None, nth
     mu = _f32(mu).copy()
     u0 = np.zeros(NJ, np.float32)
     L = np.zeros(m["K"], np.float32)
-    U = np.zeros((m["K"], D), np.float32)
+    U = np.zeros((m["K"], param_dim(m)), np.float32)
     c, mm = make_cost(cost), make_mppi(m)
     mp = _f32(mu_prop) if mu_prop is not None else None
     rc = lib().or_mppi_step(world.ptr, C.byref(c), C.byref(mm), _p(_f64(x0), C.c_double),

@@ -108,10 +108,11 @@ void or_box_muller(uint32_t a, uint32_t b, float* e0, float* e1) {
     *e1 = r * s;
 }
 
-/* the 48 normals of sample k: 12 Philox calls, counter (g, k, step, inst), key = seed */
-void or_noise(uint64_t seed, uint32_t step, uint32_t inst, uint32_t k, float eps[OR_D]) {
+/* the first D normals (D a multiple of 4) of sample k: Philox calls g = 0 .. D/4 - 1,
+ * counter (g, k, step, inst), key = seed; 48 normals for the knot representations */
+static void noise_dim(uint64_t seed, uint32_t step, uint32_t inst, uint32_t k, int D, float* eps) {
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-    for (uint32_t g = 0; g < OR_D / 4; g++) {
+    for (uint32_t g = 0; g < (uint32_t)(D / 4); g++) {
         uint32_t ctr[4] = {g, k, step, inst}, r[4];
         or_philox4x32_10(ctr, key, r);
         or_box_muller(r[0], r[1], &eps[4 * g + 0], &eps[4 * g + 1]);
@@ -119,30 +120,39 @@ void or_noise(uint64_t seed, uint32_t step, uint32_t inst, uint32_t k, float eps
     }
 }
 
+void or_noise(uint64_t seed, uint32_t step, uint32_t inst, uint32_t k, float eps[OR_D]) {
+    noise_dim(seed, step, inst, k, OR_D, eps);
+}
+
 /*
- * Knot samples U[K][48] (layout [knot][joint]).  Sample 0 is the nominal mean;
- * when n_prop > 0 the last n_prop samples are drawn around mu_prop and the
- * first of them is mu_prop itself.  U = clamp(fmaf(sigma, eps, centre), lo, hi).
+ * Samples U[K][D], D = or_param_dim(interp, H): knots [knot][joint] (D = 48) or
+ * direct targets [t][joint] (D = 12 H, sigma of joint i = sigma[i], the first
+ * knot's).  Sample 0 is the nominal mean; when n_prop > 0 the last n_prop
+ * samples are drawn around mu_prop and the first of them is mu_prop itself.
+ * U = clamp(fmaf(sigma, eps, centre), lo, hi).
  */
-void or_sample(const or_mppi* m, const float mu[OR_D], const float* mu_prop, uint32_t step,
+void or_sample(const or_mppi* m, const float* mu, const float* mu_prop, uint32_t step,
                float* U) {
+    const int D = or_param_dim(m->interp, m->H);
     int kp0 = m->K - (mu_prop ? m->n_prop : 0);
+    float* eps = (float*)malloc(sizeof(float) * (size_t)D);
     for (int k = 0; k < m->K; k++) {
         const float* ctrv = (k >= kp0) ? mu_prop : mu;
-        float eps[OR_D];
         int nominal = (k == 0) || (k == kp0 && mu_prop);
-        if (nominal) memset(eps, 0, sizeof(eps));
-        else or_noise(m->seed, step, m->inst, (uint32_t)k, eps);
-        for (int d = 0; d < OR_D; d++) {
+        if (nominal) memset(eps, 0, sizeof(float) * (size_t)D);
+        else noise_dim(m->seed, step, m->inst, (uint32_t)k, D, eps);
+        for (int d = 0; d < D; d++) {
             int jt = d % 3;
             float c = ctrv[d];
             if (k >= kp0 && !isfinite(c)) c = mu[d];   /* non-finite proposal: the plain mean */
-            float v = fmaf(m->sigma[d], eps[d], c);
+            float sg = m->interp == OR_INTERP_DIRECT ? m->sigma[d % OR_NJ] : m->sigma[d];
+            float v = fmaf(sg, eps[d], c);
             v = fmaxf(v, m->q_lo[jt]);
             v = fminf(v, m->q_hi[jt]);
-            U[(size_t)k * OR_D + d] = v;
+            U[(size_t)k * D + d] = v;
         }
     }
+    free(eps);
 }
 
 /* ---------------- Eq. 1, Eq. 2 ---------------- */
@@ -151,8 +161,8 @@ void or_sample(const or_mppi* m, const float mu[OR_D], const float* mu_prop, uin
  * Softmax weights over finite costs and the weighted mean of the knots.
  * Returns 0, or -1 when no cost is finite (mu_out left untouched).
  */
-int or_update_d(const double* L, const float* U, int K, double lambda, float mu_out[OR_D],
-                double* w_out) {
+int or_update_dim(const double* L, const float* U, int K, int D, double lambda, float* mu_out,
+                  double* w_out) {
     double Lmin = INFINITY;
     for (int k = 0; k < K; k++)
         if (isfinite(L[k]) && L[k] < Lmin) Lmin = L[k];
@@ -164,13 +174,18 @@ int or_update_d(const double* L, const float* U, int K, double lambda, float mu_
         Z += w[k];
     }
     for (int k = 0; k < K; k++) w[k] /= Z;
-    for (int d = 0; d < OR_D; d++) {
+    for (int d = 0; d < D; d++) {
         double s = 0;
-        for (int k = 0; k < K; k++) s += w[k] * (double)U[(size_t)k * OR_D + d];
+        for (int k = 0; k < K; k++) s += w[k] * (double)U[(size_t)k * D + d];
         mu_out[d] = (float)s;
     }
     if (!w_out) free(w);
     return 0;
+}
+
+int or_update_d(const double* L, const float* U, int K, double lambda, float mu_out[OR_D],
+                double* w_out) {
+    return or_update_dim(L, U, K, OR_D, lambda, mu_out, w_out);
 }
 
 int or_update(const float* L, const float* U, int K, double lambda, float mu_out[OR_D],
@@ -199,27 +214,73 @@ void or_shift(const float mu[OR_D], int H, int ctrl_steps, float mu_out[OR_D]) {
 }
 
 /*
+ * shifted(mu) for any representation: the knot representations re-sample their
+ * own interpolant at tau_j + delta (held at tau = 1 past the end); direct
+ * targets move ctrl_steps steps earlier, the last one held.
+ */
+void or_shift_mode(const float* mu, int interp, int H, int ctrl_steps, float* mu_out) {
+    if (interp == OR_INTERP_CUBIC) {
+        or_shift(mu, H, ctrl_steps, mu_out);
+        return;
+    }
+    if (interp == OR_INTERP_DIRECT) {
+        float* tmp = (float*)malloc(sizeof(float) * (size_t)OR_NJ * H);
+        for (int t = 0; t < H; t++) {
+            int src = t + ctrl_steps < H ? t + ctrl_steps : H - 1;
+            for (int i = 0; i < OR_NJ; i++) tmp[t * OR_NJ + i] = mu[src * OR_NJ + i];
+        }
+        memcpy(mu_out, tmp, sizeof(float) * (size_t)OR_NJ * H);
+        free(tmp);
+        return;
+    }
+    /* zeroth / linear: the interpolant at 3 tau = j + 3 ctrl_steps / (H - 1), held at 3;
+     * its integer part and fraction from integer arithmetic */
+    float tmp[OR_D];
+    const int den = H > 1 ? H - 1 : 1, num = H > 1 ? 3 * ctrl_steps : 0;
+    for (int j = 0; j < OR_NKNOT; j++) {
+        int jj = j + num / den;
+        double f = (double)(num % den) / (double)den;
+        if (jj >= 3) { jj = 3; f = 0; }
+        for (int i = 0; i < OR_NJ; i++) {
+            double v;
+            if (interp == OR_INTERP_ZERO) {
+                v = mu[jj * OR_NJ + i];
+            } else if (jj == 3) {
+                v = mu[3 * OR_NJ + i];
+            } else {
+                v = (1 - f) * mu[jj * OR_NJ + i] + f * mu[(jj + 1) * OR_NJ + i];
+            }
+            tmp[j * OR_NJ + i] = (float)v;
+        }
+    }
+    memcpy(mu_out, tmp, sizeof(tmp));
+}
+
+/*
  * One control step of Alg. 1: sample, roll out from x0, weight (Eq. 1),
- * update (Eq. 2), take u0 = mu[0] (the spline at tau = 0 is knot 0), shift.
- * mu is updated in place.  L_out (float costs) and U_out are optional.
+ * update (Eq. 2), take u0 = the controls of step 0 (knot 0 for every knot
+ * representation, the first direct target otherwise), shift.  mu (D floats) is
+ * updated in place.  L_out (float costs) and U_out are optional.
  * Returns 0, or -1 when every cost is non-finite (mu kept, u0 = mu[0]).
  */
 int or_mppi_step(const or_world* w, const or_cost* c, const or_mppi* m, const double* x0,
-                 float mu[OR_D], const float* mu_prop, uint32_t step, float u0[OR_NJ],
+                 float* mu, const float* mu_prop, uint32_t step, float u0[OR_NJ],
                  float* L_out, float* U_out, int nthreads) {
     int K = m->K;
-    float* U = U_out ? U_out : (float*)malloc(sizeof(float) * (size_t)K * OR_D);
+    const int D = or_param_dim(m->interp, m->H);
+    float* U = U_out ? U_out : (float*)malloc(sizeof(float) * (size_t)K * D);
     double* L = (double*)malloc(sizeof(double) * K);
     or_sample(m, mu, mu_prop, step, U);
     double t0 = (double)step * m->ctrl_steps * m->dt;
     or_rollouts(w, c, m, t0, x0, 0, U, K, L, NULL, nthreads);
     if (L_out)
         for (int k = 0; k < K; k++) L_out[k] = (float)L[k];
-    float mnew[OR_D];
-    int rc = or_update_d(L, U, K, m->lambda, mnew, NULL);
-    if (rc != 0) memcpy(mnew, mu, sizeof(mnew));
+    float* mnew = (float*)malloc(sizeof(float) * (size_t)D);
+    int rc = or_update_dim(L, U, K, D, m->lambda, mnew, NULL);
+    if (rc != 0) memcpy(mnew, mu, sizeof(float) * (size_t)D);
     for (int j = 0; j < OR_NJ; j++) u0[j] = mnew[j];
-    or_shift(mnew, m->H, m->ctrl_steps, mu);
+    or_shift_mode(mnew, m->interp, m->H, m->ctrl_steps, mu);
+    free(mnew);
     free(L);
     if (!U_out) free(U);
     return rc;

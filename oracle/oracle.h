@@ -119,7 +119,17 @@ typedef struct {
     uint64_t seed;
     uint32_t inst;
     int n_prop;                   /* last n_prop samples are drawn around mu_prop */
+    int interp;                   /* control representation, OR_INTERP_* */
 } or_mppi;
+
+/* Control representations (Sec. III-B; the ablation of Fig. 5): 4 knots at
+ * tau_j = j / 3 interpolated by the cubic through them (the default), held
+ * (zeroth order: the nearest knot at or before tau) or joined by straight
+ * lines; or one target per dt step sampled directly (D = 12 H). */
+#define OR_INTERP_CUBIC 0
+#define OR_INTERP_ZERO 1
+#define OR_INTERP_LINEAR 2
+#define OR_INTERP_DIRECT 3
 
 /* spatial algebra */
 void or_skew(const real a[3], real S[3][3]);
@@ -155,11 +165,16 @@ void or_contact_fext(const or_world* w, const real* x, real fext[][6], real fbox
 void or_substep(const or_world* w, real* x, const real u[OR_NJ], real h);
 void or_spline_basis(int H, int t, real B[OR_NKNOT]);
 void or_spline_eval(const float* U, real tau, real u[OR_NJ]);
+int  or_param_dim(int interp, int H);
+void or_interp_basis(int interp, int H, int t, real B[OR_NKNOT]);
+void or_controls(int interp, int H, int t, const float* U, real u[OR_NJ]);
 void or_gait_ref(const or_cost* c, real t_abs, real uref[OR_NJ]);
 real or_stage_cost(const or_world* w, const or_cost* c, const real* x, const real* u, real t_abs);
 real or_terminal_cost(const or_world* w, const or_cost* c, const real* x);
 real or_rollout(const or_world* w, const or_cost* c, int H, int n_sub, real dt, real t0,
                 const real* x0, const float* U, real* traj);
+real or_rollout_mode(const or_world* w, const or_cost* c, int interp, int H, int n_sub, real dt,
+                     real t0, const real* x0, const float* U, real* traj);
 void or_rollouts(const or_world* w, const or_cost* c, const or_mppi* m, double t0,
                  const double* x0, int x0_per_sample, const float* U, int n,
                  double* L_out, double* traj, int nthreads);
@@ -175,7 +190,7 @@ float or_lnf(float x);
 void  or_sincos2pi_u24(uint32_t n24, float* c, float* s);
 void  or_box_muller(uint32_t a, uint32_t b, float* e0, float* e1);
 void  or_noise(uint64_t seed, uint32_t step, uint32_t inst, uint32_t k, float eps[OR_D]);
-void  or_sample(const or_mppi* m, const float mu[OR_D], const float* mu_prop,
+void  or_sample(const or_mppi* m, const float* mu, const float* mu_prop,
                 uint32_t step, float* U);
 
 /* update (Eq. 1, Eq. 2) and shift */
@@ -184,8 +199,11 @@ int  or_update(const float* L, const float* U, int K, double lambda, float mu_ou
 int  or_update_d(const double* L, const float* U, int K, double lambda, float mu_out[OR_D],
                  double* w_out);
 void or_shift(const float mu[OR_D], int H, int ctrl_steps, float mu_out[OR_D]);
+int  or_update_dim(const double* L, const float* U, int K, int D, double lambda, float* mu_out,
+                   double* w_out);
+void or_shift_mode(const float* mu, int interp, int H, int ctrl_steps, float* mu_out);
 int  or_mppi_step(const or_world* w, const or_cost* c, const or_mppi* m, const double* x0,
-                  float mu[OR_D], const float* mu_prop, uint32_t step, float u0[OR_NJ],
+                  float* mu, const float* mu_prop, uint32_t step, float u0[OR_NJ],
                   float* L_out, float* U_out, int nthreads);
 
 /* helpers for the Python test harness */

@@ -383,6 +383,55 @@ void or_spline_eval(const float* U, real tau, real u[OR_NJ]) {
     }
 }
 
+/* parameters per sample: 4 knots x 12 joints, or 12 targets per dt step (direct) */
+int or_param_dim(int interp, int H) { return interp == OR_INTERP_DIRECT ? OR_NJ * H : OR_D; }
+
+/*
+ * Knot weights of dt step t for the knot representations.  The knot interval of
+ * step t is found in integers, j = floor(3 t / (H - 1)), so that the step at a
+ * knot time belongs to that knot exactly; within it f = (3 t - j (H - 1)) / (H - 1).
+ *   zeroth order: B_j = 1 (the knot at or before tau_t);
+ *   linear: B_j = 1 - f, B_{j+1} = f (j <= 2);
+ *   cubic: the Lagrange basis (or_spline_basis).
+ */
+void or_interp_basis(int interp, int H, int t, real B[OR_NKNOT]) {
+    if (interp == OR_INTERP_CUBIC) {
+        or_spline_basis(H, t, B);
+        return;
+    }
+    for (int j = 0; j < OR_NKNOT; j++) B[j] = 0;
+    if (H <= 1) {
+        B[0] = 1;
+        return;
+    }
+    int j = (3 * t) / (H - 1);
+    if (j > 3) j = 3;
+    if (interp == OR_INTERP_ZERO) {
+        B[j] = 1;
+        return;
+    }
+    if (j > 2) j = 2;
+    real f = (real)(3 * t - j * (H - 1)) / (real)(H - 1);
+    B[j] = 1 - f;
+    B[j + 1] = f;
+}
+
+/* joint targets of dt step t: the knot representation's interpolant, or the
+ * step's own sampled targets (direct; U layout [t][joint]) */
+void or_controls(int interp, int H, int t, const float* U, real u[OR_NJ]) {
+    if (interp == OR_INTERP_DIRECT) {
+        for (int j = 0; j < OR_NJ; j++) u[j] = U[(size_t)t * OR_NJ + j];
+        return;
+    }
+    real B[OR_NKNOT];
+    or_interp_basis(interp, H, t, B);
+    for (int j = 0; j < OR_NJ; j++) {
+        real s = 0;
+        for (int k = 0; k < OR_NKNOT; k++) s += B[k] * U[k * OR_NJ + j];
+        u[j] = s;
+    }
+}
+
 /* ---------------- cost ---------------- */
 
 /* control reference u_ref(t): the stand pose, or an open-loop trot (diagonal
@@ -442,26 +491,26 @@ real or_terminal_cost(const or_world* w, const or_cost* c, const real* x) {
  * stage cost of step t is taken on (x_t, u_t) at the start of the step, the
  * terminal term on x_H.  traj (optional): x_0 .. x_H, (H + 1) x nx.
  */
-real or_rollout(const or_world* w, const or_cost* c, int H, int n_sub, real dt, real t0,
-                const real* x0, const float* U, real* traj) {
-    real x[64], u[OR_NJ], B[OR_NKNOT];
+real or_rollout_mode(const or_world* w, const or_cost* c, int interp, int H, int n_sub, real dt,
+                     real t0, const real* x0, const float* U, real* traj) {
+    real x[64], u[OR_NJ];
     int nx = w->nx;
     memcpy(x, x0, sizeof(real) * nx);
     if (traj) memcpy(traj, x, sizeof(real) * nx);
     real L = 0, h = dt / n_sub;
     for (int t = 0; t < H; t++) {
-        or_spline_basis(H, t, B);
-        for (int j = 0; j < OR_NJ; j++) {
-            real s = 0;
-            for (int k = 0; k < OR_NKNOT; k++) s += B[k] * U[k * OR_NJ + j];
-            u[j] = s;
-        }
+        or_controls(interp, H, t, U, u);
         L += or_stage_cost(w, c, x, u, t0 + t * dt);
         for (int s = 0; s < n_sub; s++) or_substep(w, x, u, h);
         if (traj) memcpy(traj + (size_t)(t + 1) * nx, x, sizeof(real) * nx);
     }
     L += or_terminal_cost(w, c, x);
     return L;
+}
+
+real or_rollout(const or_world* w, const or_cost* c, int H, int n_sub, real dt, real t0,
+                const real* x0, const float* U, real* traj) {
+    return or_rollout_mode(w, c, OR_INTERP_CUBIC, H, n_sub, dt, t0, x0, U, traj);
 }
 
 /* ---------------- many rollouts over host threads ---------------- */
@@ -480,8 +529,9 @@ static void* rollout_worker(void* arg) {
     for (int k = j->tid; k < j->n; k += j->nthreads) {
         const double* x0 = j->x0 + (j->x0_per_sample ? (size_t)k * nx : 0);
         for (int i = 0; i < nx; i++) x0r[i] = (real)x0[i];
-        j->L[k] = (double)or_rollout(j->w, j->c, H, j->m->n_sub, (real)j->m->dt, (real)j->t0, x0r,
-                                     j->U + (size_t)k * OR_D, tr);
+        j->L[k] = (double)or_rollout_mode(j->w, j->c, j->m->interp, H, j->m->n_sub, (real)j->m->dt,
+                                          (real)j->t0, x0r,
+                                          j->U + (size_t)k * or_param_dim(j->m->interp, H), tr);
         if (tr)
             for (size_t i = 0; i < (size_t)(H + 1) * nx; i++)
                 j->traj[(size_t)k * (H + 1) * nx + i] = (double)tr[i];
