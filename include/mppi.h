@@ -84,6 +84,19 @@ typedef struct {
     double w_terminal;
 } mppi_cost_t;
 
+/* Control representation of a sample (Sec. III-B, the ablation of Fig. 5).
+ * The knot representations sample 4 knots x 12 joints at normalised times
+ * tau_j = j / 3 (tau_t = t / (H - 1) for dt step t) and interpolate them:
+ *   CUBIC  the cubic through the 4 knots (Lagrange basis; the paper's choice);
+ *   ZERO   zeroth-order hold: knot j = floor(3 t / (H - 1)) (integer division);
+ *   LINEAR straight lines between knots j and j + 1 (j <= 2) at that t.
+ * DIRECT samples one 12-joint target per dt step: D = 12 H parameters, joint i
+ * perturbed with sigma[i] (the first knot's).  D = 48 for the knot forms. */
+#define MPPI_INTERP_CUBIC 0
+#define MPPI_INTERP_ZERO 1
+#define MPPI_INTERP_LINEAR 2
+#define MPPI_INTERP_DIRECT 3
+
 /* Alg. 1 inputs N (= K), T (= H), lambda, Sigma (diagonal sigma), plus the model's
  * sub-step count and the control period in dt steps. */
 typedef struct {
@@ -95,13 +108,14 @@ typedef struct {
     uint32_t inst;               /* instance id (Philox counter word 3) */
     int n_prop;                  /* last n_prop samples centre on a proposal mean */
     int block;                   /* rollout kernel block size in threads (0 = default) */
+    int interp;                  /* MPPI_INTERP_* (0 = cubic) */
 } mppi_config_t;
 
 /* Create a controller: copies model, cost and config, derives the model's
- * device constants, allocates its workspace (U[K][48], L[K], mu, u0, status)
- * for up to cfg->K samples.  stream: a cudaStream_t or NULL.
- * Errors: ARG (K < 1, H < 2, n_sub < 1, dt <= 0, lambda <= 0, bad terrain),
- * OOM, CUDA. */
+ * device constants, allocates its workspace (U[K][D], L[K], mu[D], u0, status;
+ * D = mppi_param_dim) for up to cfg->K samples.  stream: a cudaStream_t or NULL.
+ * Errors: ARG (K < 1, H < 2, n_sub < 1, dt <= 0, lambda <= 0, bad terrain,
+ * unknown interp, n_prop > 0 with DIRECT), OOM, CUDA. */
 mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t* cost,
                         const mppi_config_t* cfg, void* stream, mppi_handle* out);
 
@@ -110,6 +124,11 @@ mppi_status mppi_destroy(mppi_handle h);
 
 /* Text of the last error on this handle ("" if none); valid until the next call. */
 const char* mppi_last_error(mppi_handle h);
+
+/* Parameters per sample D: 48 (4 knots x 12 joints) for the knot representations,
+ * 12 H for DIRECT.  Every float[48] / float[n][48] below is float[D] / float[n][D]
+ * for a DIRECT handle (u0 stays float[12]). */
+int mppi_param_dim(mppi_handle h);
 
 /* Nominal knots mu (float[48], host or device): write / read. */
 mppi_status mppi_set_nominal(mppi_handle h, const float* mu);

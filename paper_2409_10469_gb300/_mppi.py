@@ -33,7 +33,14 @@ EXPORTS = ("mppi_create", "mppi_destroy", "mppi_last_error", "mppi_set_nominal",
            "mppi_server_drain", "mppi_mlp_create", "mppi_mlp_destroy", "mppi_mlp_last_error",
            "mppi_mlp_param_count", "mppi_mlp_set_params", "mppi_mlp_get_params", "mppi_mlp_forward",
            "mppi_mlp_train_step", "mppi_tc_gemm_bf16", "mppi_features", "mppi_set_proposal",
-           "mppi_batch_get_means", "mppi_selftest_wait_timeout")
+           "mppi_batch_get_means", "mppi_selftest_wait_timeout", "mppi_param_dim")
+
+# control representations (MPPI_INTERP_* of include/mppi.h; Sec. III-B, Fig. 5)
+INTERP = {"cubic": 0, "zero": 1, "linear": 2, "direct": 3}
+
+
+def interp_code(v) -> int:
+    return INTERP[v] if isinstance(v, str) else int(v)
 
 
 class MppiError(RuntimeError):
@@ -84,6 +91,7 @@ class MppiConfig(C.Structure):
         ("dt", C.c_double), ("lam", C.c_double),
         ("sigma", C.c_float * 48), ("q_lo", C.c_float * 3), ("q_hi", C.c_float * 3),
         ("seed", C.c_uint64), ("inst", C.c_uint32), ("n_prop", C.c_int), ("block", C.c_int),
+        ("interp", C.c_int),
     ]
 
 
@@ -158,8 +166,10 @@ def lib():
         L.mppi_set_proposal.argtypes = [vp, vp]
         L.mppi_state_size.argtypes = [vp]
         L.mppi_state_size.restype = C.c_int
+        L.mppi_param_dim.argtypes = [vp]
+        L.mppi_param_dim.restype = C.c_int
         for name in EXPORTS:
-            if name not in ("mppi_last_error", "mppi_state_size", "mppi_batch_last_error",
+            if name not in ("mppi_last_error", "mppi_state_size", "mppi_param_dim", "mppi_batch_last_error",
                             "mppi_server_last_error", "mppi_mlp_last_error", "mppi_mlp_param_count"):
                 getattr(L, name).restype = C.c_int
         _lib = L
@@ -223,6 +233,7 @@ def config_struct(mp: dict, block: int = 0):
         c.q_hi[i] = float(mp["q_hi"][i])
     c.seed, c.inst, c.n_prop = int(mp["seed"]), int(mp["inst"]), int(mp.get("n_prop", 0))
     c.block = int(block or mp.get("block", 0))
+    c.interp = interp_code(mp.get("interp", 0))
     return c
 
 
@@ -253,6 +264,7 @@ class Controller:
         self.K = mppi["K"]
         self.H = mppi["H"]
         self.nx = L.mppi_state_size(h)
+        self.D = L.mppi_param_dim(h)   # parameters per sample: 48, or 12 H (direct)
 
     def _check(self, rc):
         if rc != MPPI_OK:
@@ -274,7 +286,7 @@ class Controller:
         self._check(lib().mppi_set_nominal(self.h, _ptr(mu)))
 
     def get_nominal(self, out=None):
-        out = np.zeros(48, np.float32) if out is None else out
+        out = np.zeros(self.D, np.float32) if out is None else out
         self._check(lib().mppi_get_nominal(self.h, _ptr(out)))
         return out
 

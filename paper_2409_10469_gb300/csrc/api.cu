@@ -180,6 +180,10 @@ static bool all_finite(const float* p, size_t n) {
     return true;
 }
 
+static_assert(MPPI_INTERP_CUBIC == INTERP_CUBIC && MPPI_INTERP_ZERO == INTERP_ZERO &&
+                  MPPI_INTERP_LINEAR == INTERP_LINEAR && MPPI_INTERP_DIRECT == INTERP_DIRECT,
+              "representation codes of the ABI and the kernels agree");
+
 // ------------------------------------------------------------------ ABI
 
 extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t* cost, const mppi_config_t* cfg,
@@ -190,6 +194,8 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
         cfg->ctrl_steps < 1 || cfg->n_prop < 0 || cfg->n_prop >= cfg->K || cfg->K > (1 << 24))
         return MPPI_ERR_ARG;
     if (cfg->block != 0 && (cfg->block % 32 != 0 || cfg->block < 32 || cfg->block > 256)) return MPPI_ERR_ARG;
+    if (cfg->interp < MPPI_INTERP_CUBIC || cfg->interp > MPPI_INTERP_DIRECT) return MPPI_ERR_ARG;
+    if (cfg->interp == MPPI_INTERP_DIRECT && (cfg->n_prop > 0 || cfg->H > (1 << 16))) return MPPI_ERR_ARG;
     if (model->terrain == 1 && (!model->hf || model->hf_nx < 2 || model->hf_ny < 2 || !(model->hf_cell > 0)))
         return MPPI_ERR_ARG;
     if (model->terrain != 0 && model->terrain != 1) return MPPI_ERR_ARG;
@@ -205,7 +211,8 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
     derive_model(*model, cfg->dt / cfg->n_sub, h->dm);
     derive_cost(*cost, h->dc);
     h->nx = h->dm.nx;
-    const size_t K = (size_t)cfg->K;
+    h->D = cfg->interp == MPPI_INTERP_DIRECT ? NJ * cfg->H : D;
+    const size_t K = (size_t)cfg->K, Dp = (size_t)h->D;
     auto al = [&](void** p, size_t bytes) -> bool {
         if (cudaMalloc(p, bytes) != cudaSuccess) {
             cudaGetLastError();
@@ -213,12 +220,12 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
         }
         return true;
     };
-    bool ok = al((void**)&h->d_mu, D * sizeof(float)) && al((void**)&h->d_mu_prop, D * sizeof(float)) &&
-              al((void**)&h->d_mu_upd, D * sizeof(float)) && al((void**)&h->d_U, K * D * sizeof(float)) &&
+    bool ok = al((void**)&h->d_mu, Dp * sizeof(float)) && al((void**)&h->d_mu_prop, D * sizeof(float)) &&
+              al((void**)&h->d_mu_upd, Dp * sizeof(float)) && al((void**)&h->d_U, K * Dp * sizeof(float)) &&
               al((void**)&h->d_L, K * sizeof(float)) && al((void**)&h->d_x0, K * NX_BOX * sizeof(float)) &&
               al((void**)&h->d_u0, NJ * sizeof(float)) && al((void**)&h->d_status, sizeof(int)) &&
               al((void**)&h->d_wsum, sizeof(double)) &&
-              al((void**)&h->d_part, (size_t)UPDATE_MAX_CTAS * (D + 1) * sizeof(double)) &&
+              al((void**)&h->d_part, (size_t)UPDATE_MAX_CTAS * (Dp + 1) * sizeof(double)) &&
               al((void**)&h->d_counter, sizeof(unsigned));
     if (ok && model->terrain == 1) {
         size_t nh = (size_t)model->hf_nx * model->hf_ny;
@@ -245,10 +252,10 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
         return MPPI_ERR_OOM;
     }
     for (int i = 0; i < 4; i++) cudaEventCreate(&h->ev[i]);
-    // default nominal: the cost's stand pose at every knot
-    float mu0[D];
-    for (int d = 0; d < D; d++) mu0[d] = (float)cost->stand[d % 3];
-    if (cudaMemcpy(h->d_mu, mu0, sizeof(mu0), cudaMemcpyHostToDevice) != cudaSuccess ||
+    // default nominal: the cost's stand pose at every knot (every step for DIRECT)
+    std::vector<float> mu0(Dp);
+    for (size_t d = 0; d < Dp; d++) mu0[d] = (float)cost->stand[d % 3];
+    if (cudaMemcpy(h->d_mu, mu0.data(), Dp * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(h->d_counter, 0, sizeof(unsigned)) != cudaSuccess) {
         mppi_destroy(h);
@@ -277,10 +284,12 @@ extern "C" const char* mppi_last_error(mppi_handle h) { return h ? h->err.c_str(
 
 extern "C" int mppi_state_size(mppi_handle h) { return h ? h->nx : 0; }
 
+extern "C" int mppi_param_dim(mppi_handle h) { return h ? h->D : 0; }
+
 extern "C" mppi_status mppi_set_nominal(mppi_handle h, const float* mu) {
     if (!h || !mu) return fail(h, MPPI_ERR_ARG, "null argument");
     cudaMemcpyKind kind = is_device(mu) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CK(cudaMemcpyAsync(h->d_mu, mu, D * sizeof(float), kind, h->stream));
+    CK(cudaMemcpyAsync(h->d_mu, mu, (size_t)h->D * sizeof(float), kind, h->stream));
     if (kind == cudaMemcpyHostToDevice) CK(cudaStreamSynchronize(h->stream));
     return MPPI_OK;
 }
@@ -288,8 +297,8 @@ extern "C" mppi_status mppi_set_nominal(mppi_handle h, const float* mu) {
 extern "C" mppi_status mppi_get_nominal(mppi_handle h, float* mu_out) {
     if (!h || !mu_out) return fail(h, MPPI_ERR_ARG, "null argument");
     bool dev = is_device(mu_out);
-    CK(cudaMemcpyAsync(mu_out, h->d_mu, D * sizeof(float), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                       h->stream));
+    CK(cudaMemcpyAsync(mu_out, h->d_mu, (size_t)h->D * sizeof(float),
+                       dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
     if (!dev) CK(cudaStreamSynchronize(h->stream));
     return MPPI_OK;
 }
@@ -314,6 +323,8 @@ static mppi_status do_sample(mppi_handle h, uint32_t step, const float* mu_prop,
     a.inst = h->cfg.inst;
     a.K = h->cfg.K;
     a.n_prop = h->cfg.n_prop;
+    a.Dp = h->D;
+    a.interp = h->cfg.interp;
     CK(launch_sample(a, h->stream));
     h->launches++;
     return MPPI_OK;
@@ -327,7 +338,8 @@ extern "C" mppi_status mppi_sample(mppi_handle h, uint32_t step, const float* mu
     mppi_status s = do_sample(h, step, mu_prop, dst);
     if (s != MPPI_OK) return s;
     if (host_out) {
-        CK(cudaMemcpyAsync(U_out, h->d_U, (size_t)h->cfg.K * D * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaMemcpyAsync(U_out, h->d_U, (size_t)h->cfg.K * h->D * sizeof(float), cudaMemcpyDeviceToHost,
+                           h->stream));
         CK(cudaStreamSynchronize(h->stream));
     }
     return MPPI_OK;
@@ -351,6 +363,8 @@ static RolloutArgs rollout_args(mppi_handle h, const float* x0, int per, const f
     a.inv_Hm1 = (float)(1.0 / (h->cfg.H - 1));
     a.t0 = mppi_reduce_t0(h, t0);
     a.arm = (float)armature(h->model_in, h->cfg.dt / h->cfg.n_sub);
+    a.Dp = h->D;
+    a.interp = h->cfg.interp;
     return a;
 }
 
@@ -382,7 +396,7 @@ extern "C" mppi_status mppi_rollouts(mppi_handle h, const float* x0, int x0_per_
             dU = U;
         } else {
             if (n > h->cfg.K) return fail(h, MPPI_ERR_ARG, "host U limited to K samples");
-            CK(cudaMemcpyAsync(h->d_U, U, (size_t)n * D * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+            CK(cudaMemcpyAsync(h->d_U, U, (size_t)n * h->D * sizeof(float), cudaMemcpyHostToDevice, h->stream));
         }
     }
     // outputs
@@ -433,6 +447,8 @@ static mppi_status do_update(mppi_handle h, const float* dL, const float* dU, in
     a.H = h->cfg.H;
     a.ctrl_steps = h->cfg.ctrl_steps;
     a.inv_lambda = (float)(1.0 / h->cfg.lambda);
+    a.Dp = h->D;
+    a.interp = h->cfg.interp;
     CK(launch_update(a, h->stream));
     h->launches++;
     return MPPI_OK;
@@ -450,7 +466,7 @@ static mppi_status finish_outputs(mppi_handle h, float* u0_out, float* mu_out) {
     if (mu_out) {
         bool dev = is_device(mu_out);
         any_host |= !dev;
-        CK(cudaMemcpyAsync(mu_out, h->d_mu_upd, D * sizeof(float),
+        CK(cudaMemcpyAsync(mu_out, h->d_mu_upd, (size_t)h->D * sizeof(float),
                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
     }
     if (any_host) {
@@ -479,7 +495,7 @@ extern "C" mppi_status mppi_update(mppi_handle h, const float* L, const float* U
             dU = U;
         } else {
             if (n > h->cfg.K) return fail(h, MPPI_ERR_ARG, "host U limited to K");
-            CK(cudaMemcpyAsync(h->d_U, U, (size_t)n * D * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+            CK(cudaMemcpyAsync(h->d_U, U, (size_t)n * h->D * sizeof(float), cudaMemcpyHostToDevice, h->stream));
         }
     }
     mppi_status s = do_update(h, dL, dU, n);

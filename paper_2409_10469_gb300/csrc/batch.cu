@@ -134,15 +134,7 @@ __device__ void block_update(const InstDesc& d, float* u0_row) {
     }
     if (tid == 0) *d.status = ok ? 0 : 4;
     __syncthreads();
-    if (tid < D) {
-        const int j = tid / NJ, i = tid % NJ;
-        const float delta = (float)d.ctrl_steps / (float)(d.H - 1);
-        const float tau = fminf((float)j * (1.f / 3.f) + delta, 1.f);
-        const float d0 = tau, d1 = tau - (1.f / 3.f), d2 = tau - (2.f / 3.f), d3 = tau - 1.f;
-        const float B0 = d1 * d2 * d3 * -4.5f, B1 = d0 * d2 * d3 * 13.5f;
-        const float B2 = d0 * d1 * d3 * -13.5f, B3 = d0 * d1 * d2 * 4.5f;
-        d.mu[tid] = B0 * s_mu[i] + B1 * s_mu[NJ + i] + B2 * s_mu[2 * NJ + i] + B3 * s_mu[3 * NJ + i];
-    }
+    if (tid < D) d.mu[tid] = shifted_knot(s_mu, d.interp, d.H, d.ctrl_steps, tid / NJ, tid % NJ);
 }
 
 template <int BLOCK>
@@ -171,15 +163,15 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 1 : 384 / BLOCK) k_batch
         // gait time of this horizon: step * control period, reduced modulo the gait period
         const double t0d = (double)step * sd.ctrl_steps * sd.dt_d;
         const float t0 = (sd.gait == 1 && sd.period_d > 0) ? (float)fmod(t0d, sd.period_d) : (float)t0d;
-        const HorizonArgs hz = {sd.H, sd.n_sub, sd.nx, sd.h, sd.dt, sd.inv_Hm1, t0, sd.arm};
+        const HorizonArgs hz = {sd.H, sd.n_sub, sd.nx, sd.h, sd.dt, sd.inv_Hm1, t0, sd.arm, sd.interp};
         const float* x0 = a.x0s + (size_t)w.inst * NX_BOX;
         float L;
         if (sd.model.terrain != 0 || sd.model.n_sbox > 0)
-            L = sd.model.has_box ? rollout_lane<1, true>(sd.model, sd.cost, hz, x0, Uk, leg, k, valid, nullptr)
-                                 : rollout_lane<1, false>(sd.model, sd.cost, hz, x0, Uk, leg, k, valid, nullptr);
+            L = sd.model.has_box ? rollout_lane<1, true>(sd.model, sd.cost, hz, x0, Uk, nullptr, leg, k, valid, nullptr)
+                                 : rollout_lane<1, false>(sd.model, sd.cost, hz, x0, Uk, nullptr, leg, k, valid, nullptr);
         else
-            L = sd.model.has_box ? rollout_lane<0, true>(sd.model, sd.cost, hz, x0, Uk, leg, k, valid, nullptr)
-                                 : rollout_lane<0, false>(sd.model, sd.cost, hz, x0, Uk, leg, k, valid, nullptr);
+            L = sd.model.has_box ? rollout_lane<0, true>(sd.model, sd.cost, hz, x0, Uk, nullptr, leg, k, valid, nullptr)
+                                 : rollout_lane<0, false>(sd.model, sd.cost, hz, x0, Uk, nullptr, leg, k, valid, nullptr);
         if (valid && leg == 0) sd.L[k] = L;
         __threadfence();
         __syncthreads();
@@ -297,6 +289,7 @@ InstDesc mppi::make_desc(const mppi_handle_s* h) {
     d.inv_lambda = (float)(1.0 / h->cfg.lambda);
     d.dt_d = h->cfg.dt;
     d.period_d = h->cost_in.gait_period;
+    d.interp = h->cfg.interp;
     memcpy(d.sigma, h->cfg.sigma, sizeof(d.sigma));
     memcpy(d.q_lo, h->cfg.q_lo, sizeof(d.q_lo));
     memcpy(d.q_hi, h->cfg.q_hi, sizeof(d.q_hi));
@@ -386,7 +379,7 @@ extern "C" mppi_status mppi_batch_create(const mppi_handle* hs, int n, void* str
     std::vector<InstDesc> descs;
     int max_items = 0;
     for (int i = 0; i < n; i++) {
-        if (!hs[i]) {
+        if (!hs[i] || hs[i]->cfg.interp == MPPI_INTERP_DIRECT) {  // batches run the knot representations
             delete b;
             return MPPI_ERR_ARG;
         }

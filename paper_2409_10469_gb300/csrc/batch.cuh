@@ -26,6 +26,7 @@ struct InstDesc {
     double dt_d, period_d;
     float sigma[D], q_lo[3], q_hi[3];
     uint32_t key0, key1, inst_id;
+    int interp;           // MPPI_INTERP_* (knot representations only)
 };
 
 struct WorkItem {

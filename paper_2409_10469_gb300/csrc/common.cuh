@@ -17,6 +17,8 @@ constexpr int D = NKNOT * NJ;
 constexpr int NX_ROBOT = 37;
 constexpr int NX_BOX = 50;
 constexpr int MAX_SBOX = 4;
+// control representations (the ABI's MPPI_INTERP_* values)
+constexpr int INTERP_CUBIC = 0, INTERP_ZERO = 1, INTERP_LINEAR = 2, INTERP_DIRECT = 3;
 
 // Symmetric 6x6 [[A, B], [B^T, C]]: A and C by their 6 unique entries
 // (order 00 01 02 11 12 22), B in full.
@@ -71,6 +73,31 @@ struct DevCost {
     float stand[3];
     float w_term;
 };
+
+// shifted(mu) knot j, joint i for the knot representations: the representation's
+// interpolant of mu (4 x 12 knots) at tau_j + ctrl / (H - 1), held at tau = 1.
+// Cubic: the Lagrange basis; zeroth order / linear: the knot interval at
+// 3 tau = j + 3 ctrl / (H - 1), whose integer part and fraction come from
+// integer arithmetic.
+__device__ __forceinline__ float shifted_knot(const float* mu, int interp, int H, int ctrl, int j, int i) {
+    if (interp == INTERP_CUBIC) {
+        const float delta = H > 1 ? (float)ctrl / (float)(H - 1) : 0.f;
+        const float tau = fminf((float)j * (1.f / 3.f) + delta, 1.f);
+        const float d0 = tau, d1 = tau - (1.f / 3.f), d2 = tau - (2.f / 3.f), d3 = tau - 1.f;
+        const float B0 = d1 * d2 * d3 * -4.5f, B1 = d0 * d2 * d3 * 13.5f;
+        const float B2 = d0 * d1 * d3 * -13.5f, B3 = d0 * d1 * d2 * 4.5f;
+        return B0 * mu[i] + B1 * mu[NJ + i] + B2 * mu[2 * NJ + i] + B3 * mu[3 * NJ + i];
+    }
+    const int den = H > 1 ? H - 1 : 1, num = H > 1 ? 3 * ctrl : 0;
+    int jj = j + num / den;
+    float f = (float)(num % den) / (float)den;
+    if (jj >= 3) {
+        jj = 3;
+        f = 0.f;
+    }
+    if (interp == INTERP_ZERO || jj == 3) return mu[jj * NJ + i];
+    return (1.f - f) * mu[jj * NJ + i] + f * mu[(jj + 1) * NJ + i];
+}
 
 // ---------------------------------------------------------------- float3 ops
 __device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }

@@ -18,6 +18,7 @@ struct mppi_handle_s {
     cudaStream_t stream = nullptr;
     int device = 0;
     int nx = mppi::NX_ROBOT;
+    int D = mppi::D;  // parameters per sample: 48, or 12 H for direct targets
     float *d_mu = nullptr, *d_mu_prop = nullptr, *d_mu_upd = nullptr, *d_U = nullptr, *d_L = nullptr;
     float *d_x0 = nullptr, *d_u0 = nullptr, *d_hf = nullptr, *d_sbox = nullptr;
     int* d_status = nullptr;

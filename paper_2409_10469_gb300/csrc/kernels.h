@@ -10,11 +10,13 @@ namespace mppi {
 struct SampleArgs {
     const float* mu;       // [48] device
     const float* mu_prop;  // [48] device or null
-    float* U;              // [K][48] device
-    float sigma[D];
+    float* U;              // [K][Dp] device
+    float sigma[D];        // per knot and joint (DIRECT: sigma[i] for joint i)
     float q_lo[3], q_hi[3];
     uint32_t key0, key1, step, inst;
     int K, n_prop;
+    int Dp;                // parameters per sample: 48, or 12 H (DIRECT)
+    int interp;            // MPPI_INTERP_*
 };
 
 struct RolloutArgs {
@@ -22,26 +24,28 @@ struct RolloutArgs {
     DevCost cost;
     const float* x0;       // [nx] or [n][nx] device
     int x0_per_sample;
-    const float* U;        // [n][48] device
+    const float* U;        // [n][Dp] device
     float* L;              // [n] device
     float* traj;           // [n][H+1][nx] device or null
     int n, H, n_sub;
+    int Dp, interp;        // parameters per sample, MPPI_INTERP_*
     float h, dt, inv_Hm1, t0;  // t0: gait time of step 0 (reduced modulo the gait period)
     float arm;             // implicit-PD armature h (kd + h kp) + a0
 };
 
 struct UpdateArgs {
     const float* L;        // [n]
-    const float* U;        // [n][48]
-    float* mu;             // [48] in: unused; out: shifted nominal
-    float* mu_upd;         // [48] updated mean before the shift (optional)
+    const float* U;        // [n][Dp]
+    float* mu;             // [Dp] in: the previous mean (kept when no cost is finite); out: shifted nominal
+    float* mu_upd;         // [Dp] updated mean before the shift (required when Dp > 48)
     float* u0;             // [12]
     int* status;           // 0 ok, 4 all costs non-finite
     double* wsum;          // normaliser (FP64) of the last update, optional
-    double* part;          // scratch [UPDATE_MAX_CTAS][D + 1] per-CTA partial sums
+    double* part;          // scratch [UPDATE_MAX_CTAS][Dp + 1] per-CTA partial sums
     unsigned* counter;     // scratch: CTAs finished (0 between launches)
     int n, H, ctrl_steps;
     float inv_lambda;
+    int Dp, interp;        // parameters per sample, MPPI_INTERP_*
 };
 
 constexpr int UPDATE_MAX_CTAS = 128;

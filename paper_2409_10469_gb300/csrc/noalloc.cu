@@ -96,5 +96,7 @@ extern "C" mppi_status mppi_update_noalloc(const float* L, const float* U, int n
     a.H = H;
     a.ctrl_steps = ctrl_steps;
     a.inv_lambda = (float)(1.0 / lambda);
+    a.Dp = D;                 // the cubic knot representation
+    a.interp = INTERP_CUBIC;
     return launch_update(a, st) == cudaSuccess ? MPPI_OK : MPPI_ERR_CUDA;
 }

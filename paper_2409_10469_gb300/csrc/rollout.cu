@@ -19,13 +19,20 @@ __global__ void __launch_bounds__(256, 1) k_rollout(RolloutArgs a) {
     const int nx = a.model.nx;
     const float* x0 = a.x0 + (a.x0_per_sample ? (size_t)kk * nx : 0);
     float Uk[NKNOT][3];
-    const float* Urow = a.U + (size_t)kk * D;
+    const float* Urow = a.U + (size_t)kk * a.Dp;
+    if (a.interp != INTERP_DIRECT) {
 #pragma unroll
-    for (int j = 0; j < NKNOT; j++)
+        for (int j = 0; j < NKNOT; j++)
 #pragma unroll
-        for (int i = 0; i < 3; i++) Uk[j][i] = Urow[j * NJ + 3 * leg + i];
-    const HorizonArgs hz = {a.H, a.n_sub, nx, a.h, a.dt, a.inv_Hm1, a.t0, a.arm};
-    const float L = rollout_lane<TERR, BOX>(a.model, a.cost, hz, x0, Uk, leg, k, valid, a.traj);
+            for (int i = 0; i < 3; i++) Uk[j][i] = Urow[j * NJ + 3 * leg + i];
+    } else {
+#pragma unroll
+        for (int j = 0; j < NKNOT; j++)
+#pragma unroll
+            for (int i = 0; i < 3; i++) Uk[j][i] = 0.f;
+    }
+    const HorizonArgs hz = {a.H, a.n_sub, nx, a.h, a.dt, a.inv_Hm1, a.t0, a.arm, a.interp};
+    const float L = rollout_lane<TERR, BOX>(a.model, a.cost, hz, x0, Uk, Urow, leg, k, valid, a.traj);
     if (valid && leg == 0) a.L[k] = L;
 }
 

@@ -9,8 +9,10 @@
 // implementation of the same spec: every rounding step is an explicit _rn
 // intrinsic, so nvcc cannot contract or reorder it.
 //
-// One thread per (sample, Philox call): it writes 4 consecutive knots of one
-// sample as a single 16-byte store, so a warp writes 512 contiguous bytes.
+// One thread per (sample, Philox call): it writes 4 consecutive parameters of
+// one sample as a single 16-byte store, so a warp writes 512 contiguous bytes.
+// Knot representations: 12 calls per sample (48 knots); DIRECT: 3 H calls (one
+// 12-joint target per dt step, joint i perturbed with sigma[i]).
 #include "kernels.h"
 #include "noise.cuh"
 
@@ -18,7 +20,8 @@ namespace mppi {
 
 __global__ void __launch_bounds__(256) k_sample(SampleArgs a) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int k = tid / (D / 4), g = tid % (D / 4);
+    const int G = a.Dp / 4;
+    const int k = tid / G, g = tid % G;
     if (k >= a.K) return;
     const int kp0 = a.K - (a.mu_prop ? a.n_prop : 0);
     const bool prop = a.mu_prop && k >= kp0;
@@ -37,15 +40,16 @@ __global__ void __launch_bounds__(256) k_sample(SampleArgs a) {
         const int d = 4 * g + i, jt = d % 3;
         float c = __ldg(ctr + d);
         if (prop && !(fabsf(c) <= 3.402823466e38f)) c = __ldg(a.mu + d);  // non-finite proposal: plain mean
-        float v = __fmaf_rn(a.sigma[d], eps[i], c);
+        const float sg = a.interp == INTERP_DIRECT ? a.sigma[d % NJ] : a.sigma[d];
+        float v = __fmaf_rn(sg, eps[i], c);
         o[i] = fminf(fmaxf(v, a.q_lo[jt]), a.q_hi[jt]);
     }
-    reinterpret_cast<float4*>(a.U + (size_t)k * D)[g] = out;
+    reinterpret_cast<float4*>(a.U + (size_t)k * a.Dp)[g] = out;
 }
 
 cudaError_t launch_sample(const SampleArgs& a, cudaStream_t st) {
     if (a.K <= 0) return cudaSuccess;
-    const long threads = (long)a.K * (D / 4);
+    const long threads = (long)a.K * (a.Dp / 4);
     const int block = 256;
     k_sample<<<(int)((threads + block - 1) / block), block, 0, st>>>(a);
     return cudaGetLastError();

@@ -208,6 +208,7 @@ extern "C" const char* mppi_server_last_error(mppi_server s) { return s ? s->err
 
 extern "C" mppi_status mppi_server_add_robot(mppi_server s, mppi_handle h, int* robot_id) {
     if (!s || !h || !robot_id) return MPPI_ERR_ARG;
+    if (h->cfg.interp == MPPI_INTERP_DIRECT) return sfail(s, MPPI_ERR_ARG, "served robots use a knot representation");
     if ((int)s->robots.size() >= s->max_robots) return sfail(s, MPPI_ERR_ARG, "max_robots reached");
     if (h->cfg.K > (s->max_items / s->max_robots) * 16) return sfail(s, MPPI_ERR_ARG, "K above max_samples");
     Robot r;

@@ -30,7 +30,7 @@ class Episodes:
     """E closed-loop episodes of one task, stepped together."""
 
     def __init__(self, make_cfg, E: int, K: int, H: int, seed: int = 0, n_prop: int = 0,
-                 perturb: float = 0.05, inst0: int = 0):
+                 perturb: float = 0.05, inst0: int = 0, interp="cubic"):
         import torch
         self.torch = torch
         self.E, self.K, self.H = E, K, H
@@ -38,16 +38,18 @@ class Episodes:
         self.cfgs, self.ctls = [], []
         for e in range(E):
             cfg = make_cfg(e)
-            m = dict(cfg.mppi, K=K, H=H, n_prop=n_prop, inst=inst0 + e, seed=seed)
+            m = dict(cfg.mppi, K=K, H=H, n_prop=n_prop, inst=inst0 + e, seed=seed, interp=interp)
             c = _mppi.Controller(cfg.robot, cfg.cost, m)
-            c.set_nominal(cfg.mu0)
+            # the warm start: the task's knots, or its first knot held over the horizon (direct)
+            c.set_nominal(cfg.mu0 if c.D == 48 else np.tile(cfg.mu0[:12], c.D // 12).astype(np.float32))
             self.cfgs.append(cfg)
             self.ctls.append(c)
         cfg0 = self.cfgs[0]
         self.nx = len(cfg0.x0)
         self.ctrl_steps = cfg0.mppi["ctrl_steps"]
         self.dt = cfg0.mppi["dt"]
-        self.batch = _mppi.Batch(self.ctls)
+        # knot representations step as one batch; direct targets step controller by controller
+        self.batch = _mppi.Batch(self.ctls) if self.ctls[0].D == 48 else None
         # plant: the same simulator, E rollouts over one control period
         pm = dict(cfg0.mppi, K=E, H=max(2, self.ctrl_steps))
         self.plant = _mppi.Controller(cfg0.robot, cfg0.cost, pm)
@@ -73,7 +75,11 @@ class Episodes:
         if mu_props is not None:
             for e, c in enumerate(self.ctls):
                 c.set_proposal(mu_props[e])
-        self.batch.step(self.X, np.full(self.E, self.step_idx), u0s=self.u0)
+        if self.batch is not None:
+            self.batch.step(self.X, np.full(self.E, self.step_idx), u0s=self.u0)
+        else:
+            for e, c in enumerate(self.ctls):
+                c.step(self.X[e, :self.nx].contiguous(), self.step_idx, u0_out=self.u0[e])
 
     def advance(self):
         """Apply u0 for one control period on the plant, record the visited state."""
@@ -96,7 +102,8 @@ class Episodes:
         return mu
 
     def close(self):
-        self.batch.close()
+        if self.batch is not None:
+            self.batch.close()
         self.plant.close()
         for c in self.ctls:
             c.close()
@@ -138,11 +145,12 @@ def train(F, T, epochs=40, batch=512, lr=2e-3, wd=1e-4, seed=0, params=None):
     return net, hist
 
 
-def run_episodes(make_cfg, E, K, H, steps, seed, net=None, n_prop=0):
-    """Closed-loop episodes; with `net`, n_prop samples come from the proposal.
+def run_episodes(make_cfg, E, K, H, steps, seed, net=None, n_prop=0, interp="cubic"):
+    """Closed-loop episodes; with `net`, n_prop samples come from the proposal;
+    `interp` selects the control representation (Sec. III-B, Fig. 5).
     Returns the visited states [steps][E][nx] and applied controls [steps][E][12]."""
     torch = __import__("torch")
-    ep = Episodes(make_cfg, E, K, H, seed=seed, n_prop=n_prop if net is not None else 0)
+    ep = Episodes(make_cfg, E, K, H, seed=seed, n_prop=n_prop if net is not None else 0, interp=interp)
     for s in range(steps):
         props = None
         if net is not None:
