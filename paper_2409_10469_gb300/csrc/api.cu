@@ -180,6 +180,40 @@ static bool all_finite(const float* p, size_t n) {
     return true;
 }
 
+// Knot weights of every dt step t of an H-step horizon for a knot representation
+// (Sec. III-B; Fig. 5's forms), in double, rounded once: knots at tau_j = j / 3,
+// tau_t = t / (H - 1).  Cubic: the Lagrange basis of the 4 knots.  Zeroth order:
+// knot j = floor(3 t / (H - 1)) (integer division; 3 at the end).  Linear: knots
+// j and j + 1 (j <= 2) with weights 1 - f and f, f = (3 t - j (H - 1)) / (H - 1).
+static void knot_weights(int interp, int H, std::vector<float>& B) {
+    B.assign((size_t)4 * H, 0.f);
+    if (interp == MPPI_INTERP_DIRECT) return;
+    for (int t = 0; t < H; t++) {
+        double w[4] = {0, 0, 0, 0};
+        if (interp == MPPI_INTERP_CUBIC) {
+            const double tau = H > 1 ? (double)t / (double)(H - 1) : 0.0;
+            for (int j = 0; j < 4; j++) {
+                double b = 1.0;
+                for (int m = 0; m < 4; m++)
+                    if (m != j) b *= (tau - m / 3.0) / (j / 3.0 - m / 3.0);
+                w[j] = b;
+            }
+        } else {
+            const int den = H > 1 ? H - 1 : 1;
+            int j = (3 * t) / den;
+            if (interp == MPPI_INTERP_ZERO) {
+                w[j > 3 ? 3 : j] = 1.0;
+            } else {
+                if (j > 2) j = 2;
+                const double f = (double)(3 * t - j * den) / (double)den;
+                w[j] = 1.0 - f;
+                w[j + 1] = f;
+            }
+        }
+        for (int j = 0; j < 4; j++) B[(size_t)4 * t + j] = (float)w[j];
+    }
+}
+
 static_assert(MPPI_INTERP_CUBIC == INTERP_CUBIC && MPPI_INTERP_ZERO == INTERP_ZERO &&
                   MPPI_INTERP_LINEAR == INTERP_LINEAR && MPPI_INTERP_DIRECT == INTERP_DIRECT,
               "representation codes of the ABI and the kernels agree");
@@ -226,7 +260,8 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
               al((void**)&h->d_u0, NJ * sizeof(float)) && al((void**)&h->d_status, sizeof(int)) &&
               al((void**)&h->d_wsum, sizeof(double)) &&
               al((void**)&h->d_part, (size_t)UPDATE_MAX_CTAS * (Dp + 1) * sizeof(double)) &&
-              al((void**)&h->d_counter, sizeof(unsigned));
+              al((void**)&h->d_counter, sizeof(unsigned)) &&
+              al((void**)&h->d_B, (size_t)4 * cfg->H * sizeof(float));
     if (ok && model->terrain == 1) {
         size_t nh = (size_t)model->hf_nx * model->hf_ny;
         ok = al((void**)&h->d_hf, nh * sizeof(float));
@@ -255,7 +290,10 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
     // default nominal: the cost's stand pose at every knot (every step for DIRECT)
     std::vector<float> mu0(Dp);
     for (size_t d = 0; d < Dp; d++) mu0[d] = (float)cost->stand[d % 3];
+    std::vector<float> Bw;
+    knot_weights(cfg->interp, cfg->H, Bw);
     if (cudaMemcpy(h->d_mu, mu0.data(), Dp * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_B, Bw.data(), Bw.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(h->d_counter, 0, sizeof(unsigned)) != cudaSuccess) {
         mppi_destroy(h);
@@ -271,7 +309,7 @@ extern "C" mppi_status mppi_destroy(mppi_handle h) {
     else cudaDeviceSynchronize();
     void* bufs[] = {h->d_mu,  h->d_mu_prop, h->d_mu_upd, h->d_U,    h->d_L,    h->d_x0,
                     h->d_u0,  h->d_hf,      h->d_status, h->d_wsum, h->d_part, h->d_counter,
-                    h->d_sbox};
+                    h->d_sbox, h->d_B};
     for (void* p : bufs)
         if (p) cudaFree(p);
     for (int i = 0; i < 4; i++)
@@ -365,6 +403,7 @@ static RolloutArgs rollout_args(mppi_handle h, const float* x0, int per, const f
     a.arm = (float)armature(h->model_in, h->cfg.dt / h->cfg.n_sub);
     a.Dp = h->D;
     a.interp = h->cfg.interp;
+    a.Bt = reinterpret_cast<const float4*>(h->d_B);
     return a;
 }
 

@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 1 : 384 / BLOCK) k_batch
         // gait time of this horizon: step * control period, reduced modulo the gait period
         const double t0d = (double)step * sd.ctrl_steps * sd.dt_d;
         const float t0 = (sd.gait == 1 && sd.period_d > 0) ? (float)fmod(t0d, sd.period_d) : (float)t0d;
-        const HorizonArgs hz = {sd.H, sd.n_sub, sd.nx, sd.h, sd.dt, sd.inv_Hm1, t0, sd.arm, sd.interp};
+        const HorizonArgs hz = {sd.H, sd.n_sub, sd.nx, sd.h, sd.dt, sd.inv_Hm1, t0, sd.arm, sd.interp, sd.Bt};
         const float* x0 = a.x0s + (size_t)w.inst * NX_BOX;
         float L;
         if (sd.model.terrain != 0 || sd.model.n_sbox > 0)
@@ -290,6 +290,7 @@ InstDesc mppi::make_desc(const mppi_handle_s* h) {
     d.dt_d = h->cfg.dt;
     d.period_d = h->cost_in.gait_period;
     d.interp = h->cfg.interp;
+    d.Bt = reinterpret_cast<const float4*>(h->d_B);
     memcpy(d.sigma, h->cfg.sigma, sizeof(d.sigma));
     memcpy(d.q_lo, h->cfg.q_lo, sizeof(d.q_lo));
     memcpy(d.q_hi, h->cfg.q_hi, sizeof(d.q_hi));

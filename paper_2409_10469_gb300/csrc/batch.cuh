@@ -27,6 +27,7 @@ struct InstDesc {
     float sigma[D], q_lo[3], q_hi[3];
     uint32_t key0, key1, inst_id;
     int interp;           // MPPI_INTERP_* (knot representations only)
+    const float4* Bt;     // [H] knot weights of each dt step
 };
 
 struct WorkItem {

@@ -21,6 +21,7 @@ struct mppi_handle_s {
     int D = mppi::D;  // parameters per sample: 48, or 12 H for direct targets
     float *d_mu = nullptr, *d_mu_prop = nullptr, *d_mu_upd = nullptr, *d_U = nullptr, *d_L = nullptr;
     float *d_x0 = nullptr, *d_u0 = nullptr, *d_hf = nullptr, *d_sbox = nullptr;
+    float* d_B = nullptr;  // [H][4] knot weights of each dt step (16-B aligned rows)
     int* d_status = nullptr;
     double* d_wsum = nullptr;
     double* d_part = nullptr;      // update scratch: per-CTA partial sums

@@ -29,6 +29,7 @@ struct RolloutArgs {
     float* traj;           // [n][H+1][nx] device or null
     int n, H, n_sub;
     int Dp, interp;        // parameters per sample, MPPI_INTERP_*
+    const float4* Bt;      // [H] knot weights of each dt step (knot representations)
     float h, dt, inv_Hm1, t0;  // t0: gait time of step 0 (reduced modulo the gait period)
     float arm;             // implicit-PD armature h (kd + h kp) + a0
 };

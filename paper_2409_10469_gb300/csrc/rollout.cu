@@ -10,7 +10,7 @@
 
 namespace mppi {
 
-template <int TERR, bool BOX>
+template <int TERR, bool BOX, bool DIRECT>
 __global__ void __launch_bounds__(256, 1) k_rollout(RolloutArgs a) {
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = gt >> 2, leg = gt & 3;
@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(256, 1) k_rollout(RolloutArgs a) {
     const float* x0 = a.x0 + (a.x0_per_sample ? (size_t)kk * nx : 0);
     float Uk[NKNOT][3];
     const float* Urow = a.U + (size_t)kk * a.Dp;
-    if (a.interp != INTERP_DIRECT) {
+    if (!DIRECT) {
 #pragma unroll
         for (int j = 0; j < NKNOT; j++)
 #pragma unroll
@@ -31,8 +31,8 @@ __global__ void __launch_bounds__(256, 1) k_rollout(RolloutArgs a) {
 #pragma unroll
             for (int i = 0; i < 3; i++) Uk[j][i] = 0.f;
     }
-    const HorizonArgs hz = {a.H, a.n_sub, nx, a.h, a.dt, a.inv_Hm1, a.t0, a.arm, a.interp};
-    const float L = rollout_lane<TERR, BOX>(a.model, a.cost, hz, x0, Uk, Urow, leg, k, valid, a.traj);
+    const HorizonArgs hz = {a.H, a.n_sub, nx, a.h, a.dt, a.inv_Hm1, a.t0, a.arm, a.interp, a.Bt};
+    const float L = rollout_lane<TERR, BOX, DIRECT>(a.model, a.cost, hz, x0, Uk, Urow, leg, k, valid, a.traj);
     if (valid && leg == 0) a.L[k] = L;
 }
 
@@ -40,7 +40,8 @@ template <int TERR, bool BOX>
 static cudaError_t launch_t(const RolloutArgs& a, int block, cudaStream_t st) {
     long threads = 4L * a.n;
     int grid = (int)((threads + block - 1) / block);
-    k_rollout<TERR, BOX><<<grid, block, 0, st>>>(a);
+    if (a.interp == INTERP_DIRECT) k_rollout<TERR, BOX, true><<<grid, block, 0, st>>>(a);
+    else k_rollout<TERR, BOX, false><<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
 }
 

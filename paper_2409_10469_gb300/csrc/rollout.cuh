@@ -562,6 +562,7 @@ struct HorizonArgs {
     int H, n_sub, nx;
     float h, dt, inv_Hm1, t0, arm;
     int interp;           // INTERP_*
+    const float4* Bt;     // [H] knot weights of each dt step (knot representations)
 };
 
 // x_t of rollout k: lane 0 writes the trunk, every lane its leg's joints
@@ -601,52 +602,29 @@ __device__ __forceinline__ float* opaque_ptr(float* p) {
 }
 
 // Joint targets of this lane's leg at dt step t: the knot representation's
-// interpolant of Uk (cubic: Lagrange basis at tau = t / (H - 1); zeroth order /
-// linear: the knot interval j = floor(3 t / (H - 1)) in integers, fraction f), or
-// the step's own sampled targets (DIRECT: Urow = the sample's [t][12] targets).
+// weights of step t (a table computed per controller: the cubic's Lagrange
+// basis, the zeroth-order or linear weights) applied to Uk, or, DIRECT, the
+// step's own sampled targets (Urow = the sample's [t][12] targets).
+template <bool DIRECT>
 __device__ __forceinline__ void leg_controls(const HorizonArgs& a, int t, int leg, const float (&Uk)[NKNOT][3],
                                              const float* Urow, float u[3]) {
-    if (a.interp == INTERP_DIRECT) {
+    if (DIRECT) {
         const float* ut = Urow + t * NJ + 3 * leg;
         u[0] = __ldg(ut);
         u[1] = __ldg(ut + 1);
         u[2] = __ldg(ut + 2);
         return;
     }
-    float B0, B1, B2, B3;
-    if (a.interp == INTERP_CUBIC) {
-        // cubic through 4 knots at tau_j = j / 3 (Lagrange basis)
-        const float tau = (float)t * a.inv_Hm1;
-        const float d0 = tau, d1 = tau - (1.f / 3.f), d2 = tau - (2.f / 3.f), d3 = tau - 1.f;
-        B0 = d1 * d2 * d3 * -4.5f;
-        B1 = d0 * d2 * d3 * 13.5f;
-        B2 = d0 * d1 * d3 * -13.5f;
-        B3 = d0 * d1 * d2 * 4.5f;
-    } else {
-        const int den = a.H - 1;
-        int j = (3 * t) / den;
-        float wl = 1.f, wh = 0.f;
-        if (a.interp == INTERP_ZERO) {
-            j = min(j, 3);
-        } else {
-            j = min(j, 2);
-            wh = (float)(3 * t - j * den) / (float)den;
-            wl = 1.f - wh;
-        }
-        B0 = j == 0 ? wl : 0.f;
-        B1 = j == 1 ? wl : (j == 0 ? wh : 0.f);
-        B2 = j == 2 ? wl : (j == 1 ? wh : 0.f);
-        B3 = j == 3 ? wl : (j == 2 ? wh : 0.f);
-    }
+    const float4 b = __ldg(a.Bt + t);
 #pragma unroll
-    for (int i = 0; i < 3; i++) u[i] = B0 * Uk[0][i] + B1 * Uk[1][i] + B2 * Uk[2][i] + B3 * Uk[3][i];
+    for (int i = 0; i < 3; i++) u[i] = b.x * Uk[0][i] + b.y * Uk[1][i] + b.z * Uk[2][i] + b.w * Uk[3][i];
 }
 
 // One lane's share of rollout k: x0 (state), Uk[4][3] (this leg's knots) or, for
 // DIRECT, Urow (the sample's H x 12 targets), the horizon, optional trajectory
 // output traj (float[n][H + 1][nx], or nullptr); returns the rollout's total cost
 // on every lane of the rollout.
-template <int TERR, bool BOX>
+template <int TERR, bool BOX, bool DIRECT = false>
 __device__ __forceinline__ float rollout_lane(const DevModel& m, const DevCost& c, const HorizonArgs& a,
                                               const float* x0, const float (&Uk)[NKNOT][3], const float* Urow,
                                               int leg, int k, bool valid, float* traj) {
@@ -676,7 +654,7 @@ __device__ __forceinline__ float rollout_lane(const DevModel& m, const DevCost& 
     if (float* tp = opaque_ptr(traj)) store_state<BOX>(tp, a.H, k, 0, leg, valid, T, S, Bx, a.nx);
     for (int t = 0; t < a.H; t++) {
         float u[3];
-        leg_controls(a, t, leg, Uk, Urow, u);
+        leg_controls<DIRECT>(a, t, leg, Uk, Urow, u);
         // stage cost: this leg's control term; the trunk terms on lane 0
         {
             float ds = 0.f, dk = 0.f;

@@ -1,0 +1,90 @@
+"""Hyperparameter sweeps of Fig. 6 / Sec. IV-E on the GPU path: control rate,
+temperature lambda, horizon H and sample count K for the trot task, closed-loop
+episodes paired across settings (same start states and noise streams), judged
+by the FP64 oracle's L_walk along the realised trajectory.  The cost reported
+is the time average of the stage cost (states are sampled at the control
+instants, so settings with different control rates compare per unit time).
+
+The default-size tests assert what the paper finds and this simulator
+reproduces robustly: more samples help up to a plateau, and a 10 Hz controller
+is worse than a 100 Hz one.  `MPPI_FULL=1` runs the full sweeps (10 episodes
+per point, as the paper averages 10 seeds) and writes them to MPPI_FULL_OUT."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import oracle as O  # noqa: E402
+from paper_2409_10469_gb300 import proposal as P, workloads as W  # noqa: E402
+
+SECONDS = 1.5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as g
+    g.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def time_avg_cost(states, controls, cfgs):
+    out = []
+    for e, cfg in enumerate(cfgs):
+        w = O.World(cfg.robot)
+        S = states.shape[0]
+        t = np.arange(S) * cfg.mppi["ctrl_steps"] * cfg.mppi["dt"]
+        out.append(O.stage_costs(w, cfg.cost, states[:, e], controls[:, e].astype(np.float64), t).mean())
+    return np.array(out)
+
+
+def point(E, K=256, H=60, lam=None, ctrl_steps=None, seed=5, seconds=SECONDS):
+    def make(e):
+        cfg = W.config_trot(K=K, H=H)
+        if lam is not None:
+            cfg.mppi["lam"] = lam
+        if ctrl_steps is not None:
+            cfg.mppi["ctrl_steps"] = ctrl_steps
+        return cfg
+    cfg0 = make(0)
+    steps = int(round(seconds / (cfg0.mppi["ctrl_steps"] * cfg0.mppi["dt"])))
+    st, ct, cfgs = P.run_episodes(make, E, K, H, steps, seed=seed)
+    assert np.all(np.isfinite(st))
+    return time_avg_cost(st, ct, cfgs)
+
+
+def test_more_samples_help_and_slow_control_hurts():
+    E = 8
+    k5, k256 = point(E, K=5), point(E, K=256)
+    r10, r100 = point(E, ctrl_steps=20), point(E, ctrl_steps=2)   # dt 0.005: 10 Hz, 100 Hz
+    print(json.dumps({"K5": k5.mean(), "K256": k256.mean(), "10Hz": r10.mean(), "100Hz": r100.mean()}))
+    assert (k5 - k256).mean() > 0
+    assert (r10 - r100).mean() > 0
+
+
+@pytest.mark.skipif(os.environ.get("MPPI_FULL") != "1", reason="sweep-scale run: set MPPI_FULL=1")
+def test_hyperparameter_sweeps_full():
+    E = 10
+    res = {"rate_hz": {}, "lambda": {}, "H": {}, "K": {}}
+
+    def rec(table, key, c):
+        res[table][str(key)] = {"mean": float(c.mean()), "sem": float(c.std() / np.sqrt(E))}
+
+    for cs in (20, 10, 4, 2, 1):                  # 10, 20, 50, 100, 200 Hz at dt = 0.005
+        rec("rate_hz", round(1.0 / (cs * 0.005)), point(E, ctrl_steps=cs))
+    for lam in (0.005, 0.01, 0.03, 0.1, 0.3, 1.0):
+        rec("lambda", lam, point(E, lam=lam))
+    for H in (5, 10, 20, 40, 60, 100):
+        rec("H", H, point(E, H=H))
+    for K in (5, 10, 20, 40, 100, 250, 500):
+        rec("K", K, point(E, K=K))
+    print(json.dumps(res))
+    path = os.environ.get("MPPI_FULL_OUT")
+    if path:
+        with open(path, "w") as f:
+            json.dump(res, f, indent=1)
