@@ -517,7 +517,7 @@ extern "C" mppi_status mppi_batch_autotune(mppi_batch b, const float* x0s, int t
     const int blocks[3] = {64, 128, 256};
     for (int bi = 0; bi < 3; bi++) {
         const int mx = max_blocks_per_sm(blocks[bi]);
-        for (int p = 1; p <= mx && p <= 16; p *= 2) {
+        for (int p = 1; p <= mx && p <= 16; p++) {  // every occupancy level up to the limit
             b->block = blocks[bi];
             b->blocks_per_sm = p;
             BCK(cudaStreamSynchronize(b->stream));

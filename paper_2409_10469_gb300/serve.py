@@ -88,3 +88,25 @@ def run(n_robots=64, rate_hz=50.0, duration=1.0, seed=4, budget_bytes=512 << 20,
     for c in ctls:
         c.close()
     return out
+
+
+def main():
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="serving loop: Poisson requests of simulated robots")
+    ap.add_argument("--robots", type=int, default=64)
+    ap.add_argument("--rate", type=float, default=50.0, help="requests per second per robot")
+    ap.add_argument("--duration", type=float, default=1.0, help="arrival window in seconds")
+    ap.add_argument("--seed", type=int, default=4)
+    ap.add_argument("--budget-mb", type=int, default=512)
+    ap.add_argument("--k-min", type=int, default=512)
+    ap.add_argument("--k-max", type=int, default=8192)
+    a = ap.parse_args()
+    from . import build as B
+    B.build()
+    print(json.dumps(run(n_robots=a.robots, rate_hz=a.rate, duration=a.duration, seed=a.seed,
+                         budget_bytes=a.budget_mb << 20, K_range=(a.k_min, a.k_max))))
+
+
+if __name__ == "__main__":
+    main()
