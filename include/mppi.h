@@ -75,13 +75,21 @@ typedef struct {
     int n_static_boxes; double sbox_lo[4][3], sbox_hi[4][3];
 } mppi_model_t;
 
-/* L_walk (Sec. IV-B) + L_box (Sec. IV-D) weights and references. */
+/* L_walk (Sec. IV-B) + L_box (Sec. IV-D) weights and references.  gait 2 is the
+ * trot reference with the Raibert heuristic's foot placement (Sec. IV-B): a
+ * swinging leg's hip-flexion target moves by -dx / raibert_len (clamped to
+ * 0.4 rad, weighted by the swing profile), dx = (gait_period / 4) v_x +
+ * raibert_k (v_x - v_ref), v_x the trunk's body-frame forward velocity.  z_rel:
+ * the height reference counts from the ground under the trunk (terrain or the
+ * top of a static box containing the trunk's xy), for climbing (Sec. IV-C). */
 typedef struct {
     double w_z, z_ref, w_o, w_v, v_ref, w_p, goal_xy[2], w_u, w_box, box_goal_xy[2];
-    int gait;                    /* 0 stand reference, 1 open-loop trot */
+    int gait;                    /* 0 stand reference, 1 open-loop trot, 2 trot + Raibert feedback */
     double gait_period, gait_hip_amp, gait_knee_amp;
     double stand[3];
     double w_terminal;
+    double raibert_k, raibert_len;
+    int z_rel;
 } mppi_cost_t;
 
 /* Control representation of a sample (Sec. III-B, the ablation of Fig. 5).

@@ -55,6 +55,7 @@ class OrCost(C.Structure):
         ("w_u", C.c_double), ("w_box", C.c_double), ("box_goal_xy", C.c_double * 2),
         ("gait", C.c_int), ("gait_period", C.c_double), ("gait_hip_amp", C.c_double),
         ("gait_knee_amp", C.c_double), ("stand", C.c_double * 3), ("w_terminal", C.c_double),
+        ("raibert_k", C.c_double), ("raibert_len", C.c_double), ("z_rel", C.c_int),
     ]
 
 
@@ -110,6 +111,9 @@ def lib():
         L.or_spline_basis.argtypes = [C.c_int, C.c_int, dp]
         L.or_spline_eval.argtypes = [fp, C.c_double, dp]
         L.or_gait_ref.argtypes = [C.POINTER(OrCost), C.c_double, dp]
+        L.or_gait_ref_x.argtypes = [C.POINTER(OrCost), C.c_double, dp, dp]
+        L.or_ground_under.restype = C.c_double
+        L.or_ground_under.argtypes = [C.c_void_p, C.c_double, C.c_double]
         L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
         L.or_lnf.restype = C.c_float
         L.or_lnf.argtypes = [C.c_float]
@@ -542,3 +546,17 @@ class use_count:
     def __exit__(self, *a):
         global _lib
         _lib, _build.build = self._saved
+
+
+def gait_ref_x(cost: dict, t_abs: float, x=None):
+    """u_ref(t) with the state's feedback (gait 2 reads the trunk's v_x)."""
+    u = np.zeros(NJ)
+    xx = _f64(x) if x is not None else None
+    lib().or_gait_ref_x(C.byref(make_cost(cost)), t_abs, _p(xx, C.c_double) if xx is not None else None,
+                        _p(u, C.c_double))
+    return u
+
+
+def ground_under(world: World, x: float, y: float) -> float:
+    """Ground height under (x, y): terrain, or a static box top whose footprint contains it."""
+    return lib().or_ground_under(world.ptr, x, y)

@@ -27,7 +27,7 @@ def features(x, cost: dict, ctrl_steps: int, dt: float, step: int) -> np.ndarray
         f[48:50] = np.asarray(cost["box_goal_xy"]) - x[37:39]
     f[50:52] = np.asarray(cost["goal_xy"]) - x[0:2]
     phase = 0.0
-    if cost["gait"] == 1 and cost["gait_period"] > 0:
+    if cost["gait"] in (1, 2) and cost["gait_period"] > 0:
         t = step * ctrl_steps * dt
         phase = 2 * math.pi * math.fmod(t, cost["gait_period"]) / cost["gait_period"]
     f[52], f[53] = math.sin(phase), math.cos(phase)

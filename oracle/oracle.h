@@ -104,10 +104,13 @@ typedef struct {
     double w_p, goal_xy[2];     /* trunk xy position */
     double w_u;                 /* R = w_u I on (u - u_ref(t)) */
     double w_box, box_goal_xy[2];  /* Q_box || xbar_box - x_box ||_1 (xy) */
-    int gait;                   /* 0: u_ref = stand pose; 1: open-loop trot */
+    int gait;                   /* 0: u_ref = stand pose; 1: open-loop trot; 2: trot with
+                                   Raibert foot-placement feedback */
     double gait_period, gait_hip_amp, gait_knee_amp;
     double stand[3];            /* (abd, hip, knee) stand pose */
     double w_terminal;          /* multiplier of the t = H state terms */
+    double raibert_k, raibert_len;  /* gait 2: velocity-error gain (s), effective leg length (m) */
+    int z_rel;                  /* 1: z_ref is measured from the ground under the trunk */
 } or_cost;
 
 /* ---------------- MPPI parameters ---------------- */
@@ -169,6 +172,8 @@ int  or_param_dim(int interp, int H);
 void or_interp_basis(int interp, int H, int t, real B[OR_NKNOT]);
 void or_controls(int interp, int H, int t, const float* U, real u[OR_NJ]);
 void or_gait_ref(const or_cost* c, real t_abs, real uref[OR_NJ]);
+void or_gait_ref_x(const or_cost* c, real t_abs, const real* x, real uref[OR_NJ]);
+real or_ground_under(const or_world* w, real x, real y);
 real or_stage_cost(const or_world* w, const or_cost* c, const real* x, const real* u, real t_abs);
 real or_terminal_cost(const or_world* w, const or_cost* c, const real* x);
 real or_rollout(const or_world* w, const or_cost* c, int H, int n_sub, real dt, real t0,

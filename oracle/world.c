@@ -434,22 +434,53 @@ void or_controls(int interp, int H, int t, const float* U, real u[OR_NJ]) {
 
 /* ---------------- cost ---------------- */
 
-/* control reference u_ref(t): the stand pose, or an open-loop trot (diagonal
- * pairs FR+RL and FL+RR in antiphase) in place of the Raibert-heuristic gait */
-void or_gait_ref(const or_cost* c, real t_abs, real uref[OR_NJ]) {
+/*
+ * control reference u_ref(t): the stand pose, an open-loop trot (diagonal pairs
+ * FR+RL and FL+RR in antiphase), or (gait 2) that trot with the Raibert
+ * heuristic's foot placement fed back from the trunk's forward velocity v_x
+ * (Sec. IV-B cites the heuristic for the gait reference): a swinging foot is
+ * placed dx = (T_stance / 2) v_x + k (v_x - v_ref) ahead of its hip, T_stance =
+ * half the gait period, which the hip-flexion target realises as the small-angle
+ * rotation -dx / L of the leg (L the effective leg length), clamped to 0.4 rad
+ * and weighted by the swing profile max(0, sin phase).  x == NULL: v_x = v_ref.
+ */
+void or_gait_ref_x(const or_cost* c, real t_abs, const real* x, real uref[OR_NJ]) {
     static const double phase0[4] = {0, 1, 1, 0};
+    real dth = 0;
+    if (c->gait == 2) {
+        real vx = x ? x[22] : (real)c->v_ref;
+        real dx = 0.25 * c->gait_period * vx + c->raibert_k * (vx - c->v_ref);
+        dth = -dx / c->raibert_len;
+        if (dth > 0.4) dth = 0.4;
+        if (dth < -0.4) dth = -0.4;
+    }
     for (int l = 0; l < 4; l++) {
         real dh = 0, dk = 0;
-        if (c->gait == 1) {
+        if (c->gait == 1 || c->gait == 2) {
             real ph = 2 * M_PI * t_abs / c->gait_period + M_PI * phase0[l];
             real s = sin(ph);
-            dh = c->gait_hip_amp * s;
-            dk = -c->gait_knee_amp * (s > 0 ? s : 0);
+            real sw = s > 0 ? s : 0;
+            dh = c->gait_hip_amp * s + sw * dth;
+            dk = -c->gait_knee_amp * sw;
         }
         uref[3 * l + 0] = c->stand[0];
         uref[3 * l + 1] = c->stand[1] + dh;
         uref[3 * l + 2] = c->stand[2] + dk;
     }
+}
+
+void or_gait_ref(const or_cost* c, real t_abs, real uref[OR_NJ]) { or_gait_ref_x(c, t_abs, NULL, uref); }
+
+/* height of the ground under (x, y): the plane or heightfield, or the top of a
+ * static box whose footprint contains (x, y), whichever is higher */
+real or_ground_under(const or_world* w, real x, real y) {
+    real h, hx, hy;
+    or_terrain_height(w, x, y, &h, &hx, &hy);
+    for (int b = 0; b < w->n_sbox; b++)
+        if (x >= w->sbox_lo[b][0] && x <= w->sbox_hi[b][0] && y >= w->sbox_lo[b][1] && y <= w->sbox_hi[b][1] &&
+            w->sbox_hi[b][2] > h)
+            h = w->sbox_hi[b][2];
+    return h;
 }
 
 /* state terms of L_walk and L_box (x_ref: height, upright attitude, forward
@@ -458,7 +489,7 @@ static real state_cost(const or_world* w, const or_cost* c, const real* x) {
     const real* q = x;
     const real* v = x + 19;
     real L = 0;
-    real dz = q[2] - c->z_ref;
+    real dz = q[2] - c->z_ref - (c->z_rel ? or_ground_under(w, q[0], q[1]) : 0);
     L += c->w_z * dz * dz;
     /* e_rot = 2 vec(q_ref^-1 (x) q), q_ref = identity, sign chosen so w >= 0 */
     real sg = q[3] < 0 ? -1 : 1;
@@ -477,7 +508,7 @@ static real state_cost(const or_world* w, const or_cost* c, const real* x) {
 
 real or_stage_cost(const or_world* w, const or_cost* c, const real* x, const real* u, real t_abs) {
     real uref[OR_NJ], L = state_cost(w, c, x);
-    or_gait_ref(c, t_abs, uref);
+    or_gait_ref_x(c, t_abs, x, uref);
     for (int j = 0; j < OR_NJ; j++) L += c->w_u * (u[j] - uref[j]) * (u[j] - uref[j]);
     return L;
 }

@@ -82,6 +82,7 @@ class MppiCost(C.Structure):
         ("box_goal_xy", C.c_double * 2),
         ("gait", C.c_int), ("gait_period", C.c_double), ("gait_hip_amp", C.c_double),
         ("gait_knee_amp", C.c_double), ("stand", C.c_double * 3), ("w_terminal", C.c_double),
+        ("raibert_k", C.c_double), ("raibert_len", C.c_double), ("z_rel", C.c_int),
     ]
 
 

@@ -153,13 +153,17 @@ static void derive_cost(const mppi_cost_t& c, DevCost& d) {
     d.hip_amp = (float)c.gait_hip_amp; d.knee_amp = (float)c.gait_knee_amp;
     for (int i = 0; i < 3; i++) d.stand[i] = (float)c.stand[i];
     d.w_term = (float)c.w_terminal;
+    d.quarter_period = (float)(0.25 * c.gait_period);
+    d.raibert_k = (float)c.raibert_k;
+    d.inv_raibert_len = c.raibert_len > 0 ? (float)(1.0 / c.raibert_len) : 0.f;
+    d.z_rel = c.z_rel;
 }
 
 // gait time of step 0 of a horizon starting at absolute time t0, reduced
 // modulo the gait period so that FP32 keeps its resolution over long runs
 float mppi_reduce_t0(const mppi_handle h, double t0) {
     const double P = h->cost_in.gait_period;
-    if (h->cost_in.gait == 1 && P > 0) return (float)fmod(t0, P);
+    if ((h->cost_in.gait == 1 || h->cost_in.gait == 2) && P > 0) return (float)fmod(t0, P);
     return (float)t0;
 }
 
@@ -235,6 +239,7 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
     if (model->terrain != 0 && model->terrain != 1) return MPPI_ERR_ARG;
     if (model->n_static_boxes < 0 || model->n_static_boxes > MAX_SBOX) return MPPI_ERR_ARG;
     if (model->n_trunk_spheres < 0 || model->n_trunk_spheres > 4) return MPPI_ERR_ARG;
+    if (cost->gait < 0 || cost->gait > 2 || (cost->gait == 2 && !(cost->raibert_len > 0))) return MPPI_ERR_ARG;
 
     mppi_handle h = new mppi_handle_s();
     h->model_in = *model;

@@ -162,7 +162,8 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 1 : 384 / BLOCK) k_batch
         sample_lane(sd, k, leg, step, valid, Uk);
         // gait time of this horizon: step * control period, reduced modulo the gait period
         const double t0d = (double)step * sd.ctrl_steps * sd.dt_d;
-        const float t0 = (sd.gait == 1 && sd.period_d > 0) ? (float)fmod(t0d, sd.period_d) : (float)t0d;
+        const float t0 = ((sd.gait == 1 || sd.gait == 2) && sd.period_d > 0) ? (float)fmod(t0d, sd.period_d)
+                                                                          : (float)t0d;
         const HorizonArgs hz = {sd.H, sd.n_sub, sd.nx, sd.h, sd.dt, sd.inv_Hm1, t0, sd.arm, sd.interp, sd.Bt};
         const float* x0 = a.x0s + (size_t)w.inst * NX_BOX;
         float L;

@@ -72,6 +72,8 @@ struct DevCost {
     float two_pi_over_period, hip_amp, knee_amp;
     float stand[3];
     float w_term;
+    float quarter_period, raibert_k, inv_raibert_len;  // gait 2: T_stance / 2, velocity gain, 1 / leg length
+    int z_rel;                                          // height reference from the ground under the trunk
 };
 
 // shifted(mu) knot j, joint i for the knot representations: the representation's

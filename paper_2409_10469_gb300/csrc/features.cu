@@ -108,7 +108,7 @@ extern "C" mppi_status mppi_features(mppi_handle h, const float* X, int n, uint3
     a.box_gy = (float)h->cost_in.box_goal_xy[1];
     const double t = (double)step * h->cfg.ctrl_steps * h->cfg.dt;
     const double P = h->cost_in.gait_period;
-    a.phase = (h->cost_in.gait == 1 && P > 0) ? (float)(2.0 * M_PI * fmod(t, P) / P) : 0.f;
+    a.phase = ((h->cost_in.gait == 1 || h->cost_in.gait == 2) && P > 0) ? (float)(2.0 * M_PI * fmod(t, P) / P) : 0.f;
     a.F = fdv ? F : dF;
     if (e == cudaSuccess) {
         k_features<<<(n + 127) / 128, 128, 0, st>>>(a);

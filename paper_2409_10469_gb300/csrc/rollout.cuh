@@ -206,8 +206,23 @@ __device__ __forceinline__ void sphere_env(const DevModel& m, float3 xw, float r
 
 // ---------------------------------------------------------------- cost
 
-__device__ __forceinline__ float trunk_state_cost(const DevCost& c, const Trunk& T) {
+// height of the ground under (x, y): the plane or heightfield, or the top of a
+// static box whose footprint contains (x, y), whichever is higher
+__device__ __forceinline__ float ground_under(const DevModel& m, float x, float y) {
+    float h, hx, hy;
+    ground(m, x, y, h, hx, hy);
+    for (int b = 0; b < m.n_sbox; b++) {
+        const float* bx = m.sbox + 6 * b;
+        if (x >= __ldg(bx) && x <= __ldg(bx + 3) && y >= __ldg(bx + 1) && y <= __ldg(bx + 4))
+            h = fmaxf(h, __ldg(bx + 5));
+    }
+    return h;
+}
+
+template <int TERR>
+__device__ __forceinline__ float trunk_state_cost(const DevModel& m, const DevCost& c, const Trunk& T) {
     float dz = T.p[2] - c.z_ref;
+    if (TERR != 0 && c.z_rel) dz -= ground_under(m, T.p[0], T.p[1]);   // flat ground without boxes: 0
     float L = c.w_z * dz * dz;
     float sg = T.quat[0] < 0.f ? -2.f : 2.f;
     float ex = sg * T.quat[1], ey = sg * T.quat[2], ez = sg * T.quat[3];
@@ -658,21 +673,29 @@ __device__ __forceinline__ float rollout_lane(const DevModel& m, const DevCost& 
         // stage cost: this leg's control term; the trunk terms on lane 0
         {
             float ds = 0.f, dk = 0.f;
-            if (c.gait == 1) {
+            if (c.gait != 0) {
                 float s, cq;
                 sincos_r(c.two_pi_over_period * (a.t0 + (float)t * a.dt) + ph0, s, cq);
+                const float sw = fmaxf(s, 0.f);
                 ds = c.hip_amp * s;
-                dk = -c.knee_amp * fmaxf(s, 0.f);
+                dk = -c.knee_amp * sw;
+                if (c.gait == 2) {
+                    // Raibert foot placement: dx ahead of the hip, as a hip-flexion rotation
+                    const float vx = T.v.x;
+                    const float dx = c.quarter_period * vx + c.raibert_k * (vx - c.v_ref);
+                    const float dth = fminf(fmaxf(-dx * c.inv_raibert_len, -0.4f), 0.4f);
+                    ds += sw * dth;
+                }
             }
             float e0 = u[0] - c.stand[0], e1 = u[1] - (c.stand[1] + ds), e2 = u[2] - (c.stand[2] + dk);
             L += c.w_u * (e0 * e0 + e1 * e1 + e2 * e2);
-            if (leg == 0) L += trunk_state_cost(c, T) + (BOX ? box_cost(c, Bx) : 0.f);
+            if (leg == 0) L += trunk_state_cost<TERR>(m, c, T) + (BOX ? box_cost(c, Bx) : 0.f);
         }
         const float kpu[3] = {m.kp * u[0], m.kp * u[1], m.kp * u[2]};
         for (int sb = 0; sb < a.n_sub; sb++) substep<TERR, BOX>(m, leg, T, S, kpu, h, kdh, hg, a.arm, Bx);
         if (float* tp = opaque_ptr(traj)) store_state<BOX>(tp, a.H, k, t + 1, leg, valid, T, S, Bx, a.nx);
     }
-    if (leg == 0) L += c.w_term * (trunk_state_cost(c, T) + (BOX ? box_cost(c, Bx) : 0.f));
+    if (leg == 0) L += c.w_term * (trunk_state_cost<TERR>(m, c, T) + (BOX ? box_cost(c, Bx) : 0.f));
     return xsum4(L);
 }
 

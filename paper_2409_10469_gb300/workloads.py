@@ -68,9 +68,16 @@ def cost(task: str = "stand", box_goal=(1.5, 0.0)) -> dict:
     """Cost weights of L_walk (+ L_box for the push task), model-spec readings."""
     c = dict(w_z=1.0e3, z_ref=0.3, w_o=1.0e2, w_v=0.0, v_ref=0.0, w_p=0.0, goal_xy=(0.0, 0.0),
              w_u=1.0, w_box=0.0, box_goal_xy=(0.0, 0.0), gait=0, gait_period=0.5,
-             gait_hip_amp=0.1, gait_knee_amp=0.3, stand=STAND, w_terminal=1.0)
+             gait_hip_amp=0.1, gait_knee_amp=0.3, stand=STAND, w_terminal=1.0,
+             raibert_k=0.0, raibert_len=0.3, z_rel=0)
     if task == "trot":
         c.update(w_v=1.0e2, v_ref=0.5, gait=1)
+    elif task == "trot_raibert":
+        # the trot reference with the Raibert heuristic's foot-placement feedback
+        c.update(w_v=1.0e2, v_ref=0.5, gait=2, raibert_k=0.1)
+    elif task == "climb":
+        # the trot reference, a waypoint on top of the box, height from the ground under the trunk
+        c.update(w_v=1.0e2, v_ref=0.5, gait=1, w_p=1.0e1, goal_xy=(1.1, 0.0), z_rel=1)
     elif task == "push":
         c.update(w_box=1.0e2, box_goal_xy=tuple(box_goal), w_p=1.0e1, gait=1)
     elif task != "stand":
@@ -194,6 +201,13 @@ def config_trot(K: int = 1024, H: int = 100) -> Workload:
                     mppi(K, H, dt, 0.3, n_sub_for(dt), seed=0), perturbed_stand(1), stand_mu(), 200)
 
 
+def config_trot_raibert(K: int = 1024, H: int = 100) -> Workload:
+    """The trot task with the Raibert-feedback gait reference."""
+    dt = 0.005
+    return Workload("trot_raibert_K%d_H%d" % (K, H), robot(), cost("trot_raibert"),
+                    mppi(K, H, dt, 0.3, n_sub_for(dt), seed=0), perturbed_stand(1), stand_mu(), 200)
+
+
 def config_terrain(K: int = 1024, H: int = 100, seed: int = 3) -> Workload:
     """Trot over a 128 x 128 heightfield (2 cm cells) plus a 0.3 m step-up box."""
     dt = 0.005
@@ -202,6 +216,17 @@ def config_terrain(K: int = 1024, H: int = 100, seed: int = 3) -> Workload:
                static_boxes=[((0.8, -0.5, -0.2), (1.4, 0.5, 0.3))])
     return Workload("trot_terrain_K%d_H%d" % (K, H), rb, cost("trot"),
                     mppi(K, H, dt, 0.3, n_sub_for(dt), seed=0), stand_state(z=0.42), stand_mu(), 50)
+
+
+def config_climb(K: int = 1024, H: int = 100, box_height: float = 0.24, gait: str = "climb") -> Workload:
+    """Climb onto a box (Sec. IV-C: up to 0.24 m, about the standing height):
+    flat plane, static box from x = 0.45 m to 1.65 m (1.2 m wide) of the given
+    height, waypoint at x = 1.1 m on top of it; trot reference; the height
+    reference is measured from the ground under the trunk."""
+    dt = 0.005
+    rb = robot(static_boxes=[((0.45, -0.6, -0.2), (1.65, 0.6, box_height))])
+    return Workload("climb_%02dcm_K%d_H%d" % (round(100 * box_height), K, H), rb, cost(gait),
+                    mppi(K, H, dt, 0.3, n_sub_for(dt), seed=0), perturbed_stand(1), stand_mu(), 400)
 
 
 def config_push(K: int = 4096, H: int = 100, seed: int = 100, n_prop: int = 0) -> Workload:

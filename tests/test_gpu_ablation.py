@@ -68,11 +68,12 @@ def test_direct_sampling_is_worst_on_trot():
 
 @pytest.mark.skipif(os.environ.get("MPPI_FULL") != "1", reason="ablation-scale run: set MPPI_FULL=1")
 def test_sampling_representation_ablation_full():
-    """Trot (K = 1024, H = 100) and the terrain step (K = 1024, H = 100), 32
+    """Trot, the terrain step and the 0.24 m box climb (K = 1024, H = 100), 32
     paired episodes of 2 s each per representation."""
     res = {}
     for task, make in (("trot", lambda e: W.config_trot(K=1024, H=100)),
-                       ("terrain_step", lambda e: W.config_terrain(K=1024, H=100, seed=3))):
+                       ("terrain_step", lambda e: W.config_terrain(K=1024, H=100, seed=3)),
+                       ("box_climb_24cm", lambda e: W.config_climb(K=1024, H=100, box_height=0.24))):
         cost = ablation(make, 32, 1024, 100, 200, seed=11)
         res[task] = summary(cost)
         res[task]["paired_vs_cubic"] = {k: float((v - cost["cubic"]).mean()) for k, v in cost.items()}
