@@ -59,9 +59,9 @@ __device__ __forceinline__ bool sphere_aabb(float3 x, float r, float3 lo, float3
     float3 d = x - cp;
     float d2 = dot3(d, d);
     if (d2 > 0.f) {
-        float dn = sqrtf(d2);
+        const float inv = rsqrtf(d2);   // approximate, branch-free (no IEEE slow path)
+        const float dn = d2 * inv;
         if (dn >= r) return false;
-        float inv = 1.f / dn;
         n = inv * d;
         pen = r - dn;
         return true;
@@ -477,7 +477,7 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
         ci[3] = C00 * C22 - C02 * C02;
         ci[4] = C01 * C02 - C00 * C12;
         ci[5] = C00 * C11 - C01 * C01;
-        const float idc = __frcp_rn(C00 * ci[0] + C01 * ci[1] + C02 * ci[2]);
+        const float idc = __fdividef(1.f, C00 * ci[0] + C01 * ci[1] + C02 * ci[2]);
 #pragma unroll
         for (int i = 0; i < 6; i++) ci[i] *= idc;
         // W = B C^-1 (3x3)
@@ -501,7 +501,7 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
         si[3] = S[0] * S[5] - S[2] * S[2];
         si[4] = S[1] * S[2] - S[0] * S[4];
         si[5] = S[0] * S[3] - S[1] * S[1];
-        const float ids = __frcp_rn(S[0] * si[0] + S[1] * si[1] + S[2] * si[2]);
+        const float ids = __fdividef(1.f, S[0] * si[0] + S[1] * si[1] + S[2] * si[2]);
         // [A B; B^T C] [x; y] = -[p; q]:  x = S^-1 (-p + W q),  y = C^-1 (-q - B^T x)
         float rx[3];
 #pragma unroll
