@@ -101,6 +101,20 @@ __device__ __forceinline__ float shifted_knot(const float* mu, int interp, int H
     return (1.f - f) * mu[jj * NJ + i] + f * mu[(jj + 1) * NJ + i];
 }
 
+// MUFU reciprocal and reciprocal square root with subnormals flushed to zero:
+// one instruction each, no subnormal-handling branch (the arguments here --
+// pivots, determinants, norms plus a positive floor -- are never subnormal)
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // ---------------------------------------------------------------- float3 ops
 __device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
 __device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
@@ -359,7 +373,7 @@ __device__ __forceinline__ void quat_integrate(float q[4], float3 w, float h) {
     float r1 = q[0] * d1 + q[1] * d0 + q[2] * d3 - q[3] * d2;
     float r2 = q[0] * d2 - q[1] * d3 + q[2] * d0 + q[3] * d1;
     float r3 = q[0] * d3 + q[1] * d2 - q[2] * d1 + q[3] * d0;
-    float inv = rsqrtf(r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
+    float inv = rsqrt_approx(r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
     q[0] = r0 * inv; q[1] = r1 * inv; q[2] = r2 * inv; q[3] = r3 * inv;
 }
 

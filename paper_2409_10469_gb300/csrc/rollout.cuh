@@ -94,7 +94,7 @@ __device__ __forceinline__ void contact_wrench(const DevModel& m, float pen, flo
     const float vn = dot3(vp, nb);
     const float fn = active ? fmaxf(fmaf(m.kc, pen, -m.cc * vn), 0.f) : 0.f;
     const float3 vt = f3(fmaf(-vn, nb.x, vp.x), fmaf(-vn, nb.y, vp.y), fmaf(-vn, nb.z, vp.z));
-    const float fr = m.mu * fn * rsqrtf(fmaf(vt.x, vt.x, fmaf(vt.y, vt.y, fmaf(vt.z, vt.z, m.eps2))));
+    const float fr = m.mu * fn * rsqrt_approx(fmaf(vt.x, vt.x, fmaf(vt.y, vt.y, fmaf(vt.z, vt.z, m.eps2))));
     const float sn = SG > 0 ? fn : -fn, st = SG > 0 ? -fr : fr;
     const float3 f = f3(fmaf(sn, nb.x, st * vt.x), fmaf(sn, nb.y, st * vt.y), fmaf(sn, nb.z, st * vt.z));
     force = force + f;
@@ -164,7 +164,7 @@ __device__ __forceinline__ void sphere_vs_box(const DevModel& m, const BoxKin& B
     const float vn = dot3(vrel, nw);
     const float fn = fmaxf(m.kc * pen - m.cc * vn, 0.f);
     const float3 vt = vrel - vn * nw;
-    const float fr = m.mu * fn * rsqrtf(dot3(vt, vt) + m.eps2);
+    const float fr = m.mu * fn * rsqrt_approx(dot3(vt, vt) + m.eps2);
     const float3 fw = fn * nw - fr * vt;
     const float3 fbody = SG > 0 ? F(fw) : -F(fw);
     force = force + fbody;
@@ -189,7 +189,7 @@ __device__ __forceinline__ void sphere_env(const DevModel& m, float3 xw, float r
     }
     float h, hx, hy;
     ground(m, xw.x, xw.y, h, hx, hy);
-    float inv = rsqrtf(hx * hx + hy * hy + 1.f);
+    float inv = rsqrt_approx(hx * hx + hy * hy + 1.f);
     float3 n = f3(-hx * inv, -hy * inv, inv);
     const float pen = r - (xw.z - h) * n.z;
     // computed unconditionally and zeroed out of contact (no branch)
@@ -313,9 +313,30 @@ __device__ __forceinline__ void force_up_abd(float c, float s, float3 r, float3&
     f = ff;
 }
 
+// The leg-dependent constants of a lane, computed once per rollout (outside the
+// time loops): legs FR, FL, RR, RL -- front (+x) for legs 0, 1, left (+y) for odd
+// legs -- and the trunk sphere this lane carries (lanes past the last sphere
+// carry none).
+struct LegGeom {
+    float3 rh;   // abduction joint in the trunk frame
+    float ty;    // flexion joint (0, ty, 0) in the hip frame
+    float tx;    // this lane's trunk sphere on the trunk x axis
+    bool tsph;   // whether this lane carries a trunk sphere
+};
+
+__device__ __forceinline__ LegGeom leg_geom(const DevModel& m, int leg) {
+    const float fx = leg < 2 ? 1.f : -1.f, sy = (leg & 1) ? 1.f : -1.f;
+    LegGeom g;
+    g.rh = f3(fx * m.hip_x, sy * m.hip_y, m.hip_z);
+    g.ty = sy * m.thigh_y;
+    g.tsph = leg < m.n_tsph;
+    g.tx = leg == 0 ? m.tsph_x[0] : (leg == 1 ? m.tsph_x[1] : (leg == 2 ? m.tsph_x[2] : m.tsph_x[3]));
+    return g;
+}
+
 template <int TERR, bool BOX>
-__device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, LegState& S, const float kpu[3],
-                                        float h, float kdh, float hg, float arm, BoxState& Bx) {
+__device__ __forceinline__ void substep(const DevModel& m, int leg, const LegGeom& G, Trunk& T, LegState& S,
+                                        const float kpu[3], float h, float kdh, float hg, float arm, BoxState& Bx) {
     const float g = m.gz;
     float R0[3][3];
     quat_R(T.quat, R0);
@@ -333,10 +354,8 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
     sincos_r(S.q[0], s0, c0);
     sincos_r(S.q[1], s1, c1);
     sincos_r(S.q[2], s2, c2);
-    // legs FR, FL, RR, RL: front (+x) for legs 0, 1; left (+y) for odd legs
-    const float fx = leg < 2 ? 1.f : -1.f, sy = (leg & 1) ? 1.f : -1.f;
-    const float3 rh = f3(fx * m.hip_x, sy * m.hip_y, m.hip_z);   // abduction joint in the trunk
-    const float ty = sy * m.thigh_y;                               // flexion joint (0, ty, 0) in the hip
+    const float3 rh = G.rh;                                        // abduction joint in the trunk
+    const float ty = G.ty;                                         // flexion joint (0, ty, 0) in the hip
     const float kz = m.r_knee[2], fz = m.foot[2];                  // knee (0, 0, kz), foot (0, 0, fz)
     float3 wh = Ex(c0, s0, T.w);
     float3 vh = Ex(c0, s0, cross_acc(T.w, rh, T.v));
@@ -392,7 +411,7 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
         body_bias_acc(m.I_thigh, wt, vt, pa_n, pa_f);
 #pragma unroll
         for (int i = 0; i < 3; i++) { U1a[i] = IA.A[sidx(i, 1)]; U1l[i] = IA.B[1][i]; }
-        D1inv = __fdividef(1.f, U1a[1] + arm);
+        D1inv = rcp_approx(U1a[1] + arm);
         u1 = tau[1] - pa_n.y;
     }
     project<1>(IA, pa_n, pa_f, D1inv, u1, ct_w, ct_v);
@@ -403,7 +422,7 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
         body_bias_acc(m.I_hip, wh, vh, pa_n, pa_f);
 #pragma unroll
         for (int i = 0; i < 3; i++) { U0a[i] = IA.A[sidx(i, 0)]; U0l[i] = IA.B[0][i]; }
-        D0inv = __fdividef(1.f, U0a[0] + arm);
+        D0inv = rcp_approx(U0a[0] + arm);
         u0 = tau[0] - pa_n.x;
     }
     project<0>(IA, pa_n, pa_f, D0inv, u0, ch_w, ch_v);
@@ -414,8 +433,8 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
     // ---- contacts of the trunk spheres, one per lane (lanes past the last
     // sphere compute a zero wrench), minus into this lane's trunk bias
     {
-        const bool on = leg < m.n_tsph;
-        const float tx = leg == 0 ? m.tsph_x[0] : (leg == 1 ? m.tsph_x[1] : (leg == 2 ? m.tsph_x[2] : m.tsph_x[3]));
+        const bool on = G.tsph;
+        const float tx = G.tx;
         const float3 cb = f3(tx, 0.f, 0.f);
         const float3 xw = f3(fmaf(R0[0][0], tx, T.p[0]), fmaf(R0[1][0], tx, T.p[1]), fmaf(R0[2][0], tx, T.p[2]));
         const TrunkFrame toTrunk = {R0[0][0], R0[0][1], R0[0][2], R0[1][0], R0[1][1], R0[1][2],
@@ -477,7 +496,7 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
         ci[3] = C00 * C22 - C02 * C02;
         ci[4] = C01 * C02 - C00 * C12;
         ci[5] = C00 * C11 - C01 * C01;
-        const float idc = __fdividef(1.f, C00 * ci[0] + C01 * ci[1] + C02 * ci[2]);
+        const float idc = rcp_approx(C00 * ci[0] + C01 * ci[1] + C02 * ci[2]);
 #pragma unroll
         for (int i = 0; i < 6; i++) ci[i] *= idc;
         // W = B C^-1 (3x3)
@@ -501,7 +520,7 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, Trunk& T, Le
         si[3] = S[0] * S[5] - S[2] * S[2];
         si[4] = S[1] * S[2] - S[0] * S[4];
         si[5] = S[0] * S[3] - S[1] * S[1];
-        const float ids = __fdividef(1.f, S[0] * si[0] + S[1] * si[1] + S[2] * si[2]);
+        const float ids = rcp_approx(S[0] * si[0] + S[1] * si[1] + S[2] * si[2]);
         // [A B; B^T C] [x; y] = -[p; q]:  x = S^-1 (-p + W q),  y = C^-1 (-q - B^T x)
         float rx[3];
 #pragma unroll
@@ -664,6 +683,7 @@ __device__ __forceinline__ float rollout_lane(const DevModel& m, const DevCost& 
     }
     const float h = a.h;
     const float kdh = fmaf(m.kp, h, m.kd), hg = h * m.gz;
+    const LegGeom G = leg_geom(m, leg);
     const float ph0 = (leg == 1 || leg == 2) ? 3.14159265358979f : 0.f;
     float L = 0.f;
     if (float* tp = opaque_ptr(traj)) store_state<BOX>(tp, a.H, k, 0, leg, valid, T, S, Bx, a.nx);
@@ -692,7 +712,7 @@ __device__ __forceinline__ float rollout_lane(const DevModel& m, const DevCost& 
             if (leg == 0) L += trunk_state_cost<TERR>(m, c, T) + (BOX ? box_cost(c, Bx) : 0.f);
         }
         const float kpu[3] = {m.kp * u[0], m.kp * u[1], m.kp * u[2]};
-        for (int sb = 0; sb < a.n_sub; sb++) substep<TERR, BOX>(m, leg, T, S, kpu, h, kdh, hg, a.arm, Bx);
+        for (int sb = 0; sb < a.n_sub; sb++) substep<TERR, BOX>(m, leg, G, T, S, kpu, h, kdh, hg, a.arm, Bx);
         if (float* tp = opaque_ptr(traj)) store_state<BOX>(tp, a.H, k, t + 1, leg, valid, T, S, Bx, a.nx);
     }
     if (leg == 0) L += c.w_term * (trunk_state_cost<TERR>(m, c, T) + (BOX ? box_cost(c, Bx) : 0.f));
