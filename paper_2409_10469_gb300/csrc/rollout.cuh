@@ -709,7 +709,9 @@ __device__ __forceinline__ float rollout_lane(const DevModel& m, const DevCost& 
             }
             float e0 = u[0] - c.stand[0], e1 = u[1] - (c.stand[1] + ds), e2 = u[2] - (c.stand[2] + dk);
             L += c.w_u * (e0 * e0 + e1 * e1 + e2 * e2);
-            if (leg == 0) L += trunk_state_cost<TERR>(m, c, T) + (BOX ? box_cost(c, Bx) : 0.f);
+            // every lane evaluates the trunk terms (no divergent branch), lane 0 keeps them
+            const float Lt = trunk_state_cost<TERR>(m, c, T) + (BOX ? box_cost(c, Bx) : 0.f);
+            L += leg == 0 ? Lt : 0.f;
         }
         const float kpu[3] = {m.kp * u[0], m.kp * u[1], m.kp * u[2]};
         for (int sb = 0; sb < a.n_sub; sb++) substep<TERR, BOX>(m, leg, G, T, S, kpu, h, kdh, hg, a.arm, Bx);
