@@ -46,6 +46,7 @@ struct GemmArgs {
     long ldo;
     __nv_bfloat16* out_b;     // BF16 [M][ldob] (optional)
     long ldob;
+    int vec_a, vec_b;         // stage with 16-byte loads (K-contiguous rows, K and strides multiples of 8, aligned)
     int* err;                 // set when a wait runs out
     uint32_t wait_limit;      // mbarrier polls before giving up (0 = default)
     int withhold_commit;      // self-test: never signal completion, so the wait runs out
@@ -84,22 +85,44 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g) {
     const int nk = (g.K + tc::KCHUNK - 1) / tc::KCHUNK;
     for (int kc = 0; kc < nk; kc++) {
         const int k0 = kc * tc::KCHUNK;
-        // stage A (128 x 64) and B (NT x 64), zero outside the matrices
-        for (int idx = tid; idx < 128 * tc::KCHUNK; idx += 128) {
-            int r, k;
-            if (g.a_sk == 1) { r = idx >> 6; k = idx & 63; } else { k = idx >> 7; r = idx & 127; }
-            const int gm = m0 + r, gk = k0 + k;
-            __nv_bfloat16 v = __float2bfloat16(0.f);
-            if (gm < g.M && gk < g.K) v = g.A[(long)gm * g.a_sm + (long)gk * g.a_sk];
-            *reinterpret_cast<__nv_bfloat16*>(sA + tc::tile_offset(r, k)) = v;
+        // stage A (128 x 64) and B (NT x 64), zero outside the matrices: 8 k-elements
+        // (one 16-byte core-matrix row) per load when the rows are K-contiguous and
+        // aligned, element by element otherwise (the transposed operands of backprop)
+        if (g.vec_a) {
+            for (int idx = tid; idx < 128 * (tc::KCHUNK / 8); idx += 128) {
+                const int r = idx >> 3, k = (idx & 7) * 8;
+                const int gm = m0 + r, gk = k0 + k;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (gm < g.M && gk < g.K) v = __ldg(reinterpret_cast<const uint4*>(g.A + (long)gm * g.a_sm + gk));
+                *reinterpret_cast<uint4*>(sA + tc::tile_offset(r, k)) = v;
+            }
+        } else {
+            for (int idx = tid; idx < 128 * tc::KCHUNK; idx += 128) {
+                int r, k;
+                if (g.a_sk == 1) { r = idx >> 6; k = idx & 63; } else { k = idx >> 7; r = idx & 127; }
+                const int gm = m0 + r, gk = k0 + k;
+                __nv_bfloat16 v = __float2bfloat16(0.f);
+                if (gm < g.M && gk < g.K) v = g.A[(long)gm * g.a_sm + (long)gk * g.a_sk];
+                *reinterpret_cast<__nv_bfloat16*>(sA + tc::tile_offset(r, k)) = v;
+            }
         }
-        for (int idx = tid; idx < NT * tc::KCHUNK; idx += 128) {
-            int r, k;
-            if (g.b_sk == 1) { r = idx >> 6; k = idx & 63; } else { k = idx / NT; r = idx % NT; }
-            const int gn = n0 + r, gk = k0 + k;
-            __nv_bfloat16 v = __float2bfloat16(0.f);
-            if (gn < g.N && gk < g.K) v = g.B[(long)gn * g.b_sn + (long)gk * g.b_sk];
-            *reinterpret_cast<__nv_bfloat16*>(sB + tc::tile_offset(r, k)) = v;
+        if (g.vec_b) {
+            for (int idx = tid; idx < NT * (tc::KCHUNK / 8); idx += 128) {
+                const int r = idx >> 3, k = (idx & 7) * 8;
+                const int gn = n0 + r, gk = k0 + k;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (gn < g.N && gk < g.K) v = __ldg(reinterpret_cast<const uint4*>(g.B + (long)gn * g.b_sn + gk));
+                *reinterpret_cast<uint4*>(sB + tc::tile_offset(r, k)) = v;
+            }
+        } else {
+            for (int idx = tid; idx < NT * tc::KCHUNK; idx += 128) {
+                int r, k;
+                if (g.b_sk == 1) { r = idx >> 6; k = idx & 63; } else { k = idx / NT; r = idx % NT; }
+                const int gn = n0 + r, gk = k0 + k;
+                __nv_bfloat16 v = __float2bfloat16(0.f);
+                if (gn < g.N && gk < g.K) v = g.B[(long)gn * g.b_sn + (long)gk * g.b_sk];
+                *reinterpret_cast<__nv_bfloat16*>(sB + tc::tile_offset(r, k)) = v;
+            }
         }
         tc::fence_proxy_async();
         __syncthreads();
@@ -151,7 +174,16 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g) {
 
 static size_t gemm_smem(int nt) { return (size_t)(128 + nt) * tc::KCHUNK * 2; }
 
-static cudaError_t launch_gemm(const GemmArgs& g, cudaStream_t st) {
+// 16-byte staging applies when every row of an operand starts on a 16-byte
+// boundary and k runs along it, so every in-range 8-element group is whole
+static bool vec_ok(const __nv_bfloat16* p, long s_row, long s_k, int K) {
+    return s_k == 1 && K % 8 == 0 && s_row % 8 == 0 && (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
+}
+
+static cudaError_t launch_gemm(const GemmArgs& g0, cudaStream_t st) {
+    GemmArgs g = g0;
+    g.vec_a = vec_ok(g.A, g.a_sm, g.a_sk, g.K);
+    g.vec_b = vec_ok(g.B, g.b_sn, g.b_sk, g.K);
     const int nt = g.N <= 64 ? 64 : 256;
     dim3 grid((g.M + 127) / 128, (g.N + nt - 1) / nt);
     if (nt == 64) {
@@ -175,6 +207,72 @@ __global__ void k_to_bf16(const float* x, int B, int in, int ld, __nv_bfloat16* 
     if (i >= (long)B * ld) return;
     const int r = (int)(i / ld), c = (int)(i % ld);
     y[i] = __float2bfloat16(c < in ? x[(long)r * in + c] : 0.f);
+}
+
+// Small-batch forward on the CUDA cores (a control step's inference: a few
+// robots' features).  The tensor-core tile is 128 rows, so a batch of a few
+// samples would run a handful of mostly empty CTAs through four GEMM launches;
+// here one block of 256 threads carries SMB samples through all four layers
+// with the activations in shared memory: thread j computes output neuron j of
+// every sample from its BF16 weight row (16-byte loads; the weights stay in L2
+// across calls).  Rounding points as on the tensor-core path: BF16 inputs,
+// BF16 weights, FP32 accumulation, FP32 pre-activation + bias, BF16 of GELU
+// for the next layer; the last layer's FP32 output is the result.
+constexpr int SMB = 8;          // samples per block
+struct SmallFwdArgs {
+    const float* X;             // [B][62]
+    int B;
+    const __nv_bfloat16* W[4];  // [out][ld] BF16
+    const float* bias[4];       // [out]
+    float* Y;                   // [B][48]
+};
+
+__global__ void __launch_bounds__(256) k_mlp_small(SmallFwdArgs a) {
+    __shared__ float h[2][SMB][256];
+    const int j = threadIdx.x, b0 = blockIdx.x * SMB;
+    const int nb = min(SMB, a.B - b0);
+    for (int b = 0; b < SMB; b++) {
+        float v = 0.f;
+        if (b < nb && j < 62) v = __bfloat162float(__float2bfloat16(a.X[(long)(b0 + b) * 62 + j]));
+        h[0][b][j] = v;
+    }
+    __syncthreads();
+    int cur = 0;
+#pragma unroll
+    for (int l = 0; l < 4; l++) {
+        const int K = l == 0 ? 64 : 256, nout = l == 3 ? 48 : 256;
+        float acc[SMB];
+#pragma unroll
+        for (int b = 0; b < SMB; b++) acc[b] = 0.f;
+        if (j < nout) {
+            const uint4* wr = reinterpret_cast<const uint4*>(a.W[l] + (long)j * K);
+#pragma unroll 2
+            for (int k8 = 0; k8 < K / 8; k8++) {
+                const uint4 q = __ldg(wr + k8);
+                const __nv_bfloat162* w2 = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+                for (int t = 0; t < 4; t++) {
+                    const float2 w = __bfloat1622float2(w2[t]);
+                    const int k = 8 * k8 + 2 * t;
+#pragma unroll
+                    for (int b = 0; b < SMB; b++) {
+                        acc[b] = fmaf(w.x, h[cur][b][k], acc[b]);
+                        acc[b] = fmaf(w.y, h[cur][b][k + 1], acc[b]);
+                    }
+                }
+            }
+        }
+        if (l < 3) {
+            const float bj = a.bias[l][j];
+#pragma unroll
+            for (int b = 0; b < SMB; b++) h[cur ^ 1][b][j] = __bfloat162float(__float2bfloat16(gelu(acc[b] + bj)));
+        } else if (j < 48) {
+            const float bj = a.bias[l][j];
+            for (int b = 0; b < nb; b++) a.Y[(long)(b0 + b) * 48 + j] = acc[b] + bj;
+        }
+        cur ^= 1;
+        __syncthreads();
+    }
 }
 
 // mean-squared error over B x O: loss and dY = 2 (Y - T) / (B O), FP32 and BF16
@@ -231,6 +329,7 @@ namespace {
 
 constexpr int IN = 62, IN_PAD = 64, HID = 256, OUT = 48;
 constexpr int NL = 4;
+constexpr int SMALL_BATCH = 128;  // forward batches up to this size run on the CUDA cores
 const int LIN[NL] = {IN, HID, HID, HID};
 const int LOUT[NL] = {HID, HID, HID, OUT};
 const int LLD[NL] = {IN_PAD, HID, HID, HID};  // leading dimension of each layer's BF16 input / weight rows
@@ -441,6 +540,30 @@ static mppi_status check_err(mppi_mlp net, cudaStream_t st) {
 extern "C" mppi_status mppi_mlp_forward(mppi_mlp net, const float* X, int B, float* Y, void* stream) {
     if (!net || !X || !Y || B < 1 || B > net->max_batch) return MPPI_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
+    if (B <= SMALL_BATCH) {
+        // a few samples: the fused CUDA-core forward (one launch)
+        const float* dX = X;
+        if (!mdev(X)) {
+            MCK(cudaMemcpyAsync(net->d_X, X, (size_t)B * IN * 4, cudaMemcpyHostToDevice, st));
+            dX = net->d_X;
+        }
+        const bool dev = mdev(Y);
+        SmallFwdArgs a;
+        a.X = dX;
+        a.B = B;
+        for (int l = 0; l < NL; l++) {
+            a.W[l] = net->d_wb[l];
+            a.bias[l] = net->d_p + net->bofs[l];
+        }
+        a.Y = dev ? Y : net->d_z[NL - 1];
+        k_mlp_small<<<(B + SMB - 1) / SMB, 256, 0, st>>>(a);
+        MCK(cudaGetLastError());
+        if (!dev) {
+            MCK(cudaMemcpyAsync(Y, net->d_z[NL - 1], (size_t)B * OUT * 4, cudaMemcpyDeviceToHost, st));
+            MCK(cudaStreamSynchronize(st));
+        }
+        return MPPI_OK;
+    }
     mppi_status s = stage_x(net, X, B, st);
     if (s == MPPI_OK) s = forward_bf16(net, B, st);
     if (s != MPPI_OK) return s;
@@ -539,8 +662,15 @@ extern "C" mppi_status mppi_tc_gemm_bf16(const uint16_t* A, const uint16_t* B, f
                                          void* stream) {
     if (!A || !B || !D || M < 1 || N < 1 || N > 256 || K < 1) return MPPI_ERR_ARG;
     if (!mdev(A) || !mdev(B) || !mdev(D)) return MPPI_ERR_ARG;
-    int* err = nullptr;
-    if (cudaMalloc((void**)&err, 4) != cudaSuccess) return MPPI_ERR_OOM;
+    // the wait-timeout flag: one per device for the process, allocated on first use
+    static int* err_flag[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MPPI_ERR_CUDA;
+    if (!err_flag[dev] && cudaMalloc((void**)&err_flag[dev], 4) != cudaSuccess) {
+        err_flag[dev] = nullptr;
+        return MPPI_ERR_OOM;
+    }
+    int* err = err_flag[dev];
     cudaStream_t st = (cudaStream_t)stream;
     cudaMemsetAsync(err, 0, 4, st);
     GemmArgs g;
@@ -562,7 +692,6 @@ extern "C" mppi_status mppi_tc_gemm_bf16(const uint16_t* A, const uint16_t* B, f
     int h = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(err);
     if (e != cudaSuccess) return MPPI_ERR_CUDA;
     return h ? MPPI_ERR_TIMEOUT : MPPI_OK;
 }

@@ -44,11 +44,14 @@ def data(B, seed):
     return rng.normal(size=(B, 62)).astype(np.float32), (0.3 * rng.normal(size=(B, 48))).astype(np.float32)
 
 
-def test_forward_matches_oracle():
+@pytest.mark.parametrize("B", [1, 7, 64, 128, 129, 300])
+def test_forward_matches_oracle(B):
+    """batches up to 128 take the fused CUDA-core forward, larger ones the
+    tensor cores; both mirror the oracle's BF16 rounding points"""
     net = _mppi.MLP(512)
     p = M.init_params(5)
     net.set_params(p)
-    X, _ = data(300, 1)
+    X, _ = data(B, 1)
     Y = net.forward(X)
     Yo, _ = M.forward(p, X, mirror=True)
     err = np.max(np.abs(Y - Yo)) / max(1.0, np.max(np.abs(Yo)))
@@ -56,6 +59,10 @@ def test_forward_matches_oracle():
     # of a BF16 rounding boundary (a 2^-8 flip of one activation): 1e-3 bound
     assert err <= 1e-3, err
     assert np.array_equal(net.get_params(), p)
+    # device output buffers too
+    Yd = torch.empty((B, 48), device="cuda")
+    net.forward(torch.as_tensor(X).cuda(), out=Yd)
+    assert np.array_equal(Yd.cpu().numpy(), Y)
 
 
 def test_gradient_matches_oracle():
