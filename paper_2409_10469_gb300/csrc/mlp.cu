@@ -89,12 +89,20 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g) {
         // (one 16-byte core-matrix row) per load when the rows are K-contiguous and
         // aligned, element by element otherwise (the transposed operands of backprop)
         if (g.vec_a) {
-            for (int idx = tid; idx < 128 * (tc::KCHUNK / 8); idx += 128) {
-                const int r = idx >> 3, k = (idx & 7) * 8;
+            // all loads of the chunk in flight before the first store (one memory round trip)
+            constexpr int NA = 128 * (tc::KCHUNK / 8) / 128;
+            uint4 v[NA];
+#pragma unroll
+            for (int i = 0; i < NA; i++) {
+                const int idx = tid + 128 * i, r = idx >> 3, k = (idx & 7) * 8;
                 const int gm = m0 + r, gk = k0 + k;
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (gm < g.M && gk < g.K) v = __ldg(reinterpret_cast<const uint4*>(g.A + (long)gm * g.a_sm + gk));
-                *reinterpret_cast<uint4*>(sA + tc::tile_offset(r, k)) = v;
+                v[i] = make_uint4(0u, 0u, 0u, 0u);
+                if (gm < g.M && gk < g.K) v[i] = __ldg(reinterpret_cast<const uint4*>(g.A + (long)gm * g.a_sm + gk));
+            }
+#pragma unroll
+            for (int i = 0; i < NA; i++) {
+                const int idx = tid + 128 * i;
+                *reinterpret_cast<uint4*>(sA + tc::tile_offset(idx >> 3, (idx & 7) * 8)) = v[i];
             }
         } else {
             for (int idx = tid; idx < 128 * tc::KCHUNK; idx += 128) {
@@ -107,12 +115,19 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g) {
             }
         }
         if (g.vec_b) {
-            for (int idx = tid; idx < NT * (tc::KCHUNK / 8); idx += 128) {
-                const int r = idx >> 3, k = (idx & 7) * 8;
+            constexpr int NB = NT * (tc::KCHUNK / 8) / 128;
+            uint4 v[NB];
+#pragma unroll
+            for (int i = 0; i < NB; i++) {
+                const int idx = tid + 128 * i, r = idx >> 3, k = (idx & 7) * 8;
                 const int gn = n0 + r, gk = k0 + k;
-                uint4 v = make_uint4(0u, 0u, 0u, 0u);
-                if (gn < g.N && gk < g.K) v = __ldg(reinterpret_cast<const uint4*>(g.B + (long)gn * g.b_sn + gk));
-                *reinterpret_cast<uint4*>(sB + tc::tile_offset(r, k)) = v;
+                v[i] = make_uint4(0u, 0u, 0u, 0u);
+                if (gn < g.N && gk < g.K) v[i] = __ldg(reinterpret_cast<const uint4*>(g.B + (long)gn * g.b_sn + gk));
+            }
+#pragma unroll
+            for (int i = 0; i < NB; i++) {
+                const int idx = tid + 128 * i;
+                *reinterpret_cast<uint4*>(sB + tc::tile_offset(idx >> 3, (idx & 7) * 8)) = v[i];
             }
         } else {
             for (int idx = tid; idx < NT * tc::KCHUNK; idx += 128) {
@@ -149,14 +164,40 @@ __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g) {
     } else {
         // epilogue: warp w owns rows 32w .. 32w + 31 (TMEM lanes)
         const int m = m0 + warp * 32 + lane;
+        // 16-byte stores when a whole 16-column group is in range and the rows are aligned
+        const bool vec_o = (g.ldo % 4 == 0) && ((reinterpret_cast<uintptr_t>(g.out) & 15u) == 0) &&
+                           (!g.out_b || ((g.ldob % 8 == 0) && ((reinterpret_cast<uintptr_t>(g.out_b) & 15u) == 0)));
 #pragma unroll 1
         for (int c = 0; c < NT / 16; c++) {
             float v[16];
             tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 16), v);
-            if (m < g.M) {
+            if (m >= g.M) continue;
+            const int nb = n0 + c * 16;
+            if (vec_o && nb + 16 <= g.N) {
+                float d[16], e[16];
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
-                    const int n = n0 + c * 16 + j;
+                    d[j] = v[j];
+                    if (g.epi == EPI_BIAS || g.epi == EPI_BIAS_GELU) d[j] += __ldg(g.bias + nb + j);
+                    if (g.epi == EPI_GELU_BWD) d[j] *= gelu_grad(g.aux[(long)m * g.ldaux + nb + j]);
+                    e[j] = g.epi == EPI_BIAS_GELU ? gelu(d[j]) : d[j];
+                }
+                float4* o4 = reinterpret_cast<float4*>(g.out + (long)m * g.ldo + nb);
+#pragma unroll
+                for (int q = 0; q < 4; q++) o4[q] = make_float4(d[4 * q], d[4 * q + 1], d[4 * q + 2], d[4 * q + 3]);
+                if (g.out_b) {
+                    uint4 pk[2];
+                    __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(pk);
+#pragma unroll
+                    for (int q = 0; q < 8; q++) h2[q] = __floats2bfloat162_rn(e[2 * q], e[2 * q + 1]);
+                    uint4* ob = reinterpret_cast<uint4*>(g.out_b + (long)m * g.ldob + nb);
+                    ob[0] = pk[0];
+                    ob[1] = pk[1];
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; j++) {
+                    const int n = nb + j;
                     if (n >= g.N) break;
                     float d = v[j];
                     if (g.epi == EPI_BIAS || g.epi == EPI_BIAS_GELU) d += g.bias[n];
