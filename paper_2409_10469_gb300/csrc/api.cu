@@ -409,6 +409,18 @@ static RolloutArgs rollout_args(mppi_handle h, const float* x0, int per, const f
     a.Dp = h->D;
     a.interp = h->cfg.interp;
     a.Bt = reinterpret_cast<const float4*>(h->d_B);
+    a.sample = 0;  // the knots come from U (mppi_step turns in-kernel sampling on)
+    a.mu = a.mu_prop = nullptr;
+    a.K_all = h->cfg.K;
+    a.n_prop = h->cfg.n_prop;
+    memcpy(a.sigma, h->cfg.sigma, sizeof(a.sigma));
+    memcpy(a.q_lo, h->cfg.q_lo, sizeof(a.q_lo));
+    memcpy(a.q_hi, h->cfg.q_hi, sizeof(a.q_hi));
+    a.key0 = (uint32_t)h->cfg.seed;
+    a.key1 = (uint32_t)(h->cfg.seed >> 32);
+    a.step = 0;
+    a.inst = h->cfg.inst;
+    a.U_out = nullptr;
     return a;
 }
 
@@ -559,12 +571,22 @@ extern "C" mppi_status mppi_step(mppi_handle h, const float* x0, uint32_t step, 
         dx0 = h->d_x0;
     }
     const bool tm = h->timing != 0;
+    const bool knots = h->cfg.interp != MPPI_INTERP_DIRECT;
     if (tm) CK(cudaEventRecord(h->ev[0], h->stream));
-    mppi_status s = do_sample(h, step, h->has_prop ? h->d_mu_prop : nullptr, h->d_U);
+    mppi_status s = MPPI_OK;
+    // direct targets are sampled by K1; the knot forms sample inside the rollout kernel
+    if (!knots) s = do_sample(h, step, nullptr, h->d_U);
     if (s != MPPI_OK) return s;
     if (tm) CK(cudaEventRecord(h->ev[1], h->stream));
     const double t0 = (double)step * h->cfg.ctrl_steps * h->cfg.dt;
     RolloutArgs a = rollout_args(h, dx0, 0, h->d_U, h->cfg.K, t0, h->d_L, nullptr);
+    if (knots) {
+        a.sample = 1;
+        a.mu = h->d_mu;
+        a.mu_prop = h->has_prop ? h->d_mu_prop : nullptr;
+        a.step = step;
+        a.U_out = h->d_U;
+    }
     CK(launch_rollout(a, rollout_block(h), h->stream));
     h->launches++;
     if (tm) CK(cudaEventRecord(h->ev[2], h->stream));

@@ -32,6 +32,16 @@ struct RolloutArgs {
     const float4* Bt;      // [H] knot weights of each dt step (knot representations)
     float h, dt, inv_Hm1, t0;  // t0: gait time of step 0 (reduced modulo the gait period)
     float arm;             // implicit-PD armature h (kd + h kp) + a0
+    // in-kernel sampling (the control step, knot representations): each lane draws
+    // its leg's 12 knots exactly as k_sample would and writes them to U_out
+    int sample;
+    const float* mu;       // [48] nominal
+    const float* mu_prop;  // [48] proposal mean or null
+    int K_all, n_prop;     // the sample set's size and its proposal share
+    float sigma[D];
+    float q_lo[3], q_hi[3];
+    uint32_t key0, key1, step, inst;
+    float* U_out;          // [n][48]
 };
 
 struct UpdateArgs {

@@ -6,6 +6,7 @@
 // The per-lane arithmetic lives in rollout.cuh; this kernel maps 4 lanes to a
 // rollout (8 rollouts per warp) over the n samples of one controller.
 #include "kernels.h"
+#include "noise.cuh"
 #include "rollout.cuh"
 
 namespace mppi {
@@ -20,7 +21,27 @@ __global__ void __launch_bounds__(256, 1) k_rollout(RolloutArgs a) {
     const float* x0 = a.x0 + (a.x0_per_sample ? (size_t)kk * nx : 0);
     float Uk[NKNOT][3];
     const float* Urow = a.U + (size_t)kk * a.Dp;
-    if (!DIRECT) {
+    if (!DIRECT && a.sample) {
+        // Alg. 1's sampling step for this lane's knots, element for element the
+        // formula of k_sample (Philox counter (d / 4, k, step, inst), Box-Muller,
+        // fmaf perturbation, clamp), so the knots are bit-identical to it
+        const int kp0 = a.K_all - (a.mu_prop ? a.n_prop : 0);
+        const bool prop = a.mu_prop && kk >= kp0;
+        const float* ctr = prop ? a.mu_prop : a.mu;
+        const bool nominal = (kk == 0) || (prop && kk == kp0);
+#pragma unroll
+        for (int j = 0; j < NKNOT; j++)
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                const int d = j * NJ + 3 * leg + i;
+                const float eps = nominal ? 0.f : normal_at(a.key0, a.key1, a.step, a.inst, (uint32_t)kk, d);
+                float c = __ldg(ctr + d);
+                if (prop && !(fabsf(c) <= 3.402823466e38f)) c = __ldg(a.mu + d);  // non-finite proposal: plain mean
+                const float v = fminf(fmaxf(__fmaf_rn(a.sigma[d], eps, c), a.q_lo[i]), a.q_hi[i]);
+                Uk[j][i] = v;
+                if (valid) a.U_out[(size_t)kk * D + d] = v;
+            }
+    } else if (!DIRECT) {
 #pragma unroll
         for (int j = 0; j < NKNOT; j++)
 #pragma unroll

@@ -330,7 +330,7 @@ def test_full_step_matches_components():
     _, mu_same, _ = O.update(Lg, U_o, m["lam"])
     assert np.abs(mu - mu_same).max() <= 1e-6 * 4
     assert np.array_equal(u0, mu[:12])
-    assert ctl.launch_count() == 3
+    assert ctl.launch_count() == 2   # rollout (sampling inside) + update
 
 
 def test_edge_cases():
