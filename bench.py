@@ -37,7 +37,7 @@ METRIC = "rollout-steps/s (MPPI step, K=4096, H=100)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture) of
 # one k_rollout launch on this workload, valid only for the kernel sources whose
 # SHA-256 prefix is given; reported as null once those sources change.
-ROLLOUT_TRAFFIC = {"bytes": 815872, "sources_sha256": "9bdaf7764bc5cd53"}
+ROLLOUT_TRAFFIC = {"bytes": 90112, "sources_sha256": "25b5ec66405fb251"}
 ROLLOUT_SOURCES = ("rollout.cu", "rollout.cuh", "common.cuh")
 
 

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_tiled(UpdateArgs a) {
 }
 
 int update_grid(int n) {
-    int g = (n + 63) / 64;  // ~64 samples per CTA
+    int g = (n + 127) / 128;  // ~128 samples per CTA (measured: 64 per CTA costs 3 us more at n = 4096)
     return g < 1 ? 1 : (g > UPDATE_MAX_CTAS ? UPDATE_MAX_CTAS : g);
 }
 
