@@ -299,10 +299,12 @@ mppi_status mppi_mlp_forward(mppi_mlp net, const float* X, int B, float* Y, void
  * update) optional.  TIMEOUT if a tensor-core wait ran out. */
 mppi_status mppi_mlp_train_step(mppi_mlp net, const float* X, const float* T, int B, float lr,
                                 float weight_decay, float* loss_out, float* grad_out, void* stream);
-/* Failure-detection self-test: runs the tensor-core GEMM with its completion
- * signal withheld, so every thread's bounded wait runs out; the kernel records
- * the timeout, releases its tensor memory and returns.  Expected result:
- * MPPI_ERR_TIMEOUT, with the CUDA context still usable afterwards. */
+/* Failure-detection self-test: runs both tensor-core GEMM kernels (the
+ * thread-staged one and the TMA-fed pipeline) with their completion signals
+ * withheld, so their bounded waits run out; each kernel records the timeout,
+ * lets its copies in flight land, releases its tensor memory and returns.
+ * Expected result: MPPI_ERR_TIMEOUT (both timed out), with the CUDA context
+ * still usable afterwards. */
 mppi_status mppi_selftest_wait_timeout(void* stream);
 
 /* The network's input for n states X (float[n][nx], host or device) of this
@@ -319,7 +321,10 @@ mppi_status mppi_features(mppi_handle h, const float* X, int n, uint32_t step, f
 mppi_status mppi_set_proposal(mppi_handle h, const float* mu_prop);
 /* D[M][N] = A[M][K] B[N][K]^T with BF16 inputs (raw uint16 bits) and FP32
  * accumulation on the tcgen05 tensor cores -- the network's GEMM; device
- * buffers, N <= 256. */
+ * buffers, N <= 256, row-major with K contiguous.  K a multiple of 8, N a
+ * multiple of 4 and 16-byte aligned buffers take the TMA-fed pipelined kernel,
+ * other shapes the thread-staged one.  Synchronous: returns once D is written
+ * (TIMEOUT if a tensor-core wait ran out). */
 mppi_status mppi_tc_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D, int M, int N, int K,
                               void* stream);
 

@@ -9,28 +9,33 @@
 // half of the samples; plain MPPI's samples stay in every step.
 //
 // Every layer is one GEMM D = A B^T (A: M x K activations, B: N x K weights,
-// both BF16, K-major in shared memory) on tcgen05 with a fused epilogue; the
-// backward pass uses the same kernel with transposed staging (dW = dZ^T H,
-// dH = dZ W).  One CTA of 4 warps owns a 128-row x NT-column output tile in
-// TMEM; operands are staged by the CTA's threads 64 k-elements at a time into
-// the core-matrix layout of tc.cuh; one thread issues the MMAs and commits them
-// to an mbarrier that every thread waits on (bounded).
+// both BF16, K-major) on tcgen05 with a fused epilogue.  The TMA-fed pipelined
+// kernel of gemm.cu runs the forward layers and the whole backward pass: the
+// epilogues also write transposed BF16 copies (activations H^T, gradients dZ^T)
+// and the weights keep a transposed BF16 copy W^T, so every backward product
+// reads K-major operands too: dH = dZ (W^T)^T, and dW = dZ^T (H^T)^T with K =
+// the batch, cut into ranges whose partial sums are added in a fixed order.
+// The thread-staged kernel below (k_gemm_tc: one 128 x NT tile per CTA,
+// operands staged by the CTA's threads into the core-matrix layout of tc.cuh,
+// one thread issuing the MMAs) remains for operands TMA cannot describe (rows
+// not 16-byte aligned) through the raw GEMM entry point, and for the
+// wait-timeout self-test.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
 #include "../../include/mppi.h"
+#include "gemm.h"
 #include "tc.cuh"
 
 using namespace mppi;
 
 namespace mppi {
-
-enum Epi { EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_GELU = 2, EPI_GELU_BWD = 3 };
 
 struct GemmArgs {
     const __nv_bfloat16* A;
@@ -51,12 +56,6 @@ struct GemmArgs {
     uint32_t wait_limit;      // mbarrier polls before giving up (0 = default)
     int withhold_commit;      // self-test: never signal completion, so the wait runs out
 };
-
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
-// d/dz of z Phi(z) = Phi(z) + z phi(z)
-__device__ __forceinline__ float gelu_grad(float z) {
-    return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
-}
 
 template <int NT>
 __global__ void __launch_bounds__(128) k_gemm_tc(GemmArgs g) {
@@ -242,12 +241,15 @@ static cudaError_t launch_gemm(const GemmArgs& g0, cudaStream_t st) {
 
 // ---------------------------------------------------------------- elementwise kernels
 
-// FP32 [B][in] -> BF16 [B][ld] (zero padding past `in`)
-__global__ void k_to_bf16(const float* x, int B, int in, int ld, __nv_bfloat16* y) {
+// FP32 [B][in] -> BF16 [B][ld] (zero padding past `in`), and optionally its
+// transpose yt[c][r] (row stride ldt)
+__global__ void k_to_bf16(const float* x, int B, int in, int ld, __nv_bfloat16* y, __nv_bfloat16* yt, long ldt) {
     const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= (long)B * ld) return;
     const int r = (int)(i / ld), c = (int)(i % ld);
-    y[i] = __float2bfloat16(c < in ? x[(long)r * in + c] : 0.f);
+    const __nv_bfloat16 v = __float2bfloat16(c < in ? x[(long)r * in + c] : 0.f);
+    if (y) y[i] = v;
+    if (yt) yt[(long)c * ldt + r] = v;
 }
 
 // Small-batch forward on the CUDA cores (a control step's inference: a few
@@ -317,34 +319,93 @@ __global__ void __launch_bounds__(256) k_mlp_small(SmallFwdArgs a) {
 }
 
 // mean-squared error over B x O: loss and dY = 2 (Y - T) / (B O), FP32 and BF16
-__global__ void k_mse(const float* Y, const float* T, int n, float scale, float* dY, __nv_bfloat16* dYb,
-                      float* loss) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// [B][O], and the BF16 gradient transposed (dYt [O][ldt]).  One block of 256
+// threads per MSE_ROWS samples: coalesced row-major reads and writes, the
+// transposed copy through a shared tile (32 consecutive samples per row
+// segment), the loss summed in the block and added once.
+constexpr int MSE_ROWS = 32, MSE_MAXO = 64;
+__global__ void __launch_bounds__(256) k_mse(const float* Y, const float* T, int B, int O, float scale, float* dY,
+                                             __nv_bfloat16* dYb, __nv_bfloat16* dYt, long ldt, float* loss) {
+    __shared__ __nv_bfloat16 tile[MSE_MAXO][MSE_ROWS + 2];
+    __shared__ float red[8];
+    const int b0 = blockIdx.x * MSE_ROWS, nb = min(MSE_ROWS, B - b0);
     float e = 0.f;
-    if (i < n) {
+    for (int k = threadIdx.x; k < nb * O; k += blockDim.x) {
+        const long i = (long)b0 * O + k;
         const float d = Y[i] - T[i];
         dY[i] = 2.f * d * scale;
-        dYb[i] = __float2bfloat16(2.f * d * scale);
-        e = d * d * scale;
+        const __nv_bfloat16 h = __float2bfloat16(2.f * d * scale);
+        dYb[i] = h;
+        tile[k % O][k / O] = h;
+        e += d * d * scale;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-    if ((threadIdx.x & 31) == 0 && loss) atomicAdd(loss, e);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (dYt)
+        for (int k = threadIdx.x; k < O * MSE_ROWS; k += blockDim.x) {
+            const int o = k / MSE_ROWS, r = k % MSE_ROWS;
+            if (r < nb) dYt[(long)o * ldt + b0 + r] = tile[o][r];
+        }
+    if (threadIdx.x == 0 && loss) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += red[w];
+        atomicAdd(loss, t);
+    }
 }
 
-// column sums of dZ [B][N] (bias gradients), one thread per column, fixed order
-__global__ void k_colsum(const float* dZ, int B, int N, long ld, float* db) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+// bias gradients: column sums of dZ [B][N] (row stride ld) in two fixed-order
+// passes.  Pass 1: block (x, r) sums rows [r rows, (r + 1) rows) of columns
+// 32 x .. 32 x + 31, warp w taking rows w, w + 8, ... (one coalesced 128-byte
+// row segment per load), then the 8 warp sums in order -> part[r][n].
+constexpr int COLSUM_SPLIT = 64;  // row ranges of pass 1 at most
+__global__ void __launch_bounds__(256) k_colsum_part(const float* dZ, int B, int N, long ld, int rows, float* part) {
+    __shared__ float s[8][33];
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int n = blockIdx.x * 32 + lane, r = blockIdx.y;
+    const int b0 = r * rows, b1 = min(B, b0 + rows);
+    float acc = 0.f;
+    if (n < N) {
+#pragma unroll 4
+        for (int b = b0 + w; b < b1; b += 8) acc += dZ[(long)b * ld + n];
+    }
+    s[w][lane] = acc;
+    __syncthreads();
+    if (w == 0 && n < N) {
+        float t = 0.f;
+#pragma unroll
+        for (int i = 0; i < 8; i++) t += s[i][lane];
+        part[(long)r * N + n] = t;
+    }
+}
+// Gradient finish of one layer, one thread per output:
+//   i < M N:          dW[m][n] = sum over K ranges sp of part[sp][m][n], in order;
+//   M N <= i < M N + M: db[m]  = sum over row ranges r of cpart[r][m], in order
+// (the column-sum pass 2).
+__global__ void k_grad_finish(const float* part, int nsplit, long sstride, int M, int N, long ldp, float* dw, long ldw,
+                              const float* cpart, int R, float* db) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float s = 0.f;
-    for (int b = 0; b < B; b++) s += dZ[(long)b * ld + n];
-    db[n] = s;
+    if (i < M * N) {
+        const int m = i / N, n = i % N;
+        const float* p = part + (long)m * ldp + n;
+#pragma unroll 8
+        for (int sp = 0; sp < nsplit; sp++) s += p[sp * sstride];
+        dw[(long)m * ldw + n] = s;
+    } else if (i < M * N + M) {
+        const int m = i - M * N;
+#pragma unroll 8
+        for (int r = 0; r < R; r++) s += cpart[(long)r * M + m];
+        db[m] = s;
+    }
 }
 
-// AdamW on FP32 master parameters, refreshing the BF16 weight copies
+// AdamW on FP32 master parameters, refreshing the BF16 weight copies (W and W^T)
 __global__ void k_adamw(float* p, const float* g, float* m1, float* m2, long n, float lr, float b1, float b2,
                         float eps, float wd, float c1, float c2, const long* wofs, const long* wlen,
-                        __nv_bfloat16* const* wb, int nw, const int* wcols, const int* wld) {
+                        __nv_bfloat16* const* wb, __nv_bfloat16* const* wbt, int nw, const int* wcols,
+                        const int* wld) {
     const long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float gi = g[i];
@@ -358,7 +419,9 @@ __global__ void k_adamw(float* p, const float* g, float* m1, float* m2, long n, 
         if (i >= wofs[w] && i < wofs[w] + wlen[w]) {
             const long j = i - wofs[w];
             const int r = (int)(j / wcols[w]), c = (int)(j % wcols[w]);
-            wb[w][(long)r * wld[w] + c] = __float2bfloat16(pi);
+            const __nv_bfloat16 b = __float2bfloat16(pi);
+            wb[w][(long)r * wld[w] + c] = b;
+            if (wbt[w]) wbt[w][(long)c * (wlen[w] / wcols[w]) + r] = b;  // W^T [in][out]
         }
 }
 
@@ -371,6 +434,7 @@ namespace {
 constexpr int IN = 62, IN_PAD = 64, HID = 256, OUT = 48;
 constexpr int NL = 4;
 constexpr int SMALL_BATCH = 128;  // forward batches up to this size run on the CUDA cores
+constexpr int MAX_SPLIT = 64;     // K ranges of a weight-gradient product (partial sums buffered)
 const int LIN[NL] = {IN, HID, HID, HID};
 const int LOUT[NL] = {HID, HID, HID, OUT};
 const int LLD[NL] = {IN_PAD, HID, HID, HID};  // leading dimension of each layer's BF16 input / weight rows
@@ -394,6 +458,14 @@ struct mppi_mlp_s {
     long *d_wofs = nullptr, *d_wlen = nullptr;
     int *d_wcols = nullptr, *d_wld = nullptr;
     __nv_bfloat16** d_wbp = nullptr;
+    // K-major operands of the backward pass (ldt = batch capacity rounded up to 8)
+    long ldt = 0;
+    __nv_bfloat16* d_wbt[NL] = {nullptr};     // W^T [in][out] BF16 (layers 1..NL-1)
+    __nv_bfloat16* d_ht[NL] = {nullptr};      // H^T of each layer's input [in padded][ldt]
+    __nv_bfloat16* d_dzt[2] = {nullptr};      // dZ^T [256][ldt], two buffers
+    float* d_part = nullptr;                  // split-K partial sums [MAX_SPLIT][256][256]
+    float* d_cpart = nullptr;                 // bias-gradient partial column sums [COLSUM_SPLIT][256]
+    __nv_bfloat16** d_wbtp = nullptr;
     int step = 0;
     std::string err;
 };
@@ -450,7 +522,17 @@ extern "C" mppi_status mppi_mlp_create(int max_batch, mppi_mlp* out) {
          cudaMalloc((void**)&net->d_loss, 4) == cudaSuccess && cudaMalloc((void**)&net->d_err, 4) == cudaSuccess &&
          cudaMalloc((void**)&net->d_wofs, NL * 8) == cudaSuccess && cudaMalloc((void**)&net->d_wlen, NL * 8) == cudaSuccess &&
          cudaMalloc((void**)&net->d_wcols, NL * 4) == cudaSuccess && cudaMalloc((void**)&net->d_wld, NL * 4) == cudaSuccess &&
-         cudaMalloc((void**)&net->d_wbp, NL * sizeof(void*)) == cudaSuccess;
+         cudaMalloc((void**)&net->d_wbp, NL * sizeof(void*)) == cudaSuccess &&
+         cudaMalloc((void**)&net->d_wbtp, NL * sizeof(void*)) == cudaSuccess &&
+         cudaMalloc((void**)&net->d_part, (size_t)MAX_SPLIT * HID * HID * 4) == cudaSuccess &&
+         cudaMalloc((void**)&net->d_cpart, (size_t)COLSUM_SPLIT * HID * 4) == cudaSuccess;
+    net->ldt = (B + 7) / 8 * 8;
+    for (int l = 0; ok && l < NL; l++) {
+        if (l >= 1)
+            ok = cudaMalloc((void**)&net->d_wbt[l], (size_t)LIN[l] * LOUT[l] * 2) == cudaSuccess;
+        ok = ok && cudaMalloc((void**)&net->d_ht[l], (size_t)LLD[l] * net->ldt * 2) == cudaSuccess;
+    }
+    for (int i = 0; ok && i < 2; i++) ok = cudaMalloc((void**)&net->d_dzt[i], (size_t)HID * net->ldt * 2) == cudaSuccess;
     if (ok) {
         long wo[NL], wl[NL];
         int wc[NL], wd[NL];
@@ -465,6 +547,7 @@ extern "C" mppi_status mppi_mlp_create(int max_batch, mppi_mlp* out) {
              cudaMemcpy(net->d_wcols, wc, sizeof(wc), cudaMemcpyHostToDevice) == cudaSuccess &&
              cudaMemcpy(net->d_wld, wd, sizeof(wd), cudaMemcpyHostToDevice) == cudaSuccess &&
              cudaMemcpy(net->d_wbp, net->d_wb, sizeof(net->d_wb), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(net->d_wbtp, net->d_wbt, sizeof(net->d_wbt), cudaMemcpyHostToDevice) == cudaSuccess &&
              cudaMemset(net->d_m1, 0, o * 4) == cudaSuccess && cudaMemset(net->d_m2, 0, o * 4) == cudaSuccess &&
              cudaMemset(net->d_p, 0, o * 4) == cudaSuccess && cudaMemset(net->d_err, 0, 4) == cudaSuccess;
     }
@@ -482,10 +565,13 @@ extern "C" mppi_status mppi_mlp_destroy(mppi_mlp net) {
     cudaDeviceSynchronize();
     std::vector<void*> ps = {net->d_p, net->d_g, net->d_m1, net->d_m2, net->d_dz, net->d_dzb, net->d_dhb, net->d_dh,
                              net->d_T, net->d_X, net->d_loss, net->d_err, net->d_wofs, net->d_wlen, net->d_wcols,
-                             net->d_wld, net->d_wbp};
+                             net->d_wld, net->d_wbp, net->d_wbtp, net->d_part, net->d_cpart, net->d_dzt[0],
+                             net->d_dzt[1]};
     for (int l = 0; l < NL; l++) {
         ps.push_back(net->d_wb[l]);
         ps.push_back(net->d_z[l]);
+        ps.push_back(net->d_wbt[l]);
+        ps.push_back(net->d_ht[l]);
     }
     for (int l = 0; l <= NL; l++) ps.push_back(net->d_hb[l]);
     for (void* p : ps)
@@ -503,7 +589,8 @@ static mppi_status refresh_bf16(mppi_mlp net, cudaStream_t st) {
     for (int l = 0; l < NL; l++) {
         const int rows = LOUT[l], cols = LIN[l], ld = LLD[l];
         // weights [rows][cols] FP32 -> [rows][ld] BF16 with zero padding
-        k_to_bf16<<<(rows * ld + 255) / 256, 256, 0, st>>>(net->d_p + net->wofs[l], rows, cols, ld, net->d_wb[l]);
+        k_to_bf16<<<(rows * ld + 255) / 256, 256, 0, st>>>(net->d_p + net->wofs[l], rows, cols, ld, net->d_wb[l],
+                                                           net->d_wbt[l], rows);
         MCK(cudaGetLastError());
     }
     return MPPI_OK;
@@ -532,40 +619,62 @@ extern "C" mppi_status mppi_mlp_get_params(mppi_mlp net, float* params, void* st
     return MPPI_OK;
 }
 
-// forward pass of B rows already converted to BF16 in d_hb[0]; outputs d_z[NL-1] (FP32)
-static mppi_status forward_bf16(mppi_mlp net, int B, cudaStream_t st) {
+// one TMA-fed GEMM: A = a [M][K] (row stride lda), B = b [N][K] (row stride ldb)
+static mppi_status tma_gemm(mppi_mlp net, TmaGemm& g, const __nv_bfloat16* a, long lda, const __nv_bfloat16* b,
+                            long ldb, cudaStream_t st) {
+    g.a = a;
+    g.lda = lda;
+    g.b = b;
+    g.ldb = ldb;
+    g.err = net->d_err;
+    if (!gemm_tma_ok(g)) return mfail(net, MPPI_ERR_CUDA, "tensor-core GEMM operands break a TMA layout rule");
+    MCK(launch_gemm_tma(g, st));
+    return MPPI_OK;
+}
+
+static TmaGemm gemm_args(int M, int N, int K, int epi) {
+    TmaGemm g;
+    memset(&g, 0, sizeof(g));
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.nsplit = 1;
+    g.epi = epi;
+    return g;
+}
+
+// forward pass of B rows already converted to BF16 in d_hb[0]; outputs d_z[NL-1]
+// (FP32); with `train` the hidden activations are also written transposed (H^T)
+// for the weight gradients
+static mppi_status forward_bf16(mppi_mlp net, int B, cudaStream_t st, bool train = false) {
     for (int l = 0; l < NL; l++) {
-        GemmArgs g;
-        memset(&g, 0, sizeof(g));
         const int ldi = (l == 0) ? IN_PAD : HID;
-        g.A = net->d_hb[l];
-        g.a_sm = ldi;
-        g.a_sk = 1;
-        g.B = net->d_wb[l];
-        g.b_sn = LLD[l];
-        g.b_sk = 1;
-        g.M = B;
-        g.N = LOUT[l];
-        g.K = LLD[l];
-        g.epi = (l < NL - 1) ? EPI_BIAS_GELU : EPI_BIAS;
+        TmaGemm g = gemm_args(B, LOUT[l], LLD[l], (l < NL - 1) ? EPI_BIAS_GELU : EPI_BIAS);
         g.bias = net->d_p + net->bofs[l];
         g.out = net->d_z[l];
         g.ldo = LOUT[l];
-        g.out_b = (l < NL - 1) ? net->d_hb[l + 1] : nullptr;
-        g.ldob = HID;
-        g.err = net->d_err;
-        MCK(launch_gemm(g, st));
+        if (l < NL - 1) {
+            g.out_b = net->d_hb[l + 1];
+            g.ldob = HID;
+            if (train) {
+                g.out_t = net->d_ht[l + 1];
+                g.ldt = net->ldt;
+            }
+        }
+        mppi_status s = tma_gemm(net, g, net->d_hb[l], ldi, net->d_wb[l], LLD[l], st);
+        if (s != MPPI_OK) return s;
     }
     return MPPI_OK;
 }
 
-static mppi_status stage_x(mppi_mlp net, const float* X, int B, cudaStream_t st) {
+static mppi_status stage_x(mppi_mlp net, const float* X, int B, cudaStream_t st, bool train = false) {
     const float* dX = X;
     if (!mdev(X)) {
         MCK(cudaMemcpyAsync(net->d_X, X, (size_t)B * IN * 4, cudaMemcpyHostToDevice, st));
         dX = net->d_X;
     }
-    k_to_bf16<<<(B * IN_PAD + 255) / 256, 256, 0, st>>>(dX, B, IN, IN_PAD, net->d_hb[0]);
+    k_to_bf16<<<(B * IN_PAD + 255) / 256, 256, 0, st>>>(dX, B, IN, IN_PAD, net->d_hb[0], train ? net->d_ht[0] : nullptr,
+                                                         net->ldt);
     MCK(cudaGetLastError());
     return MPPI_OK;
 }
@@ -619,8 +728,8 @@ extern "C" mppi_status mppi_mlp_train_step(mppi_mlp net, const float* X, const f
                                            float weight_decay, float* loss_out, float* grad_out, void* stream) {
     if (!net || !X || !T || B < 1 || B > net->max_batch) return MPPI_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    mppi_status s = stage_x(net, X, B, st);
-    if (s == MPPI_OK) s = forward_bf16(net, B, st);
+    mppi_status s = stage_x(net, X, B, st, true);
+    if (s == MPPI_OK) s = forward_bf16(net, B, st, true);
     if (s != MPPI_OK) return s;
     const float* dT = T;
     if (!mdev(T)) {
@@ -629,54 +738,47 @@ extern "C" mppi_status mppi_mlp_train_step(mppi_mlp net, const float* X, const f
     }
     MCK(cudaMemsetAsync(net->d_loss, 0, 4, st));
     const int n = B * OUT;
-    k_mse<<<(n + 255) / 256, 256, 0, st>>>(net->d_z[NL - 1], dT, n, 1.f / (float)n, net->d_dz, net->d_dzb, net->d_loss);
+    int zt = 0;  // which dZ^T buffer holds the current layer's gradient
+    static_assert(OUT <= MSE_MAXO, "output width of the loss tile");
+    k_mse<<<(B + MSE_ROWS - 1) / MSE_ROWS, 256, 0, st>>>(net->d_z[NL - 1], dT, B, OUT, 1.f / (float)n, net->d_dz,
+                                                          net->d_dzb, net->d_dzt[zt], net->ldt, net->d_loss);
     MCK(cudaGetLastError());
-    // backward, layer NL-1 .. 0: dZ (FP32 in d_dz, BF16 in d_dzb, [B][out])
+    // backward, layer NL-1 .. 0: dZ (FP32 d_dz and BF16 d_dzb [B][out], BF16 d_dzt[zt] [out][ldt])
     for (int l = NL - 1; l >= 0; l--) {
-        const int out = LOUT[l], in = LIN[l], ldi = (l == 0) ? IN_PAD : HID;
-        // dW[o][i] = sum_b dZ[b][o] H[b][i]: A[o][b] = dZ (stride out along b), B[i][b] = H (stride ldi)
-        GemmArgs g;
-        memset(&g, 0, sizeof(g));
-        g.A = net->d_dzb;
-        g.a_sm = 1;
-        g.a_sk = out;
-        g.B = net->d_hb[l];
-        g.b_sn = 1;
-        g.b_sk = ldi;
-        g.M = out;
-        g.N = in;
-        g.K = B;
-        g.epi = EPI_STORE;
-        g.out = net->d_g + net->wofs[l];
-        g.ldo = in;
-        g.err = net->d_err;
-        MCK(launch_gemm(g, st));
-        k_colsum<<<(out + 127) / 128, 128, 0, st>>>(net->d_dz, B, out, out, net->d_g + net->bofs[l]);
+        const int out = LOUT[l], in = LIN[l];
+        // dW[o][i] = sum_b dZ^T[o][b] H^T[i][b]: K = the batch, cut into ranges
+        TmaGemm g = gemm_args(out, in, B, EPI_STORE);
+        g.nsplit = gemm_tma_split(out, B, MAX_SPLIT);
+        const int ldp = (in + 63) / 64 * 64;
+        g.out = net->d_part;
+        g.ldo = ldp;
+        g.split_stride = (long)out * ldp;
+        s = tma_gemm(net, g, net->d_dzt[zt], net->ldt, net->d_ht[l], net->ldt, st);
+        if (s != MPPI_OK) return s;
+        // bias gradient pass 1, then both sums of this layer in one launch
+        const int R = std::min((B + 63) / 64, COLSUM_SPLIT), rows = (B + R - 1) / R;
+        k_colsum_part<<<dim3((out + 31) / 32, R), dim3(32, 8), 0, st>>>(net->d_dz, B, out, out, rows, net->d_cpart);
+        MCK(cudaGetLastError());
+        k_grad_finish<<<(out * in + out + 255) / 256, 256, 0, st>>>(net->d_part, g.nsplit, g.split_stride, out, in, ldp,
+                                                                   net->d_g + net->wofs[l], in, net->d_cpart, R,
+                                                                   net->d_g + net->bofs[l]);
         MCK(cudaGetLastError());
         if (l == 0) break;
-        // dH[b][i] = sum_o dZ[b][o] W[o][i], then dZ_prev = dH * gelu'(Z_prev)
-        GemmArgs h;
-        memset(&h, 0, sizeof(h));
-        h.A = net->d_dzb;
-        h.a_sm = out;
-        h.a_sk = 1;
-        h.B = net->d_wb[l];
-        h.b_sn = 1;
-        h.b_sk = LLD[l];
-        h.M = B;
-        h.N = in;
-        h.K = out;
-        h.epi = EPI_GELU_BWD;
+        // dH[b][i] = sum_o dZ[b][o] W^T[i][o], then dZ_prev = dH * gelu'(Z_prev)
+        TmaGemm h = gemm_args(B, in, out, EPI_GELU_BWD);
         h.aux = net->d_z[l - 1];
         h.ldaux = HID;
         h.out = net->d_dh;
         h.ldo = HID;
         h.out_b = net->d_dhb;
         h.ldob = HID;
-        h.err = net->d_err;
-        MCK(launch_gemm(h, st));
+        h.out_t = net->d_dzt[zt ^ 1];
+        h.ldt = net->ldt;
+        s = tma_gemm(net, h, net->d_dzb, out, net->d_wbt[l], out, st);
+        if (s != MPPI_OK) return s;
         std::swap(net->d_dz, net->d_dh);
         std::swap(net->d_dzb, net->d_dhb);
+        zt ^= 1;
     }
     if (grad_out) {
         const bool dev = mdev(grad_out);
@@ -688,7 +790,8 @@ extern "C" mppi_status mppi_mlp_train_step(mppi_mlp net, const float* X, const f
         const float c1 = 1.f - powf(b1, (float)net->step), c2 = 1.f - powf(b2, (float)net->step);
         k_adamw<<<(int)((net->nparam + 255) / 256), 256, 0, st>>>(net->d_p, net->d_g, net->d_m1, net->d_m2, net->nparam,
                                                                   lr, b1, b2, 1e-8f, weight_decay, c1, c2, net->d_wofs,
-                                                                  net->d_wlen, net->d_wbp, NL, net->d_wcols, net->d_wld);
+                                                                  net->d_wlen, net->d_wbp, net->d_wbtp, NL, net->d_wcols,
+                                                                  net->d_wld);
         MCK(cudaGetLastError());
     }
     if (loss_out) {
@@ -714,6 +817,29 @@ extern "C" mppi_status mppi_tc_gemm_bf16(const uint16_t* A, const uint16_t* B, f
     int* err = err_flag[dev];
     cudaStream_t st = (cudaStream_t)stream;
     cudaMemsetAsync(err, 0, 4, st);
+    // TMA-fed pipeline when both operands' rows start on 16-byte boundaries
+    TmaGemm t;
+    memset(&t, 0, sizeof(t));
+    t.M = M;
+    t.N = N;
+    t.K = K;
+    t.nsplit = 1;
+    t.epi = EPI_STORE;
+    t.out = D;
+    t.ldo = N;
+    t.err = err;
+    t.a = reinterpret_cast<const __nv_bfloat16*>(A);
+    t.lda = K;
+    t.b = reinterpret_cast<const __nv_bfloat16*>(B);
+    t.ldb = K;
+    if (N % 4 == 0 && gemm_tma_ok(t)) {
+        cudaError_t e = launch_gemm_tma(t, st);
+        int h = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return MPPI_ERR_CUDA;
+        return h ? MPPI_ERR_TIMEOUT : MPPI_OK;
+    }
     GemmArgs g;
     memset(&g, 0, sizeof(g));
     g.A = reinterpret_cast<const __nv_bfloat16*>(A);
@@ -738,9 +864,10 @@ extern "C" mppi_status mppi_tc_gemm_bf16(const uint16_t* A, const uint16_t* B, f
 }
 
 extern "C" mppi_status mppi_selftest_wait_timeout(void* stream) {
-    // a 128 x 64 x 64 GEMM whose completion is never signalled: every thread's
-    // bounded mbarrier wait must run out, the kernel must record it, free its
-    // tensor memory and return, and the context must stay usable
+    // a 128 x 64 x 64 GEMM whose completion is never signalled, on both
+    // tensor-core kernels: the bounded mbarrier waits must run out, each kernel
+    // must record it, drain its copies, free its tensor memory and return, and
+    // the context must stay usable
     cudaStream_t st = (cudaStream_t)stream;
     __nv_bfloat16 *A = nullptr, *B = nullptr;
     float* D = nullptr;
@@ -762,10 +889,22 @@ extern "C" mppi_status mppi_selftest_wait_timeout(void* stream) {
     g.wait_limit = 1u << 12;
     g.withhold_commit = 1;
     cudaError_t e = launch_gemm(g, st);
-    int h = 0;
+    int h = 0, h2 = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, err, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    // the same on the TMA-fed kernel
+    TmaGemm t;
+    memset(&t, 0, sizeof(t));
+    t.M = 128; t.N = 64; t.K = 64; t.nsplit = 1;
+    t.epi = EPI_STORE; t.out = D; t.ldo = 64; t.err = err;
+    t.wait_limit = 1u << 12;
+    t.withhold_commit = 1;
+    t.a = A; t.lda = 64; t.b = B; t.ldb = 64;
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 4, st);
+    if (e == cudaSuccess) e = launch_gemm_tma(t, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h2, err, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(A); cudaFree(B); cudaFree(D); cudaFree(err);
     if (e != cudaSuccess) return MPPI_ERR_CUDA;
-    return h ? MPPI_ERR_TIMEOUT : MPPI_OK;
+    return (h && h2) ? MPPI_ERR_TIMEOUT : MPPI_OK;
 }

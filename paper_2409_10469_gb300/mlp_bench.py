@@ -7,6 +7,7 @@ shape ms, TFLOP/s (2 M N K per GEMM) and the fraction of the measured dense
 BF16 peak (MEASURED_PEAKS.json, else 1.9 PFLOP/s).
 
     python -m paper_2409_10469_gb300.mlp_bench
+    python -m paper_2409_10469_gb300.mlp_bench --train 4096 --steps 3   # training steps only
 """
 from __future__ import annotations
 
@@ -70,10 +71,35 @@ def run() -> dict:
     return out
 
 
+def train_steps(batch: int, steps: int) -> dict:
+    """`steps` training steps of the network at one batch size (the launch
+    sequence a profiler captures); returns the last loss"""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(0)
+    net = _mppi.MLP(batch)
+    net.set_params(W.mlp_init(0))
+    X = torch.randn((batch, 62), device="cuda", generator=g)
+    T = torch.randn((batch, 48), device="cuda", generator=g)
+    loss = None
+    for _ in range(steps):
+        loss = net.train_step(X, T, lr=1e-4)
+    torch.cuda.synchronize()
+    net.close()
+    return {"batch": batch, "steps": steps, "loss": float(loss)}
+
+
 def main():
+    import argparse
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--train", type=int, default=0, help="only run training steps at this batch size")
+    ap.add_argument("--steps", type=int, default=3)
+    args = ap.parse_args()
     from . import build as B
     B.build()
-    print(json.dumps(run()))
+    if args.train:
+        print(json.dumps(train_steps(args.train, args.steps)))
+    else:
+        print(json.dumps(run()))
 
 
 if __name__ == "__main__":

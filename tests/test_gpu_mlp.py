@@ -22,8 +22,14 @@ def _built():
 
 
 @pytest.mark.parametrize("M_,N_,K_", [(128, 64, 64), (300, 48, 62), (256, 256, 256), (77, 200, 1000),
-                                       (1024, 256, 64)])
+                                       (1024, 256, 64), (300, 48, 64), (130, 64, 1024), (129, 256, 24),
+                                       (39013, 256, 256), (5, 16, 8), (12000, 256, 256), (20000, 200, 128)])
 def test_tc_gemm_bf16(M_, N_, K_):
+    """K a multiple of 8 takes the TMA-fed pipeline: 64-wide column tiles for few
+    row tiles (77 x 200: four column tiles, the last one ragged), 128-wide for
+    12000 rows, 256-wide from 152 row tiles on (39013 rows: several tiles per
+    persistent CTA and both accumulators); K = 24 and 8: one partial chunk
+    zero-filled by TMA.  K = 62 takes the thread-staged kernel"""
     g = torch.Generator().manual_seed(M_ + N_ + K_)
     A = torch.randn(M_, K_, generator=g).to(torch.bfloat16)
     B = torch.randn(N_, K_, generator=g).to(torch.bfloat16)
@@ -65,11 +71,14 @@ def test_forward_matches_oracle(B):
     assert np.array_equal(Yd.cpu().numpy(), Y)
 
 
-def test_gradient_matches_oracle():
-    net = _mppi.MLP(512)
+@pytest.mark.parametrize("B", [256, 129, 1000, 3])
+def test_gradient_matches_oracle(B):
+    """the backward pass reads K-major transposed copies; the weight gradients
+    sum over the batch in K ranges (1000 samples: 16 chunks, 4 ranges)"""
+    net = _mppi.MLP(1024)
     p = M.init_params(6)
     net.set_params(p)
-    X, T = data(256, 2)
+    X, T = data(B, 2)
     loss, g = net.train_step(X, T, lr=0.0, grad=True)
     lo, go = M.loss_grad(p, X, T, mirror=True)
     assert abs(loss - lo) <= 1e-4 * max(1.0, abs(lo))
@@ -108,6 +117,22 @@ def test_adamw_step_matches_oracle_and_training_converges():
     for _ in range(300):
         last = net.train_step(Xt, Tt, lr=2e-3)
     assert last < 0.2 * first, (first, last)
+
+
+def test_gradient_after_update_uses_updated_transposed_weights():
+    """AdamW refreshes W and its transposed BF16 copy W^T together: the next
+    gradient (whose dH products read W^T) matches the oracle at the new parameters"""
+    net = _mppi.MLP(512)
+    net.set_params(M.init_params(9))
+    X, T = data(300, 5)
+    for _ in range(3):
+        net.train_step(X, T, lr=5e-3)
+    p1 = net.get_params()
+    loss, g = net.train_step(X, T, lr=0.0, grad=True)
+    lo, go = M.loss_grad(p1.astype(np.float64), X, T, mirror=True)
+    assert abs(loss - lo) <= 1e-4 * max(1.0, abs(lo))
+    for (a, b) in _blocks(g, go):
+        assert np.max(np.abs(a - b)) / max(1e-12, np.max(np.abs(b))) <= 1e-2
 
 
 def test_bounded_wait_times_out_and_context_survives():
