@@ -233,6 +233,13 @@ mppi_status mppi_batch_get_means(mppi_batch b, float* mu_upds, float* nominals);
 /* Number of graph launches (one per mppi_batch_step). */
 mppi_status mppi_batch_launch_count(mppi_batch b, uint64_t* count);
 
+/* *shared = 1 when every instance of the batch simulates the same model (equal
+ * values, heights and static boxes, whichever handle holds them) under the
+ * same cost: the persistent kernel then takes both from its launch parameters
+ * (the path the single-instance kernel uses) instead of each work item's copy
+ * in shared memory.  Results are bit-identical either way. */
+mppi_status mppi_batch_shared_model(mppi_batch b, int* shared);
+
 /* ------------------------------------------------------------------ serving
  * Continuous batching of control-step requests from many robots.  A robot is a
  * controller handle (its nominal stays on the device between requests).  The

@@ -27,7 +27,7 @@ EXPORTS = ("mppi_create", "mppi_destroy", "mppi_last_error", "mppi_set_nominal",
            "mppi_set_timing", "mppi_get_timings", "mppi_launch_count", "mppi_state_size",
            "mppi_update_noalloc", "mppi_batch_create", "mppi_batch_destroy",
            "mppi_batch_last_error", "mppi_batch_step", "mppi_batch_set_shape", "mppi_batch_get_shape",
-           "mppi_batch_autotune", "mppi_batch_launch_count", "mppi_server_create",
+           "mppi_batch_autotune", "mppi_batch_launch_count", "mppi_batch_shared_model", "mppi_server_create",
            "mppi_server_destroy", "mppi_server_last_error", "mppi_server_add_robot", "mppi_server_submit",
            "mppi_server_tick", "mppi_server_poll", "mppi_server_stats", "mppi_server_reset_stats",
            "mppi_server_drain", "mppi_mlp_create", "mppi_mlp_destroy", "mppi_mlp_last_error",
@@ -139,6 +139,7 @@ def lib():
         L.mppi_batch_autotune.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                           C.POINTER(C.c_float)]
         L.mppi_batch_launch_count.argtypes = [vp, C.POINTER(C.c_uint64)]
+        L.mppi_batch_shared_model.argtypes = [vp, C.POINTER(C.c_int)]
         L.mppi_server_create.argtypes = [C.c_size_t, C.c_int, C.c_int, C.POINTER(C.c_void_p)]
         L.mppi_server_destroy.argtypes = [vp]
         L.mppi_server_last_error.argtypes = [vp]
@@ -394,6 +395,12 @@ class Batch:
         c = C.c_uint64()
         self._check(lib().mppi_batch_launch_count(self.b, C.byref(c)))
         return c.value
+
+    def shared_model(self):
+        """True when all instances share one model and cost (parameter-bank kernel)"""
+        c = C.c_int()
+        self._check(lib().mppi_batch_shared_model(self.b, C.byref(c)))
+        return bool(c.value)
 
     def means(self, mu_upds=None, nominals=None):
         self._check(lib().mppi_batch_get_means(self.b, _ptr(mu_upds), _ptr(nominals)))

@@ -10,6 +10,7 @@
 #include <stdio.h>
 #include <string.h>
 #include <string>
+#include <cstddef>
 #include <vector>
 
 #include "handle.h"
@@ -224,6 +225,28 @@ static_assert(MPPI_INTERP_CUBIC == INTERP_CUBIC && MPPI_INTERP_ZERO == INTERP_ZE
 
 // ------------------------------------------------------------------ ABI
 
+// FNV-1a (64-bit) over the model's values -- the pointer fields (device copies of
+// the heights and boxes, which every handle owns) are left out by offset ranges,
+// so no struct padding enters the hash -- then over the heights and boxes
+// themselves.  Handles with equal keys simulate the same model.
+static uint64_t fnv1a(uint64_t k, const void* p, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; i++) {
+        k ^= c[i];
+        k *= 1099511628211ull;
+    }
+    return k;
+}
+static uint64_t model_key(const DevModel& m, const std::vector<float>& heights, const float* boxes, size_t nbox) {
+    const char* b = reinterpret_cast<const char*>(&m);
+    uint64_t k = 1469598103934665603ull;
+    k = fnv1a(k, b, offsetof(DevModel, hf_y0) + sizeof(float));
+    k = fnv1a(k, b + offsetof(DevModel, n_sbox), sizeof(int));
+    k = fnv1a(k, b + offsetof(DevModel, has_box), offsetof(DevModel, nx) + sizeof(int) - offsetof(DevModel, has_box));
+    k = fnv1a(k, heights.data(), heights.size() * sizeof(float));
+    return fnv1a(k, boxes, nbox * sizeof(float));
+}
+
 extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t* cost, const mppi_config_t* cfg,
                                    void* stream, mppi_handle* out) {
     if (!model || !cost || !cfg || !out) return MPPI_ERR_ARG;
@@ -286,6 +309,13 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
         ok = al((void**)&h->d_sbox, sizeof(boxes)) &&
              cudaMemcpy(h->d_sbox, boxes, sizeof(boxes), cudaMemcpyHostToDevice) == cudaSuccess;
         h->dm.sbox = h->d_sbox;
+        std::vector<float> heights;
+        if (ok && model->terrain == 1) {
+            heights.resize((size_t)model->hf_nx * model->hf_ny);
+            ok = cudaMemcpy(heights.data(), h->d_hf, heights.size() * sizeof(float), cudaMemcpyDeviceToHost) ==
+                 cudaSuccess;
+        }
+        h->model_key = model_key(h->dm, heights, boxes, MAX_SBOX * 6);
     }
     if (!ok) {
         mppi_destroy(h);

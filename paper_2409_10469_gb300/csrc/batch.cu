@@ -17,6 +17,10 @@
 //     finished samples per instance reaches K) runs that instance's update in
 //     one block, in a fixed order, so an instance's result does not depend on
 //     which other instances share the launch.
+// When all instances share one model and one cost (equal model keys: the
+// values, heights and boxes hash alike), the launch passes them in the kernel's
+// parameters and a specialisation reads them there, as the single-instance
+// kernel does, instead of from each item's shared-memory descriptor.
 // The host side captures [work-list copy, step indices, counter resets, kernel]
 // in a CUDA graph once per block shape; the autotuner times the candidate block
 // shapes on the batch itself and keeps the fastest.
@@ -29,171 +33,34 @@
 #include <vector>
 
 #include "batch.cuh"
+#include "batch_kernel.cuh"
 #include "handle.h"
-#include "noise.cuh"
-#include "rollout.cuh"
 
 using namespace mppi;
 
 namespace mppi {
 
-// this lane's 12 knots of sample k (the leg's 3 joints at the 4 knots), and
-// write them to U[k]; the same formula as k_sample, element by element
-__device__ __forceinline__ void sample_lane(const InstDesc& d, int k, int leg, uint32_t step, bool write,
-                                            float (&Uk)[NKNOT][3]) {
-    const int kp0 = d.K - (d.mu_prop ? d.n_prop : 0);
-    const bool prop = d.mu_prop && k >= kp0;
-    const float* ctr = prop ? d.mu_prop : d.mu;
-    const bool nominal = (k == 0) || (prop && k == kp0);
-#pragma unroll
-    for (int j = 0; j < NKNOT; j++)
-#pragma unroll
-        for (int i = 0; i < 3; i++) {
-            const int dd = j * NJ + 3 * leg + i;
-            const float eps = nominal ? 0.f : normal_at(d.key0, d.key1, step, d.inst_id, (uint32_t)k, dd);
-            float c = __ldcg(ctr + dd);
-            if (prop && !(fabsf(c) <= 3.402823466e38f)) c = __ldcg(d.mu + dd);  // non-finite proposal: plain mean
-            float v = __fmaf_rn(d.sigma[dd], eps, c);
-            v = fminf(fmaxf(v, d.q_lo[i]), d.q_hi[i]);
-            Uk[j][i] = v;
-            if (write) d.U[(size_t)k * D + dd] = v;
-        }
-}
-
-__device__ __forceinline__ bool finite_f(float x) { return fabsf(x) <= 3.402823466e38f; }
-
-// Eq. 1, Eq. 2, apply, shift for one instance in one block.  The sums run over
-// 8 fixed groups of samples (k = g mod 8, each in increasing k) whatever the
-// block size, and are combined in group order: the result does not depend on
-// the block shape or on the other instances in the launch.
-constexpr int UPD_GROUPS = 8;
-
-template <int BLOCK>
-__device__ void block_update(const InstDesc& d, float* u0_row) {
-    constexpr int W = BLOCK / 32;
-    constexpr int ACTIVE = BLOCK / 24;  // groups processed at once (24 lanes each, two dims per lane)
-    __shared__ float s_min[W];
-    __shared__ double s_z[UPD_GROUPS];
-    __shared__ double s_part[UPD_GROUPS][D];
-    __shared__ float s_mu[D];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int K = d.K;
-    float lm = INFINITY;
-    for (int k = tid; k < K; k += BLOCK) {
-        float l = __ldcg(d.L + k);
-        if (finite_f(l)) lm = fminf(lm, l);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lm = fminf(lm, __shfl_xor_sync(0xffffffffu, lm, o));
-    if (lane == 0) s_min[warp] = lm;
-    __syncthreads();
-    float Lmin = s_min[0];
-#pragma unroll
-    for (int w = 1; w < W; w++) Lmin = fminf(Lmin, s_min[w]);
-    const bool ok = finite_f(Lmin);
-    const int li = tid % 24;
-    for (int g = tid / 24; g < UPD_GROUPS && tid < ACTIVE * 24; g += ACTIVE) {
-        float s0 = 0.f, s1 = 0.f, c0 = 0.f, c1 = 0.f;
-        double z = 0.0;
-        if (ok)
-            for (int k = g; k < K; k += UPD_GROUPS) {
-                float l = __ldcg(d.L + k);
-                float w = finite_f(l) ? expf(-(l - Lmin) * d.inv_lambda) : 0.f;
-                z += (double)w;
-                float2 u = __ldcg(reinterpret_cast<const float2*>(d.U + (size_t)k * D) + li);
-                float y0 = w * u.x - c0, y1 = w * u.y - c1;
-                float t0 = s0 + y0, t1 = s1 + y1;
-                c0 = (t0 - s0) - y0;
-                c1 = (t1 - s1) - y1;
-                s0 = t0;
-                s1 = t1;
-            }
-        s_part[g][2 * li] = (double)s0 - (double)c0;
-        s_part[g][2 * li + 1] = (double)s1 - (double)c1;
-        if (li == 0) s_z[g] = z;
-    }
-    __syncthreads();
-    if (tid < D) {
-        float mu_new;
-        if (ok) {
-            double S = 0.0, Z = 0.0;
-            for (int q = 0; q < UPD_GROUPS; q++) {
-                S += s_part[q][tid];
-                Z += s_z[q];
-            }
-            mu_new = (float)(S / Z);
-        } else {
-            mu_new = __ldcg(d.mu + tid);
-        }
-        s_mu[tid] = mu_new;
-        d.mu_upd[tid] = mu_new;
-        if (tid < NJ) {
-            d.u0[tid] = mu_new;
-            u0_row[tid] = mu_new;
-        }
-    }
-    if (tid == 0) *d.status = ok ? 0 : 4;
-    __syncthreads();
-    if (tid < D) d.mu[tid] = shifted_knot(s_mu, d.interp, d.H, d.ctrl_steps, tid / NJ, tid % NJ);
-}
-
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 1 : 384 / BLOCK) k_batch(BatchArgs a) {
-    __shared__ InstDesc sd;
-    __shared__ int s_item, s_last;
-    const int tid = threadIdx.x, leg = tid & 3, r = tid >> 2;
-    const int n_items = *a.n_items;
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(a.next, 1);
-        __syncthreads();
-        const int it = s_item;
-        if (it >= n_items) break;
-        const WorkItem w = a.items[it];
-        {
-            const int* src = reinterpret_cast<const int*>(a.desc + w.inst);
-            int* dst = reinterpret_cast<int*>(&sd);
-            for (int i = tid; i < (int)(sizeof(InstDesc) / 4); i += BLOCK) dst[i] = __ldcg(src + i);
-        }
-        __syncthreads();
-        const bool valid = r < w.n;
-        const int k = w.k0 + (valid ? r : w.n - 1);
-        const uint32_t step = __ldcg(a.steps + w.inst);
-        float Uk[NKNOT][3];
-        sample_lane(sd, k, leg, step, valid, Uk);
-        // gait time of this horizon: step * control period, reduced modulo the gait period
-        const double t0d = (double)step * sd.ctrl_steps * sd.dt_d;
-        const float t0 = ((sd.gait == 1 || sd.gait == 2) && sd.period_d > 0) ? (float)fmod(t0d, sd.period_d)
-                                                                          : (float)t0d;
-        const HorizonArgs hz = {sd.H, sd.n_sub, sd.nx, sd.h, sd.dt, sd.inv_Hm1, t0, sd.arm, sd.interp, sd.Bt};
-        const float* x0 = a.x0s + (size_t)w.inst * NX_BOX;
-        float L;
-        if (sd.model.terrain != 0 || sd.model.n_sbox > 0)
-            L = sd.model.has_box ? rollout_lane<1, true>(sd.model, sd.cost, hz, x0, Uk, nullptr, leg, k, valid, nullptr)
-                                 : rollout_lane<1, false>(sd.model, sd.cost, hz, x0, Uk, nullptr, leg, k, valid, nullptr);
-        else
-            L = sd.model.has_box ? rollout_lane<0, true>(sd.model, sd.cost, hz, x0, Uk, nullptr, leg, k, valid, nullptr)
-                                 : rollout_lane<0, false>(sd.model, sd.cost, hz, x0, Uk, nullptr, leg, k, valid, nullptr);
-        if (valid && leg == 0) sd.L[k] = L;
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) {
-            const unsigned prev = atomicAdd(a.done + w.inst, (unsigned)w.n);
-            s_last = (prev + (unsigned)w.n == (unsigned)sd.K);
-        }
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
-            block_update<BLOCK>(sd, a.u0s + (size_t)w.inst * NJ);
-            if (tid == 0) a.done[w.inst] = 0u;
-        }
-        __syncthreads();
-    }
-}
+// the uniform-model kernels are compiled in batch_uni.cu
+extern template cudaError_t launch_k_batch<64, true>(const BatchArgs&, int, cudaStream_t);
+extern template cudaError_t launch_k_batch<128, true>(const BatchArgs&, int, cudaStream_t);
+extern template cudaError_t launch_k_batch<256, true>(const BatchArgs&, int, cudaStream_t);
 
 template <int BLOCK>
 static cudaError_t launch_batch_t(const BatchArgs& a, int grid, cudaStream_t st) {
-    k_batch<BLOCK><<<grid, BLOCK, 0, st>>>(a);
-    return cudaGetLastError();
+    return a.uniform ? launch_k_batch<BLOCK, true>(a, grid, st) : launch_k_batch<BLOCK, false>(a, grid, st);
+}
+
+void set_uniform(BatchArgs& a, const InstDesc* d, int n) {
+    a.uniform = n > 0;
+    for (int i = 1; i < n && a.uniform; i++)
+        a.uniform = d[i].model_key == d[0].model_key && memcmp(&d[i].cost, &d[0].cost, sizeof(DevCost)) == 0;
+    if (a.uniform) {
+        a.model = d[0].model;
+        a.cost = d[0].cost;
+    } else {
+        memset(&a.model, 0, sizeof(a.model));
+        memset(&a.cost, 0, sizeof(a.cost));
+    }
 }
 
 cudaError_t launch_batch(const BatchArgs& a, int block, int grid, cudaStream_t st) {
@@ -208,9 +75,10 @@ cudaError_t launch_batch(const BatchArgs& a, int block, int grid, cudaStream_t s
 int max_blocks_per_sm(int block) {
     int n = 0;
     cudaError_t e = cudaErrorInvalidValue;
-    if (block == 64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<64>, 64, 0);
-    if (block == 128) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<128>, 128, 0);
-    if (block == 256) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<256>, 256, 0);
+    // (both variants have the same launch bounds)
+    if (block == 64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<64, false>, 64, 0);
+    if (block == 128) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<128, false>, 128, 0);
+    if (block == 256) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<256, false>, 256, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -229,6 +97,7 @@ struct mppi_batch_s {
     int sms = 0;
     int block = 128, blocks_per_sm = 4;
     int max_items = 0;
+    std::vector<InstDesc> h_desc;  // host copies of the descriptors (the uniform-model test)
     InstDesc* d_desc = nullptr;
     WorkItem* d_items = nullptr;
     int *d_nitems = nullptr, *d_next = nullptr;
@@ -292,6 +161,7 @@ InstDesc mppi::make_desc(const mppi_handle_s* h) {
     d.period_d = h->cost_in.gait_period;
     d.interp = h->cfg.interp;
     d.Bt = reinterpret_cast<const float4*>(h->d_B);
+    d.model_key = h->model_key;
     memcpy(d.sigma, h->cfg.sigma, sizeof(d.sigma));
     memcpy(d.q_lo, h->cfg.q_lo, sizeof(d.q_lo));
     memcpy(d.q_hi, h->cfg.q_hi, sizeof(d.q_hi));
@@ -335,7 +205,17 @@ static cudaError_t enqueue_step(mppi_batch b) {
         return e;
     if ((e = cudaMemsetAsync(b->d_next, 0, sizeof(int), b->stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(b->d_done, 0, (size_t)b->n * sizeof(unsigned), b->stream)) != cudaSuccess) return e;
-    BatchArgs a = {b->d_desc, b->d_items, b->d_nitems, b->d_next, b->d_done, b->d_x0s, b->d_steps, b->d_u0s};
+    BatchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.desc = b->d_desc;
+    a.items = b->d_items;
+    a.n_items = b->d_nitems;
+    a.next = b->d_next;
+    a.done = b->d_done;
+    a.x0s = b->d_x0s;
+    a.steps = b->d_steps;
+    a.u0s = b->d_u0s;
+    set_uniform(a, b->h_desc.data(), b->n);
     return launch_batch(a, b->block, b->blocks_per_sm * b->sms, b->stream);
 }
 
@@ -390,6 +270,7 @@ extern "C" mppi_status mppi_batch_create(const mppi_handle* hs, int n, void* str
         max_items += (hs[i]->cfg.K + 15) / 16;  // enough for the smallest block shape (64 threads)
     }
     b->max_items = max_items;
+    b->h_desc = descs;
     bool ok = cudaMalloc((void**)&b->d_desc, n * sizeof(InstDesc)) == cudaSuccess &&
               cudaMalloc((void**)&b->d_items, max_items * sizeof(WorkItem)) == cudaSuccess &&
               cudaMalloc((void**)&b->d_nitems, sizeof(int)) == cudaSuccess &&
@@ -562,6 +443,15 @@ extern "C" mppi_status mppi_batch_autotune(mppi_batch b, const float* x0s, int t
 extern "C" mppi_status mppi_batch_launch_count(mppi_batch b, uint64_t* count) {
     if (!b || !count) return MPPI_ERR_ARG;
     *count = b->launches;
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_batch_shared_model(mppi_batch b, int* shared) {
+    if (!b || !shared) return MPPI_ERR_ARG;
+    BatchArgs a;
+    memset(&a, 0, sizeof(a));
+    set_uniform(a, b->h_desc.data(), b->n);
+    *shared = a.uniform;
     return MPPI_OK;
 }
 

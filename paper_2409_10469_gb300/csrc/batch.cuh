@@ -28,6 +28,7 @@ struct InstDesc {
     uint32_t key0, key1, inst_id;
     int interp;           // MPPI_INTERP_* (knot representations only)
     const float4* Bt;     // [H] knot weights of each dt step
+    uint64_t model_key;   // the handle's model key (equal keys: the same model values)
 };
 
 struct WorkItem {
@@ -43,7 +44,16 @@ struct BatchArgs {
     const float* x0s;       // [n_inst][NX_BOX]
     const uint32_t* steps;  // [n_inst] control-step index of each instance
     float* u0s;             // [n_inst][12]
+    // when every instance of the launch has the same model and cost (set_uniform),
+    // the kernel reads them from here -- the parameter bank, whose words the
+    // arithmetic takes as operands -- instead of each item's shared-memory copy
+    int uniform;
+    DevModel model;
+    DevCost cost;
 };
+
+// fill the uniform fields of a launch over descriptors d[0 .. n)
+void set_uniform(BatchArgs& a, const InstDesc* d, int n);
 
 // launch the persistent kernel (block in {64, 128, 256}; grid = blocks_per_sm x SMs)
 cudaError_t launch_batch(const BatchArgs& a, int block, int grid, cudaStream_t st);

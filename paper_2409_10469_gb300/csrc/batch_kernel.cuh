@@ -1,0 +1,182 @@
+// batch_kernel.cuh -- device side of the persistent multi-instance step
+// (batch.cu): in-kernel sampling, the per-instance update in one block, and the
+// kernel itself.  Included by batch.cu (the general kernel) and batch_uni.cu
+// (its specialisation for launches whose instances share one model and cost),
+// so the two compile in parallel.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "batch.cuh"
+#include "noise.cuh"
+#include "rollout.cuh"
+
+namespace mppi {
+
+// this lane's 12 knots of sample k (the leg's 3 joints at the 4 knots), and
+// write them to U[k]; the same formula as k_sample, element by element
+__device__ __forceinline__ void sample_lane(const InstDesc& d, int k, int leg, uint32_t step, bool write,
+                                            float (&Uk)[NKNOT][3]) {
+    const int kp0 = d.K - (d.mu_prop ? d.n_prop : 0);
+    const bool prop = d.mu_prop && k >= kp0;
+    const float* ctr = prop ? d.mu_prop : d.mu;
+    const bool nominal = (k == 0) || (prop && k == kp0);
+#pragma unroll
+    for (int j = 0; j < NKNOT; j++)
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            const int dd = j * NJ + 3 * leg + i;
+            const float eps = nominal ? 0.f : normal_at(d.key0, d.key1, step, d.inst_id, (uint32_t)k, dd);
+            float c = __ldcg(ctr + dd);
+            if (prop && !(fabsf(c) <= 3.402823466e38f)) c = __ldcg(d.mu + dd);  // non-finite proposal: plain mean
+            float v = __fmaf_rn(d.sigma[dd], eps, c);
+            v = fminf(fmaxf(v, d.q_lo[i]), d.q_hi[i]);
+            Uk[j][i] = v;
+            if (write) d.U[(size_t)k * D + dd] = v;
+        }
+}
+
+__device__ __forceinline__ bool finite_f(float x) { return fabsf(x) <= 3.402823466e38f; }
+
+// Eq. 1, Eq. 2, apply, shift for one instance in one block.  The sums run over
+// 8 fixed groups of samples (k = g mod 8, each in increasing k) whatever the
+// block size, and are combined in group order: the result does not depend on
+// the block shape or on the other instances in the launch.
+constexpr int UPD_GROUPS = 8;
+
+template <int BLOCK>
+__device__ void block_update(const InstDesc& d, float* u0_row) {
+    constexpr int W = BLOCK / 32;
+    constexpr int ACTIVE = BLOCK / 24;  // groups processed at once (24 lanes each, two dims per lane)
+    __shared__ float s_min[W];
+    __shared__ double s_z[UPD_GROUPS];
+    __shared__ double s_part[UPD_GROUPS][D];
+    __shared__ float s_mu[D];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int K = d.K;
+    float lm = INFINITY;
+    for (int k = tid; k < K; k += BLOCK) {
+        float l = __ldcg(d.L + k);
+        if (finite_f(l)) lm = fminf(lm, l);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lm = fminf(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+    if (lane == 0) s_min[warp] = lm;
+    __syncthreads();
+    float Lmin = s_min[0];
+#pragma unroll
+    for (int w = 1; w < W; w++) Lmin = fminf(Lmin, s_min[w]);
+    const bool ok = finite_f(Lmin);
+    const int li = tid % 24;
+    for (int g = tid / 24; g < UPD_GROUPS && tid < ACTIVE * 24; g += ACTIVE) {
+        float s0 = 0.f, s1 = 0.f, c0 = 0.f, c1 = 0.f;
+        double z = 0.0;
+        if (ok)
+            for (int k = g; k < K; k += UPD_GROUPS) {
+                float l = __ldcg(d.L + k);
+                float w = finite_f(l) ? expf(-(l - Lmin) * d.inv_lambda) : 0.f;
+                z += (double)w;
+                float2 u = __ldcg(reinterpret_cast<const float2*>(d.U + (size_t)k * D) + li);
+                float y0 = w * u.x - c0, y1 = w * u.y - c1;
+                float t0 = s0 + y0, t1 = s1 + y1;
+                c0 = (t0 - s0) - y0;
+                c1 = (t1 - s1) - y1;
+                s0 = t0;
+                s1 = t1;
+            }
+        s_part[g][2 * li] = (double)s0 - (double)c0;
+        s_part[g][2 * li + 1] = (double)s1 - (double)c1;
+        if (li == 0) s_z[g] = z;
+    }
+    __syncthreads();
+    if (tid < D) {
+        float mu_new;
+        if (ok) {
+            double S = 0.0, Z = 0.0;
+            for (int q = 0; q < UPD_GROUPS; q++) {
+                S += s_part[q][tid];
+                Z += s_z[q];
+            }
+            mu_new = (float)(S / Z);
+        } else {
+            mu_new = __ldcg(d.mu + tid);
+        }
+        s_mu[tid] = mu_new;
+        d.mu_upd[tid] = mu_new;
+        if (tid < NJ) {
+            d.u0[tid] = mu_new;
+            u0_row[tid] = mu_new;
+        }
+    }
+    if (tid == 0) *d.status = ok ? 0 : 4;
+    __syncthreads();
+    if (tid < D) d.mu[tid] = shifted_knot(s_mu, d.interp, d.H, d.ctrl_steps, tid / NJ, tid % NJ);
+}
+
+// one item's rollouts on the terrain / box variant its model needs
+__device__ __forceinline__ float rollout_item(const DevModel& m, const DevCost& c, const HorizonArgs& hz,
+                                              const float* x0, const float (&Uk)[NKNOT][3], int leg, int k,
+                                              bool valid) {
+    if (m.terrain != 0 || m.n_sbox > 0)
+        return m.has_box ? rollout_lane<1, true>(m, c, hz, x0, Uk, nullptr, leg, k, valid, nullptr)
+                         : rollout_lane<1, false>(m, c, hz, x0, Uk, nullptr, leg, k, valid, nullptr);
+    return m.has_box ? rollout_lane<0, true>(m, c, hz, x0, Uk, nullptr, leg, k, valid, nullptr)
+                     : rollout_lane<0, false>(m, c, hz, x0, Uk, nullptr, leg, k, valid, nullptr);
+}
+
+// UNI: every instance has the launch's model and cost (a.model, a.cost)
+template <int BLOCK, bool UNI>
+__global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 1 : 384 / BLOCK) k_batch(const __grid_constant__ BatchArgs a) {
+    __shared__ InstDesc sd;
+    __shared__ int s_item, s_last;
+    const int tid = threadIdx.x, leg = tid & 3, r = tid >> 2;
+    const int n_items = *a.n_items;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(a.next, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const WorkItem w = a.items[it];
+        {
+            const int* src = reinterpret_cast<const int*>(a.desc + w.inst);
+            int* dst = reinterpret_cast<int*>(&sd);
+            for (int i = tid; i < (int)(sizeof(InstDesc) / 4); i += BLOCK) dst[i] = __ldcg(src + i);
+        }
+        __syncthreads();
+        const bool valid = r < w.n;
+        const int k = w.k0 + (valid ? r : w.n - 1);
+        const uint32_t step = __ldcg(a.steps + w.inst);
+        float Uk[NKNOT][3];
+        sample_lane(sd, k, leg, step, valid, Uk);
+        // gait time of this horizon: step * control period, reduced modulo the gait period
+        const double t0d = (double)step * sd.ctrl_steps * sd.dt_d;
+        const float t0 = ((sd.gait == 1 || sd.gait == 2) && sd.period_d > 0) ? (float)fmod(t0d, sd.period_d)
+                                                                          : (float)t0d;
+        const HorizonArgs hz = {sd.H, sd.n_sub, sd.nx, sd.h, sd.dt, sd.inv_Hm1, t0, sd.arm, sd.interp, sd.Bt};
+        const float* x0 = a.x0s + (size_t)w.inst * NX_BOX;
+        const float L = UNI ? rollout_item(a.model, a.cost, hz, x0, Uk, leg, k, valid)
+                            : rollout_item(sd.model, sd.cost, hz, x0, Uk, leg, k, valid);
+        if (valid && leg == 0) sd.L[k] = L;
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) {
+            const unsigned prev = atomicAdd(a.done + w.inst, (unsigned)w.n);
+            s_last = (prev + (unsigned)w.n == (unsigned)sd.K);
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            block_update<BLOCK>(sd, a.u0s + (size_t)w.inst * NJ);
+            if (tid == 0) a.done[w.inst] = 0u;
+        }
+        __syncthreads();
+    }
+}
+
+template <int BLOCK, bool UNI>
+cudaError_t launch_k_batch(const BatchArgs& a, int grid, cudaStream_t st) {
+    k_batch<BLOCK, UNI><<<grid, BLOCK, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace mppi

@@ -15,6 +15,7 @@ struct mppi_handle_s {
     mppi_config_t cfg;
     mppi::DevModel dm;
     mppi::DevCost dc;
+    uint64_t model_key = 0;  // hash of dm's values, heights and static boxes (equal keys: the same model)
     cudaStream_t stream = nullptr;
     int device = 0;
     int nx = mppi::NX_ROBOT;

@@ -309,7 +309,17 @@ static int admit_and_launch(mppi_server s, Launch& l, mppi_status* st) {
     ok(cudaMemcpyAsync(l.d_steps, l.h_steps, n * sizeof(uint32_t), cudaMemcpyHostToDevice, l.st));
     ok(cudaMemsetAsync(l.d_next, 0, sizeof(int), l.st));
     ok(cudaMemsetAsync(l.d_done, 0, n * sizeof(unsigned), l.st));
-    BatchArgs a = {l.d_desc, l.d_items, l.d_nitems, l.d_next, l.d_done, l.d_x0s, l.d_steps, l.d_u0s};
+    BatchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.desc = l.d_desc;
+    a.items = l.d_items;
+    a.n_items = l.d_nitems;
+    a.next = l.d_next;
+    a.done = l.d_done;
+    a.x0s = l.d_x0s;
+    a.steps = l.d_steps;
+    a.u0s = l.d_u0s;
+    set_uniform(a, l.h_desc, n);
     ok(launch_batch(a, s->block, s->bpsm * s->sms, l.st));
     ok(cudaMemcpyAsync(l.h_u0s, l.d_u0s, (size_t)n * NJ * sizeof(float), cudaMemcpyDeviceToHost, l.st));
     ok(cudaEventRecord(l.ev, l.st));

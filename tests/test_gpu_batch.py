@@ -56,7 +56,31 @@ def test_batch_matches_single_instance_steps():
     assert batch.launch_count() == 2
 
 
+def test_shared_model_batch_matches_single_instance_steps():
+    """three heightfield controllers (each handle uploads its own copy of the
+    same heights) with different K, H and noise streams share one model: the
+    batch takes the parameter-bank kernel and matches the single-instance path;
+    a mix of tasks does not share"""
+    items = [(W.config_terrain(), 64, 60), (W.config_terrain(), 200, 100), (W.config_terrain(), 96, 50)]
+    singles = [make(c, K, H, seed=11, inst=i) for i, (c, K, H) in enumerate(items)]
+    batched = [make(c, K, H, seed=11, inst=i) for i, (c, K, H) in enumerate(items)]
+    batch = _mppi.Batch([c for c, _ in batched])
+    assert batch.shared_model()
+    x0s = np.stack([x0_row(c) for c, _, _ in items])
+    for step in (0, 1, 2):
+        u0b = np.zeros((len(items), 12), np.float32)
+        batch.step(x0s, np.full(len(items), step), u0s=u0b)
+        for i, ((cfg, K, H), (ctl, m)) in enumerate(zip(items, singles)):
+            u0 = np.zeros(12, np.float32)
+            ctl.step(cfg.x0.astype(np.float32), step, u0_out=u0)
+            assert np.max(np.abs(u0b[i] - u0) / np.maximum(np.abs(u0), 1)) <= 1e-6, (i, step)
+    mixed = _mppi.Batch([make(c, K, H, inst=i)[0] for i, (c, K, H) in enumerate(mix())])
+    assert not mixed.shared_model()
+
+
 def test_batch_alone_equals_mixed_bit_exact():
+    """a one-instance batch takes the parameter-bank kernel, the mixed batch the
+    general one: the same instance's results are bit-identical"""
     cfg = W.config_trot()
     alone, _ = make(cfg, 256, 50, seed=7, inst=3)
     b1 = _mppi.Batch([alone])
