@@ -37,8 +37,8 @@ METRIC = "rollout-steps/s (MPPI step, K=4096, H=100)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture) of
 # one k_rollout launch on this workload, valid only for the kernel sources whose
 # SHA-256 prefix is given; reported as null once those sources change.
-ROLLOUT_TRAFFIC = {"bytes": 90112, "sources_sha256": "25b5ec66405fb251"}
-ROLLOUT_SOURCES = ("rollout.cu", "rollout.cuh", "common.cuh")
+ROLLOUT_TRAFFIC = {"bytes": 118528, "sources_sha256": "53dafe7b95650ac4"}
+ROLLOUT_SOURCES = ("rollout.cu", "rollout.cuh", "common.cuh", "noise.cuh", "kernels.h")
 
 
 def rollout_traffic():
@@ -225,16 +225,6 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def hbm_line(nbytes, ms, peaks):
-    """An HBM roofline entry for a byte-moving kernel: algorithmic bytes over its
-    CUDA-event time against the measured copy bandwidth."""
-    peak = (peaks or {}).get("hbm_gbs", 6800.0)
-    ach = nbytes / (ms * 1e-3) / 1e9
-    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "bytes_per_launch": nbytes, "ms": ms,
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6.8 TB/s"}
-
-
 def run_ours(args):
     import torch
     from paper_2409_10469_gb300 import _mppi, flops as F, workloads as W
@@ -301,7 +291,7 @@ def run_ours(args):
     from paper_2409_10469_gb300 import dist as D
     mean_ms = D.max_over_ranks(mean_ms, device="cuda")
     ker = np.array(ker)
-    timed_launches = 2 * args.steps   # rollout (sampling inside) and update per step (timed loop only)
+    timed_launches = args.steps   # one kernel per step: sampling, rollouts, update (timed loop only)
 
     # end to end through the C ABI with host buffers (pinned x0 in, u0 out)
     x0_h = torch.tensor(cfg.x0, dtype=torch.float32).pin_memory()
@@ -340,11 +330,8 @@ def run_ours(args):
                    "parallelism": "independent instance per GPU"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "max": float(step_ms.max())},
-        "kernel_ms": {"sample": float(ker[:, 0].mean()), "rollout": rollout_ms,
-                      "update": float(ker[:, 2].mean())},
-        "roofline_aux": {
-            "k_sample": hbm_line(F.sample_bytes(K_BENCH), float(ker[:, 0].mean()), peaks),
-            "k_update": hbm_line(F.update_bytes(K_BENCH), float(ker[:, 2].mean()), peaks)},
+        # the step is one kernel: knot sampling, rollouts and the fused update (Eq. 1-2, shift)
+        "kernel_ms": {"k_rollout": rollout_ms},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": rollout_traffic(),
                      "kernel": "k_rollout", "flops_per_launch": fl,

@@ -171,15 +171,19 @@ mppi_status mppi_update(mppi_handle h, const float* L, const float* U, int n, fl
  * step * ctrl_steps * dt): sample, roll out from x0 (float[nx]), update, shift.
  * u0_out: float[12] joint targets to apply; mu_out optional float[48] (updated
  * mean before the shift).  With host outputs the call returns after the step
- * completed.  Two kernels for the knot representations (the rollout kernel draws
- * the knots itself, bit-identical to mppi_sample, and leaves them in the
- * handle's U), three for direct targets. */
+ * completed.  One kernel for the knot representations: the rollout kernel draws
+ * the knots itself (bit-identical to mppi_sample, left in the handle's U) and
+ * ends with the update (each CTA sums its rollouts' weights around its own cost
+ * minimum in FP64, the last CTA combines them); three kernels for direct
+ * targets. */
 mppi_status mppi_step(mppi_handle h, const float* x0, uint32_t step, float* u0_out,
                       float* mu_out);
 
 /* Per-kernel device time of the last mppi_step, measured with CUDA events on
- * the handle's stream when timing is on: ms[0] sample (0 for the knot forms,
- * whose sampling runs inside the rollout), ms[1] rollout, ms[2] update.  Timing is off by default (events add a few microseconds). */
+ * the handle's stream when timing is on: ms[0] sample, ms[1] rollout, ms[2]
+ * update (for the knot forms sampling and update run inside the rollout kernel,
+ * so ms[0] and ms[2] are 0).  Timing is off by default (events add a few
+ * microseconds). */
 mppi_status mppi_set_timing(mppi_handle h, int on);
 mppi_status mppi_get_timings(mppi_handle h, float ms[3]);
 

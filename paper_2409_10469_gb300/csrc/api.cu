@@ -9,6 +9,7 @@
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
+#include <algorithm>
 #include <string>
 #include <cstddef>
 #include <vector>
@@ -225,6 +226,15 @@ static_assert(MPPI_INTERP_CUBIC == INTERP_CUBIC && MPPI_INTERP_ZERO == INTERP_ZE
 
 // ------------------------------------------------------------------ ABI
 
+// threads per block of the rollout kernel (4 per rollout)
+static int rollout_block_cfg(const mppi_config_t& c) { return c.block ? c.block : 128; }
+// scratch of the update fused into the control step's rollout launch (0 when the
+// grid is too large to fuse)
+static size_t fused_part_doubles(const mppi_config_t& c) {
+    const int g = rollout_grid(c.K, rollout_block_cfg(c));
+    return g <= FUSE_MAX_CTAS ? (size_t)g * FUSE_W : 0;
+}
+
 // FNV-1a (64-bit) over the model's values -- the pointer fields (device copies of
 // the heights and boxes, which every handle owns) are left out by offset ranges,
 // so no struct padding enters the hash -- then over the heights and boxes
@@ -287,7 +297,8 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
               al((void**)&h->d_L, K * sizeof(float)) && al((void**)&h->d_x0, K * NX_BOX * sizeof(float)) &&
               al((void**)&h->d_u0, NJ * sizeof(float)) && al((void**)&h->d_status, sizeof(int)) &&
               al((void**)&h->d_wsum, sizeof(double)) &&
-              al((void**)&h->d_part, (size_t)UPDATE_MAX_CTAS * (Dp + 1) * sizeof(double)) &&
+              al((void**)&h->d_part, std::max((size_t)UPDATE_MAX_CTAS * (Dp + 1), fused_part_doubles(*cfg)) *
+                                         sizeof(double)) &&
               al((void**)&h->d_counter, sizeof(unsigned)) &&
               al((void**)&h->d_B, (size_t)4 * cfg->H * sizeof(float));
     if (ok && model->terrain == 1) {
@@ -451,10 +462,20 @@ static RolloutArgs rollout_args(mppi_handle h, const float* x0, int per, const f
     a.step = 0;
     a.inst = h->cfg.inst;
     a.U_out = nullptr;
+    a.fuse = 0;  // mppi_step's knot representations fuse the update into the launch
+    a.inv_lambda = (float)(1.0 / h->cfg.lambda);
+    a.ctrl_steps = h->cfg.ctrl_steps;
+    a.mu_w = nullptr;
+    a.mu_upd = nullptr;
+    a.u0 = nullptr;
+    a.status = nullptr;
+    a.wsum = nullptr;
+    a.part = nullptr;
+    a.counter = nullptr;
     return a;
 }
 
-static int rollout_block(mppi_handle h) { return h->cfg.block ? h->cfg.block : 128; }
+static int rollout_block(mppi_handle h) { return rollout_block_cfg(h->cfg); }
 
 extern "C" mppi_status mppi_rollouts(mppi_handle h, const float* x0, int x0_per_sample, const float* U, int n,
                                      double t0, float* L_out, float* traj_out) {
@@ -610,18 +631,31 @@ extern "C" mppi_status mppi_step(mppi_handle h, const float* x0, uint32_t step, 
     if (tm) CK(cudaEventRecord(h->ev[1], h->stream));
     const double t0 = (double)step * h->cfg.ctrl_steps * h->cfg.dt;
     RolloutArgs a = rollout_args(h, dx0, 0, h->d_U, h->cfg.K, t0, h->d_L, nullptr);
+    // Eq. 1, Eq. 2, apply and shift at the end of the same launch (grids of up to
+    // FUSE_MAX_CTAS CTAs; larger ones run the update kernel after it)
+    const bool fuse = knots && rollout_grid(h->cfg.K, rollout_block(h)) <= FUSE_MAX_CTAS;
     if (knots) {
         a.sample = 1;
         a.mu = h->d_mu;
         a.mu_prop = h->has_prop ? h->d_mu_prop : nullptr;
         a.step = step;
         a.U_out = h->d_U;
+        a.fuse = fuse ? 1 : 0;
+        a.mu_w = h->d_mu;
+        a.mu_upd = h->d_mu_upd;
+        a.u0 = h->d_u0;
+        a.status = h->d_status;
+        a.wsum = h->d_wsum;
+        a.part = h->d_part;
+        a.counter = h->d_counter;
     }
     CK(launch_rollout(a, rollout_block(h), h->stream));
     h->launches++;
     if (tm) CK(cudaEventRecord(h->ev[2], h->stream));
-    s = do_update(h, h->d_L, h->d_U, h->cfg.K);
-    if (s != MPPI_OK) return s;
+    if (!fuse) {
+        s = do_update(h, h->d_L, h->d_U, h->cfg.K);
+        if (s != MPPI_OK) return s;
+    }
     if (tm) {
         CK(cudaEventRecord(h->ev[3], h->stream));
         h->timed_valid = 1;

@@ -42,7 +42,24 @@ struct RolloutArgs {
     float q_lo[3], q_hi[3];
     uint32_t key0, key1, step, inst;
     float* U_out;          // [n][48]
+    // fused update (the control step, knot representations): each CTA folds its
+    // rollouts into FP64 partial sums around its own cost minimum, the last CTA
+    // to finish combines them (Eq. 1, Eq. 2), applies and shifts; these are the
+    // outputs and scratch of UpdateArgs, with part sized FUSE_W per CTA
+    int fuse;
+    float inv_lambda;
+    int ctrl_steps;
+    float* mu_w;           // [48] the nominal (== mu), overwritten by the shifted nominal
+    float* mu_upd;         // [48]
+    float* u0;             // [12]
+    int* status;
+    double* wsum;
+    double* part;          // [grid][FUSE_W] (used as float pairs)
+    unsigned* counter;     // 0 between launches
 };
+
+constexpr int FUSE_W = D + 2;  // per-CTA partial: 48 weighted sums, the weight sum, the CTA's cost minimum
+constexpr int FUSE_MAX_CTAS = 1024;  // grids up to this size fuse the update (its factors sit in shared memory)
 
 struct UpdateArgs {
     const float* L;        // [n]
@@ -64,6 +81,8 @@ int update_grid(int n);
 
 cudaError_t launch_sample(const SampleArgs& a, cudaStream_t st);
 cudaError_t launch_rollout(const RolloutArgs& a, int block, cudaStream_t st);
+// CTAs of a rollout launch of n samples at this block size
+inline int rollout_grid(int n, int block) { return (int)((4L * n + block - 1) / block); }
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t st);
 
 }  // namespace mppi

@@ -330,7 +330,35 @@ def test_full_step_matches_components():
     _, mu_same, _ = O.update(Lg, U_o, m["lam"])
     assert np.abs(mu - mu_same).max() <= 1e-6 * 4
     assert np.array_equal(u0, mu[:12])
-    assert ctl.launch_count() == 2   # rollout (sampling inside) + update
+    assert ctl.launch_count() == 1   # one kernel: sampling, rollouts and the update
+
+
+@pytest.mark.parametrize("K,block", [(1000, 0), (4096, 0), (500, 32)])
+def test_fused_update_matches_oracle(K, block):
+    """the control step's update runs at the end of the rollout kernel (per-CTA
+    sums around each CTA's own cost minimum, combined by the last CTA): its mean
+    equals the oracle's Eq. 1-2 on the same samples and GPU costs, u0 is knot 0
+    and the nominal is the oracle's shift of it (1000 samples: a ragged last CTA;
+    block 32: 63 CTAs of 8 rollouts)"""
+    cfg = W.config_trot(K=K, H=30)
+    mp = dict(cfg.mppi, block=block) if block else cfg.mppi
+    ctl = _mppi.Controller(cfg.robot, cfg.cost, mp)
+    ctl.set_nominal(cfg.mu0)
+    u0 = np.zeros(12, np.float32)
+    mu = np.zeros(48, np.float32)
+    assert ctl.step(cfg.x0.astype(np.float32), 3, u0_out=u0, mu_out=mu) == 0
+    assert ctl.launch_count() == 1
+    U_o = O.sample(mp, cfg.mu0, 3)
+    ctl2 = _mppi.Controller(cfg.robot, cfg.cost, mp)
+    L = torch.empty(K, device="cuda")
+    ctl2.rollouts(dev(cfg.x0), U=dev(U_o), n=K, L_out=L, t0=3 * mp["ctrl_steps"] * mp["dt"])
+    _, mu_o, _ = O.update(L.cpu().numpy(), U_o, mp["lam"])
+    assert np.abs(mu - mu_o).max() <= 4e-6 * max(1.0, np.abs(mu_o).max())
+    assert np.array_equal(u0, mu[:12])
+    sh = O.shift(mu, mp["H"], mp["ctrl_steps"])
+    assert np.abs(ctl.get_nominal() - sh).max() <= 1e-6 * max(1.0, np.abs(sh).max())
+    ctl.close()
+    ctl2.close()
 
 
 def test_edge_cases():
