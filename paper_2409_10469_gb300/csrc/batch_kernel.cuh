@@ -47,7 +47,7 @@ constexpr int UPD_GROUPS = 8;
 template <int BLOCK>
 __device__ void block_update(const InstDesc& d, float* u0_row) {
     constexpr int W = BLOCK / 32;
-    constexpr int ACTIVE = BLOCK / 24;  // groups processed at once (24 lanes each, two dims per lane)
+    constexpr int ACTIVE = BLOCK / 12;  // groups processed at once (12 lanes each, four dims per lane)
     __shared__ float s_min[W];
     __shared__ double s_z[UPD_GROUPS];
     __shared__ double s_part[UPD_GROUPS][D];
@@ -67,25 +67,42 @@ __device__ void block_update(const InstDesc& d, float* u0_row) {
 #pragma unroll
     for (int w = 1; w < W; w++) Lmin = fminf(Lmin, s_min[w]);
     const bool ok = finite_f(Lmin);
-    const int li = tid % 24;
-    for (int g = tid / 24; g < UPD_GROUPS && tid < ACTIVE * 24; g += ACTIVE) {
-        float s0 = 0.f, s1 = 0.f, c0 = 0.f, c1 = 0.f;
+    const int li = tid % 12;
+    for (int g = tid / 12; g < UPD_GROUPS && tid < ACTIVE * 12; g += ACTIVE) {
+        float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
         double z = 0.0;
+        // samples g, g + 8, ... in order; the loads of 8 of them are issued together
+        // (one L2 round trip per 8 samples), the sums still run one sample at a time
+        constexpr int NB = 8;
         if (ok)
-            for (int k = g; k < K; k += UPD_GROUPS) {
-                float l = __ldcg(d.L + k);
-                float w = finite_f(l) ? expf(-(l - Lmin) * d.inv_lambda) : 0.f;
-                z += (double)w;
-                float2 u = __ldcg(reinterpret_cast<const float2*>(d.U + (size_t)k * D) + li);
-                float y0 = w * u.x - c0, y1 = w * u.y - c1;
-                float t0 = s0 + y0, t1 = s1 + y1;
-                c0 = (t0 - s0) - y0;
-                c1 = (t1 - s1) - y1;
-                s0 = t0;
-                s1 = t1;
+            for (int k0 = g; k0 < K; k0 += NB * UPD_GROUPS) {
+                float lb[NB];
+                float4 ub[NB];
+#pragma unroll
+                for (int q = 0; q < NB; q++) {
+                    const int k = k0 + q * UPD_GROUPS;
+                    lb[q] = k < K ? __ldcg(d.L + k) : 0.f;
+                    ub[q] = k < K ? __ldcg(reinterpret_cast<const float4*>(d.U + (size_t)k * D) + li)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int q = 0; q < NB; q++) {
+                    if (k0 + q * UPD_GROUPS >= K) break;
+                    const float l = lb[q];
+                    const float w = finite_f(l) ? expf(-(l - Lmin) * d.inv_lambda) : 0.f;
+                    z += (double)w;
+                    const float u[4] = {ub[q].x, ub[q].y, ub[q].z, ub[q].w};
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {  // compensated (Kahan) sums per dimension
+                        const float y = w * u[e] - c[e];
+                        const float t = s[e] + y;
+                        c[e] = (t - s[e]) - y;
+                        s[e] = t;
+                    }
+                }
             }
-        s_part[g][2 * li] = (double)s0 - (double)c0;
-        s_part[g][2 * li + 1] = (double)s1 - (double)c1;
+#pragma unroll
+        for (int e = 0; e < 4; e++) s_part[g][4 * li + e] = (double)s[e] - (double)c[e];
         if (li == 0) s_z[g] = z;
     }
     __syncthreads();
