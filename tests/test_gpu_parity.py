@@ -361,6 +361,32 @@ def test_fused_update_matches_oracle(K, block):
     ctl2.close()
 
 
+def test_fused_update_all_costs_nonfinite():
+    """an infinite cost weight makes every rollout cost non-finite: the one-kernel
+    step keeps the mean, reports NONFINITE and shifts the kept mean, exactly as
+    the separate update kernel does on the same (all non-finite) costs"""
+    cfg = W.config_trot(K=256, H=12)
+    cost = dict(cfg.cost, w_z=float("inf"))
+    ctl = _mppi.Controller(cfg.robot, cost, cfg.mppi)
+    ctl.set_nominal(cfg.mu0)
+    u0 = np.zeros(12, np.float32)
+    mu = np.zeros(48, np.float32)
+    assert ctl.step(cfg.x0.astype(np.float32), 0, u0_out=u0, mu_out=mu) == _mppi.MPPI_ERR_NONFINITE
+    assert ctl.launch_count() == 1
+    assert np.array_equal(mu, cfg.mu0.astype(np.float32))
+    assert np.array_equal(u0, mu[:12])
+    ref = _mppi.Controller(cfg.robot, cfg.cost, cfg.mppi)
+    ref.set_nominal(cfg.mu0)
+    U = torch.as_tensor(np.tile(cfg.mu0.astype(np.float32), (256, 1))).cuda()
+    L = torch.full((256,), float("inf"), device="cuda")
+    mu_r = np.zeros(48, np.float32)
+    assert ref.update(L, U, n=256, mu_out=mu_r) == _mppi.MPPI_ERR_NONFINITE
+    assert np.array_equal(mu_r, mu)
+    assert np.array_equal(ref.get_nominal().view(np.uint32), ctl.get_nominal().view(np.uint32))
+    ctl.close()
+    ref.close()
+
+
 def test_edge_cases():
     cfg = W.config_stand()
     ctl, m = ctl_for(cfg, K=16)
