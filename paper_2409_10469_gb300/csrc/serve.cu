@@ -269,7 +269,6 @@ static void retire(mppi_server s, Launch& l) {
 static int admit_and_launch(mppi_server s, Launch& l, mppi_status* st) {
     *st = MPPI_OK;
     int n = 0;
-    const int R = s->block / 4;
     while (!s->queue.empty() && n < s->max_robots) {
         Request q = s->queue.front();
         Robot& r = s->robots[q.robot];
@@ -288,6 +287,16 @@ static int admit_and_launch(mppi_server s, Launch& l, mppi_status* st) {
         n++;
     }
     if (n == 0) return 0;
+    // block shape: a set sharing one model runs the parameter-bank kernel at the
+    // server's shape; a mixed set runs the general kernel at 256 threads, one
+    // block per SM, where it needs no spill (at 128 threads it spills to local
+    // memory; on the 64-robot mix 256 x 1 is the autotuner's choice)
+    BatchArgs a;
+    memset(&a, 0, sizeof(a));
+    set_uniform(a, l.h_desc, n);
+    const int block = a.uniform ? s->block : 256;
+    const int bpsm = a.uniform ? s->bpsm : 1;
+    const int R = block / 4;
     // work items, longest horizons first
     std::vector<int> order(n);
     for (int i = 0; i < n; i++) order[i] = i;
@@ -309,8 +318,6 @@ static int admit_and_launch(mppi_server s, Launch& l, mppi_status* st) {
     ok(cudaMemcpyAsync(l.d_steps, l.h_steps, n * sizeof(uint32_t), cudaMemcpyHostToDevice, l.st));
     ok(cudaMemsetAsync(l.d_next, 0, sizeof(int), l.st));
     ok(cudaMemsetAsync(l.d_done, 0, n * sizeof(unsigned), l.st));
-    BatchArgs a;
-    memset(&a, 0, sizeof(a));
     a.desc = l.d_desc;
     a.items = l.d_items;
     a.n_items = l.d_nitems;
@@ -319,8 +326,7 @@ static int admit_and_launch(mppi_server s, Launch& l, mppi_status* st) {
     a.x0s = l.d_x0s;
     a.steps = l.d_steps;
     a.u0s = l.d_u0s;
-    set_uniform(a, l.h_desc, n);
-    ok(launch_batch(a, s->block, s->bpsm * s->sms, l.st));
+    ok(launch_batch(a, block, bpsm * s->sms, l.st));
     ok(cudaMemcpyAsync(l.h_u0s, l.d_u0s, (size_t)n * NJ * sizeof(float), cudaMemcpyDeviceToHost, l.st));
     ok(cudaEventRecord(l.ev, l.st));
     if (e != cudaSuccess) {

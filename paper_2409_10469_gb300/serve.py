@@ -34,7 +34,7 @@ def build_robots(n_robots, seed, K_range=(512, 8192), H_range=(50, 150)):
 
 
 def run(n_robots=64, rate_hz=50.0, duration=1.0, seed=4, budget_bytes=512 << 20,
-        K_range=(512, 8192), H_range=(50, 150), warmup=0.1):
+        K_range=(512, 8192), H_range=(50, 150), warmup=0.1, capacity=False):
     """Serve Poisson arrivals for `duration` s; returns a metrics dict."""
     specs, ctls, x0s = build_robots(n_robots, seed, K_range, H_range)
     server = _mppi.Server(budget_bytes, n_robots, max(K for _, K, _ in specs))
@@ -85,9 +85,35 @@ def run(n_robots=64, rate_hz=50.0, duration=1.0, seed=4, budget_bytes=512 << 20,
         "budget_bytes": int(budget_bytes),
     }
     server.close()
+    if capacity:
+        out["capacity"] = batch_capacity(specs, ctls, x0s)
     for c in ctls:
         c.close()
     return out
+
+
+def batch_capacity(specs, ctls, x0s, steps=10):
+    """What the GPU sustains on this exact mix: every robot's solve in one
+    persistent batch launch per step (autotuned block shape), CUDA events over
+    `steps` steps -> rollout-steps/s; the serving rate is read against it."""
+    import torch
+    batch = _mppi.Batch(ctls)
+    X = np.zeros((len(ctls), 50), np.float32)
+    for i, x in enumerate(x0s):
+        X[i, :len(x)] = x
+    block, bpsm, _ = batch.autotune(X)
+    batch.step(X, np.zeros(len(ctls), np.uint32))  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for s in range(steps):
+        batch.step(X, np.full(len(ctls), 1 + s, np.uint32))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    batch.close()
+    work = sum(K * H for _, K, H in specs)
+    return {"ms_per_batch_step": ms, "rollout_steps_per_s": work / (ms * 1e-3), "shape": [block, bpsm]}
 
 
 def main():
@@ -101,11 +127,13 @@ def main():
     ap.add_argument("--budget-mb", type=int, default=512)
     ap.add_argument("--k-min", type=int, default=512)
     ap.add_argument("--k-max", type=int, default=8192)
+    ap.add_argument("--capacity", action="store_true",
+                    help="also time every robot's solve as one batch launch (the mix's GPU capacity)")
     a = ap.parse_args()
     from . import build as B
     B.build()
     print(json.dumps(run(n_robots=a.robots, rate_hz=a.rate, duration=a.duration, seed=a.seed,
-                         budget_bytes=a.budget_mb << 20, K_range=(a.k_min, a.k_max))))
+                         budget_bytes=a.budget_mb << 20, K_range=(a.k_min, a.k_max), capacity=a.capacity)))
 
 
 if __name__ == "__main__":
