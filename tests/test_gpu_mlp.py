@@ -71,11 +71,12 @@ def test_forward_matches_oracle(B):
     assert np.array_equal(Yd.cpu().numpy(), Y)
 
 
-@pytest.mark.parametrize("B", [256, 129, 1000, 3])
+@pytest.mark.parametrize("B", [256, 129, 1000, 3, 4096])
 def test_gradient_matches_oracle(B):
     """the backward pass reads K-major transposed copies; the weight gradients
-    sum over the batch in K ranges (1000 samples: 16 chunks, 4 ranges)"""
-    net = _mppi.MLP(1024)
+    sum over the batch in K ranges (1000 samples: 16 chunks, 4 ranges; 4096: 64
+    chunks, 16 ranges, and the forward in 64-wide column tiles)"""
+    net = _mppi.MLP(4096)
     p = M.init_params(6)
     net.set_params(p)
     X, T = data(B, 2)
