@@ -25,6 +25,38 @@ constexpr int UPD_TILE = D;   // parameters per dimension tile
 
 __device__ __forceinline__ bool finitef(float x) { return fabsf(x) <= 3.402823466e38f; }
 
+// One warp's share of a CTA chunk: samples k = kb, kb + UPD_WARPS, ... < ke, the
+// lane's parameter pair u2[k * row2] weighted by w_k = exp(-(L_k - L_min) / lambda)
+// (0 for a non-finite cost) into compensated (Kahan) sums, one sample at a time
+// in order; the loads of 8 samples are issued together (one L2 round trip each)
+__device__ __forceinline__ void sum_chunk(const float* L, const float2* u2, int row2, int kb, int ke, float Lmin,
+                                          float inv_lambda, float& s0, float& s1, float& c0, float& c1) {
+    constexpr int NB = 8;
+    for (int kk = kb; kk < ke; kk += NB * UPD_WARPS) {
+        float lb[NB];
+        float2 ub[NB];
+#pragma unroll
+        for (int q = 0; q < NB; q++) {
+            const int k = kk + q * UPD_WARPS;
+            lb[q] = k < ke ? __ldg(L + k) : 0.f;
+            ub[q] = k < ke ? __ldg(u2 + (size_t)k * row2) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < NB; q++) {
+            if (kk + q * UPD_WARPS >= ke) break;
+            const float l = lb[q];
+            const float w = finitef(l) ? expf(-(l - Lmin) * inv_lambda) : 0.f;
+            const float2 u = ub[q];
+            float y0 = w * u.x - c0, y1 = w * u.y - c1;
+            float t0 = s0 + y0, t1 = s1 + y1;
+            c0 = (t0 - s0) - y0;
+            c1 = (t1 - s1) - y1;
+            s0 = t0;
+            s1 = t1;
+        }
+    }
+}
+
 // Knot representations (48 parameters): one parameter tile.
 __global__ void __launch_bounds__(UPD_THREADS) k_update_knots(UpdateArgs a) {
     __shared__ float s_min[UPD_WARPS];
@@ -65,19 +97,9 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_knots(UpdateArgs a) {
     if (lane == 0) s_z[warp] = z;
     // sum_k w_k U_k: warp w takes k0 + w, k0 + w + 8, ...; lane i < 24 owns dims 2i, 2i + 1
     float s0 = 0.f, s1 = 0.f, c0 = 0.f, c1 = 0.f;
-    if (ok && lane < D / 2) {
-        for (int k = k0 + warp; k < k1; k += UPD_WARPS) {
-            float l = __ldg(a.L + k);
-            float w = finitef(l) ? expf(-(l - Lmin) * a.inv_lambda) : 0.f;
-            float2 u = __ldg(reinterpret_cast<const float2*>(a.U + (size_t)k * D) + lane);
-            float y0 = w * u.x - c0, y1 = w * u.y - c1;
-            float t0 = s0 + y0, t1 = s1 + y1;
-            c0 = (t0 - s0) - y0;
-            c1 = (t1 - s1) - y1;
-            s0 = t0;
-            s1 = t1;
-        }
-    }
+    if (ok && lane < D / 2)
+        sum_chunk(a.L, reinterpret_cast<const float2*>(a.U) + lane, D / 2, k0 + warp, k1, Lmin, a.inv_lambda, s0, s1,
+                  c0, c1);
     if (lane < D / 2) {
         s_part[warp][2 * lane] = (double)s0 - (double)c0;
         s_part[warp][2 * lane + 1] = (double)s1 - (double)c1;
@@ -169,19 +191,9 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_tiled(UpdateArgs a) {
     // parameters d0 + 2i, d0 + 2i + 1 (Dp is even, so a pair never straddles the end)
     const bool own = lane < UPD_TILE / 2 && d0 + 2 * lane < Dp;
     float s0 = 0.f, s1 = 0.f, c0 = 0.f, c1 = 0.f;
-    if (ok && own) {
-        for (int k = k0 + warp; k < k1; k += UPD_WARPS) {
-            float l = __ldg(a.L + k);
-            float w = finitef(l) ? expf(-(l - Lmin) * a.inv_lambda) : 0.f;
-            float2 u = __ldg(reinterpret_cast<const float2*>(a.U + (size_t)k * Dp + d0) + lane);
-            float y0 = w * u.x - c0, y1 = w * u.y - c1;
-            float t0 = s0 + y0, t1 = s1 + y1;
-            c0 = (t0 - s0) - y0;
-            c1 = (t1 - s1) - y1;
-            s0 = t0;
-            s1 = t1;
-        }
-    }
+    if (ok && own)
+        sum_chunk(a.L, reinterpret_cast<const float2*>(a.U + d0) + lane, Dp / 2, k0 + warp, k1, Lmin, a.inv_lambda, s0,
+                  s1, c0, c1);
     if (lane < UPD_TILE / 2) {
         s_part[warp][2 * lane] = (double)s0 - (double)c0;
         s_part[warp][2 * lane + 1] = (double)s1 - (double)c1;
