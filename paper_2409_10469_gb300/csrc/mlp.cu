@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(256) k_mlp_small(SmallFwdArgs a) {
         for (int b = 0; b < SMB; b++) acc[b] = 0.f;
         if (j < nout) {
             const uint4* wr = reinterpret_cast<const uint4*>(a.W[l] + (long)j * K);
-#pragma unroll 2
+#pragma unroll 8
             for (int k8 = 0; k8 < K / 8; k8++) {
                 const uint4 q = __ldg(wr + k8);
                 const __nv_bfloat162* w2 = reinterpret_cast<const __nv_bfloat162*>(&q);
