@@ -78,7 +78,6 @@ __device__ __forceinline__ uint32_t sw64(int r, int c) { return (uint32_t)(r * 6
 template <int NBUF>
 __device__ __forceinline__ void gt_epilogue(const TmaGemm& g, int m0, int nb, int sp, const float (&v)[32],
                                             unsigned char* S, uint32_t s_addr, int lane) {
-    const int m = m0 + lane;
     const int ncol = min(32, g.N - nb);
     const bool bias = g.epi == EPI_BIAS || g.epi == EPI_BIAS_GELU;
     if (lane == 0) tc::bulk_wait_read<NBUF - 1>();
