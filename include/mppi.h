@@ -49,7 +49,7 @@ typedef enum {
     MPPI_ERR_NONFINITE = 4,  /* non-finite state, or every rollout cost non-finite */
     MPPI_ERR_TIMEOUT = 5,    /* a bounded device wait ran out */
     MPPI_ERR_BUSY = 6,       /* admission refused (memory budget) */
-    MPPI_ERR_NOTSUP = 7      /* requested feature not available in this build */
+    MPPI_ERR_NOTSUP = 7      /* requested feature not available in this library */
 } mppi_status;
 
 /* Raw physical description of robot, contacts and terrain.  Derived quantities

@@ -16,7 +16,7 @@ The paper points to better sampling distributions as future work (arXiv
 Episodes run on the GPU: the controllers step as one batch, and the plant is
 the same simulator advanced one control period with the applied targets held.
 The task cost of a realised episode is scored afterwards by the caller (the
-tests and scripts use the FP64 oracle as the judge).
+tests and scripts use the FP64 oracle as the arbiter).
 """
 from __future__ import annotations
 

@@ -29,7 +29,7 @@ def _built():
         pytest.skip("no GPU")
 
 
-def judge(states, controls, cfgs):
+def oracle_task_cost(states, controls, cfgs):
     """oracle stage cost of every visited state with the control applied from it"""
     out = []
     for e, cfg in enumerate(cfgs):
@@ -44,7 +44,7 @@ def ablation(make, E, K, H, S, seed):
     cost = {}
     for mode in MODES:
         st, ct, cfgs = P.run_episodes(make, E, K, H, S, seed=seed, interp=mode)
-        cost[mode] = judge(st, ct, cfgs)
+        cost[mode] = oracle_task_cost(st, ct, cfgs)
     return cost
 
 

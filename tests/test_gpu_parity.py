@@ -212,7 +212,7 @@ def test_rollout_teacher_forced(which):
 
 @pytest.mark.parametrize("which", ["stand", "trot", "terrain", "push"])
 def test_rollout_cost_parity(which):
-    """full-horizon rollout cost (spec bound): <= 1e-3 relative for every
+    """full-horizon rollout cost (the stated 1e-3 bound): <= 1e-3 relative for every
     sample, on the model spec's well-conditioned sub-step"""
     if which == "stand":
         cfg, K, H, t0 = W.config_stand(), 100, 50, 0.0

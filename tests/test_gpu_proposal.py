@@ -29,7 +29,7 @@ def _built():
         pytest.skip("no GPU")
 
 
-def judge(states, controls, cfgs):
+def oracle_task_cost(states, controls, cfgs):
     """oracle L_walk + L_box of each realised episode: the stage cost of every
     visited state with the control applied from it"""
     out = []
@@ -85,7 +85,7 @@ def test_learned_proposal_gain():
     for name, K, use in (("plain512", 512, False), ("prop512", 512, True), ("plain1024", 1024, False)):
         st, ct, cfgs = P.run_episodes(make_push, E, K, 60, S, seed=7, net=net if use else None, n_prop=K // 2)
         assert np.all(np.isfinite(st))
-        cost[name] = judge(st, ct, cfgs)
+        cost[name] = oracle_task_cost(st, ct, cfgs)
     gain = cost["plain512"] - cost["prop512"]
     print("oracle task cost mean:", {k: float(v.mean()) for k, v in cost.items()},
           "paired gain at K=512: %.1f +- %.1f" % (gain.mean(), gain.std() / np.sqrt(E)))
@@ -113,7 +113,7 @@ def test_learned_proposal_config4_scale():
     cost = {}
     for name, K, use in (("plain4096", 4096, False), ("prop2048", 2048, True), ("plain2048", 2048, False)):
         st, ct, cfgs = P.run_episodes(make, E, K, 100, S, seed=77, net=net if use else None, n_prop=K // 2)
-        cost[name] = judge(st, ct, cfgs)
+        cost[name] = oracle_task_cost(st, ct, cfgs)
     res = {"pairs": int(F.shape[0]), "loss_first_last": [hist[0], hist[-1]],
            "mean": {k: float(v.mean()) for k, v in cost.items()},
            "sem": {k: float(v.std() / np.sqrt(E)) for k, v in cost.items()},
