@@ -389,6 +389,48 @@ def test_fused_update_all_costs_nonfinite():
     ref.close()
 
 
+def test_closed_loop_ten_control_steps_stand():
+    """the stand workload as specified (flat plane, K = 64, H = 50, dt = 0.01,
+    sigma 0.2, lambda 0.1): ten control steps in closed loop.  Each step runs on
+    the GPU (one kernel) from the state the loop has reached; from the same state
+    and nominal the oracle's costs of the same samples agree with the GPU's to
+    1e-3, and the step's mean equals the oracle's update of those samples on the
+    GPU's costs to 4e-6; the plant (the oracle's simulator) then advances one
+    control period with the applied targets, so every step of the loop is checked
+    (trajectory-level parity over many steps is ill-posed: Eq. 1 amplifies
+    rounding differences between near-equal costs)"""
+    cfg = W.config_stand(K=64, H=50)
+    m = cfg.mppi
+    world = O.World(cfg.robot)
+    ctl = _mppi.Controller(cfg.robot, cfg.cost, m)
+    ctl.set_nominal(cfg.mu0)
+    costs = _mppi.Controller(cfg.robot, cfg.cost, m)
+    x = cfg.x0.astype(np.float32).astype(np.float64)
+    h = m["dt"] / m["n_sub"]
+    for step in range(10):
+        x32 = x.astype(np.float32)
+        nominal = ctl.get_nominal()
+        u0 = np.zeros(12, np.float32)
+        mu = np.zeros(48, np.float32)
+        assert ctl.step(x32, step, u0_out=u0, mu_out=mu) == 0
+        t0 = step * m["ctrl_steps"] * m["dt"]
+        U_o = O.sample(m, nominal, step)
+        L = torch.empty(m["K"], device="cuda")
+        costs.rollouts(dev(x32), U=dev(U_o), n=m["K"], L_out=L, t0=t0)
+        Lg = L.cpu().numpy()
+        Lo = O.rollouts(world, cfg.cost, m, t0, x32.astype(np.float64), U_o)
+        assert (np.abs(Lg - Lo) / np.maximum(np.abs(Lo), 1.0)).max() <= 1e-3, step
+        _, mu_o, _ = O.update(Lg, U_o, m["lam"])
+        assert np.abs(mu - mu_o).max() <= 4e-6 * max(1.0, np.abs(mu_o).max()), step
+        assert np.array_equal(u0, mu[:12])
+        for _ in range(m["ctrl_steps"]):
+            x = O.dt_steps(world, x[None], u0.astype(np.float64)[None], m["n_sub"], h)[0]
+        assert np.all(np.isfinite(x))
+    assert ctl.launch_count() == 10
+    ctl.close()
+    costs.close()
+
+
 def test_edge_cases():
     cfg = W.config_stand()
     ctl, m = ctl_for(cfg, K=16)
