@@ -292,6 +292,68 @@ def full_occupancy_roofline(cfg_fn, F, flush, peak, steps=30):
             "frac": ach / peak, "note": "same kernel, two warps per scheduler (the metric's K = 4096 fills one)"}
 
 
+def proposal_form(flush, steps=200, warmup=10):
+    """The learned-proposal form beside the plain one: the same trot workload at
+    K = 2048 with half the samples drawn around the network's mean (random-init
+    weights of the network's architecture; timing does not depend on them).  One
+    control step = the features of the current state, the network's forward
+    (small-batch kernel), the proposal handed to the controller, and the control
+    step (one kernel) -- all device-resident on one stream, enqueued by one call;
+    timed too as the four separate calls.  CUDA events around each step, L2
+    flushed between steps."""
+    import torch
+    from paper_2409_10469_gb300 import _mppi, workloads as W
+    K = K_BENCH // 2
+    cfg = W.config_trot(K=K, H=H_BENCH)
+    m = dict(cfg.mppi, n_prop=K // 2)
+    st = torch.cuda.Stream()
+    ctl = _mppi.Controller(cfg.robot, cfg.cost, m, stream=st.cuda_stream)
+    ctl.set_nominal(cfg.mu0)
+    net = _mppi.MLP(1, stream=st.cuda_stream)
+    net.set_params(W.mlp_init(0))
+    x0 = torch.tensor(cfg.x0, dtype=torch.float32, device="cuda")
+    feat = torch.empty((1, 62), dtype=torch.float32, device="cuda")
+    mu_p = torch.empty((1, 48), dtype=torch.float32, device="cuda")
+    u0 = torch.empty(12, dtype=torch.float32, device="cuda")
+
+    def four(s):
+        ctl.features(x0[None], s, out=feat)
+        net.forward(feat, out=mu_p)
+        ctl.set_proposal(mu_p[0])
+        ctl.step(x0, s, u0_out=u0)
+
+    def one(s):
+        ctl.step_proposal(net, x0, s, u0_out=u0)
+
+    def timed(fn):
+        for s in range(warmup):
+            fn(s)
+        st.synchronize()
+        ms = []
+        for s in range(steps):
+            with torch.cuda.stream(st):
+                flush.fill_(float(s))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn(warmup + s)
+            e1.record(st)
+            st.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return np.array(ms)
+
+    ms4 = timed(four)
+    ms = timed(one)
+    net.close()
+    ctl.close()
+    t = float(ms.mean())
+    return {"K": K, "n_prop": K // 2, "H": H_BENCH, "ms_per_step": t,
+            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+            "rollout_steps_per_s": K * H_BENCH / (t * 1e-3),
+            "four_calls_ms_per_step": float(ms4.mean()),
+            "step": "mppi_step_proposal: features + network forward + proposal + control step in one call "
+                    "on one stream (four_calls: the same as four separate calls)"}
+
+
 def run_ours(args):
     import torch
     from paper_2409_10469_gb300 import _mppi, flops as F, workloads as W
@@ -388,6 +450,7 @@ def run_ours(args):
     sm_max = (peaks or {}).get("sm_max_mhz", 2070.0)
     peak = F.fp32_peak_tflops(152, sm_max)
     full_occ = full_occupancy_roofline(W.config_trot, F, flush, peak)
+    prop = proposal_form(flush)
     value = D.job_throughput(K_BENCH * H_BENCH, world_size, mean_ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "rollout-steps/s", "n_gpus": world_size,
@@ -405,6 +468,8 @@ def run_ours(args):
         "roofline_aux": {"k_sample": hbm_line(F.sample_bytes(K_BENCH), comp["k_sample"], peaks),
                          "k_update": hbm_line(F.update_bytes(K_BENCH), comp["k_update"], peaks)},
         "roofline_full_occupancy": full_occ,
+        # the learned-proposal form (K = 2048, half the samples around the network's mean)
+        "proposal_form": prop,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": rollout_traffic(),
                      "kernel": "k_rollout", "flops_per_launch": fl,

@@ -330,6 +330,17 @@ mppi_status mppi_features(mppi_handle h, const float* X, int n, uint32_t step, f
  * around it (the first of them is the proposal itself); a non-finite entry
  * falls back to the plain mean.  ARG if the handle has n_prop = 0. */
 mppi_status mppi_set_proposal(mppi_handle h, const float* mu_prop);
+/* The learned-proposal form's control step in one call: the features of x0
+ * (float[nx], host or device) at control index `step`, the network's forward on
+ * them (one small-batch kernel computes both), the result taken as the proposal
+ * mean, and mppi_step -- all enqueued on the handle's stream, with no host round
+ * trip in between (host outputs synchronise as in mppi_step).  Equal to mppi_features ->
+ * mppi_mlp_forward -> mppi_set_proposal -> mppi_step on the same inputs.  The
+ * network's parameters must be complete (mppi_mlp_set_params synchronises; a
+ * training step still running on another stream races with this call).  ARG if
+ * the handle has n_prop = 0 or uses direct targets; NONFINITE as mppi_step. */
+mppi_status mppi_step_proposal(mppi_handle h, mppi_mlp net, const float* x0, uint32_t step, float* u0_out,
+                               float* mu_out);
 /* D[M][N] = A[M][K] B[N][K]^T with BF16 inputs (raw uint16 bits) and FP32
  * accumulation on the tcgen05 tensor cores -- the network's GEMM; device
  * buffers, N <= 256, row-major with K contiguous.  K a multiple of 8, N a

@@ -32,7 +32,7 @@ EXPORTS = ("mppi_create", "mppi_destroy", "mppi_last_error", "mppi_set_nominal",
            "mppi_server_tick", "mppi_server_poll", "mppi_server_stats", "mppi_server_reset_stats",
            "mppi_server_drain", "mppi_mlp_create", "mppi_mlp_destroy", "mppi_mlp_last_error",
            "mppi_mlp_param_count", "mppi_mlp_set_params", "mppi_mlp_get_params", "mppi_mlp_forward",
-           "mppi_mlp_train_step", "mppi_tc_gemm_bf16", "mppi_features", "mppi_set_proposal",
+           "mppi_mlp_train_step", "mppi_tc_gemm_bf16", "mppi_features", "mppi_set_proposal", "mppi_step_proposal",
            "mppi_batch_get_means", "mppi_selftest_wait_timeout", "mppi_param_dim")
 
 # control representations (MPPI_INTERP_* of include/mppi.h; Sec. III-B, Fig. 5)
@@ -161,6 +161,7 @@ def lib():
         L.mppi_mlp_get_params.argtypes = [vp, vp, vp]
         L.mppi_mlp_forward.argtypes = [vp, vp, C.c_int, vp, vp]
         L.mppi_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_float, C.c_float, vp, vp, vp]
+        L.mppi_step_proposal.argtypes = [vp, vp, vp, C.c_uint32, vp, vp]
         L.mppi_tc_gemm_bf16.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, vp]
         L.mppi_features.argtypes = [vp, vp, C.c_int, C.c_uint32, vp]
         L.mppi_batch_get_means.argtypes = [vp, vp, vp]
@@ -322,6 +323,14 @@ class Controller:
         out = np.zeros((n, 62), np.float32) if out is None else out
         self._check(lib().mppi_features(self.h, _ptr(X), n, step, _ptr(out)))
         return out
+
+    def step_proposal(self, net, x0, step, u0_out=None, mu_out=None, check=True):
+        """the learned-proposal step in one call (mppi_step_proposal): features,
+        the network's forward, the proposal, the control step"""
+        rc = lib().mppi_step_proposal(self.h, net.n, _ptr(x0), step, _ptr(u0_out), _ptr(mu_out))
+        if check and rc != MPPI_ERR_NONFINITE:
+            self._check(rc)
+        return rc
 
     def set_proposal(self, mu_prop):
         if mu_prop is not None and isinstance(mu_prop, np.ndarray):

@@ -663,6 +663,29 @@ extern "C" mppi_status mppi_step(mppi_handle h, const float* x0, uint32_t step, 
     return finish_outputs(h, u0_out, mu_out);
 }
 
+extern "C" mppi_status mppi_step_proposal(mppi_handle h, mppi_mlp net, const float* x0, uint32_t step, float* u0_out,
+                                          float* mu_out) {
+    if (!h || !net || !x0) return fail(h, MPPI_ERR_ARG, "null argument");
+    if (h->cfg.n_prop < 1) return fail(h, MPPI_ERR_ARG, "the handle was created with n_prop = 0");
+    if (h->cfg.interp == MPPI_INTERP_DIRECT) return fail(h, MPPI_ERR_ARG, "the proposal is a knot mean");
+    const int nx = h->nx;
+    const float* dx0;
+    if (is_device(x0)) {
+        dx0 = x0;
+    } else {
+        if (!all_finite(x0, nx)) return fail(h, MPPI_ERR_NONFINITE, "x0 not finite");
+        CK(cudaMemcpyAsync(h->d_x0, x0, nx * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        dx0 = h->d_x0;
+    }
+    // the network's forward on the features of x0 (computed in its kernel)
+    // straight into the handle's proposal mean, then the step: two launches on
+    // the handle's stream
+    CK(mppi_mlp_forward_states_dev(net, dx0, nx, 1, mppi_feature_params(h, step), h->d_mu_prop, h->stream));
+    h->launches++;
+    h->has_prop = 1;
+    return mppi_step(h, dx0, step, u0_out, mu_out);
+}
+
 extern "C" mppi_status mppi_set_timing(mppi_handle h, int on) {
     if (!h) return MPPI_ERR_ARG;
     h->timing = on;

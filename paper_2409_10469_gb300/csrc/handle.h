@@ -7,6 +7,7 @@
 #include <string>
 
 #include "../../include/mppi.h"
+#include "features.cuh"
 #include "kernels.h"
 
 struct mppi_handle_s {
@@ -35,6 +36,16 @@ struct mppi_handle_s {
     std::string err;
 };
 
+
+// internal launchers shared by the units (no host synchronisation)
+// what the proposal network's features take besides the state, for this handle at control index `step`
+mppi::FeatParams mppi_feature_params(mppi_handle h, uint32_t step);
+// the network's small-batch forward: n <= 128 device rows dX [n][62] -> dY [n][48]
+cudaError_t mppi_mlp_forward_small_dev(mppi_mlp net, const float* dX, int n, float* dY, cudaStream_t st);
+// the same on the features (features.cuh) of n device states dS (row stride lds),
+// computed inside the forward's kernel
+cudaError_t mppi_mlp_forward_states_dev(mppi_mlp net, const float* dS, int lds, int n, const mppi::FeatParams& fp,
+                                        float* dY, cudaStream_t st);
 
 // implicit-PD armature of one sub-step: h (kd + h kp) + a0
 double mppi_armature(const mppi_model_t& p, double h);

@@ -31,6 +31,7 @@
 
 #include "../../include/mppi.h"
 #include "gemm.h"
+#include "handle.h"
 #include "tc.cuh"
 
 using namespace mppi;
@@ -253,68 +254,152 @@ __global__ void k_to_bf16(const float* x, int B, int in, int ld, __nv_bfloat16* 
 }
 
 // Small-batch forward on the CUDA cores (a control step's inference: a few
-// robots' features).  The tensor-core tile is 128 rows, so a batch of a few
-// samples would run a handful of mostly empty CTAs through four GEMM launches;
-// here one block of 256 threads carries SMB samples through all four layers
-// with the activations in shared memory: thread j computes output neuron j of
-// every sample from its BF16 weight row (16-byte loads; the weights stay in L2
-// across calls).  Rounding points as on the tensor-core path: BF16 inputs,
-// BF16 weights, FP32 accumulation, FP32 pre-activation + bias, BF16 of GELU
-// for the next layer; the last layer's FP32 output is the result.
-constexpr int SMB = 8;          // samples per block
+// robots' features).  A tensor-core tile is 128 rows, so a handful of samples
+// would run mostly empty CTAs through four GEMM launches; and one CTA carrying
+// them through all four layers waits on its 320 KB of weights one dependent
+// load after another (40 us for one sample).  Here a cluster of SC_CL = 8 CTAs
+// carries SC_B samples.  CTA c owns rows [c R_l, (c + 1) R_l) of every layer's
+// weights (R_l = 32, 32, 32, 6) and pulls all four slices (39 KB) into its
+// shared memory with bulk copies at launch, so the weights cost one memory
+// latency, spread over 8 SMs.  Layer by layer, CTA c computes its R_l outputs
+// of every sample and stores them, as BF16, into the activation buffer of all
+// 8 CTAs (distributed shared memory); one cluster barrier separates layers.
+// Thread (r, p) of a layer sums the 16-byte chunks p, p + 8, ... of row r's dot
+// product; three xor shuffles add the 8 parts.  With states as input instead of
+// features, each CTA computes its samples' features (features.cuh) while the
+// weights are in flight.  Rounding points as on the tensor-core path: BF16
+// inputs, BF16 weights, FP32 accumulation, FP32 pre-activation + bias, BF16 of
+// GELU for the next layer; the last layer's FP32 output is the result.
+constexpr int SC_CL = 8;   // CTAs per cluster
+constexpr int SC_B = 8;    // samples per cluster (= the parts of a row, one result per lane)
+constexpr int SC_T = 256;  // threads per CTA: 32 rows x 8 parts
+__host__ __device__ constexpr int sc_k(int l) { return l == 0 ? 64 : 256; }   // input width (padded)
+__host__ __device__ constexpr int sc_rows(int l) { return (l == 3 ? 48 : 256) / SC_CL; }
+__host__ __device__ constexpr int sc_wofs(int l) { return l == 0 ? 0 : sc_wofs(l - 1) + sc_rows(l - 1) * sc_k(l - 1); }
+constexpr int SC_WELEM = sc_wofs(4);  // a CTA's weight slices, BF16 elements
+static_assert(SC_WELEM * 2 + 2 * SC_B * 256 * 2 + 32 <= 48 * 1024, "static shared memory");
+static_assert(SC_B * 62 * 4 <= SC_B * 256 * 2, "feature scratch fits an activation buffer");
+
 struct SmallFwdArgs {
-    const float* X;             // [B][62]
+    const float* X;             // [B][62] features, or nullptr: computed from S
+    const float* S;             // [B][lds] states
+    int lds;
+    FeatParams fp;
     int B;
     const __nv_bfloat16* W[4];  // [out][ld] BF16
     const float* bias[4];       // [out]
     float* Y;                   // [B][48]
+    int* err;                   // set to 1 when a weight copy's wait runs out
+    uint32_t wait_limit;
 };
 
-__global__ void __launch_bounds__(256) k_mlp_small(SmallFwdArgs a) {
-    __shared__ float h[2][SMB][256];
-    const int j = threadIdx.x, b0 = blockIdx.x * SMB;
-    const int nb = min(SMB, a.B - b0);
-    for (int b = 0; b < SMB; b++) {
-        float v = 0.f;
-        if (b < nb && j < 62) v = __bfloat162float(__float2bfloat16(a.X[(long)(b0 + b) * 62 + j]));
-        h[0][b][j] = v;
+__global__ void __cluster_dims__(SC_CL, 1, 1) __launch_bounds__(SC_T) k_mlp_cluster(SmallFwdArgs a) {
+    __shared__ __align__(128) __nv_bfloat16 w_s[SC_WELEM];
+    __shared__ __align__(16) __nv_bfloat16 h_s[2][SC_B][256];
+    __shared__ __align__(8) uint64_t bar[4];
+    const int t = threadIdx.x;
+    const uint32_t c = tc::cluster_rank();
+    const int b0 = (blockIdx.x / SC_CL) * SC_B;
+    const int nb = min(SC_B, a.B - b0);
+    if (t == 0) {
+#pragma unroll
+        for (int l = 0; l < 4; l++) tc::mbar_init(&bar[l], 1);
+#pragma unroll
+        for (int l = 0; l < 4; l++) {
+            const uint32_t bytes = sc_rows(l) * sc_k(l) * 2;
+            tc::mbar_arrive_expect_tx(&bar[l], bytes);
+            tc::bulk_load(tc::smem_u32(w_s + sc_wofs(l)), a.W[l] + (size_t)c * sc_rows(l) * sc_k(l), bytes, &bar[l]);
+        }
     }
-    __syncthreads();
-    int cur = 0;
+    // layer-0 input: BF16 features, zero past 62 and past the last sample
+    if (a.X) {
+        for (int i = t; i < SC_B * 64; i += SC_T) {
+            const int b = i >> 6, k = i & 63;
+            h_s[0][b][k] = __float2bfloat16(b < nb && k < 62 ? a.X[(size_t)(b0 + b) * 62 + k] : 0.f);
+        }
+    } else {
+        float* f_s = reinterpret_cast<float*>(&h_s[1][0][0]);  // [SC_B][62], free until layer 0 writes
+        if (t < nb) state_features(a.S + (size_t)(b0 + t) * a.lds, a.fp, f_s + t * 62);
+        __syncthreads();
+        for (int i = t; i < SC_B * 64; i += SC_T) {
+            const int b = i >> 6, k = i & 63;
+            h_s[0][b][k] = __float2bfloat16(b < nb && k < 62 ? f_s[b * 62 + k] : 0.f);
+        }
+    }
+    // every CTA of the cluster has started and is done with its scratch before
+    // any remote store; the barrier's init is visible to all threads
+    tc::cluster_sync();
+    const uint32_t lim = a.wait_limit ? a.wait_limit : (1u << 22);
+    bool ok = true;
+    const int r = t >> 3, p = t & 7;
 #pragma unroll
     for (int l = 0; l < 4; l++) {
-        const int K = l == 0 ? 64 : 256, nout = l == 3 ? 48 : 256;
-        float acc[SMB];
+        const int K = sc_k(l), R = sc_rows(l), in = l & 1;
+        if (!tc::mbar_wait(&bar[l], 0, lim)) ok = false;
+        if ((t >> 5) * 4 < R) {  // warp-uniform: the warp holds a row of this layer
+            const int rr = min(r, R - 1);
+            const uint4* wrow = reinterpret_cast<const uint4*>(w_s + sc_wofs(l) + rr * K);
+            float acc[SC_B];
 #pragma unroll
-        for (int b = 0; b < SMB; b++) acc[b] = 0.f;
-        if (j < nout) {
-            const uint4* wr = reinterpret_cast<const uint4*>(a.W[l] + (long)j * K);
-#pragma unroll 8
-            for (int k8 = 0; k8 < K / 8; k8++) {
-                const uint4 q = __ldg(wr + k8);
-                const __nv_bfloat162* w2 = reinterpret_cast<const __nv_bfloat162*>(&q);
+            for (int b = 0; b < SC_B; b++) acc[b] = 0.f;
 #pragma unroll
-                for (int t = 0; t < 4; t++) {
-                    const float2 w = __bfloat1622float2(w2[t]);
-                    const int k = 8 * k8 + 2 * t;
+            for (int i = 0; i < K / 64; i++) {
+                const int ci = i * 8 + p;
+                const uint4 wq = wrow[ci];
+                const __nv_bfloat162* w2 = reinterpret_cast<const __nv_bfloat162*>(&wq);
+                float w[8];
 #pragma unroll
-                    for (int b = 0; b < SMB; b++) {
-                        acc[b] = fmaf(w.x, h[cur][b][k], acc[b]);
-                        acc[b] = fmaf(w.y, h[cur][b][k + 1], acc[b]);
+                for (int q = 0; q < 4; q++) {
+                    const float2 f = __bfloat1622float2(w2[q]);
+                    w[2 * q] = f.x;
+                    w[2 * q + 1] = f.y;
+                }
+#pragma unroll
+                for (int b = 0; b < SC_B; b++) {
+                    const uint4 xq = *reinterpret_cast<const uint4*>(&h_s[in][b][ci * 8]);
+                    const __nv_bfloat162* x2 = reinterpret_cast<const __nv_bfloat162*>(&xq);
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        const float2 f = __bfloat1622float2(x2[q]);
+                        acc[b] = fmaf(w[2 * q], f.x, acc[b]);
+                        acc[b] = fmaf(w[2 * q + 1], f.y, acc[b]);
                     }
                 }
             }
-        }
-        if (l < 3) {
-            const float bj = a.bias[l][j];
+            // the 8 parts of each row are lanes 8j .. 8j + 7: after the butterfly
+            // every lane holds all SC_B sums; lane p keeps sample p's
 #pragma unroll
-            for (int b = 0; b < SMB; b++) h[cur ^ 1][b][j] = __bfloat162float(__float2bfloat16(gelu(acc[b] + bj)));
-        } else if (j < 48) {
-            const float bj = a.bias[l][j];
-            for (int b = 0; b < nb; b++) a.Y[(long)(b0 + b) * 48 + j] = acc[b] + bj;
+            for (int b = 0; b < SC_B; b++) {
+                acc[b] += __shfl_xor_sync(0xffffffffu, acc[b], 1);
+                acc[b] += __shfl_xor_sync(0xffffffffu, acc[b], 2);
+                acc[b] += __shfl_xor_sync(0xffffffffu, acc[b], 4);
+            }
+            float v = acc[0];
+#pragma unroll
+            for (int b = 1; b < SC_B; b++)
+                if (p == b) v = acc[b];
+            if (r < R) {
+                const int o = (int)c * R + r;
+                const float z = v + __ldg(a.bias[l] + o);
+                if (l < 3) {
+                    const uint16_t y = __bfloat16_as_ushort(__float2bfloat16(gelu(z)));
+                    const uint32_t loc = tc::smem_u32(&h_s[in ^ 1][p][o]);
+#pragma unroll
+                    for (int q = 0; q < SC_CL; q++) tc::st_cluster_u16(tc::cluster_map(loc, q), y);
+                } else if (p < nb) {
+                    a.Y[(size_t)(b0 + p) * 48 + o] = z;
+                }
+            }
         }
-        cur ^= 1;
-        __syncthreads();
+        // layer l's outputs are in every CTA before layer l + 1 reads them, and
+        // no CTA still reads the buffer layer l + 1 overwrites
+        if (l < 3) tc::cluster_sync();
+    }
+    if (!ok) {
+        atomicExch(a.err, 1);
+        // the copies still in flight land before this CTA's shared memory is released
+#pragma unroll
+        for (int l = 0; l < 4; l++) tc::mbar_wait(&bar[l], 0, lim);
     }
 }
 
@@ -687,6 +772,35 @@ static mppi_status check_err(mppi_mlp net, cudaStream_t st) {
     return MPPI_OK;
 }
 
+static cudaError_t launch_small(mppi_mlp net, const float* dX, const float* dS, int lds, const FeatParams* fp, int n,
+                                float* dY, cudaStream_t st) {
+    if (!net || n < 1 || n > SMALL_BATCH || n > net->max_batch) return cudaErrorInvalidValue;
+    SmallFwdArgs a = {};
+    a.X = dX;
+    a.S = dS;
+    a.lds = lds;
+    if (fp) a.fp = *fp;
+    a.B = n;
+    for (int l = 0; l < NL; l++) {
+        a.W[l] = net->d_wb[l];
+        a.bias[l] = net->d_p + net->bofs[l];
+    }
+    a.Y = dY;
+    a.err = net->d_err;
+    k_mlp_cluster<<<SC_CL * ((n + SC_B - 1) / SC_B), SC_T, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t mppi_mlp_forward_small_dev(mppi_mlp net, const float* dX, int n, float* dY, cudaStream_t st) {
+    return launch_small(net, dX, nullptr, 0, nullptr, n, dY, st);
+}
+
+cudaError_t mppi_mlp_forward_states_dev(mppi_mlp net, const float* dS, int lds, int n, const FeatParams& fp, float* dY,
+                                        cudaStream_t st) {
+    if (!dS || lds < fp.nx) return cudaErrorInvalidValue;
+    return launch_small(net, nullptr, dS, lds, &fp, n, dY, st);
+}
+
 extern "C" mppi_status mppi_mlp_forward(mppi_mlp net, const float* X, int B, float* Y, void* stream) {
     if (!net || !X || !Y || B < 1 || B > net->max_batch) return MPPI_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
@@ -698,19 +812,10 @@ extern "C" mppi_status mppi_mlp_forward(mppi_mlp net, const float* X, int B, flo
             dX = net->d_X;
         }
         const bool dev = mdev(Y);
-        SmallFwdArgs a;
-        a.X = dX;
-        a.B = B;
-        for (int l = 0; l < NL; l++) {
-            a.W[l] = net->d_wb[l];
-            a.bias[l] = net->d_p + net->bofs[l];
-        }
-        a.Y = dev ? Y : net->d_z[NL - 1];
-        k_mlp_small<<<(B + SMB - 1) / SMB, 256, 0, st>>>(a);
-        MCK(cudaGetLastError());
+        MCK(mppi_mlp_forward_small_dev(net, dX, B, dev ? Y : net->d_z[NL - 1], st));
         if (!dev) {
             MCK(cudaMemcpyAsync(Y, net->d_z[NL - 1], (size_t)B * OUT * 4, cudaMemcpyDeviceToHost, st));
-            MCK(cudaStreamSynchronize(st));
+            return check_err(net, st);
         }
         return MPPI_OK;
     }

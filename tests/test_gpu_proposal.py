@@ -125,3 +125,33 @@ def test_learned_proposal_config4_scale():
         with open(path, "w") as f:
             json.dump(res, f, indent=1)
     assert np.all(np.isfinite([v.mean() for v in cost.values()]))
+
+
+def test_step_proposal_one_call_equals_four_calls():
+    """mppi_step_proposal (features, forward, proposal, step on the handle's stream)
+    gives bit-for-bit the outputs of features -> forward -> set_proposal -> step,
+    over a short closed loop, with host and with device x0"""
+    cfg = W.config_push(K=1024, H=60, seed=11)
+    m = dict(cfg.mppi, n_prop=512)
+    rng = np.random.default_rng(5)
+    net = _mppi.MLP(64)
+    net.set_params((rng.standard_normal(net.nparam) * 0.05).astype(np.float32))
+    a = _mppi.Controller(cfg.robot, cfg.cost, m)
+    b = _mppi.Controller(cfg.robot, cfg.cost, m)
+    x = W.random_states(1, 3, box=True)[0].astype(np.float32)
+    for c in (a, b):
+        c.set_nominal(W.stand_mu())
+    ua, ub = np.zeros(12, np.float32), np.zeros(12, np.float32)
+    mua, mub = np.zeros(48, np.float32), np.zeros(48, np.float32)
+    for step in range(4):
+        F = a.features(x[None], step)
+        mp = net.forward(F)[0]
+        a.set_proposal(mp)
+        a.step(x, step, ua, mua)
+        xin = x if step % 2 == 0 else torch.tensor(x).cuda()
+        b.step_proposal(net, xin, step, ub, mub)
+        assert np.array_equal(ua.view(np.uint32), ub.view(np.uint32)), step
+        assert np.array_equal(mua.view(np.uint32), mub.view(np.uint32)), step
+        x = x + np.float32(0.01) * np.float32(step + 1)
+    c0 = _mppi.Controller(cfg.robot, cfg.cost, cfg.mppi)
+    assert c0.step_proposal(net, x, 0, ub, mub, check=False) == _mppi.MPPI_ERR_ARG
