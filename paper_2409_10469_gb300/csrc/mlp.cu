@@ -258,27 +258,30 @@ __global__ void k_to_bf16(const float* x, int B, int in, int ld, __nv_bfloat16* 
 // would run mostly empty CTAs through four GEMM launches; and one CTA carrying
 // them through all four layers waits on its 320 KB of weights one dependent
 // load after another (40 us for one sample).  Here a cluster of SC_CL = 8 CTAs
-// carries SC_B samples.  CTA c owns rows [c R_l, (c + 1) R_l) of every layer's
-// weights (R_l = 32, 32, 32, 6) and pulls all four slices (39 KB) into its
-// shared memory with bulk copies at launch, so the weights cost one memory
-// latency, spread over 8 SMs.  Layer by layer, CTA c computes its R_l outputs
-// of every sample and stores them, as BF16, into the activation buffer of all
-// 8 CTAs (distributed shared memory); one cluster barrier separates layers.
-// Thread (r, p) of a layer sums the 16-byte chunks p, p + 8, ... of row r's dot
-// product; three xor shuffles add the 8 parts.  With states as input instead of
-// features, each CTA computes its samples' features (features.cuh) while the
-// weights are in flight.  Rounding points as on the tensor-core path: BF16
-// inputs, BF16 weights, FP32 accumulation, FP32 pre-activation + bias, BF16 of
-// GELU for the next layer; the last layer's FP32 output is the result.
+// carries SB <= 8 samples (SB = 1, 2, 4 or 8, the fewest that hold them).
+// CTA c owns rows [c R_l, (c + 1) R_l) of every layer's weights (R_l = 32, 32,
+// 32, 6) and pulls all four slices (39 KB) into its shared memory with bulk
+// copies at launch, so the weights cost one memory latency, spread over 8 SMs.
+// Layer by layer, CTA c computes its R_l outputs of every sample and stores
+// them into the activation buffer of all 8 CTAs (distributed shared memory, 4
+// rows of a sample per 16-byte store); one cluster barrier separates layers.
+// Thread (r, p) of a layer sums row r's dot product over k = 64 i + 4 p + {0..3}
+// and 64 i + 32 + 4 p + {0..3} (so that 8 threads' 16-byte activation loads
+// cover 128 contiguous bytes); three xor shuffles add the 8 parts.  With
+// states as input instead of features, each CTA computes its samples'
+// features (features.cuh) while the weights are in flight.  Rounding points as
+// on the tensor-core path: BF16 inputs, BF16 weights, FP32 accumulation, FP32
+// pre-activation + bias, BF16 of GELU for the next layer (held as FP32); the
+// last layer's FP32 output is the result.
 constexpr int SC_CL = 8;   // CTAs per cluster
-constexpr int SC_B = 8;    // samples per cluster (= the parts of a row, one result per lane)
 constexpr int SC_T = 256;  // threads per CTA: 32 rows x 8 parts
 __host__ __device__ constexpr int sc_k(int l) { return l == 0 ? 64 : 256; }   // input width (padded)
 __host__ __device__ constexpr int sc_rows(int l) { return (l == 3 ? 48 : 256) / SC_CL; }
 __host__ __device__ constexpr int sc_wofs(int l) { return l == 0 ? 0 : sc_wofs(l - 1) + sc_rows(l - 1) * sc_k(l - 1); }
 constexpr int SC_WELEM = sc_wofs(4);  // a CTA's weight slices, BF16 elements
-static_assert(SC_WELEM * 2 + 2 * SC_B * 256 * 2 + 32 <= 48 * 1024, "static shared memory");
-static_assert(SC_B * 62 * 4 <= SC_B * 256 * 2, "feature scratch fits an activation buffer");
+// dynamic shared memory: weights, two activation buffers [SB][256] FP32, 4 mbarriers
+__host__ __device__ constexpr int sc_smem(int SB) { return SC_WELEM * 2 + 2 * SB * 256 * 4 + 4 * 8; }
+static_assert(SC_WELEM * 2 % 16 == 0, "activation buffers 16-byte aligned");
 
 struct SmallFwdArgs {
     const float* X;             // [B][62] features, or nullptr: computed from S
@@ -293,17 +296,33 @@ struct SmallFwdArgs {
     uint32_t wait_limit;
 };
 
+template <int SB>
 __global__ void __cluster_dims__(SC_CL, 1, 1) __launch_bounds__(SC_T) k_mlp_cluster(SmallFwdArgs a) {
-    __shared__ __align__(128) __nv_bfloat16 w_s[SC_WELEM];
-    __shared__ __align__(16) __nv_bfloat16 h_s[2][SC_B][256];
-    __shared__ __align__(8) uint64_t bar[4];
-    const int t = threadIdx.x;
+    extern __shared__ __align__(128) unsigned char sc_sm[];
+    __nv_bfloat16* w_s = reinterpret_cast<__nv_bfloat16*>(sc_sm);
+    float* h_s = reinterpret_cast<float*>(sc_sm + SC_WELEM * 2);  // [2][SB][256]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sc_sm + SC_WELEM * 2 + 2 * SB * 256 * 4);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const uint32_t c = tc::cluster_rank();
-    const int b0 = (blockIdx.x / SC_CL) * SC_B;
-    const int nb = min(SC_B, a.B - b0);
-    if (t == 0) {
+    const int b0 = (blockIdx.x / SC_CL) * SB;
+    const int nb = min(SB, a.B - b0);
+    const int rl = lane >> 3, p = lane & 7, r = warp * 4 + rl;
+    // warp 0 issues the weight copies first; the other warps meanwhile load
+    // the given features (element i by thread 32 + i % 224) and every thread
+    // its bias of each layer, all before anything waits on them
+    constexpr int XW = SC_T - 32, XN = (SB * 64 + XW - 1) / XW;
+    float xv[XN];
+    float bias[4];
+    if (warp != 0) {
 #pragma unroll
-        for (int l = 0; l < 4; l++) tc::mbar_init(&bar[l], 1);
+        for (int j = 0; j < XN; j++) {
+            const int i = t - 32 + j * XW, b = i >> 6, k = i & 63;
+            xv[j] = (a.X && i < SB * 64 && b < nb && k < 62) ? __ldg(a.X + (size_t)(b0 + b) * 62 + k) : 0.f;
+        }
+    } else if (lane == 0) {
+#pragma unroll
+        for (int l = 0; l < 4; l++) tc::mbar_init_nofence(&bar[l], 1);
+        tc::mbar_init_fence();
 #pragma unroll
         for (int l = 0; l < 4; l++) {
             const uint32_t bytes = sc_rows(l) * sc_k(l) * 2;
@@ -311,84 +330,96 @@ __global__ void __cluster_dims__(SC_CL, 1, 1) __launch_bounds__(SC_T) k_mlp_clus
             tc::bulk_load(tc::smem_u32(w_s + sc_wofs(l)), a.W[l] + (size_t)c * sc_rows(l) * sc_k(l), bytes, &bar[l]);
         }
     }
-    // layer-0 input: BF16 features, zero past 62 and past the last sample
+#pragma unroll
+    for (int l = 0; l < 4; l++) bias[l] = __ldg(a.bias[l] + (int)c * sc_rows(l) + min(r, sc_rows(l) - 1));
+    // layer-0 input: BF16-rounded features, zero past 62 and past the last sample
     if (a.X) {
-        for (int i = t; i < SC_B * 64; i += SC_T) {
-            const int b = i >> 6, k = i & 63;
-            h_s[0][b][k] = __float2bfloat16(b < nb && k < 62 ? a.X[(size_t)(b0 + b) * 62 + k] : 0.f);
+        if (warp != 0) {
+#pragma unroll
+            for (int j = 0; j < XN; j++) {
+                const int i = t - 32 + j * XW;
+                if (i < SB * 64) h_s[(i >> 6) * 256 + (i & 63)] = __bfloat162float(__float2bfloat16(xv[j]));
+            }
         }
     } else {
-        float* f_s = reinterpret_cast<float*>(&h_s[1][0][0]);  // [SC_B][62], free until layer 0 writes
-        if (t < nb) state_features(a.S + (size_t)(b0 + t) * a.lds, a.fp, f_s + t * 62);
+        float* f_s = h_s + SB * 256;  // [SB][62] in the second buffer, free until layer 0 writes it
+        if (warp == 1 && lane < nb) state_features(a.S + (size_t)(b0 + lane) * a.lds, a.fp, f_s + lane * 62);
         __syncthreads();
-        for (int i = t; i < SC_B * 64; i += SC_T) {
+        for (int i = t; i < SB * 64; i += SC_T) {
             const int b = i >> 6, k = i & 63;
-            h_s[0][b][k] = __float2bfloat16(b < nb && k < 62 ? f_s[b * 62 + k] : 0.f);
+            h_s[b * 256 + k] = __bfloat162float(__float2bfloat16(b < nb && k < 62 ? f_s[b * 62 + k] : 0.f));
         }
     }
-    // every CTA of the cluster has started and is done with its scratch before
-    // any remote store; the barrier's init is visible to all threads
-    tc::cluster_sync();
+    // the input is in place and the barriers' init visible to every thread;
+    // the cluster barrier's wait (before layer 0's first remote store) then
+    // finds every CTA started and done with its scratch
+    __syncthreads();
+    tc::cluster_arrive();
     const uint32_t lim = a.wait_limit ? a.wait_limit : (1u << 22);
     bool ok = true;
-    const int r = t >> 3, p = t & 7;
 #pragma unroll
     for (int l = 0; l < 4; l++) {
-        const int K = sc_k(l), R = sc_rows(l), in = l & 1;
+        const int K = sc_k(l), R = sc_rows(l);
+        const float* hin = h_s + (l & 1) * SB * 256;
+        float* hout = h_s + ((l & 1) ^ 1) * SB * 256;
         if (!tc::mbar_wait(&bar[l], 0, lim)) ok = false;
-        if ((t >> 5) * 4 < R) {  // warp-uniform: the warp holds a row of this layer
-            const int rr = min(r, R - 1);
-            const uint4* wrow = reinterpret_cast<const uint4*>(w_s + sc_wofs(l) + rr * K);
-            float acc[SC_B];
+        if (warp * 4 < R) {  // warp-uniform: the warp holds a row of this layer
+            const __nv_bfloat16* wrow = w_s + sc_wofs(l) + min(r, R - 1) * K;
+            float acc[SB];
 #pragma unroll
-            for (int b = 0; b < SC_B; b++) acc[b] = 0.f;
+            for (int b = 0; b < SB; b++) acc[b] = 0.f;
 #pragma unroll
             for (int i = 0; i < K / 64; i++) {
-                const int ci = i * 8 + p;
-                const uint4 wq = wrow[ci];
-                const __nv_bfloat162* w2 = reinterpret_cast<const __nv_bfloat162*>(&wq);
-                float w[8];
 #pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    const float2 f = __bfloat1622float2(w2[q]);
-                    w[2 * q] = f.x;
-                    w[2 * q + 1] = f.y;
-                }
+                for (int h = 0; h < 2; h++) {
+                    // odd row groups take the halves in the other order: the two
+                    // rows of a half-warp then read different banks
+                    const int k = 64 * i + 32 * (h ^ (rl & 1)) + 4 * p;
+                    const uint2 wq = *reinterpret_cast<const uint2*>(wrow + k);
+                    const float2 w01 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wq.x));
+                    const float2 w23 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&wq.y));
 #pragma unroll
-                for (int b = 0; b < SC_B; b++) {
-                    const uint4 xq = *reinterpret_cast<const uint4*>(&h_s[in][b][ci * 8]);
-                    const __nv_bfloat162* x2 = reinterpret_cast<const __nv_bfloat162*>(&xq);
-#pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        const float2 f = __bfloat1622float2(x2[q]);
-                        acc[b] = fmaf(w[2 * q], f.x, acc[b]);
-                        acc[b] = fmaf(w[2 * q + 1], f.y, acc[b]);
+                    for (int b = 0; b < SB; b++) {
+                        const float4 x = *reinterpret_cast<const float4*>(hin + b * 256 + k);
+                        acc[b] = fmaf(w01.x, x.x, acc[b]);
+                        acc[b] = fmaf(w01.y, x.y, acc[b]);
+                        acc[b] = fmaf(w23.x, x.z, acc[b]);
+                        acc[b] = fmaf(w23.y, x.w, acc[b]);
                     }
                 }
             }
-            // the 8 parts of each row are lanes 8j .. 8j + 7: after the butterfly
-            // every lane holds all SC_B sums; lane p keeps sample p's
+            // the 8 parts of row r are lanes 8 rl .. 8 rl + 7: after the
+            // butterfly each of them holds all SB sums; lane p keeps sample p's
 #pragma unroll
-            for (int b = 0; b < SC_B; b++) {
+            for (int b = 0; b < SB; b++) {
                 acc[b] += __shfl_xor_sync(0xffffffffu, acc[b], 1);
                 acc[b] += __shfl_xor_sync(0xffffffffu, acc[b], 2);
                 acc[b] += __shfl_xor_sync(0xffffffffu, acc[b], 4);
             }
             float v = acc[0];
 #pragma unroll
-            for (int b = 1; b < SC_B; b++)
+            for (int b = 1; b < SB; b++)
                 if (p == b) v = acc[b];
-            if (r < R) {
-                const int o = (int)c * R + r;
-                const float z = v + __ldg(a.bias[l] + o);
-                if (l < 3) {
-                    const uint16_t y = __bfloat16_as_ushort(__float2bfloat16(gelu(z)));
-                    const uint32_t loc = tc::smem_u32(&h_s[in ^ 1][p][o]);
+            const int o = (int)c * R + min(r, R - 1);
+            const float z = v + bias[l];
+            if (l == 0) tc::cluster_wait();  // layer 0 has rows in every warp: all threads wait
+            if (l < 3) {
+                // (row rl, sample p) is on lane 8 rl + p: item (b, q) gathers the
+                // warp's 4 rows of sample b and stores them into CTA q
+                const float y = __bfloat162float(__float2bfloat16(gelu(z)));
 #pragma unroll
-                    for (int q = 0; q < SC_CL; q++) tc::st_cluster_u16(tc::cluster_map(loc, q), y);
-                } else if (p < nb) {
-                    a.Y[(size_t)(b0 + p) * 48 + o] = z;
+                for (int i = 0; i < (SB * 8 + 31) / 32; i++) {
+                    const int item = lane + 32 * i, b = min(item >> 3, SB - 1), q = item & 7;
+                    float4 u;
+                    u.x = __shfl_sync(0xffffffffu, y, b);
+                    u.y = __shfl_sync(0xffffffffu, y, 8 + b);
+                    u.z = __shfl_sync(0xffffffffu, y, 16 + b);
+                    u.w = __shfl_sync(0xffffffffu, y, 24 + b);
+                    if (item < SB * 8)
+                        tc::st_cluster_v4(tc::cluster_map(tc::smem_u32(hout + b * 256 + (int)c * R + warp * 4), q), u);
                 }
+            } else if (r < R && p < nb) {
+                a.Y[(size_t)(b0 + p) * 48 + o] = z;
             }
         }
         // layer l's outputs are in every CTA before layer l + 1 reads them, and
@@ -772,6 +803,19 @@ static mppi_status check_err(mppi_mlp net, cudaStream_t st) {
     return MPPI_OK;
 }
 
+template <int SB>
+static cudaError_t launch_cluster(const SmallFwdArgs& a, int n, cudaStream_t st) {
+    static bool attr = false;  // idempotent; set once per sample count
+    if (!attr) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_mlp_cluster<SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, sc_smem(SB));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_mlp_cluster<SB><<<SC_CL * ((n + SB - 1) / SB), SC_T, sc_smem(SB), st>>>(a);
+    return cudaGetLastError();
+}
+
 static cudaError_t launch_small(mppi_mlp net, const float* dX, const float* dS, int lds, const FeatParams* fp, int n,
                                 float* dY, cudaStream_t st) {
     if (!net || n < 1 || n > SMALL_BATCH || n > net->max_batch) return cudaErrorInvalidValue;
@@ -787,8 +831,10 @@ static cudaError_t launch_small(mppi_mlp net, const float* dX, const float* dS, 
     }
     a.Y = dY;
     a.err = net->d_err;
-    k_mlp_cluster<<<SC_CL * ((n + SC_B - 1) / SC_B), SC_T, 0, st>>>(a);
-    return cudaGetLastError();
+    if (n == 1) return launch_cluster<1>(a, n, st);
+    if (n == 2) return launch_cluster<2>(a, n, st);
+    if (n <= 4) return launch_cluster<4>(a, n, st);
+    return launch_cluster<8>(a, n, st);
 }
 
 cudaError_t mppi_mlp_forward_small_dev(mppi_mlp net, const float* dX, int n, float* dY, cudaStream_t st) {
