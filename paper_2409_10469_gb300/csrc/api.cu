@@ -328,6 +328,11 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
         }
         h->model_key = model_key(h->dm, heights, boxes, MAX_SBOX * 6);
     }
+    if (ok) {
+        ok = cudaHostAlloc((void**)&h->h_box, BOX_FLOATS * sizeof(float), cudaHostAllocMapped) == cudaSuccess &&
+             cudaHostGetDevicePointer((void**)&h->d_box, h->h_box, 0) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+    }
     if (!ok) {
         mppi_destroy(h);
         return MPPI_ERR_OOM;
@@ -358,6 +363,7 @@ extern "C" mppi_status mppi_destroy(mppi_handle h) {
                     h->d_sbox, h->d_B};
     for (void* p : bufs)
         if (p) cudaFree(p);
+    if (h->h_box) cudaFreeHost(h->h_box);
     for (int i = 0; i < 4; i++)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     delete h;
@@ -463,6 +469,8 @@ static RolloutArgs rollout_args(mppi_handle h, const float* x0, int per, const f
     a.inst = h->cfg.inst;
     a.U_out = nullptr;
     a.fuse = 0;  // mppi_step's knot representations fuse the update into the launch
+    a.u0_host = a.mu_host = nullptr;
+    a.status_host = nullptr;
     a.inv_lambda = (float)(1.0 / h->cfg.lambda);
     a.ctrl_steps = h->cfg.ctrl_steps;
     a.mu_w = nullptr;
@@ -562,27 +570,45 @@ static mppi_status do_update(mppi_handle h, const float* dL, const float* dU, in
 }
 
 // copy the step's outputs (u0, mu before the shift) and read the status
-static mppi_status finish_outputs(mppi_handle h, float* u0_out, float* mu_out) {
-    bool any_host = false;
-    if (u0_out) {
-        bool dev = is_device(u0_out);
-        any_host |= !dev;
-        CK(cudaMemcpyAsync(u0_out, h->d_u0, NJ * sizeof(float), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                           h->stream));
-    }
-    if (mu_out) {
-        bool dev = is_device(mu_out);
-        any_host |= !dev;
+// where the caller wants the outputs (u0_out / mu_out may be null)
+struct OutPlace {
+    bool u0_host = false, mu_host = false;
+};
+static OutPlace out_place(const float* u0_out, const float* mu_out) {
+    OutPlace o;
+    o.u0_host = u0_out && !is_device(u0_out);
+    o.mu_host = mu_out && !is_device(mu_out);
+    return o;
+}
+
+// device outputs are copied on the stream; host outputs come through a
+// synchronisation, from the mailbox when the kernel wrote them there (boxed),
+// else by copies from the device buffers
+static mppi_status finish_outputs(mppi_handle h, float* u0_out, float* mu_out, const OutPlace& o, bool boxed) {
+    if (u0_out && (!o.u0_host || !boxed))
+        CK(cudaMemcpyAsync(u0_out, h->d_u0, NJ * sizeof(float),
+                           o.u0_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream));
+    if (mu_out && (!o.mu_host || !boxed))
         CK(cudaMemcpyAsync(mu_out, h->d_mu_upd, (size_t)h->D * sizeof(float),
-                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
-    }
-    if (any_host) {
+                           o.mu_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->stream));
+    if (o.u0_host || o.mu_host) {
         int st = 0;
-        CK(cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        if (!boxed) CK(cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
         CK(cudaStreamSynchronize(h->stream));
+        if (boxed) {
+            const volatile float* box = h->h_box;
+            if (o.u0_host)
+                for (int i = 0; i < NJ; i++) u0_out[i] = box[BOX_U0 + i];
+            if (o.mu_host)
+                for (int i = 0; i < D; i++) mu_out[i] = box[BOX_MU + i];
+            st = reinterpret_cast<const volatile int*>(box)[BOX_STATUS];
+        }
         if (st != 0) return fail(h, MPPI_ERR_NONFINITE, "every rollout cost is non-finite; mean kept");
     }
     return MPPI_OK;
+}
+static mppi_status finish_outputs(mppi_handle h, float* u0_out, float* mu_out) {
+    return finish_outputs(h, u0_out, mu_out, out_place(u0_out, mu_out), false);
 }
 
 extern "C" mppi_status mppi_update(mppi_handle h, const float* L, const float* U, int n, float* mu_out,
@@ -649,6 +675,14 @@ extern "C" mppi_status mppi_step(mppi_handle h, const float* x0, uint32_t step, 
         a.part = h->d_part;
         a.counter = h->d_counter;
     }
+    // host-bound outputs of a fused step: the kernel writes them into the mailbox
+    const OutPlace op = out_place(u0_out, mu_out);
+    const bool boxed = fuse && (op.u0_host || op.mu_host);
+    if (boxed) {
+        a.u0_host = op.u0_host ? h->d_box + BOX_U0 : nullptr;
+        a.mu_host = op.mu_host ? h->d_box + BOX_MU : nullptr;
+        a.status_host = reinterpret_cast<int*>(h->d_box) + BOX_STATUS;
+    }
     CK(launch_rollout(a, rollout_block(h), h->stream));
     h->launches++;
     if (tm) CK(cudaEventRecord(h->ev[2], h->stream));
@@ -660,7 +694,7 @@ extern "C" mppi_status mppi_step(mppi_handle h, const float* x0, uint32_t step, 
         CK(cudaEventRecord(h->ev[3], h->stream));
         h->timed_valid = 1;
     }
-    return finish_outputs(h, u0_out, mu_out);
+    return finish_outputs(h, u0_out, mu_out, op, boxed);
 }
 
 extern "C" mppi_status mppi_step_proposal(mppi_handle h, mppi_mlp net, const float* x0, uint32_t step, float* u0_out,

@@ -10,6 +10,9 @@
 #include "features.cuh"
 #include "kernels.h"
 
+// the mailbox's layout (floats): u0, mu', status (an int)
+constexpr int BOX_U0 = 0, BOX_MU = mppi::NJ, BOX_STATUS = mppi::NJ + mppi::D, BOX_FLOATS = 64;
+
 struct mppi_handle_s {
     mppi_model_t model_in;
     mppi_cost_t cost_in;
@@ -25,6 +28,10 @@ struct mppi_handle_s {
     float *d_x0 = nullptr, *d_u0 = nullptr, *d_hf = nullptr, *d_sbox = nullptr;
     float* d_B = nullptr;  // [H][4] knot weights of each dt step (16-B aligned rows)
     int* d_status = nullptr;
+    // pinned, device-mapped mailbox: u0 [12], mu' [48], status; the control
+    // step's kernel writes host-bound outputs here (no device-to-host copies)
+    float* h_box = nullptr;
+    float* d_box = nullptr;  // its device address
     double* d_wsum = nullptr;
     double* d_part = nullptr;      // update scratch: per-CTA partial sums
     unsigned* d_counter = nullptr;  // update scratch: finished-CTA counter

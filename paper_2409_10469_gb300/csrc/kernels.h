@@ -56,6 +56,12 @@ struct RolloutArgs {
     double* wsum;
     double* part;          // [grid][FUSE_W] (used as float pairs)
     unsigned* counter;     // 0 between launches
+    // the outputs again in pinned, device-mapped host memory (the handle's
+    // mailbox), for callers that want them on the host, or null: u0 [12],
+    // mu' [48], status
+    float* u0_host;
+    float* mu_host;
+    int* status_host;
 };
 
 constexpr int FUSE_W = D + 2;  // per-CTA partial: 48 weighted sums, the weight sum, the CTA's cost minimum

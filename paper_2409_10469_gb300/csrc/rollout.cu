@@ -173,11 +173,16 @@ __device__ __forceinline__ void fused_update(const RolloutArgs& a, float L, cons
         const float mu_new = ok ? (float)(((double)s_sum[0][d].x + (double)s_sum[0][d].y) / Z) : a.mu_w[d];
         s_mu[d] = mu_new;
         if (a.mu_upd) a.mu_upd[d] = mu_new;
-        if (d < NJ) a.u0[d] = mu_new;  // the spline at tau = 0 is knot 0
+        if (a.mu_host) a.mu_host[d] = mu_new;
+        if (d < NJ) {
+            a.u0[d] = mu_new;  // the spline at tau = 0 is knot 0
+            if (a.u0_host) a.u0_host[d] = mu_new;
+        }
     }
     if (tid == 0) {
         if (a.wsum && ok) *a.wsum = Z;
         if (a.status) *a.status = ok ? 0 : 4;
+        if (a.status_host) *a.status_host = ok ? 0 : 4;
         *a.counter = 0u;  // re-arm for the next launch (kernels on one stream are ordered)
     }
     __syncthreads();

@@ -480,3 +480,29 @@ def test_full_size_sampled_parity():
                        np.tile(tabs, 24)).reshape(24, 100).sum(1) + O.stage_costs(world, cfg.cost, tg[:, 100])
     rel = np.abs(L2.cpu().numpy() - sc) / np.maximum(np.abs(sc), 1)
     assert rel.max() <= 1e-5, rel.max()
+
+
+def test_step_outputs_same_bits_on_host_and_device():
+    """Host-bound outputs of the control step are written by its kernel into the
+    handle's pinned, device-mapped mailbox; device-bound ones are copied on the
+    stream.  Every placement of u0 and mu' (both host, both device, mixed) gives
+    the same bits as the all-host run, step after step."""
+    cfg = W.config_trot(K=1000, H=40)
+    ref = _mppi.Controller(cfg.robot, cfg.cost, cfg.mppi)
+    ctl = _mppi.Controller(cfg.robot, cfg.cost, cfg.mppi)
+    for c in (ref, ctl):
+        c.set_nominal(cfg.mu0)
+    x = cfg.x0.astype(np.float32)
+    for s in range(8):
+        u_r, mu_r = np.zeros(12, np.float32), np.zeros(48, np.float32)
+        assert ref.step(x, s, u0_out=u_r, mu_out=mu_r) == _mppi.MPPI_OK
+        u_host, mu_host = s % 2 == 0, (s // 2) % 2 == 0
+        u = np.zeros(12, np.float32) if u_host else torch.zeros(12, device="cuda")
+        mu = np.zeros(48, np.float32) if mu_host else torch.zeros(48, device="cuda")
+        assert ctl.step(x, s, u0_out=u, mu_out=mu) == _mppi.MPPI_OK
+        torch.cuda.synchronize()
+        u = u if u_host else u.cpu().numpy()
+        mu = mu if mu_host else mu.cpu().numpy()
+        assert np.array_equal(u.view(np.uint32), u_r.view(np.uint32)), s
+        assert np.array_equal(mu.view(np.uint32), mu_r.view(np.uint32)), s
+        x = x + np.float32(0.002)
