@@ -37,7 +37,7 @@ METRIC = "rollout-steps/s (MPPI step, K=4096, H=100)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture) of
 # one k_rollout launch on this workload, valid only for the kernel sources whose
 # SHA-256 prefix is given; reported as null once those sources change.
-ROLLOUT_TRAFFIC = {"bytes": 118528, "sources_sha256": "53dafe7b95650ac4"}
+ROLLOUT_TRAFFIC = {"bytes": 161024, "sources_sha256": "cd959651ebbc5f49"}
 ROLLOUT_SOURCES = ("rollout.cu", "rollout.cuh", "common.cuh", "noise.cuh", "kernels.h")
 
 
