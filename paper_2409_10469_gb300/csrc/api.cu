@@ -297,9 +297,9 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
               al((void**)&h->d_L, K * sizeof(float)) && al((void**)&h->d_x0, K * NX_BOX * sizeof(float)) &&
               al((void**)&h->d_u0, NJ * sizeof(float)) && al((void**)&h->d_status, sizeof(int)) &&
               al((void**)&h->d_wsum, sizeof(double)) &&
-              al((void**)&h->d_part, std::max((size_t)UPDATE_MAX_CTAS * (Dp + 1), fused_part_doubles(*cfg)) *
+              al((void**)&h->d_part, std::max(update_part_doubles((int)Dp), fused_part_doubles(*cfg)) *
                                          sizeof(double)) &&
-              al((void**)&h->d_counter, sizeof(unsigned)) &&
+              al((void**)&h->d_counter, update_counters((int)Dp) * sizeof(unsigned)) &&
               al((void**)&h->d_B, (size_t)4 * cfg->H * sizeof(float));
     if (ok && model->terrain == 1) {
         size_t nh = (size_t)model->hf_nx * model->hf_ny;
@@ -346,7 +346,7 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
     if (cudaMemcpy(h->d_mu, mu0.data(), Dp * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->d_B, Bw.data(), Bw.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess ||
-        cudaMemset(h->d_counter, 0, sizeof(unsigned)) != cudaSuccess) {
+        cudaMemset(h->d_counter, 0, update_counters(h->D) * sizeof(unsigned)) != cudaSuccess) {
         mppi_destroy(h);
         return MPPI_ERR_CUDA;
     }
@@ -401,6 +401,10 @@ static mppi_status do_sample(mppi_handle h, uint32_t step, const float* mu_prop,
         const float* mp;
         mppi_status s = stage_in(h, mu_prop, D, h->d_mu_prop, &mp);
         if (s != MPPI_OK) return s;
+        if (!aligned16(mp)) {  // the sampler reads the means as float4
+            CK(cudaMemcpyAsync(h->d_mu_prop, mp, D * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+            mp = h->d_mu_prop;
+        }
         a.mu_prop = mp;
     }
     a.U = U;

@@ -17,6 +17,7 @@ struct SampleArgs {
     int K, n_prop;
     int Dp;                // parameters per sample: 48, or 12 H (DIRECT)
     int interp;            // MPPI_INTERP_*
+    uint32_t g_magic;      // floor(2^32 / (Dp / 4)), set by launch_sample
 };
 
 struct RolloutArgs {
@@ -75,8 +76,8 @@ struct UpdateArgs {
     float* u0;             // [12]
     int* status;           // 0 ok, 4 all costs non-finite
     double* wsum;          // normaliser (FP64) of the last update, optional
-    double* part;          // scratch [UPDATE_MAX_CTAS][Dp + 1] per-CTA partial sums
-    unsigned* counter;     // scratch: CTAs finished (0 between launches)
+    double* part;          // scratch [tiles][grid][50]: per-CTA partial sums, weight sum, cost minimum
+    unsigned* counter;     // scratch [1 + tiles]: CTAs finished (0 between launches)
     int n, H, ctrl_steps;
     float inv_lambda;
     int Dp, interp;        // parameters per sample, MPPI_INTERP_*
@@ -84,6 +85,11 @@ struct UpdateArgs {
 
 constexpr int UPDATE_MAX_CTAS = 128;
 int update_grid(int n);
+// parameter tiles of 48 for Dp parameters per sample, the update scratch's
+// doubles and its counters
+constexpr int update_tiles(int Dp) { return (Dp + D - 1) / D; }
+constexpr size_t update_part_doubles(int Dp) { return (size_t)UPDATE_MAX_CTAS * update_tiles(Dp) * (D + 2); }
+constexpr int update_counters(int Dp) { return 1 + update_tiles(Dp); }
 
 cudaError_t launch_sample(const SampleArgs& a, cudaStream_t st);
 cudaError_t launch_rollout(const RolloutArgs& a, int block, cudaStream_t st);

@@ -28,7 +28,7 @@ using namespace mppi;
 
 namespace {
 
-constexpr size_t PART_DOUBLES = (size_t)UPDATE_MAX_CTAS * (D + 1);
+constexpr size_t PART_DOUBLES = update_part_doubles(D);
 constexpr size_t SCRATCH_BYTES = PART_DOUBLES * sizeof(double) + 256;  // partials + counter slot
 
 static __device__ __align__(256) unsigned char g_update_scratch[SCRATCH_BYTES];

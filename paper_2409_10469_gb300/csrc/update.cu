@@ -2,19 +2,21 @@
 // control u = mu[0] and the receding-horizon shift (Alg. 1, last steps) of
 // arXiv 2409.10469, Sec. II-B.
 //
-// G CTAs split the n samples into contiguous chunks (a second grid dimension T
-// tiles the 12 H parameters of direct targets into groups of 48; the knot
-// representations have one tile and their own kernel).  Every CTA first takes
-// L_min over all n costs (finite only; 4 B per sample, L2-resident), then for
-// its chunk the FP32 weights w_k = exp(-(L_k - L_min)/lambda) (0 if L_k is not
-// finite), their sum in FP64 (the normaliser: the only FP64 on the GPU path)
-// and the sums sum_k w_k U_k of its 48 parameters (compensated FP32 per lane,
-// FP64 across warps).  Each CTA writes its partial sums to scratch and bumps a
-// counter; the CTA that sees the counter reach the grid size - 1 (no waiting:
-// it is simply the last to finish) adds the partials in CTA order -- so the
-// result does not depend on scheduling -- forms mu' = S / Z, writes u0 = the
-// controls of step 0 (knot 0, or the first direct target), the shifted
-// nominal, the status, and re-arms the counter for the next launch.
+// G CTAs split the n samples into contiguous chunks of about 128 (a second grid
+// dimension T tiles the 12 H parameters of direct targets into groups of 48;
+// the knot representations have one tile and their own kernel).  Every CTA
+// reads only its chunk's costs: their minimum m_c over the finite ones, the
+// FP32 weights w_k = exp(-(L_k - m_c)/lambda) (0 if L_k is not finite), their
+// sum z_c in FP64 and the sums S_c = sum_k w_k U_k of its tile's parameters
+// (compensated FP32 per lane, FP64 across warps).  It writes these and m_c to
+// scratch and bumps a counter; the CTA that sees the counter reach the grid
+// size - 1 (no waiting: it is simply the last to finish) takes L_min = min_c m_c
+// and scales chunk c by f_c = exp(-(m_c - L_min)/lambda) -- Eq. 1's weights
+// factor as exp(-(L_k - L_min)/lambda) = w_k f_c -- so that mu' = sum_c f_c S_c /
+// sum_c f_c z_c.  The chunks are added in a fixed order and tree, so the result
+// does not depend on scheduling.  It writes mu', u0 = the controls of step 0
+// (knot 0, or the first direct target), the shifted nominal and the status, and
+// re-arms the counter for the next launch.
 #include "kernels.h"
 
 namespace mppi {
@@ -26,10 +28,10 @@ constexpr int UPD_TILE = D;   // parameters per dimension tile
 __device__ __forceinline__ bool finitef(float x) { return fabsf(x) <= 3.402823466e38f; }
 
 // One warp's share of a CTA chunk: samples k = kb, kb + UPD_WARPS, ... < ke, the
-// lane's parameter pair u2[k * row2] weighted by w_k = exp(-(L_k - L_min) / lambda)
+// lane's parameter pair u2[k * row2] weighted by w_k = exp(-(L_k - m) / lambda)
 // (0 for a non-finite cost) into compensated (Kahan) sums, one sample at a time
 // in order; the loads of 8 samples are issued together (one L2 round trip each)
-__device__ __forceinline__ void sum_chunk(const float* L, const float2* u2, int row2, int kb, int ke, float Lmin,
+__device__ __forceinline__ void sum_chunk(const float* L, const float2* u2, int row2, int kb, int ke, float m,
                                           float inv_lambda, float& s0, float& s1, float& c0, float& c1) {
     constexpr int NB = 8;
     for (int kk = kb; kk < ke; kk += NB * UPD_WARPS) {
@@ -45,7 +47,7 @@ __device__ __forceinline__ void sum_chunk(const float* L, const float2* u2, int 
         for (int q = 0; q < NB; q++) {
             if (kk + q * UPD_WARPS >= ke) break;
             const float l = lb[q];
-            const float w = finitef(l) ? expf(-(l - Lmin) * inv_lambda) : 0.f;
+            const float w = finitef(l) ? expf(-(l - m) * inv_lambda) : 0.f;
             const float2 u = ub[q];
             float y0 = w * u.x - c0, y1 = w * u.y - c1;
             float t0 = s0 + y0, t1 = s1 + y1;
@@ -57,89 +59,171 @@ __device__ __forceinline__ void sum_chunk(const float* L, const float2* u2, int 
     }
 }
 
-// Knot representations (48 parameters): one parameter tile.
-__global__ void __launch_bounds__(UPD_THREADS) k_update_knots(UpdateArgs a) {
-    __shared__ float s_min[UPD_WARPS];
-    __shared__ double s_z[UPD_WARPS];
-    __shared__ double s_part[UPD_WARPS][D];
-    __shared__ float s_mu[D];
-    __shared__ int s_last;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int G = gridDim.x, b = blockIdx.x;
+constexpr int UPD_NB = 8;             // chunk partials a combining lane loads per round trip
+constexpr int UPD_ROW = UPD_TILE + 2;  // a chunk's scratch row: 48 sums, z_c, m_c
+static_assert(UPDATE_MAX_CTAS <= UPD_THREADS, "the last CTA holds one chunk per thread");
 
-    // L_min over all finite costs
-    float lm = INFINITY;
-    for (int k = tid; k < a.n; k += UPD_THREADS) {
-        float l = __ldg(a.L + k);
-        if (finitef(l)) lm = fminf(lm, l);
-    }
+struct UpdSmem {
+    float red[UPD_WARPS];
+    double z[UPD_WARPS];
+    double part[UPD_WARPS][UPD_TILE];
+    float f[UPDATE_MAX_CTAS];  // the chunks' factors exp(-(m_c - L_min) / lambda)
+    double Z;
+    int last;
+};
+
+// minimum of v over the CTA, returned to every thread
+__device__ __forceinline__ float block_min(float v, float* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lm = fminf(lm, __shfl_xor_sync(0xffffffffu, lm, o));
-    if (lane == 0) s_min[warp] = lm;
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();  // red is free
+    if (lane == 0) red[warp] = v;
     __syncthreads();
-    float Lmin = s_min[0];
+    float m = red[0];
 #pragma unroll
-    for (int w = 1; w < UPD_WARPS; w++) Lmin = fminf(Lmin, s_min[w]);
-    const bool ok = finitef(Lmin);
+    for (int w = 1; w < UPD_WARPS; w++) m = fminf(m, red[w]);
+    return m;
+}
 
-    // this CTA's chunk
+// CTA b's chunk on the parameter tile starting at d0: its row of the tile's
+// scratch gets S_c of the tile's parameters, then z_c and m_c
+__device__ __forceinline__ void chunk_partials(const UpdateArgs& a, int b, int G, int d0, double* rows, UpdSmem& s) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int Dp = a.Dp;
     const int chunk = (a.n + G - 1) / G;
     const int k0 = b * chunk, k1 = min(a.n, k0 + chunk);
-    // normaliser partial (FP64)
+    float lm = INFINITY;
+    for (int k = k0 + tid; k < k1; k += UPD_THREADS) {
+        const float l = __ldg(a.L + k);
+        if (finitef(l)) lm = fminf(lm, l);
+    }
+    const float m = block_min(lm, s.red);
+    const bool okc = finitef(m);
     double z = 0.0;
-    if (ok)
+    if (okc)
         for (int k = k0 + tid; k < k1; k += UPD_THREADS) {
-            float l = __ldg(a.L + k);
-            if (finitef(l)) z += (double)expf(-(l - Lmin) * a.inv_lambda);
+            const float l = __ldg(a.L + k);
+            if (finitef(l)) z += (double)expf(-(l - m) * a.inv_lambda);
         }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
-    if (lane == 0) s_z[warp] = z;
-    // sum_k w_k U_k: warp w takes k0 + w, k0 + w + 8, ...; lane i < 24 owns dims 2i, 2i + 1
+    if (lane == 0) s.z[warp] = z;
+    // sum_k w_k U_k: warp w takes k0 + w, k0 + w + 8, ...; lane i < 24 owns
+    // parameters d0 + 2i, d0 + 2i + 1 (Dp is even, so a pair never straddles the end)
+    const bool own = lane < UPD_TILE / 2 && d0 + 2 * lane < Dp;
     float s0 = 0.f, s1 = 0.f, c0 = 0.f, c1 = 0.f;
-    if (ok && lane < D / 2)
-        sum_chunk(a.L, reinterpret_cast<const float2*>(a.U) + lane, D / 2, k0 + warp, k1, Lmin, a.inv_lambda, s0, s1,
-                  c0, c1);
-    if (lane < D / 2) {
-        s_part[warp][2 * lane] = (double)s0 - (double)c0;
-        s_part[warp][2 * lane + 1] = (double)s1 - (double)c1;
+    if (okc && own)
+        sum_chunk(a.L, reinterpret_cast<const float2*>(a.U + d0) + lane, Dp / 2, k0 + warp, k1, m, a.inv_lambda, s0,
+                  s1, c0, c1);
+    if (lane < UPD_TILE / 2) {
+        s.part[warp][2 * lane] = (double)s0 - (double)c0;
+        s.part[warp][2 * lane + 1] = (double)s1 - (double)c1;
     }
     __syncthreads();
-    if (tid <= D) {
+    double* row = rows + (size_t)b * UPD_ROW;
+    if (tid < UPD_TILE && d0 + tid < Dp) {
         double acc = 0.0;
-        if (tid < D)
-            for (int w = 0; w < UPD_WARPS; w++) acc += s_part[w][tid];
-        else
-            for (int w = 0; w < UPD_WARPS; w++) acc += s_z[w];
-        a.part[(size_t)b * (D + 1) + tid] = acc;
+        for (int w = 0; w < UPD_WARPS; w++) acc += s.part[w][tid];
+        row[tid] = acc;
     }
-    // publish the partials, then count this CTA in
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(a.counter, 1u) == (unsigned)(G - 1));
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+    if (tid == UPD_TILE) {
+        double acc = 0.0;
+        for (int w = 0; w < UPD_WARPS; w++) acc += s.z[w];
+        row[UPD_TILE] = acc;
+    }
+    if (tid == UPD_TILE + 1) row[UPD_TILE + 1] = (double)m;
+}
 
-    // last CTA: combine in CTA order, apply, shift
-    if (tid < D) {
-        float mu_new;
-        if (ok) {
-            double S = 0.0, Z = 0.0;
-            for (int g = 0; g < G; g++) {
-                S += __ldcg(a.part + (size_t)g * (D + 1) + tid);
-                Z += __ldcg(a.part + (size_t)g * (D + 1) + D);
-            }
-            mu_new = (float)(S / Z);
-            if (tid == 0 && a.wsum) *a.wsum = Z;
-        } else {
-            mu_new = a.mu[tid];  // every cost non-finite: keep the previous mean
+// publish this CTA's writes and count it in: true in the last of `total` CTAs
+__device__ __forceinline__ bool count_in(unsigned* counter, unsigned total, UpdSmem& s) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s.last = (atomicAdd(counter, 1u) == total - 1);
+    __syncthreads();
+    if (!s.last) return false;
+    __threadfence();
+    return true;
+}
+
+// the last CTA of a tile: L_min over the G chunk minima of the tile's rows, the
+// factors f_c, and Z = sum_c f_c z_c (warp 0: lane j takes chunks j, j + 32, ...
+// in order, then a fixed xor tree).  Returns whether any cost is finite.
+__device__ __forceinline__ bool combine_setup(const UpdateArgs& a, int G, const double* rows, UpdSmem& s) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float mc = tid < G ? (float)__ldcg(rows + (size_t)tid * UPD_ROW + UPD_TILE + 1) : INFINITY;
+    const float Lmin = block_min(mc, s.red);
+    const bool ok = finitef(Lmin);
+    if (tid < G) s.f[tid] = (ok && finitef(mc)) ? expf(-(mc - Lmin) * a.inv_lambda) : 0.f;
+    __syncthreads();
+    if (warp == 0) {
+        constexpr int NQ = UPDATE_MAX_CTAS / 32;
+        double v[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            const int c = lane + 32 * q;
+            v[q] = c < G ? __ldcg(rows + (size_t)c * UPD_ROW + UPD_TILE) : 0.0;
         }
-        s_mu[tid] = mu_new;
-        if (a.mu_upd) a.mu_upd[tid] = mu_new;
-        if (tid < NJ) a.u0[tid] = mu_new;  // the spline at tau = 0 is knot 0
+        double z = 0.0;
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            const int c = lane + 32 * q;
+            if (c < G) z = fma((double)s.f[c], v[q], z);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+        if (lane == 0) s.Z = z;
+    }
+    __syncthreads();
+    return ok;
+}
+
+// S_j = sum_c f_c S_c[j] for tile parameter j by the 4 lanes q of a quad (chunks
+// c = q mod 4 in order, UPD_NB loads per round trip), added over the quad by a
+// fixed xor tree; every lane of the quad returns it.  The whole warp calls it.
+__device__ __forceinline__ double combine_param(int G, const double* rows, int j, int q, const UpdSmem& s) {
+    double acc = 0.0;
+    for (int c0 = q; c0 < G; c0 += 4 * UPD_NB) {
+        double v[UPD_NB];
+#pragma unroll
+        for (int i = 0; i < UPD_NB; i++) {
+            const int c = c0 + 4 * i;
+            v[i] = c < G ? __ldcg(rows + (size_t)c * UPD_ROW + j) : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < UPD_NB; i++) {
+            const int c = c0 + 4 * i;
+            if (c < G) acc = fma((double)s.f[c], v[i], acc);
+        }
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    return acc;
+}
+
+// Knot representations (48 parameters): one parameter tile.
+__global__ void __launch_bounds__(UPD_THREADS) k_update_knots(UpdateArgs a) {
+    __shared__ UpdSmem s;
+    __shared__ float s_mu[D];
+    const int tid = threadIdx.x, G = gridDim.x;
+    chunk_partials(a, blockIdx.x, G, 0, a.part, s);
+    if (!count_in(a.counter, (unsigned)G, s)) return;
+
+    // last CTA: combine, apply, shift
+    const bool ok = combine_setup(a, G, a.part, s);
+    {
+        const int j = tid >> 2, q = tid & 3;  // 64 quads, 48 parameters
+        const double S = combine_param(G, a.part, min(j, D - 1), q, s);
+        if (j < D && q == 0) {
+            // every cost non-finite: keep the previous mean
+            const float mu_new = ok ? (float)(S / s.Z) : a.mu[j];
+            s_mu[j] = mu_new;
+            if (a.mu_upd) a.mu_upd[j] = mu_new;
+            if (j < NJ) a.u0[j] = mu_new;  // the spline at tau = 0 is knot 0
+        }
     }
     if (tid == 0) {
+        if (ok && a.wsum) *a.wsum = s.Z;
         if (a.status) *a.status = ok ? 0 : 4;
         *a.counter = 0u;  // re-arm for the next launch (kernels on one stream are ordered)
     }
@@ -149,109 +233,46 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_knots(UpdateArgs a) {
     if (tid < D) a.mu[tid] = shifted_knot(s_mu, a.interp, a.H, a.ctrl_steps, tid / NJ, tid % NJ);
 }
 
-// Direct targets (12 H parameters): G x T CTAs, T = ceil(12 H / 48) parameter tiles.
+// Direct targets (12 H parameters): G x T CTAs, T = ceil(12 H / 48) parameter
+// tiles, each tile its own update: the last CTA of tile y (counter[1 + y])
+// combines the tile's 48 parameters from its G rows (every tile's rows carry
+// z_c and m_c, computed identically); the last tile to finish (counter[0])
+// applies the shift, which moves targets across tiles.
 __global__ void __launch_bounds__(UPD_THREADS) k_update_tiled(UpdateArgs a) {
-    __shared__ float s_min[UPD_WARPS];
-    __shared__ double s_z[UPD_WARPS];
-    __shared__ double s_part[UPD_WARPS][UPD_TILE];
-    __shared__ int s_last;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int G = gridDim.x, b = blockIdx.x, T = gridDim.y, y = blockIdx.y;
+    __shared__ UpdSmem s;
+    const int tid = threadIdx.x, G = gridDim.x, T = gridDim.y, y = blockIdx.y;
     const int Dp = a.Dp, d0 = y * UPD_TILE;
+    double* rows = a.part + (size_t)y * G * UPD_ROW;
+    chunk_partials(a, blockIdx.x, G, d0, rows, s);
+    if (!count_in(a.counter + 1 + y, (unsigned)G, s)) return;
 
-    // L_min over all finite costs
-    float lm = INFINITY;
-    for (int k = tid; k < a.n; k += UPD_THREADS) {
-        float l = __ldg(a.L + k);
-        if (finitef(l)) lm = fminf(lm, l);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lm = fminf(lm, __shfl_xor_sync(0xffffffffu, lm, o));
-    if (lane == 0) s_min[warp] = lm;
-    __syncthreads();
-    float Lmin = s_min[0];
-#pragma unroll
-    for (int w = 1; w < UPD_WARPS; w++) Lmin = fminf(Lmin, s_min[w]);
-    const bool ok = finitef(Lmin);
-
-    // this CTA's chunk
-    const int chunk = (a.n + G - 1) / G;
-    const int k0 = b * chunk, k1 = min(a.n, k0 + chunk);
-    // normaliser partial (FP64), tile 0
-    double z = 0.0;
-    if (ok && y == 0)
-        for (int k = k0 + tid; k < k1; k += UPD_THREADS) {
-            float l = __ldg(a.L + k);
-            if (finitef(l)) z += (double)expf(-(l - Lmin) * a.inv_lambda);
+    // last CTA of this tile: combine and apply its parameters
+    const bool ok = combine_setup(a, G, rows, s);
+    {
+        const int j = tid >> 2, q = tid & 3, d = d0 + j;
+        const double S = combine_param(G, rows, min(j, UPD_TILE - 1), q, s);
+        if (j < UPD_TILE && d < Dp && q == 0) {
+            const float mu_new = ok ? (float)(S / s.Z) : a.mu[d];  // every cost non-finite: keep the mean
+            a.mu_upd[d] = mu_new;
+            if (d < NJ) a.u0[d] = mu_new;  // the controls of step 0: the first direct target
         }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
-    if (lane == 0) s_z[warp] = z;
-    // sum_k w_k U_k: warp w takes k0 + w, k0 + w + 8, ...; lane i < 24 owns
-    // parameters d0 + 2i, d0 + 2i + 1 (Dp is even, so a pair never straddles the end)
-    const bool own = lane < UPD_TILE / 2 && d0 + 2 * lane < Dp;
-    float s0 = 0.f, s1 = 0.f, c0 = 0.f, c1 = 0.f;
-    if (ok && own)
-        sum_chunk(a.L, reinterpret_cast<const float2*>(a.U + d0) + lane, Dp / 2, k0 + warp, k1, Lmin, a.inv_lambda, s0,
-                  s1, c0, c1);
-    if (lane < UPD_TILE / 2) {
-        s_part[warp][2 * lane] = (double)s0 - (double)c0;
-        s_part[warp][2 * lane + 1] = (double)s1 - (double)c1;
-    }
-    __syncthreads();
-    if (tid < UPD_TILE && d0 + tid < Dp) {
-        double acc = 0.0;
-        for (int w = 0; w < UPD_WARPS; w++) acc += s_part[w][tid];
-        a.part[(size_t)b * (Dp + 1) + d0 + tid] = acc;
-    }
-    if (y == 0 && tid == UPD_TILE) {
-        double acc = 0.0;
-        for (int w = 0; w < UPD_WARPS; w++) acc += s_z[w];
-        a.part[(size_t)b * (Dp + 1) + Dp] = acc;
-    }
-    // publish the partials, then count this CTA in
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(a.counter, 1u) == (unsigned)(G * T - 1));
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-
-    // last CTA: combine in CTA order (each thread's normaliser alongside its first
-    // parameter), apply, shift
-    double Z = 0.0;
-    for (int d = tid; d < Dp; d += UPD_THREADS) {
-        float mu_new;
-        if (ok) {
-            double S = 0.0;
-            if (d == tid) {
-                for (int g = 0; g < G; g++) {
-                    S += __ldcg(a.part + (size_t)g * (Dp + 1) + d);
-                    Z += __ldcg(a.part + (size_t)g * (Dp + 1) + Dp);
-                }
-            } else {
-                for (int g = 0; g < G; g++) S += __ldcg(a.part + (size_t)g * (Dp + 1) + d);
-            }
-            mu_new = (float)(S / Z);
-        } else {
-            mu_new = a.mu[d];  // every cost non-finite: keep the previous mean
-        }
-        a.mu_upd[d] = mu_new;
-        if (d < NJ) a.u0[d] = mu_new;  // the controls of step 0: the first direct target
     }
     if (tid == 0) {
-        if (ok && a.wsum) *a.wsum = Z;  // thread 0 always owns parameter 0
-        if (a.status) *a.status = ok ? 0 : 4;
-        *a.counter = 0u;  // re-arm for the next launch (kernels on one stream are ordered)
+        if (y == 0) {
+            if (ok && a.wsum) *a.wsum = s.Z;
+            if (a.status) *a.status = ok ? 0 : 4;
+        }
+        a.counter[1 + y] = 0u;  // re-arm for the next launch
     }
-    __syncthreads();
-    // direct targets move ctrl_steps steps earlier, the last one held (mu_upd was
-    // written by this CTA before the barrier)
+    if (!count_in(a.counter, (unsigned)T, s)) return;
+    // the last tile: direct targets move ctrl_steps steps earlier, the last one
+    // held (every tile's mu_upd was published before its count)
     for (int d = tid; d < Dp; d += UPD_THREADS) {
         const int t = d / NJ, i = d % NJ;
         const int src = min(t + a.ctrl_steps, a.H - 1);
-        a.mu[d] = a.mu_upd[src * NJ + i];
+        a.mu[d] = __ldcg(a.mu_upd + src * NJ + i);
     }
+    if (tid == 0) a.counter[0] = 0u;
 }
 
 int update_grid(int n) {
