@@ -37,7 +37,7 @@ METRIC = "rollout-steps/s (MPPI step, K=4096, H=100)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture) of
 # one k_rollout launch on this workload, valid only for the kernel sources whose
 # SHA-256 prefix is given; reported as null once those sources change.
-ROLLOUT_TRAFFIC = {"bytes": 161024, "sources_sha256": "cd959651ebbc5f49"}
+ROLLOUT_TRAFFIC = {"bytes": 119040, "sources_sha256": "1597a3536bf04e92"}
 ROLLOUT_SOURCES = ("rollout.cu", "rollout.cuh", "common.cuh", "noise.cuh", "kernels.h")
 
 
@@ -354,6 +354,49 @@ def proposal_form(flush, steps=200, warmup=10):
                     "on one stream (four_calls: the same as four separate calls)"}
 
 
+def direct_form(flush, peaks, steps=60, warmup=5):
+    """Direct targets (the paper's sampling ablation, Sec. IV-E): the same trot
+    workload at K = 4096, H = 100 with 12 H = 1200 sampled parameters per
+    sample instead of 48 knots.  The step is three kernels (sampling, rollouts,
+    update), each timed by the library's CUDA events on the stream
+    (mppi_set_timing); L2 flushed between steps.  The sampler writes and the
+    update reads 19.7 MB per step, so these two are HBM kernels."""
+    import torch
+    from paper_2409_10469_gb300 import _mppi, flops as F, workloads as W
+    K, H = K_BENCH, H_BENCH
+    Dp = 12 * H
+    cfg = W.config_trot(K=K, H=H)
+    st = torch.cuda.Stream()
+    ctl = _mppi.Controller(cfg.robot, cfg.cost, dict(cfg.mppi, interp="direct"), stream=st.cuda_stream)
+    ctl.set_nominal(np.tile(W.stand_mu()[:12], H).astype(np.float32))
+    ctl.set_timing(True)
+    x0 = torch.tensor(cfg.x0, dtype=torch.float32, device="cuda")
+    u0 = torch.empty(12, dtype=torch.float32, device="cuda")
+    for s in range(warmup):
+        ctl.step(x0, s, u0_out=u0)
+    st.synchronize()
+    ms, parts = [], []
+    for s in range(steps):
+        with torch.cuda.stream(st):
+            flush.fill_(float(s))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        ctl.step(x0, warmup + s, u0_out=u0)
+        e1.record(st)
+        st.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        parts.append(ctl.timings())
+    ctl.close()
+    p = np.mean(np.array(parts), axis=0)
+    t = float(np.mean(ms))
+    return {"K": K, "H": H, "params_per_sample": Dp, "ms_per_step": t,
+            "rollout_steps_per_s": K * H / (t * 1e-3),
+            "stages_ms": {"k_sample": float(p[0]), "k_rollout": float(p[1]), "k_update": float(p[2])},
+            "k_sample": dict(hbm_line(F.sample_bytes(K, Dp), float(p[0]), peaks),
+                             note="issue-bound: a Philox call and two Box-Muller pairs per 16-byte store"),
+            "k_update": hbm_line(F.update_bytes(K, Dp), float(p[2]), peaks)}
+
+
 def run_ours(args):
     import torch
     from paper_2409_10469_gb300 import _mppi, flops as F, workloads as W
@@ -451,6 +494,7 @@ def run_ours(args):
     peak = F.fp32_peak_tflops(152, sm_max)
     full_occ = full_occupancy_roofline(W.config_trot, F, flush, peak)
     prop = proposal_form(flush)
+    direct = direct_form(flush, peaks)
     value = D.job_throughput(K_BENCH * H_BENCH, world_size, mean_ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "rollout-steps/s", "n_gpus": world_size,
@@ -470,6 +514,8 @@ def run_ours(args):
         "roofline_full_occupancy": full_occ,
         # the learned-proposal form (K = 2048, half the samples around the network's mean)
         "proposal_form": prop,
+        # direct targets (12 H sampled parameters per sample): three kernels per step
+        "direct_form": direct,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": rollout_traffic(),
                      "kernel": "k_rollout", "flops_per_launch": fl,

@@ -58,14 +58,16 @@ def rollout_flops(K: int, H: int, n_sub: int) -> float:
     return float(K) * H * (n_sub * SUBSTEP + PER_DT_STEP)
 
 
-def sample_bytes(K: int) -> float:
-    """K1: writes U[K][48] floats (reads 48 floats of mu)."""
-    return 4.0 * K * 48 + 4 * 48
+def sample_bytes(K: int, D: int = 48) -> float:
+    """K1: writes U[K][D] floats (reads D floats of mu); D = 48 knots, or 12 H
+    direct targets."""
+    return 4.0 * K * D + 4 * D
 
 
-def update_bytes(K: int) -> float:
-    """K3/K4: reads L[K] and U[K][48]; writes mu, u0."""
-    return 4.0 * K * 49 + 4 * (48 + 48 + 12)
+def update_bytes(K: int, D: int = 48) -> float:
+    """K3/K4: reads L[K] and U[K][D]; writes the updated and the shifted mean
+    and u0."""
+    return 4.0 * K * (D + 1) + 4 * (D + D + 12)
 
 
 def fp32_peak_tflops(sms: int = 152, mhz: float = 2070.0) -> float:
