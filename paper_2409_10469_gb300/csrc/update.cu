@@ -7,8 +7,9 @@
 // the knot representations have one tile and their own kernel).  Every CTA
 // reads only its chunk's costs: their minimum m_c over the finite ones, the
 // FP32 weights w_k = exp(-(L_k - m_c)/lambda) (0 if L_k is not finite), their
-// sum z_c in FP64 and the sums S_c = sum_k w_k U_k of its tile's parameters
-// (compensated FP32 per lane, FP64 across warps).  It writes these and m_c to
+// sum z_c and the sums S_c = sum_k w_k U_k of its tile's parameters (compensated
+// FP32 per lane, float-float pairs across lanes and warps: FP64 runs at 1/64 of
+// the FP32 rate on this part, so only the last CTA's combine uses it).  It writes these and m_c to
 // scratch and bumps a counter; the CTA that sees the counter reach the grid
 // size - 1 (no waiting: it is simply the last to finish) takes L_min = min_c m_c
 // and scales chunk c by f_c = exp(-(m_c - L_min)/lambda) -- Eq. 1's weights
@@ -26,6 +27,17 @@ constexpr int UPD_WARPS = UPD_THREADS / 32;
 constexpr int UPD_TILE = D;   // parameters per dimension tile
 
 __device__ __forceinline__ bool finitef(float x) { return fabsf(x) <= 3.402823466e38f; }
+
+// float-float accumulation: (s, e) += (v, ve), s + v split exactly into the new
+// s and an error term by Knuth's TwoSum, the error and the low parts into e
+// (about 48 significant bits on the FP32 pipe, which runs 64x the FP64 rate)
+__device__ __forceinline__ void ff_acc(float& s, float& e, float v, float ve) {
+    const float t = s + v;
+    const float bp = t - s;
+    const float err = (s - (t - bp)) + (v - bp);
+    s = t;
+    e += ve + err;
+}
 
 // One warp's share of a CTA chunk: samples k = kb, kb + UPD_WARPS, ... < ke, the
 // lane's parameter pair u2[k * row2] weighted by w_k = exp(-(L_k - m) / lambda)
@@ -65,8 +77,8 @@ static_assert(UPDATE_MAX_CTAS <= UPD_THREADS, "the last CTA holds one chunk per 
 
 struct UpdSmem {
     float red[UPD_WARPS];
-    double z[UPD_WARPS];
-    double part[UPD_WARPS][UPD_TILE];
+    float2 z[UPD_WARPS];              // per-warp weight sums (hi, lo)
+    float2 part[UPD_WARPS][UPD_TILE];  // per-warp parameter sums (hi, lo)
     float f[UPDATE_MAX_CTAS];  // the chunks' factors exp(-(m_c - L_min) / lambda)
     double Z;
     int last;
@@ -100,15 +112,18 @@ __device__ __forceinline__ void chunk_partials(const UpdateArgs& a, int b, int G
     }
     const float m = block_min(lm, s.red);
     const bool okc = finitef(m);
-    double z = 0.0;
+    float zs = 0.f, ze = 0.f;
     if (okc)
         for (int k = k0 + tid; k < k1; k += UPD_THREADS) {
             const float l = __ldg(a.L + k);
-            if (finitef(l)) z += (double)expf(-(l - m) * a.inv_lambda);
+            if (finitef(l)) ff_acc(zs, ze, expf(-(l - m) * a.inv_lambda), 0.f);
         }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
-    if (lane == 0) s.z[warp] = z;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float v = __shfl_xor_sync(0xffffffffu, zs, o), ve = __shfl_xor_sync(0xffffffffu, ze, o);
+        ff_acc(zs, ze, v, ve);
+    }
+    if (lane == 0) s.z[warp] = make_float2(zs, ze);
     // sum_k w_k U_k: warp w takes k0 + w, k0 + w + 8, ...; lane i < 24 owns
     // parameters d0 + 2i, d0 + 2i + 1 (Dp is even, so a pair never straddles the end)
     const bool own = lane < UPD_TILE / 2 && d0 + 2 * lane < Dp;
@@ -116,21 +131,22 @@ __device__ __forceinline__ void chunk_partials(const UpdateArgs& a, int b, int G
     if (okc && own)
         sum_chunk(a.L, reinterpret_cast<const float2*>(a.U + d0) + lane, Dp / 2, k0 + warp, k1, m, a.inv_lambda, s0,
                   s1, c0, c1);
-    if (lane < UPD_TILE / 2) {
-        s.part[warp][2 * lane] = (double)s0 - (double)c0;
-        s.part[warp][2 * lane + 1] = (double)s1 - (double)c1;
+    if (lane < UPD_TILE / 2) {  // Kahan's sum s with compensation c stands for s - c
+        s.part[warp][2 * lane] = make_float2(s0, -c0);
+        s.part[warp][2 * lane + 1] = make_float2(s1, -c1);
     }
     __syncthreads();
+    // the warps' pairs added in warp order; the row holds hi + lo as a double
     double* row = rows + (size_t)b * UPD_ROW;
     if (tid < UPD_TILE && d0 + tid < Dp) {
-        double acc = 0.0;
-        for (int w = 0; w < UPD_WARPS; w++) acc += s.part[w][tid];
-        row[tid] = acc;
+        float hi = s.part[0][tid].x, lo = s.part[0][tid].y;
+        for (int w = 1; w < UPD_WARPS; w++) ff_acc(hi, lo, s.part[w][tid].x, s.part[w][tid].y);
+        row[tid] = (double)hi + (double)lo;
     }
     if (tid == UPD_TILE) {
-        double acc = 0.0;
-        for (int w = 0; w < UPD_WARPS; w++) acc += s.z[w];
-        row[UPD_TILE] = acc;
+        float hi = s.z[0].x, lo = s.z[0].y;
+        for (int w = 1; w < UPD_WARPS; w++) ff_acc(hi, lo, s.z[w].x, s.z[w].y);
+        row[UPD_TILE] = (double)hi + (double)lo;
     }
     if (tid == UPD_TILE + 1) row[UPD_TILE + 1] = (double)m;
 }
