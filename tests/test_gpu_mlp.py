@@ -50,10 +50,12 @@ def data(B, seed):
     return rng.normal(size=(B, 62)).astype(np.float32), (0.3 * rng.normal(size=(B, 48))).astype(np.float32)
 
 
-@pytest.mark.parametrize("B", [1, 7, 64, 128, 129, 300])
+@pytest.mark.parametrize("B", [1, 2, 3, 7, 9, 64, 128, 129, 300])
 def test_forward_matches_oracle(B):
-    """batches up to 128 take the fused CUDA-core forward, larger ones the
-    tensor cores; both mirror the oracle's BF16 rounding points"""
+    """batches up to 128 take the CUDA-core cluster forward (1, 2, 4 or 8
+    samples per 8-CTA cluster: B = 1, 2, 3, 7, one ragged second cluster at 9,
+    8 and 16 clusters), larger ones the tensor cores; both mirror the oracle's
+    BF16 rounding points"""
     net = _mppi.MLP(512)
     p = M.init_params(5)
     net.set_params(p)
