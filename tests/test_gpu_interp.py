@@ -83,7 +83,7 @@ def test_rollout_cost_parity(mode, which):
 
 
 @pytest.mark.parametrize("mode", MODES)
-@pytest.mark.parametrize("K,H,lam", [(7, 12, 1e6), (513, 40, 0.05), (4096, 100, 0.1)])
+@pytest.mark.parametrize("K,H,lam", [(7, 12, 1e6), (513, 40, 0.05), (4096, 100, 0.1), (1000, 50, 0.2)])
 def test_update_and_shift_parity(mode, K, H, lam):
     cfg = W.config_trot()
     ctl, m = ctl_for(cfg, K=K, H=H, lam=lam, interp=mode)
@@ -168,3 +168,29 @@ def test_batch_runs_knot_representations_and_rejects_direct():
     d, _ = ctl_for(cfg, interp="direct")
     with pytest.raises(_mppi.MppiError):
         _mppi.Batch([d])
+
+
+@pytest.mark.parametrize("mode", ["cubic", "direct"])
+def test_update_with_whole_chunks_non_finite(mode):
+    """The update kernel takes each chunk's cost minimum and rescales the chunks
+    by exp(-(m_c - L_min)/lambda): chunks whose costs are all non-finite (m_c
+    infinite) must drop out, the chunk holding L_min must weigh 1.  K = 1000 is 8
+    chunks of 125; chunks 1 and 4 are all inf / NaN, chunk 6 holds the minimum."""
+    cfg = W.config_trot()
+    K, H, lam = 1000, 50, 0.1
+    ctl, m = ctl_for(cfg, K=K, H=H, lam=lam, interp=mode)
+    Dm = ctl.D
+    rng = np.random.default_rng(11)
+    U = (np.tile(nominal(m, W.stand_mu()), (K, 1)) + rng.normal(0, 0.3, (K, Dm))).astype(np.float32)
+    L = (100 + 3 * rng.random(K)).astype(np.float32)
+    L[125:250] = np.inf
+    L[500:625] = np.nan
+    L[777] = 98.0
+    mu_g = torch.empty(Dm, device="cuda")
+    u0_g = torch.empty(12, device="cuda")
+    assert ctl.update(dev(L), dev(U), n=K, mu_out=mu_g, u0_out=u0_g) == 0
+    _, mu_o, _ = O.update(L, U, lam, dim=Dm)
+    mg = mu_g.cpu().numpy()
+    e = np.abs(mg - mu_o) / np.maximum(np.abs(mu_o), 1)
+    assert e.max() <= 1e-6, (mode, e.max())
+    assert np.array_equal(u0_g.cpu().numpy(), mg[:12])
