@@ -318,6 +318,14 @@ mppi_status mppi_mlp_train_step(mppi_mlp net, const float* X, const float* T, in
  * still usable afterwards. */
 mppi_status mppi_selftest_wait_timeout(void* stream);
 
+/* Noise self-test (the sampler's Box-Muller transform, Sec. II-B sampling step,
+ * over its whole input domain): for every 24-bit i, radius[i] = sqrt(-2 ln u1)
+ * with u1 = (i + 1) 2^-24, and cosv[i], sinv[i] = cos, sin of 2 pi i 2^-24,
+ * computed by the device code the sampling kernels use.  radius, cosv, sinv:
+ * device float[2^24] each (caller-owned).  ARG for null or host pointers;
+ * asynchronous on `stream`. */
+mppi_status mppi_selftest_noise_tables(float* radius, float* cosv, float* sinv, void* stream);
+
 /* The network's input for n states X (float[n][nx], host or device) of this
  * handle's robot and task at control index `step`: F (float[n][62], host or
  * device) = trunk height, attitude (w >= 0), joints, velocities, joint rates

@@ -33,7 +33,8 @@ EXPORTS = ("mppi_create", "mppi_destroy", "mppi_last_error", "mppi_set_nominal",
            "mppi_server_drain", "mppi_mlp_create", "mppi_mlp_destroy", "mppi_mlp_last_error",
            "mppi_mlp_param_count", "mppi_mlp_set_params", "mppi_mlp_get_params", "mppi_mlp_forward",
            "mppi_mlp_train_step", "mppi_tc_gemm_bf16", "mppi_features", "mppi_set_proposal", "mppi_step_proposal",
-           "mppi_batch_get_means", "mppi_selftest_wait_timeout", "mppi_param_dim")
+           "mppi_batch_get_means", "mppi_selftest_wait_timeout", "mppi_param_dim",
+           "mppi_selftest_noise_tables")
 
 # control representations (MPPI_INTERP_* of include/mppi.h; Sec. III-B, Fig. 5)
 INTERP = {"cubic": 0, "zero": 1, "linear": 2, "direct": 3}
@@ -166,6 +167,7 @@ def lib():
         L.mppi_features.argtypes = [vp, vp, C.c_int, C.c_uint32, vp]
         L.mppi_batch_get_means.argtypes = [vp, vp, vp]
         L.mppi_selftest_wait_timeout.argtypes = [vp]
+        L.mppi_selftest_noise_tables.argtypes = [vp, vp, vp, vp]
         L.mppi_set_proposal.argtypes = [vp, vp]
         L.mppi_state_size.argtypes = [vp]
         L.mppi_state_size.restype = C.c_int

@@ -724,6 +724,11 @@ extern "C" mppi_status mppi_step_proposal(mppi_handle h, mppi_mlp net, const flo
     return mppi_step(h, dx0, step, u0_out, mu_out);
 }
 
+extern "C" mppi_status mppi_selftest_noise_tables(float* radius, float* cosv, float* sinv, void* stream) {
+    if (!radius || !cosv || !sinv || !is_device(radius) || !is_device(cosv) || !is_device(sinv)) return MPPI_ERR_ARG;
+    return launch_noise_tables(radius, cosv, sinv, (cudaStream_t)stream) == cudaSuccess ? MPPI_OK : MPPI_ERR_CUDA;
+}
+
 extern "C" mppi_status mppi_set_timing(mppi_handle h, int on) {
     if (!h) return MPPI_ERR_ARG;
     h->timing = on;

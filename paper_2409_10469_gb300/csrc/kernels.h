@@ -92,6 +92,8 @@ constexpr size_t update_part_doubles(int Dp) { return (size_t)UPDATE_MAX_CTAS * 
 constexpr int update_counters(int Dp) { return 1 + update_tiles(Dp); }
 
 cudaError_t launch_sample(const SampleArgs& a, cudaStream_t st);
+// the noise self-test's tables (2^24 entries each)
+cudaError_t launch_noise_tables(float* radius, float* cosv, float* sinv, cudaStream_t st);
 cudaError_t launch_rollout(const RolloutArgs& a, int block, cudaStream_t st);
 // CTAs of a rollout launch of n samples at this block size
 inline int rollout_grid(int n, int block) { return (int)((4L * n + block - 1) / block); }

@@ -79,4 +79,18 @@ cudaError_t launch_sample(const SampleArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// every 24-bit input of the Box-Muller pieces: the radius of word a = i << 8
+// and the angle of word b = i << 8
+__global__ void k_noise_tables(float* radius, float* cosv, float* sinv) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (1u << 24)) return;
+    radius[i] = box_muller_radius(i << 8);
+    sincos2pi_spec(i, cosv[i], sinv[i]);
+}
+
+cudaError_t launch_noise_tables(float* radius, float* cosv, float* sinv, cudaStream_t st) {
+    k_noise_tables<<<(1 << 24) / 256, 256, 0, st>>>(radius, cosv, sinv);
+    return cudaGetLastError();
+}
+
 }  // namespace mppi
