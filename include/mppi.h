@@ -313,9 +313,11 @@ mppi_status mppi_mlp_train_step(mppi_mlp net, const float* X, const float* T, in
 /* Failure-detection self-test: runs both tensor-core GEMM kernels (the
  * thread-staged one and the TMA-fed pipeline) with their completion signals
  * withheld, so their bounded waits run out; each kernel records the timeout,
- * lets its copies in flight land, releases its tensor memory and returns.
- * Expected result: MPPI_ERR_TIMEOUT (both timed out), with the CUDA context
- * still usable afterwards. */
+ * lets its copies in flight land, releases its tensor memory and returns.  Then
+ * the small-batch cluster forward with its first layer's weight copy withheld:
+ * its waits run out, it records that and returns in step with its cluster.
+ * Expected result: MPPI_ERR_TIMEOUT (all three timed out), with the CUDA
+ * context still usable afterwards. */
 mppi_status mppi_selftest_wait_timeout(void* stream);
 
 /* Noise self-test (the sampler's Box-Muller transform, Sec. II-B sampling step,

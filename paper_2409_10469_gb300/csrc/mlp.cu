@@ -293,7 +293,8 @@ struct SmallFwdArgs {
     const float* bias[4];       // [out]
     float* Y;                   // [B][48]
     int* err;                   // set to 1 when a weight copy's wait runs out
-    uint32_t wait_limit;
+    uint32_t wait_limit;        // mbarrier polls before giving up (0 = default)
+    int withhold;               // self-test: layer 0's copy is never issued, so its waits run out
 };
 
 template <int SB>
@@ -325,6 +326,7 @@ __global__ void __cluster_dims__(SC_CL, 1, 1) __launch_bounds__(SC_T) k_mlp_clus
         tc::mbar_init_fence();
 #pragma unroll
         for (int l = 0; l < 4; l++) {
+            if (l == 0 && a.withhold) continue;
             const uint32_t bytes = sc_rows(l) * sc_k(l) * 2;
             tc::mbar_arrive_expect_tx(&bar[l], bytes);
             tc::bulk_load(tc::smem_u32(w_s + sc_wofs(l)), a.W[l] + (size_t)c * sc_rows(l) * sc_k(l), bytes, &bar[l]);
@@ -1018,7 +1020,7 @@ extern "C" mppi_status mppi_selftest_wait_timeout(void* stream) {
     // a 128 x 64 x 64 GEMM whose completion is never signalled, on both
     // tensor-core kernels: the bounded mbarrier waits must run out, each kernel
     // must record it, drain its copies, free its tensor memory and return, and
-    // the context must stay usable
+    // the context must stay usable; then the same for the cluster forward
     cudaStream_t st = (cudaStream_t)stream;
     __nv_bfloat16 *A = nullptr, *B = nullptr;
     float* D = nullptr;
@@ -1055,7 +1057,38 @@ extern "C" mppi_status mppi_selftest_wait_timeout(void* stream) {
     if (e == cudaSuccess) e = launch_gemm_tma(t, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h2, err, 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(A); cudaFree(B); cudaFree(D); cudaFree(err);
+    // the cluster forward with its first layer's weight copy withheld: every
+    // thread's wait on that layer runs out, the kernel records it, keeps in step
+    // with its cluster's barriers and returns
+    int h3 = 0;
+    unsigned char* buf = nullptr;
+    const size_t wbytes = ((size_t)HID * IN_PAD + 2 * (size_t)HID * HID + (size_t)OUT * HID) * 2;
+    const size_t bytes = wbytes + (3 * HID + OUT) * 4 + 64 * 4 + 64 * 4;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&buf, bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, bytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 4, st);
+    if (e == cudaSuccess) {
+        SmallFwdArgs c = {};
+        size_t o = 0;
+        for (int l = 0; l < NL; l++) {
+            c.W[l] = reinterpret_cast<const __nv_bfloat16*>(buf + o);
+            o += (size_t)LOUT[l] * LLD[l] * 2;
+        }
+        for (int l = 0; l < NL; l++) {
+            c.bias[l] = reinterpret_cast<const float*>(buf + o);
+            o += (size_t)LOUT[l] * 4;
+        }
+        c.X = reinterpret_cast<const float*>(buf + o);
+        c.Y = reinterpret_cast<float*>(buf + o + 64 * 4);
+        c.B = 1;
+        c.err = err;
+        c.wait_limit = 1u << 12;
+        c.withhold = 1;
+        e = launch_cluster<1>(c, 1, st);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h3, err, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(A); cudaFree(B); cudaFree(D); cudaFree(err); cudaFree(buf);
     if (e != cudaSuccess) return MPPI_ERR_CUDA;
-    return (h && h2) ? MPPI_ERR_TIMEOUT : MPPI_OK;
+    return (h && h2 && h3) ? MPPI_ERR_TIMEOUT : MPPI_OK;
 }
