@@ -22,11 +22,13 @@ __device__ __forceinline__ void sample_lane(const InstDesc& d, int k, int leg, u
     const float* ctr = prop ? d.mu_prop : d.mu;
     const bool nominal = (k == 0) || (prop && k == kp0);
 #pragma unroll
-    for (int j = 0; j < NKNOT; j++)
+    for (int j = 0; j < NKNOT; j++) {
+        float epsv[3];
+        knot_normals(d.key0, d.key1, step, d.inst_id, (uint32_t)k, j * NJ + 3 * leg, epsv);
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             const int dd = j * NJ + 3 * leg + i;
-            const float eps = nominal ? 0.f : normal_at(d.key0, d.key1, step, d.inst_id, (uint32_t)k, dd);
+            const float eps = nominal ? 0.f : epsv[i];
             float c = __ldcg(ctr + dd);
             if (prop && !(fabsf(c) <= 3.402823466e38f)) c = __ldcg(d.mu + dd);  // non-finite proposal: plain mean
             float v = __fmaf_rn(d.sigma[dd], eps, c);
@@ -34,6 +36,7 @@ __device__ __forceinline__ void sample_lane(const InstDesc& d, int k, int leg, u
             Uk[j][i] = v;
             if (write) d.U[(size_t)k * D + dd] = v;
         }
+    }
 }
 
 __device__ __forceinline__ bool finite_f(float x) { return fabsf(x) <= 3.402823466e38f; }

@@ -210,26 +210,9 @@ __global__ void __launch_bounds__(256, 1) k_rollout(RolloutArgs a) {
         const bool nominal = (kk == 0) || (prop && kk == kp0);
 #pragma unroll
         for (int j = 0; j < NKNOT; j++) {
-            // the lane's 3 normals d0 = 12 j + 3 leg, d0 + 1, d0 + 2 lie in at most two
-            // Philox calls and two word pairs: the pair holding d0 (A) and the pair
-            // holding d0 + 2 (B); d0 + 1 shares A's pair for legs 0 and 2, B's for 1
-            // and 3.  Each normal is the same call, pair and element as k_sample's.
             const int d0 = j * NJ + 3 * leg;
-            float ea0, ea1, eb0, eb1;
-            {
-                uint32_t wa[4] = {(uint32_t)(d0 >> 2), (uint32_t)kk, a.step, a.inst};
-                uint32_t wb[4] = {(uint32_t)((d0 + 2) >> 2), (uint32_t)kk, a.step, a.inst};
-                philox4x32_10(wa, a.key0, a.key1);
-                philox4x32_10(wb, a.key0, a.key1);
-                const bool pa = (d0 & 2) != 0, pb = ((d0 + 2) & 2) != 0;
-                box_muller(pa ? wa[2] : wa[0], pa ? wa[3] : wa[1], ea0, ea1);
-                box_muller(pb ? wb[2] : wb[0], pb ? wb[3] : wb[1], eb0, eb1);
-            }
-            const bool oa = (d0 & 1) != 0;  // d0 odd: legs 1 and 3
             float epsv[3];
-            epsv[0] = oa ? ea1 : ea0;
-            epsv[1] = oa ? eb0 : ea1;       // d0 + 1: A's second element, or B's first
-            epsv[2] = oa ? eb1 : eb0;
+            knot_normals(a.key0, a.key1, a.step, a.inst, (uint32_t)kk, d0, epsv);
 #pragma unroll
             for (int i = 0; i < 3; i++) {
                 const int d = d0 + i;
