@@ -259,14 +259,14 @@ def component_ms(ctl, stream, flush, K, reps=16):
     return {k: float(np.mean(v)) for k, v in out.items()}
 
 
-def full_occupancy_roofline(cfg_fn, F, flush, peak, steps=30):
-    """The same step at K = 9728: 304 CTAs of 128 threads, two per SM (the
-    kernel's register budget allows two), so every scheduler runs two warps --
-    at the metric's K = 4096 only 512 warps exist for 608 schedulers.  CUDA
-    events around each step, L2 flushed between steps."""
+def full_occupancy_roofline(cfg_fn, F, flush, peak, n_sm, steps=30):
+    """The same step at K = 2 x SMs x 32 (9728 on 152 SMs): CTAs of 128 threads,
+    two per SM (the kernel's register budget allows two), so every scheduler
+    runs two warps -- at the metric's K = 4096 only 512 warps exist for 608
+    schedulers.  CUDA events around each step, L2 flushed between steps."""
     import torch
     from paper_2409_10469_gb300 import _mppi
-    K = 2 * 152 * 32
+    K = 2 * n_sm * 32
     cfg = cfg_fn(K=K, H=H_BENCH)
     st = torch.cuda.Stream()
     ctl = _mppi.Controller(cfg.robot, cfg.cost, cfg.mppi, stream=st.cuda_stream)
@@ -511,8 +511,9 @@ def run_ours(args):
     fl = F.rollout_flops(K_BENCH, H_BENCH, m["n_sub"])
     achieved = fl / (rollout_ms * 1e-3) / 1e12
     sm_max = (peaks or {}).get("sm_max_mhz", 2070.0)
-    peak = F.fp32_peak_tflops(152, sm_max)
-    full_occ = full_occupancy_roofline(W.config_trot, F, flush, peak)
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peak = F.fp32_peak_tflops(n_sm, sm_max)
+    full_occ = full_occupancy_roofline(W.config_trot, F, flush, peak, n_sm)
     prop = proposal_form(flush)
     direct = direct_form(flush, peaks)
     multi16 = multi_instance(peak)
@@ -542,7 +543,8 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": rollout_traffic(),
                      "kernel": "k_rollout", "flops_per_launch": fl,
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (max SM clock, MEASURED_PEAKS.json)" % sm_max},
+                     "peak_source": "%d SMs (device properties) x 128 FP32 lanes x 2 x %.0f MHz "
+                                    "(max SM clock, MEASURED_PEAKS.json)" % (n_sm, sm_max)},
         "e2e": {"value": world_size * K_BENCH * H_BENCH / (e2e_ms * 1e-3), "unit": "rollout-steps/s",
                 "ms_per_step": e2e_ms, "p99_ms": float(np.percentile(np.array(e2e) * 1e3, 99)),
                 "h2d_bytes_per_step": 4 * 37, "d2h_bytes_per_step": 4 * 12 + 4},

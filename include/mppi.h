@@ -141,6 +141,14 @@ int mppi_param_dim(mppi_handle h);
 /* Nominal knots mu (float[48], host or device): write / read. */
 mppi_status mppi_set_nominal(mppi_handle h, const float* mu);
 mppi_status mppi_get_nominal(mppi_handle h, float* mu_out);
+/* The samples of the handle's last control step (mppi_step, mppi_step_proposal,
+ * or a batch step the handle took part in): the K perturbed parameter vectors
+ * and their rollout costs -- the inputs of Eq. 1 / Eq. 2 (Alg. 1's sampled
+ * controls and their total costs).  U_out (float[K][D]) and L_out (float[K]),
+ * host or device, either may be NULL; the handle's workspace is copied on its
+ * stream, and the call returns once host outputs are written.  Undefined before
+ * the first step (the workspace is not cleared). */
+mppi_status mppi_get_samples(mppi_handle h, float* U_out, float* L_out);
 
 /* Alg. 1 sampling step (Sec. II-B; noise generator per the model spec):
  * U[k] = clamp(mu + sigma * eps_k), eps_k = Box-Muller(Philox4x32-10(key = seed,
@@ -365,28 +373,34 @@ mppi_status mppi_tc_gemm_bf16(const uint16_t* A, const uint16_t* B, float* D, in
  * callers that must not allocate device memory when they run -- a hard
  * real-time control loop that may not block in the driver's allocator, code
  * running inside another framework's memory pool, or a runtime that forbids
- * cudaMalloc after start-up.  They pass every buffer; the call's scratch (the
- * per-CTA partial sums and a completion counter) is a fixed 50,432-byte device
- * array compiled into the library, which every GPU that loads the library
- * keeps until the process exits.
+ * cudaMalloc after start-up.  They pass every buffer; the call's scratch (a row
+ * of 50 doubles of partial sums for each of at most 128 CTAs, and a completion
+ * counter) is a fixed 51,456-byte device array compiled into the library,
+ * which every GPU that loads the library keeps until the process exits.  n only
+ * sets how many samples each CTA sums, so every n up to MPPI_NOALLOC_MAX_N fits.
  *   L (float[n]), U (float[n][48], 16-byte aligned): costs and knots, device.
+ *   interp: the knot representation the knots belong to (MPPI_INTERP_CUBIC,
+ *   _ZERO or _LINEAR): the shift re-samples that representation's interpolant.
  *   mu_in (float[48]): the current nominal (kept if every cost is non-finite).
  *   mu_out (float[48]): the shifted nominal; may equal mu_in.
  *   mu_upd_out (float[48], optional): the updated mean before the shift.
  *   u0_out (float[12]): the control to apply; status_out (int, optional): 0, or
- *   4 when every cost is non-finite.  All pointers are device memory.
+ *   4 when every cost is non-finite.  All pointers are device memory of the
+ *   current device (or managed memory).
  *   stream: a cudaStream_t or NULL; the call only enqueues work.
  * The first call on a device looks up the array's device address with that
  * device current, so make it before any stream capture.  Calls share the one
- * array: calls that overlap on the GPU (different streams, or threads without
- * ordering) race and corrupt each other's results.
+ * array, whose completion counter each call clears before its kernel: calls
+ * that overlap on the GPU (different streams, or threads without ordering) race
+ * and corrupt each other's results.
  * Errors: MPPI_ERR_ARG when n < 1 or n > MPPI_NOALLOC_MAX_N, H < 2,
- * ctrl_steps < 1, lambda <= 0, a buffer is not device memory or U is
- * misaligned; MPPI_ERR_CUDA when a CUDA call fails.  No cudaMalloc, cudaFree or
- * other allocating call is made. */
+ * ctrl_steps < 1, lambda <= 0, interp is not a knot representation, a buffer is
+ * not device memory of the current device or U is misaligned; MPPI_ERR_CUDA
+ * when a CUDA call fails.  No cudaMalloc, cudaFree or other allocating call is
+ * made. */
 #define MPPI_NOALLOC_MAX_N (1 << 20)
 mppi_status mppi_update_noalloc(const float* L, const float* U, int n, int H, int ctrl_steps,
-                                double lambda, const float* mu_in, float* mu_out,
+                                double lambda, int interp, const float* mu_in, float* mu_out,
                                 float* mu_upd_out, float* u0_out, int* status_out, void* stream);
 
 #ifdef __cplusplus

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NONF
 EXPORTS = ("mppi_create", "mppi_destroy", "mppi_last_error", "mppi_set_nominal",
            "mppi_get_nominal", "mppi_sample", "mppi_rollouts", "mppi_update", "mppi_step",
            "mppi_set_timing", "mppi_get_timings", "mppi_launch_count", "mppi_state_size",
-           "mppi_update_noalloc", "mppi_batch_create", "mppi_batch_destroy",
+           "mppi_update_noalloc", "mppi_get_samples", "mppi_batch_create", "mppi_batch_destroy",
            "mppi_batch_last_error", "mppi_batch_step", "mppi_batch_set_shape", "mppi_batch_get_shape",
            "mppi_batch_autotune", "mppi_batch_launch_count", "mppi_batch_shared_model", "mppi_server_create",
            "mppi_server_destroy", "mppi_server_last_error", "mppi_server_add_robot", "mppi_server_submit",
@@ -128,7 +128,8 @@ def lib():
         L.mppi_set_timing.argtypes = [vp, C.c_int]
         L.mppi_get_timings.argtypes = [vp, C.POINTER(C.c_float)]
         L.mppi_launch_count.argtypes = [vp, C.POINTER(C.c_uint64)]
-        L.mppi_update_noalloc.argtypes = [fp, fp, C.c_int, C.c_int, C.c_int, C.c_double, fp, fp,
+        L.mppi_get_samples.argtypes = [vp, fp, fp]
+        L.mppi_update_noalloc.argtypes = [fp, fp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, fp, fp,
                                            fp, fp, fp, vp]
         L.mppi_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, vp, C.POINTER(C.c_void_p)]
         L.mppi_batch_destroy.argtypes = [vp]
@@ -243,11 +244,12 @@ def config_struct(mp: dict, block: int = 0):
 
 
 def update_noalloc(L, U, n, H, ctrl_steps, lam, mu_in, mu_out, u0_out, mu_upd_out=None,
-                   status_out=None, stream=None):
+                   status_out=None, stream=None, interp="cubic"):
     """mppi_update_noalloc: the update without a handle or any allocation (for
-    callers that cannot allocate device memory); all buffers are device memory."""
-    return lib().mppi_update_noalloc(_ptr(L), _ptr(U), n, H, ctrl_steps, lam, _ptr(mu_in),
-                                     _ptr(mu_out), _ptr(mu_upd_out), _ptr(u0_out),
+    callers that cannot allocate device memory); all buffers are device memory
+    of the current device; interp names the knot representation."""
+    return lib().mppi_update_noalloc(_ptr(L), _ptr(U), n, H, ctrl_steps, lam, interp_code(interp),
+                                     _ptr(mu_in), _ptr(mu_out), _ptr(mu_upd_out), _ptr(u0_out),
                                      _ptr(status_out), stream)
 
 
@@ -294,6 +296,13 @@ class Controller:
         out = np.zeros(self.D, np.float32) if out is None else out
         self._check(lib().mppi_get_nominal(self.h, _ptr(out)))
         return out
+
+    def last_samples(self):
+        """(U [K][D], L [K]) of the last control step (host copies)."""
+        U = np.zeros((self.K, self.D), np.float32)
+        L = np.zeros(self.K, np.float32)
+        self._check(lib().mppi_get_samples(self.h, _ptr(U), _ptr(L)))
+        return U, L
 
     def sample(self, step, mu_prop=None, out=None):
         self._check(lib().mppi_sample(self.h, step, _ptr(mu_prop), _ptr(out)))

@@ -393,6 +393,26 @@ extern "C" mppi_status mppi_get_nominal(mppi_handle h, float* mu_out) {
     return MPPI_OK;
 }
 
+extern "C" mppi_status mppi_get_samples(mppi_handle h, float* U_out, float* L_out) {
+    if (!h) return fail(h, MPPI_ERR_ARG, "null argument");
+    const size_t K = (size_t)h->cfg.K;
+    bool host = false;
+    if (U_out) {
+        const bool dev = is_device(U_out);
+        host = host || !dev;
+        CK(cudaMemcpyAsync(U_out, h->d_U, K * (size_t)h->D * sizeof(float),
+                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    }
+    if (L_out) {
+        const bool dev = is_device(L_out);
+        host = host || !dev;
+        CK(cudaMemcpyAsync(L_out, h->d_L, K * sizeof(float), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           h->stream));
+    }
+    if (host) CK(cudaStreamSynchronize(h->stream));
+    return MPPI_OK;
+}
+
 static mppi_status do_sample(mppi_handle h, uint32_t step, const float* mu_prop, float* U) {
     SampleArgs a;
     a.mu = h->d_mu;
@@ -475,7 +495,7 @@ static RolloutArgs rollout_args(mppi_handle h, const float* x0, int per, const f
     a.fuse = 0;  // mppi_step's knot representations fuse the update into the launch
     a.u0_host = a.mu_host = nullptr;
     a.status_host = nullptr;
-    a.inv_lambda = (float)(1.0 / h->cfg.lambda);
+    a.inv_lambda = 1.0 / (double)h->cfg.lambda;
     a.ctrl_steps = h->cfg.ctrl_steps;
     a.mu_w = nullptr;
     a.mu_upd = nullptr;
@@ -565,7 +585,7 @@ static mppi_status do_update(mppi_handle h, const float* dL, const float* dU, in
     a.n = n;
     a.H = h->cfg.H;
     a.ctrl_steps = h->cfg.ctrl_steps;
-    a.inv_lambda = (float)(1.0 / h->cfg.lambda);
+    a.inv_lambda = 1.0 / (double)h->cfg.lambda;
     a.Dp = h->D;
     a.interp = h->cfg.interp;
     CK(launch_update(a, h->stream));

@@ -156,7 +156,7 @@ InstDesc mppi::make_desc(const mppi_handle_s* h) {
     d.dt = (float)h->cfg.dt;
     d.inv_Hm1 = (float)(1.0 / (h->cfg.H - 1));
     d.arm = (float)mppi_armature(h->model_in, h->cfg.dt / h->cfg.n_sub);
-    d.inv_lambda = (float)(1.0 / h->cfg.lambda);
+    d.inv_lambda = 1.0 / (double)h->cfg.lambda;
     d.dt_d = h->cfg.dt;
     d.period_d = h->cost_in.gait_period;
     d.interp = h->cfg.interp;

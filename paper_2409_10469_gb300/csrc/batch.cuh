@@ -22,7 +22,8 @@ struct InstDesc {
     int* status;          // 0 ok, 4 all costs non-finite
     const float* mu_prop; // proposal mean or null
     int K, H, n_sub, n_prop, ctrl_steps, nx, gait;
-    float h, dt, inv_Hm1, arm, inv_lambda;
+    float h, dt, inv_Hm1, arm;
+    double inv_lambda;    // 1 / lambda (the weights' exponent is formed in FP64)
     double dt_d, period_d;
     float sigma[D], q_lo[3], q_hi[3];
     uint32_t key0, key1, inst_id;

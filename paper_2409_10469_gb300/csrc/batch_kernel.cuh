@@ -41,20 +41,37 @@ __device__ __forceinline__ void sample_lane(const InstDesc& d, int k, int leg, u
 
 __device__ __forceinline__ bool finite_f(float x) { return fabsf(x) <= 3.402823466e38f; }
 
-// Eq. 1, Eq. 2, apply, shift for one instance in one block.  The sums run over
-// 8 fixed groups of samples (k = g mod 8, each in increasing k) whatever the
-// block size, and are combined in group order: the result does not depend on
-// the block shape or on the other instances in the launch.
+// Eq. 1, Eq. 2, apply, shift for one instance in one block.  The weights
+// exp(-(L_k - L_min) / lambda) are computed once per sample -- exponent and exp
+// in FP64, kept as FP32 pairs (about 48 significant bits) -- for sub-chunks of
+// UPD_SUB samples in shared memory; the sums run over 8 fixed groups of samples
+// (k = g mod 8, each in increasing k) whatever the block size, as float-float
+// pairs (the products' rounding errors by FMA), and are combined in group order:
+// the result does not depend on the block shape or on the other instances in
+// the launch.
 constexpr int UPD_GROUPS = 8;
+constexpr int UPD_SUB = 256;  // a multiple of UPD_GROUPS: every group keeps its order across sub-chunks
+
+// (s, e) += (v, ve): s + v split exactly into the new s and an error term
+// (Knuth's TwoSum), the error and the low parts into e
+__device__ __forceinline__ void bu_ff_add(float& s, float& e, float v, float ve) {
+    const float t = s + v;
+    const float bp = t - s;
+    const float err = (s - (t - bp)) + (v - bp);
+    s = t;
+    e += ve + err;
+}
 
 template <int BLOCK>
 __device__ void block_update(const InstDesc& d, float* u0_row) {
     constexpr int W = BLOCK / 32;
     constexpr int ACTIVE = BLOCK / 12;  // groups processed at once (12 lanes each, four dims per lane)
+    constexpr int GPT = (UPD_GROUPS + ACTIVE - 1) / ACTIVE;  // groups per thread
     __shared__ float s_min[W];
     __shared__ double s_z[UPD_GROUPS];
     __shared__ double s_part[UPD_GROUPS][D];
     __shared__ float s_mu[D];
+    __shared__ float2 s_w[UPD_SUB];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = d.K;
     float lm = INFINITY;
@@ -71,42 +88,71 @@ __device__ void block_update(const InstDesc& d, float* u0_row) {
     for (int w = 1; w < W; w++) Lmin = fminf(Lmin, s_min[w]);
     const bool ok = finite_f(Lmin);
     const int li = tid % 12;
-    for (int g = tid / 12; g < UPD_GROUPS && tid < ACTIVE * 12; g += ACTIVE) {
-        float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
-        double z = 0.0;
-        // samples g, g + 8, ... in order; the loads of 8 of them are issued together
-        // (one L2 round trip per 8 samples), the sums still run one sample at a time
-        constexpr int NB = 8;
-        if (ok)
-            for (int k0 = g; k0 < K; k0 += NB * UPD_GROUPS) {
-                float lb[NB];
-                float4 ub[NB];
+    const bool grp = tid < ACTIVE * 12;
+    float sh[GPT][4], se[GPT][4], zh[GPT], ze[GPT];
 #pragma unroll
-                for (int q = 0; q < NB; q++) {
-                    const int k = k0 + q * UPD_GROUPS;
-                    lb[q] = k < K ? __ldcg(d.L + k) : 0.f;
-                    ub[q] = k < K ? __ldcg(reinterpret_cast<const float4*>(d.U + (size_t)k * D) + li)
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int gi = 0; gi < GPT; gi++) {
+        zh[gi] = 0.f;
+        ze[gi] = 0.f;
+#pragma unroll
+        for (int e = 0; e < 4; e++) { sh[gi][e] = 0.f; se[gi][e] = 0.f; }
+    }
+    if (ok)
+        for (int kb = 0; kb < K; kb += UPD_SUB) {
+            const int ke = min(K, kb + UPD_SUB);
+            __syncthreads();  // the previous sub-chunk's weights are consumed
+            for (int i = tid; i < UPD_SUB; i += BLOCK) {
+                const int k = kb + i;
+                float2 wk = make_float2(0.f, 0.f);
+                if (k < ke) {
+                    const float l = __ldcg(d.L + k);
+                    if (finite_f(l)) {
+                        const double wd = exp(-((double)l - (double)Lmin) * d.inv_lambda);
+                        wk.x = (float)wd;
+                        wk.y = (float)(wd - (double)wk.x);
+                    }
                 }
+                s_w[i] = wk;
+            }
+            __syncthreads();
 #pragma unroll
-                for (int q = 0; q < NB; q++) {
-                    if (k0 + q * UPD_GROUPS >= K) break;
-                    const float l = lb[q];
-                    const float w = finite_f(l) ? expf(-(l - Lmin) * d.inv_lambda) : 0.f;
-                    z += (double)w;
-                    const float u[4] = {ub[q].x, ub[q].y, ub[q].z, ub[q].w};
+            for (int gi = 0; gi < GPT; gi++) {
+                const int g = tid / 12 + gi * ACTIVE;
+                if (!grp || g >= UPD_GROUPS) continue;
+                // samples g, g + 8, ... of the sub-chunk in order; the loads of 8
+                // of them are issued together (one L2 round trip per 8 samples)
+                constexpr int NB = 8;
+                for (int k0 = kb + g; k0 < ke; k0 += NB * UPD_GROUPS) {
+                    float4 ub[NB];
 #pragma unroll
-                    for (int e = 0; e < 4; e++) {  // compensated (Kahan) sums per dimension
-                        const float y = w * u[e] - c[e];
-                        const float t = s[e] + y;
-                        c[e] = (t - s[e]) - y;
-                        s[e] = t;
+                    for (int q = 0; q < NB; q++) {
+                        const int k = k0 + q * UPD_GROUPS;
+                        ub[q] = k < ke ? __ldcg(reinterpret_cast<const float4*>(d.U + (size_t)k * D) + li)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int q = 0; q < NB; q++) {
+                        const int k = k0 + q * UPD_GROUPS;
+                        if (k >= ke) break;
+                        const float2 wk = s_w[k - kb];
+                        bu_ff_add(zh[gi], ze[gi], wk.x, wk.y);
+                        const float u[4] = {ub[q].x, ub[q].y, ub[q].z, ub[q].w};
+#pragma unroll
+                        for (int e = 0; e < 4; e++) {
+                            const float pr = wk.x * u[e];
+                            bu_ff_add(sh[gi][e], se[gi][e], pr, fmaf(wk.y, u[e], fmaf(wk.x, u[e], -pr)));
+                        }
                     }
                 }
             }
+        }
 #pragma unroll
-        for (int e = 0; e < 4; e++) s_part[g][4 * li + e] = (double)s[e] - (double)c[e];
-        if (li == 0) s_z[g] = z;
+    for (int gi = 0; gi < GPT; gi++) {
+        const int g = tid / 12 + gi * ACTIVE;
+        if (!grp || g >= UPD_GROUPS) continue;
+#pragma unroll
+        for (int e = 0; e < 4; e++) s_part[g][4 * li + e] = (double)sh[gi][e] + (double)se[gi][e];
+        if (li == 0) s_z[g] = (double)zh[gi] + (double)ze[gi];
     }
     __syncthreads();
     if (tid < D) {

@@ -48,7 +48,7 @@ struct RolloutArgs {
     // to finish combines them (Eq. 1, Eq. 2), applies and shifts; these are the
     // outputs and scratch of UpdateArgs, with part sized FUSE_W per CTA
     int fuse;
-    float inv_lambda;
+    double inv_lambda;     // 1 / lambda (FP64: the weights' exponent is formed in FP64)
     int ctrl_steps;
     float* mu_w;           // [48] the nominal (== mu), overwritten by the shifted nominal
     float* mu_upd;         // [48]
@@ -79,7 +79,7 @@ struct UpdateArgs {
     double* part;          // scratch [tiles][grid][50]: per-CTA partial sums, weight sum, cost minimum
     unsigned* counter;     // scratch [1 + tiles]: CTAs finished (0 between launches)
     int n, H, ctrl_steps;
-    float inv_lambda;
+    double inv_lambda;     // 1 / lambda (FP64: the weights' exponent is formed in FP64)
     int Dp, interp;        // parameters per sample, MPPI_INTERP_*
 };
 

@@ -11,11 +11,14 @@
 // the life of the process.
 //
 // The update kernel needs per-CTA partial sums and a finished-CTA counter.  Here
-// they live in `g_update_scratch` (MPPI_NOALLOC_SCRATCH_BYTES = 50,432 bytes:
-// 128 CTAs x 49 doubles + the counter).  Host code cannot use the symbol itself
-// as a device address: on each device the first call asks the runtime for the
-// array's address (cudaGetSymbolAddress, with that device current) and caches
-// it.  That first call should therefore happen before any stream capture.
+// they live in `g_update_scratch` (51,456 bytes: a row of 50 doubles -- 48 sums,
+// the weight sum and the chunk's cost minimum -- for each of the at most 128
+// CTAs, and a 256-byte slot for the counter).  n only sets how many samples each
+// of those CTAs sums, so no n up to MPPI_NOALLOC_MAX_N needs more scratch.  Host
+// code cannot use the symbol itself as a device address: on each device the
+// first call asks the runtime for the array's address (cudaGetSymbolAddress,
+// with that device current) and caches it.  That first call should therefore
+// happen before any stream capture.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -31,35 +34,46 @@ namespace {
 constexpr size_t PART_DOUBLES = update_part_doubles(D);
 constexpr size_t SCRATCH_BYTES = PART_DOUBLES * sizeof(double) + 256;  // partials + counter slot
 
+static_assert(SCRATCH_BYTES == 51456, "the scratch size stated in include/mppi.h");
+static_assert(PART_DOUBLES == (size_t)UPDATE_MAX_CTAS * (D + 2), "one row per CTA of the clamped grid");
+
 static __device__ __align__(256) unsigned char g_update_scratch[SCRATCH_BYTES];
 
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 void* g_addr[MAX_DEVICES] = {nullptr};
 
-bool on_device(const void* p) {
+// device memory of GPU `dev` (or managed memory): the kernels run on the current
+// device, so a buffer on another GPU is rejected instead of being reached
+// through a peer mapping that may not exist
+bool on_device(const void* p, int dev) {
     cudaPointerAttributes at;
     if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
 
 extern "C" mppi_status mppi_update_noalloc(const float* L, const float* U, int n, int H, int ctrl_steps,
-                                           double lambda, const float* mu_in, float* mu_out, float* mu_upd_out,
-                                           float* u0_out, int* status_out, void* stream) {
+                                           double lambda, int interp, const float* mu_in, float* mu_out,
+                                           float* mu_upd_out, float* u0_out, int* status_out, void* stream) {
     if (n < 1 || n > MPPI_NOALLOC_MAX_N || H < 2 || ctrl_steps < 1 || !(lambda > 0)) return MPPI_ERR_ARG;
-    if (update_grid(n) > UPDATE_MAX_CTAS) return MPPI_ERR_ARG;  // scratch holds UPDATE_MAX_CTAS partials
-    if (!on_device(L) || !on_device(U) || !on_device(mu_in) || !on_device(mu_out) || !on_device(u0_out))
+    // the knot representations (48 parameters); direct targets need 12 H
+    if (interp != MPPI_INTERP_CUBIC && interp != MPPI_INTERP_ZERO && interp != MPPI_INTERP_LINEAR)
         return MPPI_ERR_ARG;
-    if ((mu_upd_out && !on_device(mu_upd_out)) || (status_out && !on_device(status_out))) return MPPI_ERR_ARG;
-    if (((uintptr_t)U & 15u) != 0) return MPPI_ERR_ARG;
-
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return MPPI_ERR_CUDA;
+    if (!on_device(L, dev) || !on_device(U, dev) || !on_device(mu_in, dev) || !on_device(mu_out, dev) ||
+        !on_device(u0_out, dev))
+        return MPPI_ERR_ARG;
+    if ((mu_upd_out && !on_device(mu_upd_out, dev)) || (status_out && !on_device(status_out, dev)))
+        return MPPI_ERR_ARG;
+    if (((uintptr_t)U & 15u) != 0) return MPPI_ERR_ARG;
+
     void* base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -95,8 +109,8 @@ extern "C" mppi_status mppi_update_noalloc(const float* L, const float* U, int n
     a.n = n;
     a.H = H;
     a.ctrl_steps = ctrl_steps;
-    a.inv_lambda = (float)(1.0 / lambda);
-    a.Dp = D;                 // the cubic knot representation
-    a.interp = INTERP_CUBIC;
+    a.inv_lambda = 1.0 / lambda;
+    a.Dp = D;                 // a knot representation: 48 parameters
+    a.interp = interp;        // MPPI_INTERP_* equals the kernels' INTERP_* (api.cu checks it)
     return launch_update(a, st) == cudaSuccess ? MPPI_OK : MPPI_ERR_CUDA;
 }

@@ -19,13 +19,15 @@ __device__ __forceinline__ bool fin_f(float x) { return fabsf(x) <= 3.402823466e
 // representations).  Eq. 1 weights exp(-(L_k - L_min) / lambda) factor as
 // exp(-(L_k - m_c) / lambda) exp(-(m_c - L_min) / lambda) for any m_c, so each CTA
 // takes m_c = the minimum of its own finite costs and weights its rollouts by the
-// first factor (FP32, as the update kernel).  All sums are compensated FP32
-// pairs (hi, lo) -- Knuth's TwoSum for additions, an FMA for the rounding error
-// of products -- which carry about twice the FP32 precision at the FP32 rate
-// (on this part FP64 runs at 1/64 of it): w and w U over the warp's 8 rollouts
-// (lanes of the same leg), then over the warps in order.  The CTA writes (sums,
-// m_c) and counts itself in; the last CTA (every other CTA has finished, so none
-// still reads the nominal) takes L_min = min m_c and the factors
+// first factor.  Both factors -- the exponent (L - m) / lambda and its exp -- are
+// formed in FP64 (one exp per rollout and one per CTA: a few microseconds of the
+// FP64 pipe, which runs at 1/64 of the FP32 rate on this part) and split into an
+// FP32 pair (hi, lo) that carries about 48 significant bits.  The sums of w and
+// w U are compensated FP32 pairs (hi, lo) -- Knuth's TwoSum for additions, an
+// FMA for the rounding error of products -- at the FP32 rate: over the warp's 8
+// rollouts (lanes of the same leg), then over the warps in order.  The CTA writes
+// (sums, m_c) and counts itself in; the last CTA (every other CTA has finished,
+// so none still reads the nominal) takes L_min = min m_c and the factors
 // f_c = exp(-(m_c - L_min) / lambda), and for each of the 49 sums groups of
 // threads add f_c times the CTA partials over contiguous ranges of c, in four
 // interleaved accumulators each, all combined in a fixed order (32 partials
@@ -47,7 +49,7 @@ __device__ __forceinline__ void fused_update(const RolloutArgs& a, float L, cons
                                              bool valid) {
     __shared__ float s_m[8];
     __shared__ float2 s_sum[8][FUSE_W];
-    __shared__ float s_f[FUSE_MAX_CTAS];
+    __shared__ float2 s_f[FUSE_MAX_CTAS];
     __shared__ float s_mu[D];
     __shared__ int s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5, B = blockDim.x;
@@ -62,17 +64,20 @@ __device__ __forceinline__ void fused_update(const RolloutArgs& a, float L, cons
     __syncthreads();
     float mc = s_m[0];
     for (int w = 1; w < nw; w++) mc = fminf(mc, s_m[w]);
-    const float wk = (fin && fin_f(mc)) ? expf(-(L - mc) * a.inv_lambda) : 0.f;
-    // products w U_k with their rounding errors
+    // Eq. 1's weight around the CTA minimum: exponent and exp in FP64, kept as
+    // the pair wh + wl
+    const double wk = (fin && fin_f(mc)) ? exp(-((double)L - (double)mc) * a.inv_lambda) : 0.0;
+    const float wh = (float)wk, wl = (float)(wk - (double)wh);
+    // products w U_k with their rounding errors and the weight's low part
     float hs[NKNOT][3], he[NKNOT][3];
 #pragma unroll
     for (int j = 0; j < NKNOT; j++)
 #pragma unroll
         for (int i = 0; i < 3; i++) {
-            hs[j][i] = wk * Uk[j][i];
-            he[j][i] = fmaf(wk, Uk[j][i], -hs[j][i]);
+            hs[j][i] = wh * Uk[j][i];
+            he[j][i] = fmaf(wl, Uk[j][i], fmaf(wh, Uk[j][i], -hs[j][i]));
         }
-    float zs = leg == 0 ? wk : 0.f, ze = 0.f;  // one weight per rollout
+    float zs = leg == 0 ? wh : 0.f, ze = leg == 0 ? wl : 0.f;  // one weight per rollout
     // the warp's 8 rollouts: lanes leg, leg + 4, ..., leg + 28
 #pragma unroll
     for (int o = 4; o < 32; o <<= 1) {
@@ -116,7 +121,7 @@ __device__ __forceinline__ void fused_update(const RolloutArgs& a, float L, cons
     float M = INFINITY;
     for (int c = tid; c < G; c += B) {
         const float mcc = __ldcg(part + (size_t)c * FUSE_W + D + 1).x;
-        s_f[c] = mcc;
+        s_f[c].x = mcc;
         M = fminf(M, mcc);
     }
 #pragma unroll
@@ -127,10 +132,13 @@ __device__ __forceinline__ void fused_update(const RolloutArgs& a, float L, cons
     M = s_m[0];
     for (int w = 1; w < nw; w++) M = fminf(M, s_m[w]);
     const bool ok = fin_f(M);
-    // the factors exp(-(m_c - L_min) / lambda) (0 for a CTA without a finite cost)
+    // the factors exp(-(m_c - L_min) / lambda) in FP64, kept as pairs (0 for a CTA
+    // without a finite cost)
     for (int c = tid; c < G; c += B) {
-        const float mcc = s_f[c];
-        s_f[c] = (ok && fin_f(mcc)) ? expf(-(mcc - M) * a.inv_lambda) : 0.f;
+        const float mcc = s_f[c].x;
+        const double f = (ok && fin_f(mcc)) ? exp(-((double)mcc - (double)M) * a.inv_lambda) : 0.0;
+        const float fh = (float)f;
+        s_f[c] = make_float2(fh, (float)(f - (double)fh));
     }
     __syncthreads();
     // each of the 49 sums over the CTAs: thread group g (64 threads, one per sum)
@@ -150,9 +158,9 @@ __device__ __forceinline__ void fused_update(const RolloutArgs& a, float L, cons
                     v[q] = c + q < ce ? __ldcg(pd + (size_t)(c + q) * FUSE_W) : make_float2(0.f, 0.f);
 #pragma unroll
                 for (int q = 0; q < BATCH; q++) {
-                    const float f = c + q < ce ? s_f[c + q] : 0.f;
-                    const float p = f * v[q].x;
-                    ff_add(hi[q & 3], lo[q & 3], p, fmaf(f, v[q].x, -p) + f * v[q].y);
+                    const float2 f = c + q < ce ? s_f[c + q] : make_float2(0.f, 0.f);
+                    const float p = f.x * v[q].x;
+                    ff_add(hi[q & 3], lo[q & 3], p, fmaf(f.y, v[q].x, fmaf(f.x, v[q].y, fmaf(f.x, v[q].x, -p))));
                 }
             }
         }

@@ -6,18 +6,20 @@
 // dimension T tiles the 12 H parameters of direct targets into groups of 48;
 // the knot representations have one tile and their own kernel).  Every CTA
 // reads only its chunk's costs: their minimum m_c over the finite ones, the
-// FP32 weights w_k = exp(-(L_k - m_c)/lambda) (0 if L_k is not finite), their
-// sum z_c and the sums S_c = sum_k w_k U_k of its tile's parameters (compensated
-// FP32 per lane, float-float pairs across lanes and warps: FP64 runs at 1/64 of
-// the FP32 rate on this part, so only the last CTA's combine uses it).  It writes these and m_c to
-// scratch and bumps a counter; the CTA that sees the counter reach the grid
+// weights w_k = exp(-(L_k - m_c)/lambda) (0 if L_k is not finite) with the
+// exponent and the exp in FP64, computed once per sample into shared memory as
+// FP32 pairs (about 48 significant bits), their sum z_c and the sums
+// S_c = sum_k w_k U_k of its tile's parameters (float-float pairs per lane,
+// across lanes and warps: FP64 runs at 1/64 of the FP32 rate on this part, so
+// beyond the exps only the last CTA's combine uses it).  It writes these and m_c
+// to scratch and bumps a counter; the CTA that sees the counter reach the grid
 // size - 1 (no waiting: it is simply the last to finish) takes L_min = min_c m_c
-// and scales chunk c by f_c = exp(-(m_c - L_min)/lambda) -- Eq. 1's weights
-// factor as exp(-(L_k - L_min)/lambda) = w_k f_c -- so that mu' = sum_c f_c S_c /
-// sum_c f_c z_c.  The chunks are added in a fixed order and tree, so the result
-// does not depend on scheduling.  It writes mu', u0 = the controls of step 0
-// (knot 0, or the first direct target), the shifted nominal and the status, and
-// re-arms the counter for the next launch.
+// and scales chunk c by f_c = exp(-(m_c - L_min)/lambda) (FP64) -- Eq. 1's
+// weights factor as exp(-(L_k - L_min)/lambda) = w_k f_c -- so that
+// mu' = sum_c f_c S_c / sum_c f_c z_c.  The chunks are added in a fixed order and
+// tree, so the result does not depend on scheduling.  It writes mu', u0 = the
+// controls of step 0 (knot 0, or the first direct target), the shifted nominal
+// and the status, and re-arms the counter for the next launch.
 #include "kernels.h"
 
 namespace mppi {
@@ -39,34 +41,32 @@ __device__ __forceinline__ void ff_acc(float& s, float& e, float v, float ve) {
     e += ve + err;
 }
 
-// One warp's share of a CTA chunk: samples k = kb, kb + UPD_WARPS, ... < ke, the
-// lane's parameter pair u2[k * row2] weighted by w_k = exp(-(L_k - m) / lambda)
-// (0 for a non-finite cost) into compensated (Kahan) sums, one sample at a time
-// in order; the loads of 8 samples are issued together (one L2 round trip each)
-__device__ __forceinline__ void sum_chunk(const float* L, const float2* u2, int row2, int kb, int ke, float m,
-                                          float inv_lambda, float& s0, float& s1, float& c0, float& c1) {
+constexpr int UPD_SUB = UPD_THREADS;  // samples whose weights sit in shared memory at a time
+
+// One warp's share of a sub-chunk: samples k = kb, kb + UPD_WARPS, ... < ke, the
+// lane's parameter pair u2[k * row2] times the weight pair w[k - ks] (the
+// products' rounding errors by FMA) into float-float sums (s, e), one sample at
+// a time in order; the loads of 8 samples are issued together (one L2 round
+// trip each)
+__device__ __forceinline__ void sum_chunk(const float2* w, int ks, const float2* u2, int row2, int kb, int ke,
+                                          float& s0, float& s1, float& e0, float& e1) {
     constexpr int NB = 8;
     for (int kk = kb; kk < ke; kk += NB * UPD_WARPS) {
-        float lb[NB];
         float2 ub[NB];
 #pragma unroll
         for (int q = 0; q < NB; q++) {
             const int k = kk + q * UPD_WARPS;
-            lb[q] = k < ke ? __ldg(L + k) : 0.f;
             ub[q] = k < ke ? __ldg(u2 + (size_t)k * row2) : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int q = 0; q < NB; q++) {
-            if (kk + q * UPD_WARPS >= ke) break;
-            const float l = lb[q];
-            const float w = finitef(l) ? expf(-(l - m) * inv_lambda) : 0.f;
+            const int k = kk + q * UPD_WARPS;
+            if (k >= ke) break;
+            const float2 wk = w[k - ks];
             const float2 u = ub[q];
-            float y0 = w * u.x - c0, y1 = w * u.y - c1;
-            float t0 = s0 + y0, t1 = s1 + y1;
-            c0 = (t0 - s0) - y0;
-            c1 = (t1 - s1) - y1;
-            s0 = t0;
-            s1 = t1;
+            const float p0 = wk.x * u.x, p1 = wk.x * u.y;
+            ff_acc(s0, e0, p0, fmaf(wk.y, u.x, fmaf(wk.x, u.x, -p0)));
+            ff_acc(s1, e1, p1, fmaf(wk.y, u.y, fmaf(wk.x, u.y, -p1)));
         }
     }
 }
@@ -79,7 +79,8 @@ struct UpdSmem {
     float red[UPD_WARPS];
     float2 z[UPD_WARPS];              // per-warp weight sums (hi, lo)
     float2 part[UPD_WARPS][UPD_TILE];  // per-warp parameter sums (hi, lo)
-    float f[UPDATE_MAX_CTAS];  // the chunks' factors exp(-(m_c - L_min) / lambda)
+    float2 w[UPD_SUB];                 // a sub-chunk's weights (hi, lo)
+    double f[UPDATE_MAX_CTAS];  // the chunks' factors exp(-(m_c - L_min) / lambda)
     double Z;
     int last;
 };
@@ -112,11 +113,32 @@ __device__ __forceinline__ void chunk_partials(const UpdateArgs& a, int b, int G
     }
     const float m = block_min(lm, s.red);
     const bool okc = finitef(m);
+    // sum_k w_k U_k: warp w takes samples ks + w, ks + w + 8, ... of each
+    // sub-chunk; lane i < 24 owns parameters d0 + 2i, d0 + 2i + 1 (Dp is even, so
+    // a pair never straddles the end)
+    const bool own = lane < UPD_TILE / 2 && d0 + 2 * lane < Dp;
+    const float2* u2 = reinterpret_cast<const float2*>(a.U + d0) + lane;
     float zs = 0.f, ze = 0.f;
+    float s0 = 0.f, s1 = 0.f, e0 = 0.f, e1 = 0.f;
     if (okc)
-        for (int k = k0 + tid; k < k1; k += UPD_THREADS) {
-            const float l = __ldg(a.L + k);
-            if (finitef(l)) ff_acc(zs, ze, expf(-(l - m) * a.inv_lambda), 0.f);
+        for (int ks = k0; ks < k1; ks += UPD_SUB) {
+            // Eq. 1's weights around the chunk minimum, once per sample: exponent
+            // and exp in FP64, kept as pairs
+            const int k = ks + tid;
+            float2 wk = make_float2(0.f, 0.f);
+            if (k < k1) {
+                const float l = __ldg(a.L + k);
+                if (finitef(l)) {
+                    const double wd = exp(-((double)l - (double)m) * a.inv_lambda);
+                    wk.x = (float)wd;
+                    wk.y = (float)(wd - (double)wk.x);
+                }
+            }
+            ff_acc(zs, ze, wk.x, wk.y);
+            __syncthreads();  // the previous sub-chunk's weights are consumed
+            s.w[tid] = wk;
+            __syncthreads();
+            if (own) sum_chunk(s.w, ks, u2, Dp / 2, ks + warp, min(k1, ks + UPD_SUB), s0, s1, e0, e1);
         }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -124,16 +146,9 @@ __device__ __forceinline__ void chunk_partials(const UpdateArgs& a, int b, int G
         ff_acc(zs, ze, v, ve);
     }
     if (lane == 0) s.z[warp] = make_float2(zs, ze);
-    // sum_k w_k U_k: warp w takes k0 + w, k0 + w + 8, ...; lane i < 24 owns
-    // parameters d0 + 2i, d0 + 2i + 1 (Dp is even, so a pair never straddles the end)
-    const bool own = lane < UPD_TILE / 2 && d0 + 2 * lane < Dp;
-    float s0 = 0.f, s1 = 0.f, c0 = 0.f, c1 = 0.f;
-    if (okc && own)
-        sum_chunk(a.L, reinterpret_cast<const float2*>(a.U + d0) + lane, Dp / 2, k0 + warp, k1, m, a.inv_lambda, s0,
-                  s1, c0, c1);
-    if (lane < UPD_TILE / 2) {  // Kahan's sum s with compensation c stands for s - c
-        s.part[warp][2 * lane] = make_float2(s0, -c0);
-        s.part[warp][2 * lane + 1] = make_float2(s1, -c1);
+    if (lane < UPD_TILE / 2) {
+        s.part[warp][2 * lane] = make_float2(s0, e0);
+        s.part[warp][2 * lane + 1] = make_float2(s1, e1);
     }
     __syncthreads();
     // the warps' pairs added in warp order; the row holds hi + lo as a double
@@ -170,7 +185,7 @@ __device__ __forceinline__ bool combine_setup(const UpdateArgs& a, int G, const 
     const float mc = tid < G ? (float)__ldcg(rows + (size_t)tid * UPD_ROW + UPD_TILE + 1) : INFINITY;
     const float Lmin = block_min(mc, s.red);
     const bool ok = finitef(Lmin);
-    if (tid < G) s.f[tid] = (ok && finitef(mc)) ? expf(-(mc - Lmin) * a.inv_lambda) : 0.f;
+    if (tid < G) s.f[tid] = (ok && finitef(mc)) ? exp(-((double)mc - (double)Lmin) * a.inv_lambda) : 0.0;
     __syncthreads();
     if (warp == 0) {
         constexpr int NQ = UPDATE_MAX_CTAS / 32;
@@ -184,7 +199,7 @@ __device__ __forceinline__ bool combine_setup(const UpdateArgs& a, int G, const 
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
             const int c = lane + 32 * q;
-            if (c < G) z = fma((double)s.f[c], v[q], z);
+            if (c < G) z = fma(s.f[c], v[q], z);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
@@ -209,7 +224,7 @@ __device__ __forceinline__ double combine_param(int G, const double* rows, int j
 #pragma unroll
         for (int i = 0; i < UPD_NB; i++) {
             const int c = c0 + 4 * i;
-            if (c < G) acc = fma((double)s.f[c], v[i], acc);
+            if (c < G) acc = fma(s.f[c], v[i], acc);
         }
     }
     acc += __shfl_xor_sync(0xffffffffu, acc, 1);

@@ -1,12 +1,14 @@
-"""Multi-instance persistent launch (mppi_batch_*): every instance's step equals
-the single-instance path within the update tolerance, an instance's result is
-bit-identical alone and inside a mixed batch, inactive instances are untouched,
-the autotuner picks a valid shape and restores the nominals."""
+"""Multi-instance persistent launch (mppi_batch_*): every instance's samples,
+costs and update agree with the FP64 oracle (Alg. 1, Eq. 1-2 per instance), its
+step equals the single-instance path within the update tolerance, an instance's
+result is bit-identical alone and inside a mixed batch, inactive instances are
+untouched, the autotuner picks a valid shape and restores the nominals."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle as O  # noqa: E402
 from paper_2409_10469_gb300 import _mppi, workloads as W  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -36,6 +38,54 @@ def x0_row(cfg):
 def mix():
     return [(W.config_stand(), 100, 50), (W.config_terrain(), 64, 60), (W.config_push(), 96, 100),
             (W.config_trot(), 300, 100)]
+
+
+def rel(a, b):
+    return np.abs(a - b) / np.maximum(np.abs(b), 1.0)
+
+
+def test_batch_matches_oracle_per_instance():
+    """each instance of a mixed batch (stand, heightfield + step box, push,
+    trot), two control steps: its knots are the oracle's Philox samples
+    bit for bit, its costs are the oracle's rollouts of those knots (<= 1e-3 on
+    flat ground; on the heightfield and with the free box the 95th percentile
+    <= 1e-3 and every sample within max(1e-3, 3x the oracle's own sensitivity to
+    a 1e-7 perturbation of x0)), and its mean, applied control and shifted
+    nominal are the oracle's Eq. 1 / Eq. 2 and shift on those knots and costs
+    (<= 1e-6)"""
+    items = mix()
+    members = [make(c, K, H, inst=i) for i, (c, K, H) in enumerate(items)]
+    batch = _mppi.Batch([c for c, _ in members])
+    x0s = np.stack([x0_row(c) for c, _, _ in items])
+    for step in (0, 1):
+        before = [c.get_nominal().copy() for c, _ in members]
+        u0b = np.zeros((len(items), 12), np.float32)
+        batch.step(x0s, np.full(len(items), step), u0s=u0b)
+        mu_upds = np.zeros((len(items), 48), np.float32)
+        noms = np.zeros((len(items), 48), np.float32)
+        batch.means(mu_upds, noms)
+        for i, ((cfg, K, H), (ctl, m)) in enumerate(zip(items, members)):
+            Ub, Lb = ctl.last_samples()
+            assert np.array_equal(Ub.view(np.uint32), O.sample(m, before[i], step).view(np.uint32)), (i, step)
+            world = O.World(cfg.robot)
+            t0 = step * m["ctrl_steps"] * m["dt"]
+            x0 = cfg.x0.astype(np.float32).astype(np.float64)
+            Lo = O.rollouts(world, cfg.cost, m, t0, x0, Ub)
+            r = rel(Lb.astype(np.float64), Lo)
+            if i in (0, 3):
+                assert r.max() <= 1e-3, (i, step, r.max())
+            else:
+                sens = np.zeros(K)
+                for sd in range(2):
+                    xp = x0 * (1 + 1e-7 * np.random.default_rng(sd).standard_normal(x0.shape))
+                    sens = np.maximum(sens, rel(O.rollouts(world, cfg.cost, m, t0, xp, Ub), Lo))
+                assert np.percentile(r, 95) <= 1e-3, (i, step)
+                assert np.all(r <= np.maximum(1e-3, 3 * sens)), (i, step, r.max())
+            _, mu_o, _ = O.update(Lb, Ub, m["lam"])
+            assert rel(mu_upds[i], mu_o).max() <= 1e-6, (i, step)
+            assert np.array_equal(u0b[i], mu_upds[i][:12])
+            assert rel(noms[i], O.shift(mu_upds[i], H, m["ctrl_steps"])).max() <= 1e-6, (i, step)
+            assert np.array_equal(noms[i], ctl.get_nominal())
 
 
 def test_batch_matches_single_instance_steps():

@@ -133,7 +133,7 @@ def test_full_step_matches_the_oracle_update(mode):
     L = torch.empty(64, device="cuda")
     ctl2.rollouts(dev(cfg.x0), U=dev(U_o), n=64, t0=2 * m["ctrl_steps"] * m["dt"], L_out=L)
     _, mu_same, _ = O.update(L.cpu().numpy(), U_o, m["lam"], dim=ctl.D)
-    assert np.abs(mu_upd - mu_same).max() <= 4e-6
+    assert np.abs(mu_upd - mu_same).max() <= 1e-6 * max(1.0, np.abs(mu_same).max())
     assert np.array_equal(u0, mu_upd[:12])
 
 
@@ -162,9 +162,9 @@ def test_batch_runs_knot_representations_and_rejects_direct():
         for i, c in enumerate(singles):
             u0 = np.zeros(12, np.float32)
             c.step(x0s[i, :37], step, u0_out=u0)
-            assert np.abs(u0b.cpu().numpy()[i] - u0).max() <= 1e-6 * 4, (i, step)
+            assert np.abs(u0b.cpu().numpy()[i] - u0).max() <= 1e-6 * max(1.0, np.abs(u0).max()), (i, step)
             nb, ns = members[i].get_nominal(), c.get_nominal()
-            assert np.abs(nb - ns).max() <= 1e-6 * 4, (i, step)
+            assert np.abs(nb - ns).max() <= 1e-6 * max(1.0, np.abs(ns).max()), (i, step)
     d, _ = ctl_for(cfg, interp="direct")
     with pytest.raises(_mppi.MppiError):
         _mppi.Batch([d])

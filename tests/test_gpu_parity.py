@@ -328,7 +328,7 @@ def test_full_step_matches_components():
     ctl2.rollouts(dev(cfg.x0), U=dev(U_o), n=64, L_out=L)
     Lg = L.cpu().numpy()
     _, mu_same, _ = O.update(Lg, U_o, m["lam"])
-    assert np.abs(mu - mu_same).max() <= 1e-6 * 4
+    assert np.abs(mu - mu_same).max() <= 1e-6 * max(1.0, np.abs(mu_same).max())
     assert np.array_equal(u0, mu[:12])
     assert ctl.launch_count() == 1   # one kernel: sampling, rollouts and the update
 
@@ -355,7 +355,7 @@ def test_fused_update_matches_oracle(K, block):
     L = torch.empty(K, device="cuda")
     ctl2.rollouts(dev(cfg.x0), U=dev(U_o), n=K, L_out=L, t0=3 * mp["ctrl_steps"] * mp["dt"])
     _, mu_o, _ = O.update(L.cpu().numpy(), U_o, mp["lam"])
-    assert np.abs(mu - mu_o).max() <= 4e-6 * max(1.0, np.abs(mu_o).max())
+    assert np.abs(mu - mu_o).max() <= 1e-6 * max(1.0, np.abs(mu_o).max())
     assert np.array_equal(u0, mu[:12])
     sh = O.shift(mu, mp["H"], mp["ctrl_steps"])
     assert np.abs(ctl.get_nominal() - sh).max() <= 1e-6 * max(1.0, np.abs(sh).max())
@@ -395,7 +395,7 @@ def test_closed_loop_ten_control_steps_stand():
     the GPU (one kernel) from the state the loop has reached; from the same state
     and nominal the oracle's costs of the same samples agree with the GPU's to
     1e-3, and the step's mean equals the oracle's update of those samples on the
-    GPU's costs to 4e-6; the plant (the oracle's simulator) then advances one
+    GPU's costs to 1e-6; the plant (the oracle's simulator) then advances one
     control period with the applied targets, so every step of the loop is checked
     (trajectory-level parity over many steps is ill-posed: Eq. 1 amplifies
     rounding differences between near-equal costs)"""
@@ -421,7 +421,7 @@ def test_closed_loop_ten_control_steps_stand():
         Lo = O.rollouts(world, cfg.cost, m, t0, x32.astype(np.float64), U_o)
         assert (np.abs(Lg - Lo) / np.maximum(np.abs(Lo), 1.0)).max() <= 1e-3, step
         _, mu_o, _ = O.update(Lg, U_o, m["lam"])
-        assert np.abs(mu - mu_o).max() <= 4e-6 * max(1.0, np.abs(mu_o).max()), step
+        assert np.abs(mu - mu_o).max() <= 1e-6 * max(1.0, np.abs(mu_o).max()), step
         assert np.array_equal(u0, mu[:12])
         for _ in range(m["ctrl_steps"]):
             x = O.dt_steps(world, x[None], u0.astype(np.float64)[None], m["n_sub"], h)[0]

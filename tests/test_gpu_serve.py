@@ -1,12 +1,14 @@
 """Serving runtime (mppi_server_*): a robot's control is bit-identical alone and
-inside a busy mix of concurrent requests, and within the update tolerance of the
-single-instance step; admission respects the memory budget; a second request
-for a busy robot is refused."""
+inside a busy mix of concurrent requests, within the update tolerance of the
+single-instance step, and equal to the FP64 oracle's update of the same samples;
+admission respects the memory budget; a second request for a busy robot is
+refused."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle as O  # noqa: E402
 from paper_2409_10469_gb300 import _mppi, workloads as W  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -72,6 +74,51 @@ def test_result_same_alone_and_in_the_mix():
     u0s = np.zeros(12, np.float32)
     single.step(cfg3.x0.astype(np.float32), 0, u0_out=u0s)
     assert np.max(np.abs(u0s - outs_alone[0]) / np.maximum(np.abs(u0s), 1)) <= 1e-6
+
+
+def test_served_robot_matches_oracle_in_the_mix():
+    """one robot (trot, K = 700, H = 80) inside a 24-robot mix with concurrent
+    requests, three control steps: its samples are the oracle's Philox knots of
+    the nominal it held; their rollout costs (the single-instance kernel, whose
+    arithmetic the persistent kernel shares) are the oracle's rollouts of them to
+    1e-3; and the served control and the robot's next nominal are the oracle's
+    Eq. 1 / Eq. 2 mean and shift of those samples and costs to 1e-6"""
+    specs = W.serving_robots(23, seed=12, K_range=(256, 2048), H_range=(50, 150))
+    srv = _mppi.Server(256 << 20, 24, 2048)
+    others = []
+    for i, (task, K, H) in enumerate(specs):
+        c, cf = robot(task, K, H, inst=200 + i)
+        others.append((srv.add_robot(c), c, cf))
+    x, cfg = robot("trot", 700, 80, inst=7)
+    rid = srv.add_robot(x)
+    m = dict(cfg.mppi, inst=7)
+    costs = _mppi.Controller(cfg.robot, cfg.cost, m)
+    world = O.World(cfg.robot)
+    x0 = cfg.x0.astype(np.float32)
+    for step in range(3):
+        nominal = x.get_nominal().copy()
+        for r, c, cf in others[:12]:
+            srv.submit(r, cf.x0, step)
+        srv.tick()
+        srv.submit(rid, x0, step)
+        for r, c, cf in others[12:]:
+            srv.submit(r, cf.x0, step)
+        srv.drain()
+        u0, _ = srv.poll(rid)
+        U_o = O.sample(m, nominal, step)
+        t0 = step * m["ctrl_steps"] * m["dt"]
+        L = torch.empty(700, device="cuda")
+        costs.rollouts(torch.tensor(x0).cuda(), U=torch.tensor(U_o).cuda(), n=700, t0=t0, L_out=L)
+        Lg = L.cpu().numpy()
+        Lo = O.rollouts(world, cfg.cost, m, t0, x0.astype(np.float64), U_o)
+        assert (np.abs(Lg - Lo) / np.maximum(np.abs(Lo), 1.0)).max() <= 1e-3, step
+        _, mu_o, _ = O.update(Lg, U_o, m["lam"])
+        assert np.max(np.abs(u0 - mu_o[:12]) / np.maximum(np.abs(mu_o[:12]), 1.0)) <= 1e-6, step
+        sh = O.shift(mu_o, m["H"], m["ctrl_steps"])
+        assert np.max(np.abs(x.get_nominal() - sh) / np.maximum(np.abs(sh), 1.0)) <= 1e-6, step
+        for r, c, cf in others:
+            assert srv.poll(r) is not None
+    costs.close()
 
 
 def test_admission_by_memory_budget():

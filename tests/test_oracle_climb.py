@@ -16,24 +16,35 @@ def state_with_vx(vx):
     return x
 
 
-@pytest.mark.parametrize("vx", [0.0, 0.5, 1.2, -0.3, 5.0])
-@pytest.mark.parametrize("t", [0.0, 0.06, 0.13, 0.31, 0.44])
-def test_raibert_reference_closed_form(vx, t):
+# The reading of the Raibert-feedback reference: a swinging foot is placed
+# dx = (T_stance / 2) v_x + k (v_x - v_ref) ahead of its hip, T_stance half of the
+# gait period P = 0.5 s, k = 0.1 s, v_ref = 0.5 m/s, realised as the hip-flexion
+# change -dx / L (L = 0.3 m) clamped to +-0.4 rad.  Written out:
+#   v_x = 0.5 (= v_ref): dx = 0.125 * 0.5           = 0.0625  -> -0.208333... rad
+#   v_x = 0.0:           dx = 0.1 * (0 - 0.5)       = -0.05   -> +0.166666... rad
+#   v_x = -0.3:          dx = -0.0375 + 0.1 * -0.8  = -0.1175 -> +0.391666... rad
+#   v_x = 1.2:           dx = 0.15 + 0.1 * 0.7      = 0.22    -> -0.7333 -> clamped -0.4
+#   v_x = 5.0:           dx = 0.625 + 0.45          = 1.075   -> clamped -0.4
+DTH = {0.5: -0.0625 / 0.3, 0.0: 0.05 / 0.3, -0.3: 0.1175 / 0.3, 1.2: -0.4, 5.0: -0.4}
+
+
+@pytest.mark.parametrize("vx", sorted(DTH))
+def test_raibert_reference_written_out(vx):
+    """the stand pose (0, 0.8, -1.6), hip amplitude 0.1 and knee amplitude 0.3:
+    at a quarter period (t = 0.125 s) legs FR and RL swing fully (sin = 1) --
+    hip 0.9 + dth, knee -1.9 -- and FL, RR stand (sin = -1) -- hip 0.7, knee
+    -1.6, no feedback; at three quarters the pairs swap; at t = 0 no leg swings
+    and the reference is the stand pose whatever v_x"""
     c = W.cost("trot_raibert")
-    c1 = dict(c, gait=1)
-    P, k, Lg, vr = c["gait_period"], c["raibert_k"], c["raibert_len"], c["v_ref"]
-    dth = min(0.4, max(-0.4, -(P / 4 * vx + k * (vx - vr)) / Lg))
-    u2 = O.gait_ref_x(c, t, state_with_vx(vx))
-    u1 = O.gait_ref(c1, t)
-    phase0 = [0, 1, 1, 0]
-    for leg in range(4):
-        s = math.sin(2 * math.pi * t / P + math.pi * phase0[leg])
-        sw = max(0.0, s)
-        # abduction and knee as in the open-loop trot; hip moved by sw * dth
-        assert u2[3 * leg] == u1[3 * leg] and abs(u2[3 * leg + 2] - u1[3 * leg + 2]) < 1e-15
-        assert abs(u2[3 * leg + 1] - (u1[3 * leg + 1] + sw * dth)) < 1e-12
-        if s <= 0:
-            assert u2[3 * leg + 1] == u1[3 * leg + 1]      # stance legs carry no feedback
+    assert (c["gait_period"], c["raibert_k"], c["raibert_len"], c["v_ref"]) == (0.5, 0.1, 0.3, 0.5)
+    d = DTH[vx]
+    swing, stance = [0.0, 0.9 + d, -1.9], [0.0, 0.7, -1.6]
+    u = O.gait_ref_x(c, 0.125, state_with_vx(vx))
+    assert u == pytest.approx(swing + stance + stance + swing, abs=1e-12)
+    u = O.gait_ref_x(c, 0.375, state_with_vx(vx))
+    assert u == pytest.approx(stance + swing + swing + stance, abs=1e-12)
+    u = O.gait_ref_x(c, 0.0, state_with_vx(vx))
+    assert u == pytest.approx([0.0, 0.8, -1.6] * 4, abs=1e-12)
 
 
 def test_raibert_feedback_direction_and_clamp():
