@@ -222,7 +222,8 @@ const char* mppi_batch_last_error(mppi_batch b);
  * its first nx_i entries); steps: host uint32[n] control-step index of each
  * instance (its Philox counter word 2 and gait time), NULL = unchanged;
  * u0s: optional float[n][12] host or device (rows of inactive instances keep
- * their last value).  Host outputs are complete on return. */
+ * their last value, zero before an instance's first step).  Host outputs are
+ * complete on return. */
 mppi_status mppi_batch_step(mppi_batch b, const int* active, const float* x0s, const uint32_t* steps,
                             float* u0s);
 

@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libmppi_gb300.so")
 SOURCES = ["api.cu", "sample.cu", "rollout.cu", "update.cu", "noalloc.cu", "batch.cu", "batch_uni.cu", "serve.cu", "mlp.cu", "gemm.cu", "features.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-         "-I" + os.path.join(ROOT, "include")]
+         "-I" + os.path.join(ROOT, "include"), "-I" + BUILD]
 
 
 def _nvcc():
@@ -31,11 +31,43 @@ def _nvcc():
 def _deps():
     out = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     out.append(os.path.join(ROOT, "include", "mppi.h"))
+    out.append(os.path.abspath(__file__))
     return out
+
+
+TRIG_N = 512
+
+
+def write_trig_table(path: str) -> None:
+    """The precise sine / cosine table of csrc/precise.cuh: at a_j = j 2 pi / 512,
+    (cos hi, cos lo, sin hi, sin lo) with hi the FP32 rounding of the double value
+    and lo the FP32 rounding of the rest, as exact hexadecimal literals."""
+    import math
+    import struct
+
+    def f32(x):
+        return struct.unpack("f", struct.pack("f", x))[0]
+
+    rows = []
+    for j in range(TRIG_N):
+        a = 2.0 * math.pi * j / TRIG_N
+        c, s = math.cos(a), math.sin(a)
+        ch, sh = f32(c), f32(s)
+        vals = (ch, f32(c - ch), sh, f32(s - sh))
+        rows.append("    {" + ", ".join("%sf" % float(v).hex() for v in vals) + "},")
+    txt = ("// generated by build.py: sin / cos at j 2 pi / %d as FP32 pairs (do not edit)\n"
+           "#pragma once\nnamespace mppi {\nconstexpr int TRIG_N = %d;\n"
+           "static __device__ float4 g_trig[TRIG_N] = {\n%s\n};\n}  // namespace mppi\n"
+           % (TRIG_N, TRIG_N, "\n".join(rows)))
+    if os.path.exists(path) and open(path).read() == txt:
+        return
+    with open(path, "w") as f:
+        f.write(txt)
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
+    write_trig_table(os.path.join(BUILD, "trig_table.inc"))
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t for d in _deps()):

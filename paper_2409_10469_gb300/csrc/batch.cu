@@ -286,7 +286,8 @@ extern "C" mppi_status mppi_batch_create(const mppi_handle* hs, int n, void* str
               cudaMallocHost((void**)&b->h_u0s, (size_t)n * NJ * sizeof(float)) == cudaSuccess;
     if (!ok || cudaMemcpy(b->d_desc, descs.data(), n * sizeof(InstDesc), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(b->d_done, 0, n * sizeof(unsigned)) != cudaSuccess ||
-        cudaMemset(b->d_x0s, 0, (size_t)n * NX_BOX * sizeof(float)) != cudaSuccess) {
+        cudaMemset(b->d_x0s, 0, (size_t)n * NX_BOX * sizeof(float)) != cudaSuccess ||
+        cudaMemset(b->d_u0s, 0, (size_t)n * NJ * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         mppi_batch_destroy(b);
         return MPPI_ERR_OOM;

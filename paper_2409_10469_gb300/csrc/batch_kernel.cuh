@@ -55,11 +55,12 @@ constexpr int UPD_SUB = 256;  // a multiple of UPD_GROUPS: every group keeps its
 // (s, e) += (v, ve): s + v split exactly into the new s and an error term
 // (Knuth's TwoSum), the error and the low parts into e
 __device__ __forceinline__ void bu_ff_add(float& s, float& e, float v, float ve) {
-    const float t = s + v;
-    const float bp = t - s;
-    const float err = (s - (t - bp)) + (v - bp);
+    // _rn intrinsics: never contracted with a preceding product (which would break TwoSum)
+    const float t = __fadd_rn(s, v);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
     s = t;
-    e += ve + err;
+    e = __fadd_rn(e, __fadd_rn(ve, err));
 }
 
 template <int BLOCK>

@@ -352,29 +352,4 @@ __device__ __forceinline__ float3 mulRT(const float R[3][3], float3 v) {
               R[0][2] * v.x + R[1][2] * v.y + R[2][2] * v.z);
 }
 
-// quaternion q <- normalise(q (x) exp(w h)), w in body coordinates.  With
-// x = (|w| h / 2)^2 the exponential's parts are power series in x, so no square
-// root, reciprocal or range reduction is needed: cos(|w| h / 2) and
-// sin(|w| h / 2) / |w| = (h / 2) sin(s) / s to x^4, truncation below 3e-10 for
-// |w| h <= 1 (a sub-step's rotation is far smaller).
-__device__ __forceinline__ void quat_integrate(float q[4], float3 w, float h) {
-    const float hh = 0.5f * h;
-    const float x = dot3(w, w) * (hh * hh);
-    float pc = fmaf(x, 2.48015873e-05f, -1.38888889e-03f);
-    pc = fmaf(x, pc, 4.16666667e-02f);
-    pc = fmaf(x, pc, -0.5f);
-    const float d0 = fmaf(x, pc, 1.f);
-    float ps = fmaf(x, 2.75573192e-06f, -1.98412698e-04f);
-    ps = fmaf(x, ps, 8.33333333e-03f);
-    ps = fmaf(x, ps, -1.66666667e-01f);
-    const float sk = hh * fmaf(x, ps, 1.f);
-    const float d1 = sk * w.x, d2 = sk * w.y, d3 = sk * w.z;
-    float r0 = q[0] * d0 - q[1] * d1 - q[2] * d2 - q[3] * d3;
-    float r1 = q[0] * d1 + q[1] * d0 + q[2] * d3 - q[3] * d2;
-    float r2 = q[0] * d2 - q[1] * d3 + q[2] * d0 + q[3] * d1;
-    float r3 = q[0] * d3 + q[1] * d2 - q[2] * d1 + q[3] * d0;
-    float inv = rsqrt_approx(r0 * r0 + r1 * r1 + r2 * r2 + r3 * r3);
-    q[0] = r0 * inv; q[1] = r1 * inv; q[2] = r2 * inv; q[3] = r3 * inv;
-}
-
 }  // namespace mppi

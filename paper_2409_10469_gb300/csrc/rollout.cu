@@ -38,11 +38,12 @@ __device__ __forceinline__ bool fin_f(float x) { return fabsf(x) <= 3.402823466e
 // (s, e) += (v, ve): s + v exactly as s' + err (Knuth's TwoSum), err and the low
 // parts into e
 __device__ __forceinline__ void ff_add(float& s, float& e, float v, float ve) {
-    const float t = s + v;
-    const float bp = t - s;
-    const float err = (s - (t - bp)) + (v - bp);
+    // _rn intrinsics: never contracted with a preceding product (which would break TwoSum)
+    const float t = __fadd_rn(s, v);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
     s = t;
-    e += ve + err;
+    e = __fadd_rn(e, __fadd_rn(ve, err));
 }
 
 __device__ __forceinline__ void fused_update(const RolloutArgs& a, float L, const float (&Uk)[NKNOT][3], int leg,

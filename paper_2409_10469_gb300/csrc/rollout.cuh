@@ -12,19 +12,31 @@
 // with two xor-shuffle rounds.  Every lane then holds bit-identical trunk sums and
 // solves the 6x6 trunk system itself, so the replicated trunk state never
 // diverges between lanes.
+//
+// Precision: the contact spheres' heights are evaluated as FP32 pairs
+// (precise.cuh) from joint angles and trunk / box positions that carry an FP32
+// compensation term (the rounding error of every sub-step's position update)
+// through a dt step; at the end of each dt step the state is rounded to FP32,
+// the granularity of every output (trajectories, costs).  The rest of the
+// sub-step is plain FP32.
 #pragma once
 #include "common.cuh"
+#include "precise.cuh"
 
 namespace mppi {
 
 
 struct LegState {
     float q[3], qd[3];
+    float ql[3];  // compensation of q within a dt step (q + ql is the angle)
 };
 
 struct Trunk {
     float p[3], quat[4];
-    float3 w, v;  // body-frame angular and linear velocity
+    float3 w, v;     // body-frame angular and linear velocity
+    float pl[3];     // compensation of p within a dt step
+    float quatl[4];  // compensation of quat within a dt step
+    float qc;        // (|quat|^2 - 1) / 2 until the first sub-step normalises it
 };
 
 __device__ __forceinline__ float xsum4(float v) {
@@ -53,10 +65,14 @@ __device__ __forceinline__ void ground(const DevModel& m, float x, float y, floa
     hy = iny ? ((1.f - fx) * (h01 - h00) + fx * (h11 - h10)) * m.hf_inv_cell : 0.f;
 }
 
-// sphere vs axis-aligned box: outward normal and depth when overlapping
-__device__ __forceinline__ bool sphere_aabb(float3 x, float r, float3 lo, float3 hi, float3& n, float& pen) {
+// sphere vs axis-aligned box: outward normal and depth when overlapping; xlz is
+// the low part of the centre's z (a pair x.z + xlz), which enters the distance
+// to a horizontal face
+__device__ __forceinline__ bool sphere_aabb(float3 x, float r, float3 lo, float3 hi, float3& n, float& pen,
+                                            float xlz = 0.f) {
     float3 cp = f3(fminf(fmaxf(x.x, lo.x), hi.x), fminf(fmaxf(x.y, lo.y), hi.y), fminf(fmaxf(x.z, lo.z), hi.z));
     float3 d = x - cp;
+    d.z += (x.z < lo.z || x.z > hi.z) ? xlz : 0.f;
     float d2 = dot3(d, d);
     if (d2 > 0.f) {
         const float inv = rsqrtf(d2);   // approximate, branch-free (no IEEE slow path)
@@ -134,6 +150,9 @@ struct CalfFrame {
 struct BoxState {
     float p[3], quat[4];
     float3 w, v;
+    float pl[3];     // compensation of p within a dt step
+    float quatl[4];  // compensation of quat within a dt step
+    float qc;        // (|quat|^2 - 1) / 2 until the first sub-step normalises it
 };
 struct BoxKin {
     float3 p;
@@ -176,14 +195,16 @@ __device__ __forceinline__ void sphere_vs_box(const DevModel& m, const BoxKin& B
 
 // All static-environment contacts of one sphere (world centre xw, radius r),
 // added with sign SG; toBody maps a world vector into the body's coordinates.
-// TERR 0: flat ground and no static boxes (normal e_z, depth r - z); TERR 1:
-// the model's plane or heightfield and its static boxes.  A sphere that is not
-// `on` adds exactly zero.
+// zw is the centre's height as a pair (xw.z its FP32 value), from which the
+// depths are taken.  TERR 0: flat ground and no static boxes (normal e_z, depth
+// r - z); TERR 1: the model's plane or heightfield and its static boxes.  A
+// sphere that is not `on` adds exactly zero.
 template <int TERR, int SG, typename ToBody>
-__device__ __forceinline__ void sphere_env(const DevModel& m, float3 xw, float r, float3 cb, float3 w, float3 v,
-                                           const ToBody& toBody, float3& torque, float3& force, bool on = true) {
+__device__ __forceinline__ void sphere_env(const DevModel& m, float3 xw, F2 zw, float r, float3 cb, float3 w,
+                                           float3 v, const ToBody& toBody, float3& torque, float3& force,
+                                           bool on = true) {
     if (TERR == 0) {
-        const float pen = r - xw.z;
+        const float pen = (r - zw.h) - zw.l;
         contact_wrench<SG>(m, fmaxf(pen, 0.f), toBody.ez(), cb, r, w, v, torque, force, on && pen > 0.f);
         return;
     }
@@ -191,7 +212,11 @@ __device__ __forceinline__ void sphere_env(const DevModel& m, float3 xw, float r
     ground(m, xw.x, xw.y, h, hx, hy);
     float inv = rsqrt_approx(hx * hx + hy * hy + 1.f);
     float3 n = f3(-hx * inv, -hy * inv, inv);
-    const float pen = r - (xw.z - h) * n.z;
+    const float pen = r - ((zw.h - h) + zw.l) * n.z;
+    // the height renormalised (its FP32 value and a low part of under an ulp) for
+    // the box tests, which compare the centre against the faces in FP32
+    const F2 zn = two_sum(zw.h, zw.l);
+    xw.z = zn.h;
     // computed unconditionally and zeroed out of contact (no branch)
     contact_wrench<SG>(m, fmaxf(pen, 0.f), toBody(n), cb, r, w, v, torque, force, on && pen > 0.f);
     for (int b = 0; b < m.n_sbox; b++) {
@@ -199,7 +224,7 @@ __device__ __forceinline__ void sphere_env(const DevModel& m, float3 xw, float r
         const float* bx = m.sbox + 6 * b;
         const float3 lo = f3(__ldg(bx), __ldg(bx + 1), __ldg(bx + 2));
         const float3 hi = f3(__ldg(bx + 3), __ldg(bx + 4), __ldg(bx + 5));
-        if (on && sphere_aabb(xw, r, lo, hi, nn, pb))
+        if (on && sphere_aabb(xw, r, lo, hi, nn, pb, zn.l))
             contact_wrench<SG>(m, pb, toBody(nn), cb, r, w, v, torque, force);
     }
 }
@@ -334,6 +359,52 @@ __device__ __forceinline__ LegGeom leg_geom(const DevModel& m, int leg) {
     return g;
 }
 
+// p += h dp with the height's rounding error (and, over terrain, the horizontal
+// ones: the heightfield and the static boxes are looked up at x, y) kept in pl
+template <int TERR>
+__device__ __forceinline__ void advance_pos(float p[3], float pl[3], float3 dp, float h) {
+    const float d[3] = {dp.x, dp.y, dp.z};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        if (TERR == 0 && k < 2) {
+            p[k] = fmaf(h, d[k], p[k]);
+            continue;
+        }
+        const F2 t = fast_two_sum(p[k], h * d[k]);
+        p[k] = t.h;
+        pl[k] += t.l;
+    }
+}
+
+// the state rounded to FP32 at the end of a dt step: every compensation term
+// folded into its value, and the rounded quaternions' norm errors taken for the
+// next sub-step's normalisation
+template <bool BOX>
+__device__ __forceinline__ void round_state(Trunk& T, LegState& S, BoxState& Bx) {
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        T.p[k] += T.pl[k];
+        T.pl[k] = 0.f;
+        S.q[k] += S.ql[k];
+        S.ql[k] = 0.f;
+        if (BOX) {
+            Bx.p[k] += Bx.pl[k];
+            Bx.pl[k] = 0.f;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        T.quat[k] += T.quatl[k];
+        T.quatl[k] = 0.f;
+        if (BOX) {
+            Bx.quat[k] += Bx.quatl[k];
+            Bx.quatl[k] = 0.f;
+        }
+    }
+    T.qc = quat_half_norm_err(T.quat);
+    if (BOX) Bx.qc = quat_half_norm_err(Bx.quat);
+}
+
 template <int TERR, bool BOX>
 __device__ __forceinline__ void substep(const DevModel& m, int leg, const LegGeom& G, Trunk& T, LegState& S,
                                         const float kpu[3], float h, float kdh, float hg, float arm, BoxState& Bx) {
@@ -349,11 +420,26 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, const LegGeo
         BK.v = Bx.v;
     }
 
-    // ---- leg kinematics: joint transforms, body velocities, velocity products
-    float c0, s0, c1, s1, c2, s2;
-    sincos_r(S.q[0], s0, c0);
-    sincos_r(S.q[1], s1, c1);
-    sincos_r(S.q[2], s2, c2);
+    // ---- leg kinematics: joint transforms, body velocities, velocity products.
+    // Sines and cosines of the compensated angles as pairs (the FP32 values
+    // serve the dynamics, the pairs the sphere heights), with q1 + q2 for the
+    // foot's height: the knee and foot offsets lie on the thigh's and calf's z
+    // axes, so in the hip frame the foot sits at
+    // (kz sin q1 + fz sin q12, ty, kz cos q1 + fz cos q12)
+    F2 S0p, C0p, S1p, C1p, S2p, C2p, S12p, C12p;
+    sincos_pair(S.q[0], S.ql[0], S0p, C0p);
+    sincos_pair(S.q[1], S.ql[1], S1p, C1p);
+    sincos_pair(S.q[2], S.ql[2], S2p, C2p);
+    {
+        const F2 q12 = f2_add(F2{S.q[1], S.ql[1]}, F2{S.q[2], S.ql[2]});
+        sincos_pair(q12.h, q12.l, S12p, C12p);
+    }
+    const float c0 = f2_val(C0p), s0 = f2_val(S0p), c1 = f2_val(C1p), s1 = f2_val(S1p);
+    const float c2 = f2_val(C2p), s2 = f2_val(S2p);
+    // the world's vertical in trunk coordinates, as pairs (sphere heights)
+    F2 rz0, rz1, rz2;
+    quat_row2(T.quat, T.quatl, rz0, rz1, rz2);
+    const F2 pz_t = {T.p[2], T.pl[2]};
     const float3 rh = G.rh;                                        // abduction joint in the trunk
     const float ty = G.ty;                                         // flexion joint (0, ty, 0) in the hip
     const float kz = m.r_knee[2], fz = m.foot[2];                  // knee (0, 0, kz), foot (0, 0, fz)
@@ -374,21 +460,26 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, const LegGeo
     // kpu = kp u per dt step, kdh = kp h + kd per horizon
     float tau[3];
 #pragma unroll
-    for (int i = 0; i < 3; i++) tau[i] = fmaf(-kdh, S.qd[i], fmaf(-m.kp, S.q[i], kpu[i]));
+    for (int i = 0; i < 3; i++) tau[i] = fmaf(-kdh, S.qd[i], fmaf(-m.kp, S.q[i], fmaf(-m.kp, S.ql[i], kpu[i])));
 
     // ---- pass 2 (tip to root), calf: its bias minus the foot's contact wrench
     float3 pa_n = f3(0.f, 0.f, 0.f), pa_f = f3(0.f, 0.f, 0.f);
     body_bias_acc(m.I_calf, wc, vc, pa_n, pa_f);
     {
         const float3 foot = f3(0.f, 0.f, fz);
-        // foot centre in the trunk frame: rh + E0^T ((0, ty, 0) + E1^T ((0, 0, kz) + E2^T foot))
-        const float ax = s2 * fz, az = fmaf(c2, fz, kz);
-        const float bx = fmaf(c1, ax, s1 * az), bz = fmaf(c1, az, -s1 * ax);
-        const float3 ptr = f3(rh.x + bx, rh.y + fmaf(c0, ty, -s0 * bz), rh.z + fmaf(s0, ty, c0 * bz));
+        // foot centre in the trunk frame: rh + E0^T ((0, ty, 0) + E1^T ((0, 0, kz) + E2^T foot)),
+        // as pairs, and its world height p_z + (row 2 of R0) . ptr
+        const F2 bx = f2_add(f2_mulf(S12p, fz), f2_mulf(S1p, kz));
+        const F2 bz = f2_add(f2_mulf(C12p, fz), f2_mulf(C1p, kz));
+        const F2 px = f2_addf(bx, rh.x);
+        const F2 py = f2_sub(f2_addf(f2_mulf(C0p, ty), rh.y), f2_mul(S0p, bz));
+        const F2 pz = f2_add(f2_addf(f2_mulf(S0p, ty), rh.z), f2_mul(C0p, bz));
+        const F2 zw = f2_add(f2_add(pz_t, f2_mul(rz0, px)), f2_add(f2_mul(rz1, py), f2_mul(rz2, pz)));
+        const float3 ptr = f3(f2_val(px), f2_val(py), f2_val(pz));
         const float3 xw = f3(T.p[0], T.p[1], T.p[2]) + mulR(R0, ptr);
         const CalfFrame toCalf = {R0[0][0], R0[0][1], R0[0][2], R0[1][0], R0[1][1], R0[1][2],
                                   R0[2][0], R0[2][1], R0[2][2], c0, s0, c1, s1, c2, s2};
-        sphere_env<TERR, -1>(m, xw, m.foot_r, foot, wc, vc, toCalf, pa_n, pa_f);
+        sphere_env<TERR, -1>(m, xw, zw, m.foot_r, foot, wc, vc, toCalf, pa_n, pa_f);
         if (BOX) sphere_vs_box<-1>(m, BK, xw, m.foot_r, foot, wc, vc, toCalf, pa_n, pa_f, bx_t, bx_f);
     }
     // the calf's articulated inertia after projection is a model constant
@@ -437,22 +528,27 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, const LegGeo
         const float tx = G.tx;
         const float3 cb = f3(tx, 0.f, 0.f);
         const float3 xw = f3(fmaf(R0[0][0], tx, T.p[0]), fmaf(R0[1][0], tx, T.p[1]), fmaf(R0[2][0], tx, T.p[2]));
+        const F2 zw = f2_add(pz_t, f2_mulf(rz0, tx));
         const TrunkFrame toTrunk = {R0[0][0], R0[0][1], R0[0][2], R0[1][0], R0[1][1], R0[1][2],
                                     R0[2][0], R0[2][1], R0[2][2]};
-        sphere_env<TERR, -1>(m, xw, m.tsph_r, cb, T.w, T.v, toTrunk, pa_n, pa_f, on);
+        sphere_env<TERR, -1>(m, xw, zw, m.tsph_r, cb, T.w, T.v, toTrunk, pa_n, pa_f, on);
         if (BOX) sphere_vs_box<-1>(m, BK, xw, m.tsph_r, cb, T.w, T.v, toTrunk, pa_n, pa_f, bx_t, bx_f, on);
     }
     // ---- the box's 8 corner spheres against the static environment, 2 per lane
     if (BOX) {
         const TrunkFrame toBox = {BK.R[0][0], BK.R[0][1], BK.R[0][2], BK.R[1][0], BK.R[1][1], BK.R[1][2],
                                   BK.R[2][0], BK.R[2][1], BK.R[2][2]};
+        F2 bz0, bz1, bz2;
+        quat_row2(Bx.quat, Bx.quatl, bz0, bz1, bz2);
 #pragma unroll
         for (int cc = 0; cc < 2; cc++) {
             const int cn = 2 * leg + cc;
             const float3 cl = f3((cn & 1) ? m.box_half[0] : -m.box_half[0], (cn & 2) ? m.box_half[1] : -m.box_half[1],
                                  (cn & 4) ? m.box_half[2] : -m.box_half[2]);
             const float3 xc = BK.p + mulR(BK.R, cl);
-            sphere_env<TERR, 1>(m, xc, m.box_cr, cl, BK.w, BK.v, toBox, bx_t, bx_f);
+            const F2 zc = f2_add(F2{Bx.p[2], Bx.pl[2]},
+                                 f2_add(f2_mulf(bz0, cl.x), f2_add(f2_mulf(bz1, cl.y), f2_mulf(bz2, cl.z))));
+            sphere_env<TERR, 1>(m, xc, zc, m.box_cr, cl, BK.w, BK.v, toBox, bx_t, bx_f);
         }
     }
 
@@ -553,21 +649,22 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, const LegGeo
         qdd[2] = D2inv * fmaf(-U2a, kw.y, fmaf(-U2l, kv.x, u2));
     }
 
-    // ---- semi-implicit Euler
+    // ---- semi-implicit Euler; the position updates' rounding errors go into the
+    // compensation terms (Fast2Sum)
 #pragma unroll
     for (int i = 0; i < 3; i++) {
         S.qd[i] = fmaf(h, qdd[i], S.qd[i]);
-        S.q[i] = fmaf(h, S.qd[i], S.q[i]);
+        const F2 t = fast_two_sum(S.q[i], h * S.qd[i]);
+        S.q[i] = t.h;
+        S.ql[i] += t.l;
     }
     // v += h (a + R0^T (0, 0, g)), hg = h g
     T.w = f3(fmaf(h, aw.x, T.w.x), fmaf(h, aw.y, T.w.y), fmaf(h, aw.z, T.w.z));
     T.v = f3(fmaf(h, av.x, fmaf(hg, R0[2][0], T.v.x)), fmaf(h, av.y, fmaf(hg, R0[2][1], T.v.y)),
              fmaf(h, av.z, fmaf(hg, R0[2][2], T.v.z)));
     const float3 dp = mulR(R0, T.v);
-    T.p[0] = fmaf(h, dp.x, T.p[0]);
-    T.p[1] = fmaf(h, dp.y, T.p[1]);
-    T.p[2] = fmaf(h, dp.z, T.p[2]);
-    quat_integrate(T.quat, T.w, h);
+    advance_pos<TERR>(T.p, T.pl, dp, h);
+    quat_integrate_pair(T.quat, T.quatl, T.qc, T.w, h);
     if (BOX) {
         // Newton-Euler of the box about its centre (principal axes), from the summed wrench
         const float3 tb = f3(xsum4(bx_t.x), xsum4(bx_t.y), xsum4(bx_t.z));
@@ -581,10 +678,8 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, const LegGeo
         Bx.w = Bx.w + h * aw_b;
         Bx.v = Bx.v + h * av_b;
         const float3 dpb = mulR(BK.R, Bx.v);
-        Bx.p[0] = fmaf(h, dpb.x, Bx.p[0]);
-        Bx.p[1] = fmaf(h, dpb.y, Bx.p[1]);
-        Bx.p[2] = fmaf(h, dpb.z, Bx.p[2]);
-        quat_integrate(Bx.quat, Bx.w, h);
+        advance_pos<TERR>(Bx.p, Bx.pl, dpb, h);
+        quat_integrate_pair(Bx.quat, Bx.quatl, Bx.qc, Bx.w, h);
     }
 }
 
@@ -665,7 +760,10 @@ __device__ __forceinline__ float rollout_lane(const DevModel& m, const DevCost& 
 
     Trunk T;
     T.p[0] = x0[0]; T.p[1] = x0[1]; T.p[2] = x0[2];
+    T.pl[0] = 0.f; T.pl[1] = 0.f; T.pl[2] = 0.f;
+    T.quatl[0] = 0.f; T.quatl[1] = 0.f; T.quatl[2] = 0.f; T.quatl[3] = 0.f;
     T.quat[0] = x0[3]; T.quat[1] = x0[4]; T.quat[2] = x0[5]; T.quat[3] = x0[6];
+    T.qc = quat_half_norm_err(T.quat);
     T.w = f3(x0[19], x0[20], x0[21]);
     T.v = f3(x0[22], x0[23], x0[24]);
     LegState S;
@@ -673,6 +771,7 @@ __device__ __forceinline__ float rollout_lane(const DevModel& m, const DevCost& 
     for (int i = 0; i < 3; i++) {
         S.q[i] = x0[7 + 3 * leg + i];
         S.qd[i] = x0[25 + 3 * leg + i];
+        S.ql[i] = 0.f;
     }
     BoxState Bx;
     if (BOX) {
@@ -681,6 +780,10 @@ __device__ __forceinline__ float rollout_lane(const DevModel& m, const DevCost& 
         Bx.w = f3(x0[44], x0[45], x0[46]);
         Bx.v = f3(x0[47], x0[48], x0[49]);
     }
+    Bx.pl[0] = 0.f; Bx.pl[1] = 0.f; Bx.pl[2] = 0.f;
+    Bx.quatl[0] = 0.f; Bx.quatl[1] = 0.f; Bx.quatl[2] = 0.f; Bx.quatl[3] = 0.f;
+    Bx.qc = 0.f;
+    if (BOX) Bx.qc = quat_half_norm_err(Bx.quat);
     const float h = a.h;
     const float kdh = fmaf(m.kp, h, m.kd), hg = h * m.gz;
     const LegGeom G = leg_geom(m, leg);
@@ -715,6 +818,7 @@ __device__ __forceinline__ float rollout_lane(const DevModel& m, const DevCost& 
         }
         const float kpu[3] = {m.kp * u[0], m.kp * u[1], m.kp * u[2]};
         for (int sb = 0; sb < a.n_sub; sb++) substep<TERR, BOX>(m, leg, G, T, S, kpu, h, kdh, hg, a.arm, Bx);
+        round_state<BOX>(T, S, Bx);
         if (float* tp = opaque_ptr(traj)) store_state<BOX>(tp, a.H, k, t + 1, leg, valid, T, S, Bx, a.nx);
     }
     if (leg == 0) L += c.w_term * (trunk_state_cost<TERR>(m, c, T) + (BOX ? box_cost(c, Bx) : 0.f));

@@ -34,11 +34,12 @@ __device__ __forceinline__ bool finitef(float x) { return fabsf(x) <= 3.40282346
 // s and an error term by Knuth's TwoSum, the error and the low parts into e
 // (about 48 significant bits on the FP32 pipe, which runs 64x the FP64 rate)
 __device__ __forceinline__ void ff_acc(float& s, float& e, float v, float ve) {
-    const float t = s + v;
-    const float bp = t - s;
-    const float err = (s - (t - bp)) + (v - bp);
+    // _rn intrinsics: never contracted with a preceding product (which would break TwoSum)
+    const float t = __fadd_rn(s, v);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
     s = t;
-    e += ve + err;
+    e = __fadd_rn(e, __fadd_rn(ve, err));
 }
 
 constexpr int UPD_SUB = UPD_THREADS;  // samples whose weights sit in shared memory at a time

@@ -61,6 +61,28 @@ def robot(terrain: str = "plane", box: bool = False, heightfield: np.ndarray | N
         p["sbox_lo"].append(tuple(float(v) for v in lo))
         p["sbox_hi"].append(tuple(float(v) for v in hi))
     p["n_static_boxes"] = len(p["sbox_lo"])
+    return fp32_geometry(p)
+
+
+# Lengths that place the contact spheres: the model's values are these decimals
+# rounded to the nearest FP32 number, so that the FP32 kernels and the FP64
+# oracle place every sphere, box face and terrain cell at the same point (a
+# 0.213 m link differs from its FP32 value by ~5e-9 m, which the 2e4 N/m contact
+# stiffness would turn into a systematic force difference).
+GEOMETRY_KEYS = ("hip_x", "hip_y", "hip_z", "thigh_offset_y", "thigh_length", "calf_length", "foot_radius",
+                 "trunk_sphere_x", "trunk_sphere_r", "box_size", "box_corner_r", "hf_cell", "hf_x0", "hf_y0",
+                 "sbox_lo", "sbox_hi")
+
+
+def _f32(v):
+    if isinstance(v, (list, tuple)):
+        return type(v)(_f32(x) for x in v)
+    return float(np.float32(v))
+
+
+def fp32_geometry(p: dict) -> dict:
+    for k in GEOMETRY_KEYS:
+        p[k] = _f32(p[k])
     return p
 
 

@@ -108,32 +108,50 @@ def visited_states(cfg, n, seed, H=None):
     return tr[ks, ts].astype(np.float32), U[ks], ts
 
 
-STRICT = ("pos", "quat", "joints", "v", "box_pos", "box_quat")
+U_ROUND = 2.0 ** -24   # FP32 unit roundoff: the representation error of an FP32 state
 
 
-def floor_bound(e_gpu, e_f32, strict=STRICT, max_factor=2.0):
-    """per block: the p99 of the GPU error within max(1e-5, 2x the FP32 floor)
-    and its max within max(1e-5, max_factor x the floor's max); the position,
-    attitude, joint-angle and linear-velocity blocks within 1e-5"""
+def fp32_conditioning(step, X, ref, draws=2):
+    """per state and block: the largest change of the FP64 oracle's step when the
+    input state is perturbed by its own FP32 representation error (each
+    component by a relative +-2^-24, random signs) -- how well the model itself
+    determines the step at FP32 resolution, whatever the arithmetic"""
+    S = None
+    for sd in range(draws):
+        sg = np.random.default_rng(1000 + sd).choice([-1.0, 1.0], X.shape)
+        e = rel_block(step(X * (1 + U_ROUND * sg)), ref)
+        S = e if S is None else {k: np.maximum(S[k], v) for k, v in e.items()}
+    return S
+
+
+def state_parity(e_gpu, S, tol=1e-5, max_frac=0.01):
+    """the per-step bound: every block of every state <= tol (1e-5), except states
+    whose FP64 step the FP32 representation error of their input already moves
+    by more than tol/2: those are held to twice that change (the kernel rounds
+    velocities and the attitude at each of a dt step's sub-steps, a few such
+    perturbations); at most max_frac of the states may need the exception.
+    Returns (violations, number of excepted states)."""
+    n = len(next(iter(e_gpu.values())))
+    over = np.zeros(n, bool)
     bad = {}
-    for k in e_gpu:
-        for q, fac in ((100, max_factor), (99, 2.0)):
-            g, f = np.percentile(e_gpu[k], q), np.percentile(e_f32[k], q)
-            if g > max(1e-5, fac * f):
-                bad[(k, q)] = (g, f)
-        if k in strict and np.max(e_gpu[k]) > 1e-5:
-            bad[(k, "strict")] = np.max(e_gpu[k])
-    return bad
+    for k, e in e_gpu.items():
+        o = e > tol
+        over |= o
+        v = o & (e > 2 * S[k])
+        if v.any():
+            bad[k] = (int(v.sum()), float(e[v].max()), float(S[k][v].max()))
+    if over.sum() > max_frac * n:
+        bad["excepted"] = (int(over.sum()), n)
+    return bad, int(over.sum())
 
 
-@pytest.mark.parametrize("which", ["stand", "trot", "push"])
+@pytest.mark.parametrize("which", ["stand", "trot", "push", "terrain"])
 def test_one_step_state_parity(which):
     """one dt step (n_sub sub-steps) from 400 identical FP32 states that MPPI
-    rollouts visit (contacts, swing legs, falls).  Position, attitude, joints
-    and linear velocity: <= 1e-5 relative; the angular-rate blocks carry the
-    FP32 floor of the stiff contact model (k pen amplifies the ~3e-8 m rounding
-    of foot heights) and must stay within 2x that floor, measured by the same
-    oracle source compiled in float."""
+    rollouts visit (contacts, swing legs, falls): every block within 1e-5
+    relative of the FP64 oracle (the contact spheres' heights are pair-precise,
+    so the stiff contact no longer amplifies FP32 rounding of the foot height),
+    with the conditioning exception of state_parity for at most 1% of states"""
     cfg = config(which)
     n = 400
     X, U, ts = visited_states(cfg, n, 3)
@@ -143,20 +161,24 @@ def test_one_step_state_parity(which):
     L = torch.empty(n, device="cuda")
     ctl.rollouts(dev(X), U=dev(U), n=n, t0=0.0, L_out=L, traj_out=traj, x0_per_sample=True)
     tg = traj.cpu().numpy()
-    _, to = O.rollouts(O.World(cfg.robot), cfg.cost, m, 0.0, X.astype(np.float64), U, traj=True)
-    with O.use_float():
-        _, t32 = O.rollouts(O.World(cfg.robot), cfg.cost, m, 0.0, X.astype(np.float64), U, traj=True)
+    world = O.World(cfg.robot)
+
+    def step(Xs):
+        return O.rollouts(world, cfg.cost, m, 0.0, Xs, U, traj=True)[1][:, 1]
+
+    X64 = X.astype(np.float64)
+    ref = step(X64)
     assert np.array_equal(tg[:, 0], X)
-    e_gpu = rel_block(tg[:, 1].astype(np.float64), to[:, 1])
-    e_f32 = rel_block(t32[:, 1], to[:, 1])
-    bad = floor_bound(e_gpu, e_f32)
-    assert not bad, bad
+    e_gpu = rel_block(tg[:, 1].astype(np.float64), ref)
+    bad, n_exc = state_parity(e_gpu, fp32_conditioning(step, X64, ref))
+    assert not bad, (bad, n_exc)
 
 
 def teacher_forced(cfg, K, H, t0=0.0):
     """GPU rollouts with trajectories; the oracle re-steps every dt step from the
     GPU's own FP32 state (no chaotic amplification), and evaluates the cost
-    along the GPU trajectory."""
+    along the GPU trajectory.  Returns the per-step errors, the steps'
+    FP32-resolution conditioning and the cost errors."""
     ctl, m = ctl_for(cfg, K=K, H=H)
     ctl.set_nominal(cfg.mu0)
     U = torch.empty((K, 48), device="cuda")
@@ -169,29 +191,30 @@ def teacher_forced(cfg, K, H, t0=0.0):
     tg = traj.cpu().numpy().astype(np.float64)
     Uh = U.cpu().numpy()
     world = O.World(cfg.robot)
-    ut = np.array([[O.spline_eval(Uh[k], t / (H - 1)) for t in range(H)] for k in range(K)])
-    nxt = O.dt_steps(world, tg[:, :H].reshape(-1, nx), ut.reshape(-1, 12), m["n_sub"],
-                     m["dt"] / m["n_sub"]).reshape(K, H, nx)
-    r = rel_block(tg[:, 1:], nxt)
-    with O.use_float():
-        nxt32 = O.dt_steps(O.World(cfg.robot), tg[:, :H].reshape(-1, nx), ut.reshape(-1, 12), m["n_sub"],
-                           m["dt"] / m["n_sub"]).reshape(K, H, nx)
-    r32 = rel_block(nxt32, nxt)
-    step_err = (r, r32)
+    ut = np.array([[O.spline_eval(Uh[k], t / (H - 1)) for t in range(H)] for k in range(K)]).reshape(-1, 12)
+    Xs = tg[:, :H].reshape(-1, nx)
+
+    def step(X):
+        return O.dt_steps(world, X, ut, m["n_sub"], m["dt"] / m["n_sub"])
+
+    nxt = step(Xs)
+    r = rel_block(tg[:, 1:].reshape(-1, nx), nxt)
+    S = fp32_conditioning(step, Xs, nxt)
     tabs = t0 + np.arange(H) * m["dt"]
-    sc = O.stage_costs(world, cfg.cost, tg[:, :H].reshape(-1, nx), ut.reshape(-1, 12),
-                       np.tile(tabs, K)).reshape(K, H).sum(1)
+    sc = O.stage_costs(world, cfg.cost, Xs, ut, np.tile(tabs, K)).reshape(K, H).sum(1)
     sc += O.stage_costs(world, cfg.cost, tg[:, H])
     Lg = L.cpu().numpy().astype(np.float64)
     cost_rel = np.abs(Lg - sc) / np.maximum(np.abs(sc), 1)
-    return step_err, cost_rel
+    return (r, S, Xs), cost_rel
 
 
 @pytest.mark.parametrize("which", ["stand", "trot", "terrain", "push"])
 def test_rollout_teacher_forced(which):
     """every dt step of every GPU rollout matches the oracle stepped from the same
-    FP32 state; the GPU's accumulated cost matches the oracle's L_walk evaluated
-    along the GPU trajectory (<= 1e-5: the cost arithmetic alone)"""
+    FP32 state within 1e-5 per block (state_parity's conditioning exception for
+    at most 1% of steps), but for the two contact kinds evaluated from FP32
+    positions (see below); the GPU's accumulated cost matches the oracle's L_walk
+    evaluated along the GPU trajectory (<= 1e-5: the cost arithmetic alone)"""
     if which == "stand":
         cfg, K, H, t0 = W.config_stand(), 100, 50, 0.0
     elif which == "trot":
@@ -200,14 +223,34 @@ def test_rollout_teacher_forced(which):
         cfg, K, H, t0 = W.config_terrain(), 40, 60, 0.0
     else:
         cfg, K, H, t0 = W.config_push(), 40, 100, 0.0
-    (e_gpu, e_f32), cost_rel = teacher_forced(cfg, K, H, t0)
+    (e_gpu, S, X), cost_rel = teacher_forced(cfg, K, H, t0)
     assert cost_rel.max() <= 1e-5, cost_rel.max()
-    # on the heightfield a foot crossing a cell edge meets a slope jump (bilinear
-    # model): those steps are discontinuous and their worst case depends on the
-    # rounding of the crossing, so the max is held to 5x the floor there
-    bad = floor_bound({k: v.ravel() for k, v in e_gpu.items()}, {k: v.ravel() for k, v in e_f32.items()},
-                      max_factor=5.0 if which == "terrain" else 2.0)
-    assert not bad, bad
+    if which in ("stand", "trot"):
+        bad, n_exc = state_parity(e_gpu, S)
+        assert not bad, (bad, n_exc)
+        return
+    # Two contact kinds are still evaluated from FP32 positions: a robot sphere
+    # against the free box (push) and a sphere's heightfield lookup at its x, y
+    # (terrain).  Steps with a robot-box contact are held to 5e-5 and counted;
+    # every other push step, and every terrain step but at most 0.5% (each within
+    # 5e-5), meets the rule above.
+    n = len(X)
+    world = O.World(cfg.robot)
+    if which == "push":
+        away = X.copy()
+        away[:, 37:40] = (50.0, 50.0, 0.21)
+        touch = np.array([np.abs(O.contact_fext(world, X[i])[0] - O.contact_fext(world, away[i])[0]).max() > 0
+                          for i in range(n)])
+    else:
+        touch = np.zeros(n, bool)
+    keep = ~touch
+    bad, n_exc = state_parity({k: v[keep] for k, v in e_gpu.items()}, {k: v[keep] for k, v in S.items()},
+                              max_frac=0.005 if which == "terrain" else 0.01)
+    if which == "terrain":
+        bad = {k: v for k, v in bad.items() if k == "excepted" or v[1] > 5e-5}
+    assert not bad, (bad, n_exc)
+    worst_touch = max((float(v[touch].max()) for v in e_gpu.values()), default=0.0) if touch.any() else 0.0
+    assert worst_touch <= 5e-5, worst_touch
 
 
 @pytest.mark.parametrize("which", ["stand", "trot", "terrain", "push"])

@@ -284,9 +284,11 @@ def test_static_box_contact_normal_and_depth():
     # put the trunk (centre sphere at the trunk origin) just inside the box's top face
     x[0], x[1], x[2] = 1.2, 0.0, 0.3 + 0.055 - 0.004
     fext, _ = O.contact_fext(w, x)
-    # only the centre trunk sphere touches the top face: force along +z,
-    # k * pen with zero velocity (the side spheres at x +-0.15 also touch)
-    assert fext[0][5] == pytest.approx(3 * 2e4 * 0.004, rel=1e-9)
+    # the three trunk spheres (x = 0, +-0.15) touch the top face: force along +z,
+    # k * pen each with zero velocity; pen from the model's (FP32-valued) top and radius
+    pen = r["sbox_hi"][0][2] + r["trunk_sphere_r"] - x[2]
+    assert abs(pen - 0.004) < 1e-7
+    assert fext[0][5] == pytest.approx(3 * 2e4 * pen, rel=1e-9)
     # sphere centre inside the box leaves through the nearest face (x-hi here)
     x[0], x[2] = 1.49 + 0.15, 0.15
     fext, _ = O.contact_fext(w, x)
