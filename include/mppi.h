@@ -349,6 +349,33 @@ mppi_status mppi_features(mppi_handle h, const float* X, int n, uint32_t step, f
  * around it (the first of them is the proposal itself); a non-finite entry
  * falls back to the plain mean.  ARG if the handle has n_prop = 0. */
 mppi_status mppi_set_proposal(mppi_handle h, const float* mu_prop);
+/* ---- K-sharded control step (one controller over several GPUs or processes).
+ * Alg. 1's K samples are independent until Eq. 1, whose weights factor as
+ * exp(-(L_k - L_min) / lambda) = exp(-(L_k - m_r) / lambda) exp(-(m_r - L_min) / lambda)
+ * for any shard minimum m_r, so a step can be split by sample range: every rank
+ * holds a handle with the same configuration, seed and nominal, calls
+ * mppi_step_partial on its own range [k0, k0 + n) of the K samples (the same
+ * Philox stream: sample k is the same knot vector whichever rank draws it),
+ * takes L_min = min over ranks of part[0] (an all-reduce(min)), scales its
+ * part[1 .. 49] by exp(-(part[0] - L_min) / lambda) (0 when part[0] is not
+ * finite), sums them over ranks (an all-reduce(sum) of 49 doubles) and calls
+ * mppi_step_finalize with the sums: every rank then holds the same mu', u0 and
+ * shifted nominal -- those of mppi_step on all K samples, up to the order of
+ * the FP64 sums.  Knot representations only (ARG for DIRECT).
+ * mppi_step_partial: x0 float[nx] host or device; the step's samples k0 ..
+ * k0 + n - 1 (0 <= k0, 1 <= n, k0 + n <= K) are drawn, rolled out and weighted
+ * around their own finite-cost minimum m; part_out double[MPPI_SHARD_PARTIAL]
+ * (host or device) receives (m, Z = sum_k w_k, S[48] = sum_k w_k U_k), m = +inf
+ * and Z = S = 0 when no cost of the range is finite.  Host outputs are written
+ * on return.  The handle's nominal is not changed.
+ * mppi_step_finalize: sums double[49] (Z, S[48]) host or device, combined over
+ * every rank relative to the global L_min: mu' = S / Z, the applied u0, the
+ * shifted nominal (kept and NONFINITE when Z is not positive and finite);
+ * u0_out / mu_out as in mppi_step. */
+#define MPPI_SHARD_PARTIAL 50
+mppi_status mppi_step_partial(mppi_handle h, const float* x0, uint32_t step, int k0, int n, double* part_out);
+mppi_status mppi_step_finalize(mppi_handle h, const double* sums, float* u0_out, float* mu_out);
+
 /* The learned-proposal form's control step in one call: the features of x0
  * (float[nx], host or device) at control index `step`, the network's forward on
  * them (one small-batch kernel computes both), the result taken as the proposal

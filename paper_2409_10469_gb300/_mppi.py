@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NONF
 EXPORTS = ("mppi_create", "mppi_destroy", "mppi_last_error", "mppi_set_nominal",
            "mppi_get_nominal", "mppi_sample", "mppi_rollouts", "mppi_update", "mppi_step",
            "mppi_set_timing", "mppi_get_timings", "mppi_launch_count", "mppi_state_size",
-           "mppi_update_noalloc", "mppi_get_samples", "mppi_batch_create", "mppi_batch_destroy",
+           "mppi_update_noalloc", "mppi_get_samples", "mppi_step_partial", "mppi_step_finalize",
+           "mppi_batch_create", "mppi_batch_destroy",
            "mppi_batch_last_error", "mppi_batch_step", "mppi_batch_set_shape", "mppi_batch_get_shape",
            "mppi_batch_autotune", "mppi_batch_launch_count", "mppi_batch_shared_model", "mppi_server_create",
            "mppi_server_destroy", "mppi_server_last_error", "mppi_server_add_robot", "mppi_server_submit",
@@ -35,6 +36,9 @@ EXPORTS = ("mppi_create", "mppi_destroy", "mppi_last_error", "mppi_set_nominal",
            "mppi_mlp_train_step", "mppi_tc_gemm_bf16", "mppi_features", "mppi_set_proposal", "mppi_step_proposal",
            "mppi_batch_get_means", "mppi_selftest_wait_timeout", "mppi_param_dim",
            "mppi_selftest_noise_tables")
+
+# a shard's partial sums of a sharded step: m, Z, S[48] (MPPI_SHARD_PARTIAL)
+SHARD_PARTIAL = 50
 
 # control representations (MPPI_INTERP_* of include/mppi.h; Sec. III-B, Fig. 5)
 INTERP = {"cubic": 0, "zero": 1, "linear": 2, "direct": 3}
@@ -129,6 +133,8 @@ def lib():
         L.mppi_get_timings.argtypes = [vp, C.POINTER(C.c_float)]
         L.mppi_launch_count.argtypes = [vp, C.POINTER(C.c_uint64)]
         L.mppi_get_samples.argtypes = [vp, fp, fp]
+        L.mppi_step_partial.argtypes = [vp, fp, C.c_uint32, C.c_int, C.c_int, vp]
+        L.mppi_step_finalize.argtypes = [vp, vp, fp, fp]
         L.mppi_update_noalloc.argtypes = [fp, fp, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, fp, fp,
                                            fp, fp, fp, vp]
         L.mppi_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int, vp, C.POINTER(C.c_void_p)]
@@ -270,6 +276,7 @@ class Controller:
         self.h = h
         self.K = mppi["K"]
         self.H = mppi["H"]
+        self.lam = float(mppi["lam"])
         self.nx = L.mppi_state_size(h)
         self.D = L.mppi_param_dim(h)   # parameters per sample: 48, or 12 H (direct)
 
@@ -296,6 +303,19 @@ class Controller:
         out = np.zeros(self.D, np.float32) if out is None else out
         self._check(lib().mppi_get_nominal(self.h, _ptr(out)))
         return out
+
+    def step_partial(self, x0, step, k0, n, out=None):
+        """mppi_step_partial: samples k0 .. k0 + n - 1 of control step `step`
+        rolled out; returns (m, Z, S[48]) as float64[50] (host unless `out`)."""
+        out = np.zeros(SHARD_PARTIAL, np.float64) if out is None else out
+        self._check(lib().mppi_step_partial(self.h, _ptr(x0), int(step), int(k0), int(n), _ptr(out)))
+        return out
+
+    def step_finalize(self, sums, u0_out=None, mu_out=None, check=True):
+        """mppi_step_finalize from the combined sums (Z, S[48]) of every shard."""
+        sums = np.ascontiguousarray(sums, np.float64) if isinstance(sums, np.ndarray) else sums
+        rc = lib().mppi_step_finalize(self.h, _ptr(sums), _ptr(u0_out), _ptr(mu_out))
+        return self._check(rc) if check else rc
 
     def last_samples(self):
         """(U [K][D], L [K]) of the last control step (host copies)."""

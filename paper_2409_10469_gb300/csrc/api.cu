@@ -300,6 +300,7 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
               al((void**)&h->d_part, std::max(update_part_doubles((int)Dp), fused_part_doubles(*cfg)) *
                                          sizeof(double)) &&
               al((void**)&h->d_counter, update_counters((int)Dp) * sizeof(unsigned)) &&
+              al((void**)&h->d_shard, 128 * sizeof(double)) &&
               al((void**)&h->d_B, (size_t)4 * cfg->H * sizeof(float));
     if (ok && model->terrain == 1) {
         size_t nh = (size_t)model->hf_nx * model->hf_ny;
@@ -360,7 +361,7 @@ extern "C" mppi_status mppi_destroy(mppi_handle h) {
     else cudaDeviceSynchronize();
     void* bufs[] = {h->d_mu,  h->d_mu_prop, h->d_mu_upd, h->d_U,    h->d_L,    h->d_x0,
                     h->d_u0,  h->d_hf,      h->d_status, h->d_wsum, h->d_part, h->d_counter,
-                    h->d_sbox, h->d_B};
+                    h->d_sbox, h->d_B,      h->d_shard};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (h->h_box) cudaFreeHost(h->h_box);
@@ -481,6 +482,7 @@ static RolloutArgs rollout_args(mppi_handle h, const float* x0, int per, const f
     a.interp = h->cfg.interp;
     a.Bt = reinterpret_cast<const float4*>(h->d_B);
     a.sample = 0;  // the knots come from U (mppi_step turns in-kernel sampling on)
+    a.k_off = 0;
     a.mu = a.mu_prop = nullptr;
     a.K_all = h->cfg.K;
     a.n_prop = h->cfg.n_prop;
@@ -588,6 +590,7 @@ static mppi_status do_update(mppi_handle h, const float* dL, const float* dU, in
     a.inv_lambda = 1.0 / (double)h->cfg.lambda;
     a.Dp = h->D;
     a.interp = h->cfg.interp;
+    a.partial_out = nullptr;
     CK(launch_update(a, h->stream));
     h->launches++;
     return MPPI_OK;
@@ -719,6 +722,83 @@ extern "C" mppi_status mppi_step(mppi_handle h, const float* x0, uint32_t step, 
         h->timed_valid = 1;
     }
     return finish_outputs(h, u0_out, mu_out, op, boxed);
+}
+
+// ---------------------------------------------------------------- sharded step
+
+extern "C" mppi_status mppi_step_partial(mppi_handle h, const float* x0, uint32_t step, int k0, int n,
+                                         double* part_out) {
+    if (!h || !x0 || !part_out) return fail(h, MPPI_ERR_ARG, "null argument");
+    if (h->cfg.interp == MPPI_INTERP_DIRECT) return fail(h, MPPI_ERR_ARG, "sharded steps take the knot forms");
+    if (k0 < 0 || n < 1 || (long)k0 + n > h->cfg.K) return fail(h, MPPI_ERR_ARG, "sample range outside 0..K");
+    const float* dx0;
+    if (is_device(x0)) {
+        dx0 = x0;
+    } else {
+        if (!all_finite(x0, h->nx)) return fail(h, MPPI_ERR_NONFINITE, "x0 not finite");
+        CK(cudaMemcpyAsync(h->d_x0, x0, h->nx * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        dx0 = h->d_x0;
+    }
+    // samples k0 .. k0 + n - 1 of the step, drawn in the rollout kernel at their
+    // global indices and stored from row 0 of the handle's workspace
+    const double t0 = (double)step * h->cfg.ctrl_steps * h->cfg.dt;
+    RolloutArgs a = rollout_args(h, dx0, 0, h->d_U, n, t0, h->d_L, nullptr);
+    a.sample = 1;
+    a.k_off = k0;
+    a.mu = h->d_mu;
+    a.mu_prop = h->has_prop ? h->d_mu_prop : nullptr;
+    a.step = step;
+    a.U_out = h->d_U;
+    CK(launch_rollout(a, rollout_block(h), h->stream));
+    h->launches++;
+    UpdateArgs u;
+    u.L = h->d_L;
+    u.U = h->d_U;
+    u.mu = h->d_mu;
+    u.mu_upd = h->d_mu_upd;
+    u.u0 = h->d_u0;
+    u.status = h->d_status;
+    u.wsum = nullptr;
+    u.part = h->d_part;
+    u.counter = h->d_counter;
+    u.n = n;
+    u.H = h->cfg.H;
+    u.ctrl_steps = h->cfg.ctrl_steps;
+    u.inv_lambda = 1.0 / (double)h->cfg.lambda;
+    u.Dp = D;
+    u.interp = h->cfg.interp;
+    u.partial_out = h->d_shard;
+    CK(launch_update_partial(u, h->stream));
+    h->launches++;
+    const bool dev = is_device(part_out);
+    CK(cudaMemcpyAsync(part_out, h->d_shard, MPPI_SHARD_PARTIAL * sizeof(double),
+                       dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    if (!dev) CK(cudaStreamSynchronize(h->stream));
+    return MPPI_OK;
+}
+
+extern "C" mppi_status mppi_step_finalize(mppi_handle h, const double* sums, float* u0_out, float* mu_out) {
+    if (!h || !sums) return fail(h, MPPI_ERR_ARG, "null argument");
+    if (h->cfg.interp == MPPI_INTERP_DIRECT) return fail(h, MPPI_ERR_ARG, "sharded steps take the knot forms");
+    const double* ds = h->d_shard + 64;
+    if (is_device(sums)) {
+        ds = sums;
+    } else {
+        CK(cudaMemcpyAsync(h->d_shard + 64, sums, (MPPI_SHARD_PARTIAL - 1) * sizeof(double), cudaMemcpyHostToDevice,
+                           h->stream));
+    }
+    FinalizeArgs f;
+    f.sums = ds;
+    f.mu = h->d_mu;
+    f.mu_upd = h->d_mu_upd;
+    f.u0 = h->d_u0;
+    f.status = h->d_status;
+    f.H = h->cfg.H;
+    f.ctrl_steps = h->cfg.ctrl_steps;
+    f.interp = h->cfg.interp;
+    CK(launch_update_finalize(f, h->stream));
+    h->launches++;
+    return finish_outputs(h, u0_out, mu_out);
 }
 
 extern "C" mppi_status mppi_step_proposal(mppi_handle h, mppi_mlp net, const float* x0, uint32_t step, float* u0_out,

@@ -36,6 +36,7 @@ struct RolloutArgs {
     // in-kernel sampling (the control step, knot representations): each lane draws
     // its leg's 12 knots exactly as k_sample would and writes them to U_out
     int sample;
+    int k_off;             // global index of sample 0 of this launch (a shard of a K-sample step)
     const float* mu;       // [48] nominal
     const float* mu_prop;  // [48] proposal mean or null
     int K_all, n_prop;     // the sample set's size and its proposal share
@@ -81,6 +82,18 @@ struct UpdateArgs {
     int n, H, ctrl_steps;
     double inv_lambda;     // 1 / lambda (FP64: the weights' exponent is formed in FP64)
     int Dp, interp;        // parameters per sample, MPPI_INTERP_*
+    double* partial_out;   // launch_update_partial: [50] L_min, Z, S[48] of these samples
+};
+
+// Eq. 2's combined sums of a sharded step (Z, S[48], relative to the global
+// L_min) -> mu' = S / Z, u0, the shifted nominal and the status (one CTA)
+struct FinalizeArgs {
+    const double* sums;    // [49] Z, S[48] (device)
+    float* mu;             // [48] in: the nominal (kept when Z is not positive and finite); out: shifted
+    float* mu_upd;         // [48]
+    float* u0;             // [12]
+    int* status;
+    int H, ctrl_steps, interp;
 };
 
 constexpr int UPDATE_MAX_CTAS = 128;
@@ -98,5 +111,10 @@ cudaError_t launch_rollout(const RolloutArgs& a, int block, cudaStream_t st);
 // CTAs of a rollout launch of n samples at this block size
 inline int rollout_grid(int n, int block) { return (int)((4L * n + block - 1) / block); }
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t st);
+// the partial sums of the knot representations' update over a.n samples: the
+// samples' finite-cost minimum m, Z = sum exp(-(L - m) / lambda) and
+// S = sum exp(-(L - m) / lambda) U, into a.partial_out (no mean, no shift)
+cudaError_t launch_update_partial(const UpdateArgs& a, cudaStream_t st);
+cudaError_t launch_update_finalize(const FinalizeArgs& a, cudaStream_t st);
 
 }  // namespace mppi

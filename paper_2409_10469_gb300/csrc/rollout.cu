@@ -212,16 +212,18 @@ __global__ void __launch_bounds__(256, 1) k_rollout(RolloutArgs a) {
     if (!DIRECT && a.sample) {
         // Alg. 1's sampling step for this lane's knots, element for element the
         // formula of k_sample (Philox counter (d / 4, k, step, inst), Box-Muller,
-        // fmaf perturbation, clamp), so the knots are bit-identical to it
+        // fmaf perturbation, clamp), so the knots are bit-identical to it; kg is
+        // the sample's index in the whole K-sample step (a shard starts at k_off)
+        const int kg = a.k_off + kk;
         const int kp0 = a.K_all - (a.mu_prop ? a.n_prop : 0);
-        const bool prop = a.mu_prop && kk >= kp0;
+        const bool prop = a.mu_prop && kg >= kp0;
         const float* ctr = prop ? a.mu_prop : a.mu;
-        const bool nominal = (kk == 0) || (prop && kk == kp0);
+        const bool nominal = (kg == 0) || (prop && kg == kp0);
 #pragma unroll
         for (int j = 0; j < NKNOT; j++) {
             const int d0 = j * NJ + 3 * leg;
             float epsv[3];
-            knot_normals(a.key0, a.key1, a.step, a.inst, (uint32_t)kk, d0, epsv);
+            knot_normals(a.key0, a.key1, a.step, a.inst, (uint32_t)kg, d0, epsv);
 #pragma unroll
             for (int i = 0; i < 3; i++) {
                 const int d = d0 + i;

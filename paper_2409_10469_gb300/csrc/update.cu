@@ -83,6 +83,7 @@ struct UpdSmem {
     float2 w[UPD_SUB];                 // a sub-chunk's weights (hi, lo)
     double f[UPDATE_MAX_CTAS];  // the chunks' factors exp(-(m_c - L_min) / lambda)
     double Z;
+    float Lmin;  // the minimum over the chunks' cost minima (combine_setup)
     int last;
 };
 
@@ -186,6 +187,7 @@ __device__ __forceinline__ bool combine_setup(const UpdateArgs& a, int G, const 
     const float mc = tid < G ? (float)__ldcg(rows + (size_t)tid * UPD_ROW + UPD_TILE + 1) : INFINITY;
     const float Lmin = block_min(mc, s.red);
     const bool ok = finitef(Lmin);
+    if (tid == 0) s.Lmin = Lmin;
     if (tid < G) s.f[tid] = (ok && finitef(mc)) ? exp(-((double)mc - (double)Lmin) * a.inv_lambda) : 0.0;
     __syncthreads();
     if (warp == 0) {
@@ -265,6 +267,47 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_knots(UpdateArgs a) {
     if (tid < D) a.mu[tid] = shifted_knot(s_mu, a.interp, a.H, a.ctrl_steps, tid / NJ, tid % NJ);
 }
 
+// The partial sums of a shard of a K-sample step (knot representations): the
+// chunks as in k_update_knots, then the last CTA writes the shard's minimum
+// m = min_c m_c, Z = sum_c f_c z_c and S_j = sum_c f_c S_c[j] (f_c relative to m)
+// to partial_out instead of dividing and shifting.  Every rank of a sharded
+// step rescales these by exp(-(m - L_min) / lambda) once the global L_min is
+// known; the sums over ranks are Eq. 2's numerator and denominator.
+__global__ void __launch_bounds__(UPD_THREADS) k_update_partial(UpdateArgs a) {
+    __shared__ UpdSmem s;
+    const int tid = threadIdx.x, G = gridDim.x;
+    chunk_partials(a, blockIdx.x, G, 0, a.part, s);
+    if (!count_in(a.counter, (unsigned)G, s)) return;
+    const bool ok = combine_setup(a, G, a.part, s);
+    {
+        const int j = tid >> 2, q = tid & 3;
+        const double S = combine_param(G, a.part, min(j, D - 1), q, s);
+        if (j < D && q == 0) a.partial_out[2 + j] = ok ? S : 0.0;
+    }
+    if (tid == 0) {
+        a.partial_out[0] = (double)s.Lmin;
+        a.partial_out[1] = ok ? s.Z : 0.0;
+        *a.counter = 0u;  // re-arm for the next launch
+    }
+}
+
+// mu' = S / Z from the sums of every shard, u0, the status and the shift (one CTA)
+__global__ void k_update_finalize(FinalizeArgs a) {
+    __shared__ float s_mu[D];
+    const int tid = threadIdx.x;
+    const double Z = a.sums[0];
+    const bool ok = Z > 0.0 && Z <= 1.79769313486231570e308;
+    for (int j = tid; j < D; j += blockDim.x) {
+        const float mu_new = ok ? (float)(a.sums[1 + j] / Z) : a.mu[j];  // no finite cost: keep the mean
+        s_mu[j] = mu_new;
+        a.mu_upd[j] = mu_new;
+        if (j < NJ) a.u0[j] = mu_new;
+    }
+    if (tid == 0) *a.status = ok ? 0 : 4;
+    __syncthreads();
+    for (int j = tid; j < D; j += blockDim.x) a.mu[j] = shifted_knot(s_mu, a.interp, a.H, a.ctrl_steps, j / NJ, j % NJ);
+}
+
 // Direct targets (12 H parameters): G x T CTAs, T = ceil(12 H / 48) parameter
 // tiles, each tile its own update: the last CTA of tile y (counter[1 + y])
 // combines the tile's 48 parameters from its G rows (every tile's rows carry
@@ -320,6 +363,17 @@ cudaError_t launch_update(const UpdateArgs& a, cudaStream_t st) {
         const dim3 grid(update_grid(a.n), (a.Dp + UPD_TILE - 1) / UPD_TILE);
         k_update_tiled<<<grid, UPD_THREADS, 0, st>>>(a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_partial(const UpdateArgs& a, cudaStream_t st) {
+    if (a.Dp != D || !a.partial_out) return cudaErrorInvalidValue;
+    k_update_partial<<<update_grid(a.n), UPD_THREADS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_finalize(const FinalizeArgs& a, cudaStream_t st) {
+    k_update_finalize<<<1, 64, 0, st>>>(a);
     return cudaGetLastError();
 }
 
