@@ -124,6 +124,29 @@ __device__ __forceinline__ void quat_row2(const float q[4], const float ql[4], F
     r2.l = __fsub_rn(r2.l, __fmaf_rn(4.f, __fmaf_rn(x, xl, __fmul_rn(y, yl)), c.l));
 }
 
+// Rows 0 and 1 of the rotation (body -> world) of the quaternion q + ql as pairs
+// (the world's x and y axes in body coordinates), as quat_row2:
+// row 0 = (1 - 2 (y^2 + z^2), 2 (x y - w z), 2 (x z + w y)),
+// row 1 = (2 (x y + w z), 1 - 2 (x^2 + z^2), 2 (y z - w x)).
+__device__ __forceinline__ void quat_rows01(const float q[4], const float ql[4], F2 r0[3], F2 r1[3]) {
+    const float w = q[0], x = q[1], y = q[2], z = q[3];
+    const float wl = ql[0], xl = ql[1], yl = ql[2], zl = ql[3];
+    const F2 yy_zz = f2_add(two_prod(y + y, y), two_prod(z + z, z));
+    r0[0] = two_sum(1.f, -yy_zz.h);
+    r0[0].l = __fsub_rn(r0[0].l, __fmaf_rn(4.f, __fmaf_rn(y, yl, __fmul_rn(z, zl)), yy_zz.l));
+    r0[1] = f2_sub(two_prod(x + x, y), two_prod(w + w, z));
+    r0[1].l = __fmaf_rn(2.f, __fmaf_rn(xl, y, __fmaf_rn(x, yl, -__fmaf_rn(wl, z, __fmul_rn(w, zl)))), r0[1].l);
+    r0[2] = f2_add(two_prod(x + x, z), two_prod(w + w, y));
+    r0[2].l = __fmaf_rn(2.f, __fmaf_rn(xl, z, __fmaf_rn(x, zl, __fmaf_rn(wl, y, __fmul_rn(w, yl)))), r0[2].l);
+    r1[0] = f2_add(two_prod(x + x, y), two_prod(w + w, z));
+    r1[0].l = __fmaf_rn(2.f, __fmaf_rn(xl, y, __fmaf_rn(x, yl, __fmaf_rn(wl, z, __fmul_rn(w, zl)))), r1[0].l);
+    const F2 xx_zz = f2_add(two_prod(x + x, x), two_prod(z + z, z));
+    r1[1] = two_sum(1.f, -xx_zz.h);
+    r1[1].l = __fsub_rn(r1[1].l, __fmaf_rn(4.f, __fmaf_rn(x, xl, __fmul_rn(z, zl)), xx_zz.l));
+    r1[2] = f2_sub(two_prod(y + y, z), two_prod(w + w, x));
+    r1[2].l = __fmaf_rn(2.f, __fmaf_rn(yl, z, __fmaf_rn(y, zl, -__fmaf_rn(wl, x, __fmul_rn(w, xl)))), r1[2].l);
+}
+
 // a pair brought back to an FP32 value and a low part below half its ulp
 __device__ __forceinline__ F2 f2_norm(F2 a) { return two_sum(a.h, a.l); }
 

@@ -65,14 +65,41 @@ __device__ __forceinline__ void ground(const DevModel& m, float x, float y, floa
     hy = iny ? ((1.f - fx) * (h01 - h00) + fx * (h11 - h10)) * m.hf_inv_cell : 0.f;
 }
 
-// sphere vs axis-aligned box: outward normal and depth when overlapping; xlz is
-// the low part of the centre's z (a pair x.z + xlz), which enters the distance
-// to a horizontal face
+// terrain height under the point (x, y) given as pairs, as a pair (a cell
+// corner's height and the bilinear correction, below 2e-2), and its slope.  The
+// cell coordinate (x - x0) / cell is a pair too: the quotient's FP32 head and
+// the remainder, which the FMA gives exactly, over the cell.  The same bilinear
+// interpolation and edge clamping as ground().
+__device__ __forceinline__ void ground_pair(const DevModel& m, F2 x, F2 y, F2& h, float& hx, float& hy) {
+    if (m.terrain == 0) { h = F2{0.f, 0.f}; hx = 0.f; hy = 0.f; return; }
+    const F2 dx = f2_addf(x, -m.hf_x0), dy = f2_addf(y, -m.hf_y0);
+    const float qx = __fmul_rn(dx.h, m.hf_inv_cell), qy = __fmul_rn(dy.h, m.hf_inv_cell);
+    const F2 u = two_sum(qx, __fmul_rn(__fadd_rn(__fmaf_rn(-qx, m.hf_cell, dx.h), dx.l), m.hf_inv_cell));
+    const F2 v = two_sum(qy, __fmul_rn(__fadd_rn(__fmaf_rn(-qy, m.hf_cell, dy.h), dy.l), m.hf_inv_cell));
+    const float umax = (float)(m.hf_nx - 1), vmax = (float)(m.hf_ny - 1);
+    const bool inx = (u.h >= 0.f) && (u.h <= umax), iny = (v.h >= 0.f) && (v.h <= vmax);
+    const float uc = fminf(fmaxf(u.h, 0.f), umax), vc = fminf(fmaxf(v.h, 0.f), vmax);
+    const int i = min((int)floorf(uc), m.hf_nx - 2), j = min((int)floorf(vc), m.hf_ny - 2);
+    const float fx = __fadd_rn(uc - (float)i, inx ? u.l : 0.f), fy = __fadd_rn(vc - (float)j, iny ? v.l : 0.f);
+    const float* r0 = m.hf + j * m.hf_nx + i;
+    const float h00 = __ldg(r0), h10 = __ldg(r0 + 1), h01 = __ldg(r0 + m.hf_nx), h11 = __ldg(r0 + m.hf_nx + 1);
+    // (1-fx)(1-fy) h00 + fx (1-fy) h10 + (1-fx) fy h01 + fx fy h11 = h00 + fx ax + fy (ay + fx axy)
+    const float ax = h10 - h00, ay = h01 - h00, axy = (h11 - h10) - ay;
+    h = F2{h00, fmaf(fx, ax, fy * fmaf(fx, axy, ay))};
+    hx = inx ? ((1.f - fy) * ax + fy * (h11 - h01)) * m.hf_inv_cell : 0.f;
+    hy = iny ? ((1.f - fx) * ay + fx * (h11 - h10)) * m.hf_inv_cell : 0.f;
+}
+
+// sphere vs axis-aligned box: outward normal and depth when overlapping; xl is
+// the low part of the centre (pairs x + xl), which enters the distance to the
+// faces it lies beyond
 __device__ __forceinline__ bool sphere_aabb(float3 x, float r, float3 lo, float3 hi, float3& n, float& pen,
-                                            float xlz = 0.f) {
+                                            float3 xl = make_float3(0.f, 0.f, 0.f)) {
     float3 cp = f3(fminf(fmaxf(x.x, lo.x), hi.x), fminf(fmaxf(x.y, lo.y), hi.y), fminf(fmaxf(x.z, lo.z), hi.z));
     float3 d = x - cp;
-    d.z += (x.z < lo.z || x.z > hi.z) ? xlz : 0.f;
+    d.x += (x.x < lo.x || x.x > hi.x) ? xl.x : 0.f;
+    d.y += (x.y < lo.y || x.y > hi.y) ? xl.y : 0.f;
+    d.z += (x.z < lo.z || x.z > hi.z) ? xl.z : 0.f;
     float d2 = dot3(d, d);
     if (d2 > 0.f) {
         const float inv = rsqrtf(d2);   // approximate, branch-free (no IEEE slow path)
@@ -195,28 +222,31 @@ __device__ __forceinline__ void sphere_vs_box(const DevModel& m, const BoxKin& B
 
 // All static-environment contacts of one sphere (world centre xw, radius r),
 // added with sign SG; toBody maps a world vector into the body's coordinates.
-// zw is the centre's height as a pair (xw.z its FP32 value), from which the
-// depths are taken.  TERR 0: flat ground and no static boxes (normal e_z, depth
-// r - z); TERR 1: the model's plane or heightfield and its static boxes.  A
-// sphere that is not `on` adds exactly zero.
+// (xp, yp, zp) is the centre as pairs (xw its FP32 value), from which the depths
+// are taken: flat ground needs only the height; over a heightfield and against
+// static boxes the horizontal position places the sphere too.  TERR 0: flat
+// ground and no static boxes (normal e_z, depth r - z); TERR 1: the model's
+// plane or heightfield and its static boxes.  A sphere that is not `on` adds
+// exactly zero.
 template <int TERR, int SG, typename ToBody>
-__device__ __forceinline__ void sphere_env(const DevModel& m, float3 xw, F2 zw, float r, float3 cb, float3 w,
-                                           float3 v, const ToBody& toBody, float3& torque, float3& force,
-                                           bool on = true) {
+__device__ __forceinline__ void sphere_env(const DevModel& m, float3 xw, F2 xp, F2 yp, F2 zw, float r, float3 cb,
+                                           float3 w, float3 v, const ToBody& toBody, float3& torque,
+                                           float3& force, bool on = true) {
     if (TERR == 0) {
         const float pen = (r - zw.h) - zw.l;
         contact_wrench<SG>(m, fmaxf(pen, 0.f), toBody.ez(), cb, r, w, v, torque, force, on && pen > 0.f);
         return;
     }
-    float h, hx, hy;
-    ground(m, xw.x, xw.y, h, hx, hy);
+    F2 hp;
+    float hx, hy;
+    ground_pair(m, xp, yp, hp, hx, hy);
     float inv = rsqrt_approx(hx * hx + hy * hy + 1.f);
     float3 n = f3(-hx * inv, -hy * inv, inv);
-    const float pen = r - ((zw.h - h) + zw.l) * n.z;
-    // the height renormalised (its FP32 value and a low part of under an ulp) for
-    // the box tests, which compare the centre against the faces in FP32
-    const F2 zn = two_sum(zw.h, zw.l);
-    xw.z = zn.h;
+    const float pen = r - ((zw.h - hp.h) + (zw.l - hp.l)) * n.z;
+    // the centre renormalised (FP32 values and low parts of under an ulp) for the
+    // box tests, which compare it against the faces in FP32
+    const F2 xn = f2_norm(xp), yn = f2_norm(yp), zn = f2_norm(zw);
+    xw = f3(xn.h, yn.h, zn.h);
     // computed unconditionally and zeroed out of contact (no branch)
     contact_wrench<SG>(m, fmaxf(pen, 0.f), toBody(n), cb, r, w, v, torque, force, on && pen > 0.f);
     for (int b = 0; b < m.n_sbox; b++) {
@@ -224,7 +254,7 @@ __device__ __forceinline__ void sphere_env(const DevModel& m, float3 xw, F2 zw, 
         const float* bx = m.sbox + 6 * b;
         const float3 lo = f3(__ldg(bx), __ldg(bx + 1), __ldg(bx + 2));
         const float3 hi = f3(__ldg(bx + 3), __ldg(bx + 4), __ldg(bx + 5));
-        if (on && sphere_aabb(xw, r, lo, hi, nn, pb, zn.l))
+        if (on && sphere_aabb(xw, r, lo, hi, nn, pb, f3(xn.l, yn.l, zn.l)))
             contact_wrench<SG>(m, pb, toBody(nn), cb, r, w, v, torque, force);
     }
 }
@@ -440,6 +470,10 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, const LegGeo
     F2 rz0, rz1, rz2;
     quat_row2(T.quat, T.quatl, rz0, rz1, rz2);
     const F2 pz_t = {T.p[2], T.pl[2]};
+    // over terrain the spheres' horizontal positions as pairs too (rows 0 and 1)
+    F2 rx[3], ry[3];
+    if (TERR != 0) quat_rows01(T.quat, T.quatl, rx, ry);
+    const F2 px_t = {T.p[0], T.pl[0]}, py_t = {T.p[1], T.pl[1]};
     const float3 rh = G.rh;                                        // abduction joint in the trunk
     const float ty = G.ty;                                         // flexion joint (0, ty, 0) in the hip
     const float kz = m.r_knee[2], fz = m.foot[2];                  // knee (0, 0, kz), foot (0, 0, fz)
@@ -477,9 +511,14 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, const LegGeo
         const F2 zw = f2_add(f2_add(pz_t, f2_mul(rz0, px)), f2_add(f2_mul(rz1, py), f2_mul(rz2, pz)));
         const float3 ptr = f3(f2_val(px), f2_val(py), f2_val(pz));
         const float3 xw = f3(T.p[0], T.p[1], T.p[2]) + mulR(R0, ptr);
+        F2 xpw = {xw.x, 0.f}, ypw = {xw.y, 0.f};
+        if (TERR != 0) {
+            xpw = f2_add(f2_add(px_t, f2_mul(rx[0], px)), f2_add(f2_mul(rx[1], py), f2_mul(rx[2], pz)));
+            ypw = f2_add(f2_add(py_t, f2_mul(ry[0], px)), f2_add(f2_mul(ry[1], py), f2_mul(ry[2], pz)));
+        }
         const CalfFrame toCalf = {R0[0][0], R0[0][1], R0[0][2], R0[1][0], R0[1][1], R0[1][2],
                                   R0[2][0], R0[2][1], R0[2][2], c0, s0, c1, s1, c2, s2};
-        sphere_env<TERR, -1>(m, xw, zw, m.foot_r, foot, wc, vc, toCalf, pa_n, pa_f);
+        sphere_env<TERR, -1>(m, xw, xpw, ypw, zw, m.foot_r, foot, wc, vc, toCalf, pa_n, pa_f);
         if (BOX) sphere_vs_box<-1>(m, BK, xw, m.foot_r, foot, wc, vc, toCalf, pa_n, pa_f, bx_t, bx_f);
     }
     // the calf's articulated inertia after projection is a model constant
@@ -529,9 +568,11 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, const LegGeo
         const float3 cb = f3(tx, 0.f, 0.f);
         const float3 xw = f3(fmaf(R0[0][0], tx, T.p[0]), fmaf(R0[1][0], tx, T.p[1]), fmaf(R0[2][0], tx, T.p[2]));
         const F2 zw = f2_add(pz_t, f2_mulf(rz0, tx));
+        const F2 xpw = TERR != 0 ? f2_add(px_t, f2_mulf(rx[0], tx)) : F2{xw.x, 0.f};
+        const F2 ypw = TERR != 0 ? f2_add(py_t, f2_mulf(ry[0], tx)) : F2{xw.y, 0.f};
         const TrunkFrame toTrunk = {R0[0][0], R0[0][1], R0[0][2], R0[1][0], R0[1][1], R0[1][2],
                                     R0[2][0], R0[2][1], R0[2][2]};
-        sphere_env<TERR, -1>(m, xw, zw, m.tsph_r, cb, T.w, T.v, toTrunk, pa_n, pa_f, on);
+        sphere_env<TERR, -1>(m, xw, xpw, ypw, zw, m.tsph_r, cb, T.w, T.v, toTrunk, pa_n, pa_f, on);
         if (BOX) sphere_vs_box<-1>(m, BK, xw, m.tsph_r, cb, T.w, T.v, toTrunk, pa_n, pa_f, bx_t, bx_f, on);
     }
     // ---- the box's 8 corner spheres against the static environment, 2 per lane
@@ -548,7 +589,9 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, const LegGeo
             const float3 xc = BK.p + mulR(BK.R, cl);
             const F2 zc = f2_add(F2{Bx.p[2], Bx.pl[2]},
                                  f2_add(f2_mulf(bz0, cl.x), f2_add(f2_mulf(bz1, cl.y), f2_mulf(bz2, cl.z))));
-            sphere_env<TERR, 1>(m, xc, zc, m.box_cr, cl, BK.w, BK.v, toBox, bx_t, bx_f);
+            // (the free box's corners are placed horizontally from FP32 values: the
+            // box tasks run on flat ground)
+            sphere_env<TERR, 1>(m, xc, F2{xc.x, 0.f}, F2{xc.y, 0.f}, zc, m.box_cr, cl, BK.w, BK.v, toBox, bx_t, bx_f);
         }
     }
 
