@@ -38,7 +38,7 @@ METRIC = "rollout-steps/s (MPPI step, K=4096, H=100)"
 # one k_rollout launch on this workload, valid only for the kernel sources whose
 # SHA-256 prefix is given; reported as null once those sources change.
 ROLLOUT_TRAFFIC = {"bytes": 84992, "sources_sha256": "cb0be181640c96fb"}
-ROLLOUT_SOURCES = ("rollout.cu", "rollout.cuh", "common.cuh", "noise.cuh", "kernels.h")
+ROLLOUT_SOURCES = ("rollout.cu", "rollout.cuh", "common.cuh", "noise.cuh", "kernels.h", "precise.cuh")
 
 
 def rollout_traffic():
@@ -509,6 +509,7 @@ def run_ours(args):
     peaks = measured_peaks()
     rollout_ms = float(ker[:, 1].mean())
     fl = F.rollout_flops(K_BENCH, H_BENCH, m["n_sub"])
+    fl_dyn = F.rollout_flops(K_BENCH, H_BENCH, m["n_sub"], precise=False)
     achieved = fl / (rollout_ms * 1e-3) / 1e12
     sm_max = (peaks or {}).get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
@@ -543,6 +544,9 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": rollout_traffic(),
                      "kernel": "k_rollout", "flops_per_launch": fl,
+                     # the same time over the dynamics' FLOPs alone (plain FP32 contact geometry)
+                     "dynamics_only": {"flops_per_launch": fl_dyn, "achieved": fl_dyn / (rollout_ms * 1e-3) / 1e12,
+                                       "frac": fl_dyn / (rollout_ms * 1e-3) / 1e12 / peak},
                      "peak_source": "%d SMs (device properties) x 128 FP32 lanes x 2 x %.0f MHz "
                                     "(max SM clock, MEASURED_PEAKS.json)" % (n_sm, sm_max)},
         "e2e": {"value": world_size * K_BENCH * H_BENCH / (e2e_ms * 1e-3), "unit": "rollout-steps/s",

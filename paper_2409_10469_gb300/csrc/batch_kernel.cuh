@@ -191,9 +191,16 @@ __device__ __forceinline__ float rollout_item(const DevModel& m, const DevCost& 
                      : rollout_lane<0, false>(m, c, hz, x0, Uk, nullptr, leg, k, valid, nullptr);
 }
 
+// resident blocks of 128 threads per SM the register budget is sized for (a
+// tuning knob of the build: 3 caps a thread at 168 registers, 2 at 255)
+#ifndef BATCH_BLOCKS_128
+#define BATCH_BLOCKS_128 3
+#endif
+
 // UNI: every instance has the launch's model and cost (a.model, a.cost)
 template <int BLOCK, bool UNI>
-__global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 1 : 384 / BLOCK) k_batch(const __grid_constant__ BatchArgs a) {
+__global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 1 : (BLOCK == 128 ? BATCH_BLOCKS_128 : 384 / BLOCK))
+    k_batch(const __grid_constant__ BatchArgs a) {
     __shared__ InstDesc sd;
     __shared__ int s_item, s_last;
     const int tid = threadIdx.x, leg = tid & 3, r = tid >> 2;

@@ -42,7 +42,30 @@ TRUNK = (30          # rotation matrix of the quaternion
          + 120       # semi-implicit Euler of the free base incl. quaternion
          + 3 * 7)    # trunk spheres against the plane (out of contact)
 
-SUBSTEP = 4 * LEG + TRUNK          # one rollout advanced by one sub-step
+SUBSTEP_DYNAMICS = 4 * LEG + TRUNK  # one rollout advanced by one sub-step, plain FP32 geometry
+
+# ---------------------------------------------------------------- precise contact geometry
+# The per-step tolerance (1e-5 of the FP64 oracle per state block) needs the
+# contact spheres' heights to ~1e-9 m, which plain FP32 misses by ~30x (the
+# height is a difference of two ~0.3 m terms that k = 2e4 N/m amplifies).  The
+# kernel therefore evaluates them as FP32 pairs (precise.cuh) from compensated
+# angles, positions and attitude.  Counted like the rest, per operation of the
+# formulation (TwoSum = 6 adds, Fast2Sum = 3, pair product = 1 mul + 4 FMA,
+# pair x FP32 = 1 mul + 2 FMA, pair sum = TwoSum + 2 adds), as the difference
+# to the plain formulation it replaces:
+PAIR_SINCOS = 22                   # table point, exact reduction, third-order Taylor step, sin and cos
+LEG_PRECISE = ((4 * PAIR_SINCOS + 8 + 6 - JOINT_SINCOS)   # q0, q1, q2, q1 + q2 as pairs; FP32 values
+               + (154 - 37)                              # foot height as pairs, less the FP32 foot position
+               + 6                                       # PD on the compensated angles
+               + 3 * 7 - INTEGRATE_LEG)                  # joint updates with Fast2Sum compensation
+TRUNK_PRECISE = (78                # row 2 of the attitude as pairs (exact products, lo corrections)
+                 + 3 * (13 - 2)    # trunk-sphere heights as pairs
+                 + 5               # attitude step as a compensated increment (no square root)
+                 + 3)              # trunk height with Fast2Sum compensation
+PRECISE = 4 * LEG_PRECISE + TRUNK_PRECISE
+PER_DT_STEP_PRECISE = 49           # rounding the state at the dt step's end, the attitude's norm error
+
+SUBSTEP = SUBSTEP_DYNAMICS + PRECISE   # the formulation the kernel runs (flat ground)
 
 # The same sub-step as the FP64 oracle's plain formulation computes it (dense
 # 6x6 spatial algebra, general rotations, no structural zeros dropped), counted
@@ -53,9 +76,13 @@ ORACLE_PLAIN_SUBSTEP = 23200
 PER_DT_STEP = 112 + 180 + 25       # spline targets, per-leg control cost, trunk state cost
 
 
-def rollout_flops(K: int, H: int, n_sub: int) -> float:
-    """Algorithmic FLOPs of one rollout-kernel launch over K samples."""
-    return float(K) * H * (n_sub * SUBSTEP + PER_DT_STEP)
+def rollout_flops(K: int, H: int, n_sub: int, precise: bool = True) -> float:
+    """Algorithmic FLOPs of one rollout-kernel launch over K samples: the
+    formulation the kernel runs (precise contact geometry included), or with
+    precise=False the dynamics in plain FP32 geometry alone."""
+    if precise:
+        return float(K) * H * (n_sub * SUBSTEP + PER_DT_STEP + PER_DT_STEP_PRECISE)
+    return float(K) * H * (n_sub * SUBSTEP_DYNAMICS + PER_DT_STEP)
 
 
 def sample_bytes(K: int, D: int = 48) -> float:
