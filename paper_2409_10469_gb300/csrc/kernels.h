@@ -83,6 +83,8 @@ struct UpdateArgs {
     double inv_lambda;     // 1 / lambda (FP64: the weights' exponent is formed in FP64)
     int Dp, interp;        // parameters per sample, MPPI_INTERP_*
     double* partial_out;   // launch_update_partial: [50] L_min, Z, S[48] of these samples
+    float2* wts;           // direct targets: [n] the samples' weights (hi, lo) around their chunk minimum
+    double* zm;            // direct targets: [2 * grid] each chunk's weight sum and cost minimum
 };
 
 // Eq. 2's combined sums of a sharded step (Z, S[48], relative to the global

@@ -102,18 +102,26 @@ __device__ __forceinline__ float block_min(float v, float* red) {
 }
 
 // CTA b's chunk on the parameter tile starting at d0: its row of the tile's
-// scratch gets S_c of the tile's parameters, then z_c and m_c
+// scratch gets S_c of the tile's parameters, then z_c and m_c.  With PRE the
+// chunk's weights, z_c and m_c come from k_update_weights (a.wts, a.zm) instead
+// of being formed here (direct targets: every tile would repeat the FP64 exps).
+template <bool PRE>
 __device__ __forceinline__ void chunk_partials(const UpdateArgs& a, int b, int G, int d0, double* rows, UpdSmem& s) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int Dp = a.Dp;
     const int chunk = (a.n + G - 1) / G;
     const int k0 = b * chunk, k1 = min(a.n, k0 + chunk);
-    float lm = INFINITY;
-    for (int k = k0 + tid; k < k1; k += UPD_THREADS) {
-        const float l = __ldg(a.L + k);
-        if (finitef(l)) lm = fminf(lm, l);
+    float m;
+    if (PRE) {
+        m = (float)__ldcg(a.zm + 2 * b + 1);
+    } else {
+        float lm = INFINITY;
+        for (int k = k0 + tid; k < k1; k += UPD_THREADS) {
+            const float l = __ldg(a.L + k);
+            if (finitef(l)) lm = fminf(lm, l);
+        }
+        m = block_min(lm, s.red);
     }
-    const float m = block_min(lm, s.red);
     const bool okc = finitef(m);
     // sum_k w_k U_k: warp w takes samples ks + w, ks + w + 8, ... of each
     // sub-chunk; lane i < 24 owns parameters d0 + 2i, d0 + 2i + 1 (Dp is even, so
@@ -128,7 +136,9 @@ __device__ __forceinline__ void chunk_partials(const UpdateArgs& a, int b, int G
             // and exp in FP64, kept as pairs
             const int k = ks + tid;
             float2 wk = make_float2(0.f, 0.f);
-            if (k < k1) {
+            if (PRE) {
+                if (k < k1) wk = __ldcg(a.wts + k);
+            } else if (k < k1) {
                 const float l = __ldg(a.L + k);
                 if (finitef(l)) {
                     const double wd = exp(-((double)l - (double)m) * a.inv_lambda);
@@ -136,7 +146,7 @@ __device__ __forceinline__ void chunk_partials(const UpdateArgs& a, int b, int G
                     wk.y = (float)(wd - (double)wk.x);
                 }
             }
-            ff_acc(zs, ze, wk.x, wk.y);
+            if (!PRE) ff_acc(zs, ze, wk.x, wk.y);
             __syncthreads();  // the previous sub-chunk's weights are consumed
             s.w[tid] = wk;
             __syncthreads();
@@ -161,11 +171,59 @@ __device__ __forceinline__ void chunk_partials(const UpdateArgs& a, int b, int G
         row[tid] = (double)hi + (double)lo;
     }
     if (tid == UPD_TILE) {
-        float hi = s.z[0].x, lo = s.z[0].y;
-        for (int w = 1; w < UPD_WARPS; w++) ff_acc(hi, lo, s.z[w].x, s.z[w].y);
-        row[UPD_TILE] = (double)hi + (double)lo;
+        if (PRE) {
+            row[UPD_TILE] = __ldcg(a.zm + 2 * b);
+        } else {
+            float hi = s.z[0].x, lo = s.z[0].y;
+            for (int w = 1; w < UPD_WARPS; w++) ff_acc(hi, lo, s.z[w].x, s.z[w].y);
+            row[UPD_TILE] = (double)hi + (double)lo;
+        }
     }
     if (tid == UPD_TILE + 1) row[UPD_TILE + 1] = (double)m;
+}
+
+// Direct targets, first pass: chunk b's cost minimum m_c, its samples' weights
+// exp(-(L_k - m_c) / lambda) (exponent and exp in FP64, kept as FP32 pairs) into
+// a.wts and z_c = their sum into a.zm -- once per sample, for every parameter
+// tile of the second pass
+__global__ void __launch_bounds__(UPD_THREADS) k_update_weights(UpdateArgs a) {
+    __shared__ float red[UPD_WARPS];
+    __shared__ float2 zw[UPD_WARPS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, b = blockIdx.x, G = gridDim.x;
+    const int chunk = (a.n + G - 1) / G;
+    const int k0 = b * chunk, k1 = min(a.n, k0 + chunk);
+    float lm = INFINITY;
+    for (int k = k0 + tid; k < k1; k += UPD_THREADS) {
+        const float l = __ldg(a.L + k);
+        if (finitef(l)) lm = fminf(lm, l);
+    }
+    const float m = block_min(lm, red);
+    const bool okc = finitef(m);
+    float zs = 0.f, ze = 0.f;
+    for (int k = k0 + tid; k < k1; k += UPD_THREADS) {
+        const float l = __ldg(a.L + k);
+        float2 wk = make_float2(0.f, 0.f);
+        if (okc && finitef(l)) {
+            const double wd = exp(-((double)l - (double)m) * a.inv_lambda);
+            wk.x = (float)wd;
+            wk.y = (float)(wd - (double)wk.x);
+        }
+        a.wts[k] = wk;
+        ff_acc(zs, ze, wk.x, wk.y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float v = __shfl_xor_sync(0xffffffffu, zs, o), ve = __shfl_xor_sync(0xffffffffu, ze, o);
+        ff_acc(zs, ze, v, ve);
+    }
+    if (lane == 0) zw[warp] = make_float2(zs, ze);
+    __syncthreads();
+    if (tid == 0) {
+        float hi = zw[0].x, lo = zw[0].y;
+        for (int w = 1; w < UPD_WARPS; w++) ff_acc(hi, lo, zw[w].x, zw[w].y);
+        a.zm[2 * b] = (double)hi + (double)lo;
+        a.zm[2 * b + 1] = (double)m;
+    }
 }
 
 // publish this CTA's writes and count it in: true in the last of `total` CTAs
@@ -240,7 +298,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_knots(UpdateArgs a) {
     __shared__ UpdSmem s;
     __shared__ float s_mu[D];
     const int tid = threadIdx.x, G = gridDim.x;
-    chunk_partials(a, blockIdx.x, G, 0, a.part, s);
+    chunk_partials<false>(a, blockIdx.x, G, 0, a.part, s);
     if (!count_in(a.counter, (unsigned)G, s)) return;
 
     // last CTA: combine, apply, shift
@@ -276,7 +334,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_knots(UpdateArgs a) {
 __global__ void __launch_bounds__(UPD_THREADS) k_update_partial(UpdateArgs a) {
     __shared__ UpdSmem s;
     const int tid = threadIdx.x, G = gridDim.x;
-    chunk_partials(a, blockIdx.x, G, 0, a.part, s);
+    chunk_partials<false>(a, blockIdx.x, G, 0, a.part, s);
     if (!count_in(a.counter, (unsigned)G, s)) return;
     const bool ok = combine_setup(a, G, a.part, s);
     {
@@ -318,7 +376,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_tiled(UpdateArgs a) {
     const int tid = threadIdx.x, G = gridDim.x, T = gridDim.y, y = blockIdx.y;
     const int Dp = a.Dp, d0 = y * UPD_TILE;
     double* rows = a.part + (size_t)y * G * UPD_ROW;
-    chunk_partials(a, blockIdx.x, G, d0, rows, s);
+    chunk_partials<true>(a, blockIdx.x, G, d0, rows, s);
     if (!count_in(a.counter + 1 + y, (unsigned)G, s)) return;
 
     // last CTA of this tile: combine and apply its parameters
@@ -355,12 +413,20 @@ int update_grid(int n) {
     return g < 1 ? 1 : (g > UPDATE_MAX_CTAS ? UPDATE_MAX_CTAS : g);
 }
 
+// direct targets: chunks of ~128 samples (x T parameter tiles), as the knots
+static int update_grid_tiled(int n) {
+    int g = (n + 127) / 128;
+    return g < 1 ? 1 : (g > UPDATE_MAX_CTAS ? UPDATE_MAX_CTAS : g);
+}
+
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t st) {
     if (a.Dp % 2 != 0 || a.Dp < D || (a.Dp > D && !a.mu_upd)) return cudaErrorInvalidValue;
     if (a.Dp == D) {
         k_update_knots<<<update_grid(a.n), UPD_THREADS, 0, st>>>(a);
     } else {
-        const dim3 grid(update_grid(a.n), (a.Dp + UPD_TILE - 1) / UPD_TILE);
+        if (!a.wts || !a.zm) return cudaErrorInvalidValue;
+        k_update_weights<<<update_grid_tiled(a.n), UPD_THREADS, 0, st>>>(a);
+        const dim3 grid(update_grid_tiled(a.n), (a.Dp + UPD_TILE - 1) / UPD_TILE);
         k_update_tiled<<<grid, UPD_THREADS, 0, st>>>(a);
     }
     return cudaGetLastError();
