@@ -297,12 +297,12 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
               al((void**)&h->d_L, K * sizeof(float)) && al((void**)&h->d_x0, K * NX_BOX * sizeof(float)) &&
               al((void**)&h->d_u0, NJ * sizeof(float)) && al((void**)&h->d_status, sizeof(int)) &&
               al((void**)&h->d_wsum, sizeof(double)) &&
-              al((void**)&h->d_part, std::max(update_part_doubles((int)Dp), fused_part_doubles(*cfg)) *
+              al((void**)&h->d_part, std::max({update_part_doubles((int)Dp), fused_part_doubles(*cfg),
+                                                cfg->interp == MPPI_INTERP_DIRECT
+                                                    ? update_direct_part_doubles((int)Dp) : (size_t)0}) *
                                          sizeof(double)) &&
               al((void**)&h->d_counter, update_counters((int)Dp) * sizeof(unsigned)) &&
               al((void**)&h->d_shard, 128 * sizeof(double)) &&
-              (cfg->interp != MPPI_INTERP_DIRECT ||
-               al((void**)&h->d_wts, K * sizeof(float2) + 2 * UPDATE_MAX_CTAS * sizeof(double))) &&
               al((void**)&h->d_B, (size_t)4 * cfg->H * sizeof(float));
     if (ok && model->terrain == 1) {
         size_t nh = (size_t)model->hf_nx * model->hf_ny;
@@ -363,7 +363,7 @@ extern "C" mppi_status mppi_destroy(mppi_handle h) {
     else cudaDeviceSynchronize();
     void* bufs[] = {h->d_mu,  h->d_mu_prop, h->d_mu_upd, h->d_U,    h->d_L,    h->d_x0,
                     h->d_u0,  h->d_hf,      h->d_status, h->d_wsum, h->d_part, h->d_counter,
-                    h->d_sbox, h->d_B,      h->d_shard,  h->d_wts};
+                    h->d_sbox, h->d_B,      h->d_shard};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (h->h_box) cudaFreeHost(h->h_box);
@@ -593,9 +593,6 @@ static mppi_status do_update(mppi_handle h, const float* dL, const float* dU, in
     a.Dp = h->D;
     a.interp = h->cfg.interp;
     a.partial_out = nullptr;
-    a.wts = h->d_wts;  // direct targets: the first pass's weights and chunk sums
-    a.zm = h->d_wts ? reinterpret_cast<double*>(h->d_wts + h->cfg.K) : nullptr;
-    if (h->d_wts && n > h->cfg.K) return fail(h, MPPI_ERR_ARG, "direct-target updates take at most K samples");
     CK(launch_update(a, h->stream));
     h->launches++;
     return MPPI_OK;
@@ -773,8 +770,6 @@ extern "C" mppi_status mppi_step_partial(mppi_handle h, const float* x0, uint32_
     u.Dp = D;
     u.interp = h->cfg.interp;
     u.partial_out = h->d_shard;
-    u.wts = nullptr;
-    u.zm = nullptr;
     CK(launch_update_partial(u, h->stream));
     h->launches++;
     const bool dev = is_device(part_out);

@@ -231,15 +231,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 1 : (BLOCK == 128 ? BATC
         const float L = UNI ? rollout_item(a.model, a.cost, hz, x0, Uk, leg, k, valid)
                             : rollout_item(sd.model, sd.cost, hz, x0, Uk, leg, k, valid);
         if (valid && leg == 0) sd.L[k] = L;
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) {
-            const unsigned prev = atomicAdd(a.done + w.inst, (unsigned)w.n);
-            s_last = (prev + (unsigned)w.n == (unsigned)sd.K);
-        }
-        __syncthreads();
-        if (s_last) {
-            __threadfence();
+        if (cta_count_in(a.done + w.inst, (unsigned)w.n, (unsigned)sd.K, s_last)) {
             block_update<BLOCK>(sd, a.u0s + (size_t)w.inst * NJ);
             if (tid == 0) a.done[w.inst] = 0u;
         }

@@ -101,6 +101,25 @@ __device__ __forceinline__ float shifted_knot(const float* mu, int interp, int H
     return (1.f - f) * mu[jj * NJ + i] + f * mu[(jj + 1) * NJ + i];
 }
 
+// Count this CTA in on a global counter after its global writes; returns, to
+// every thread, whether this CTA brought the count to `total` (it is the last
+// of the CTAs counted), in which case the counted CTAs' writes are visible to
+// all its threads.  The barrier gathers the CTA's writes under thread 0, whose
+// one atomic add with acquire-release semantics at GPU scope publishes them
+// (release is cumulative) and, in the last CTA, acquires the others'; the
+// second barrier hands that on to the CTA's other threads.  `flag` is a shared
+// int.  No thread waits on another CTA.
+__device__ __forceinline__ bool cta_count_in(unsigned* counter, unsigned inc, unsigned total, int& flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned prev;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(prev) : "l"(counter), "r"(inc) : "memory");
+        flag = prev + inc == total;
+    }
+    __syncthreads();
+    return flag != 0;
+}
+
 // MUFU reciprocal and reciprocal square root with subnormals flushed to zero:
 // one instruction each, no subnormal-handling branch (the arguments here --
 // pivots, determinants, norms plus a positive floor -- are never subnormal)

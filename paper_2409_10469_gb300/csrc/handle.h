@@ -35,7 +35,6 @@ struct mppi_handle_s {
     double* d_wsum = nullptr;
     double* d_part = nullptr;      // update scratch: per-CTA partial sums
     double* d_shard = nullptr;     // sharded step: [64] a shard's partial sums, [64] the combined sums
-    float2* d_wts = nullptr;       // direct targets: [K] weights and [2 x 128] chunk sums and minima
     unsigned* d_counter = nullptr;  // update scratch: finished-CTA counter
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     int timing = 0;

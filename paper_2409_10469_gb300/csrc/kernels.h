@@ -77,14 +77,13 @@ struct UpdateArgs {
     float* u0;             // [12]
     int* status;           // 0 ok, 4 all costs non-finite
     double* wsum;          // normaliser (FP64) of the last update, optional
-    double* part;          // scratch [tiles][grid][50]: per-CTA partial sums, weight sum, cost minimum
-    unsigned* counter;     // scratch [1 + tiles]: CTAs finished (0 between launches)
+    double* part;          // scratch: per-chunk partial sums, weight sum, cost minimum ([grid][50] for
+                           // knots, [chunks][Dp + 2] for direct targets)
+    unsigned* counter;     // scratch: CTAs finished (0 between launches)
     int n, H, ctrl_steps;
     double inv_lambda;     // 1 / lambda (FP64: the weights' exponent is formed in FP64)
     int Dp, interp;        // parameters per sample, MPPI_INTERP_*
     double* partial_out;   // launch_update_partial: [50] L_min, Z, S[48] of these samples
-    float2* wts;           // direct targets: [n] the samples' weights (hi, lo) around their chunk minimum
-    double* zm;            // direct targets: [2 * grid] each chunk's weight sum and cost minimum
 };
 
 // Eq. 2's combined sums of a sharded step (Z, S[48], relative to the global
@@ -105,6 +104,10 @@ int update_grid(int n);
 constexpr int update_tiles(int Dp) { return (Dp + D - 1) / D; }
 constexpr size_t update_part_doubles(int Dp) { return (size_t)UPDATE_MAX_CTAS * update_tiles(Dp) * (D + 2); }
 constexpr int update_counters(int Dp) { return 1 + update_tiles(Dp); }
+// direct targets (Dp = 12 H): the most sample chunks an update of Dp parameters
+// per sample uses, and its scratch in doubles (any n: the chunk count is capped)
+int update_direct_chunks_cap(int Dp);
+size_t update_direct_part_doubles(int Dp);
 
 cudaError_t launch_sample(const SampleArgs& a, cudaStream_t st);
 // the noise self-test's tables (2^24 entries each)

@@ -113,7 +113,5 @@ extern "C" mppi_status mppi_update_noalloc(const float* L, const float* U, int n
     a.Dp = D;                 // a knot representation: 48 parameters
     a.interp = interp;        // MPPI_INTERP_* equals the kernels' INTERP_* (api.cu checks it)
     a.partial_out = nullptr;
-    a.wts = nullptr;
-    a.zm = nullptr;
     return launch_update(a, st) == cudaSuccess ? MPPI_OK : MPPI_ERR_CUDA;
 }

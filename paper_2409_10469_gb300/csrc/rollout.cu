@@ -111,12 +111,7 @@ __device__ __forceinline__ void fused_update(const RolloutArgs& a, float L, cons
     }
     if (tid == 0) mine[D + 1] = make_float2(mc, 0.f);
     // publish, then count this CTA in
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_last = (atomicAdd(a.counter, 1u) == (unsigned)(G - 1));
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
+    if (!cta_count_in(a.counter, 1u, (unsigned)G, s_last)) return;
 
     // ---- last CTA: L_min over the CTA minima (kept in s_f for the factors)
     float M = INFINITY;

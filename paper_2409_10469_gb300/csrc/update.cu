@@ -2,24 +2,38 @@
 // control u = mu[0] and the receding-horizon shift (Alg. 1, last steps) of
 // arXiv 2409.10469, Sec. II-B.
 //
-// G CTAs split the n samples into contiguous chunks of about 128 (a second grid
-// dimension T tiles the 12 H parameters of direct targets into groups of 48;
-// the knot representations have one tile and their own kernel).  Every CTA
-// reads only its chunk's costs: their minimum m_c over the finite ones, the
-// weights w_k = exp(-(L_k - m_c)/lambda) (0 if L_k is not finite) with the
-// exponent and the exp in FP64, computed once per sample into shared memory as
-// FP32 pairs (about 48 significant bits), their sum z_c and the sums
-// S_c = sum_k w_k U_k of its tile's parameters (float-float pairs per lane,
-// across lanes and warps: FP64 runs at 1/64 of the FP32 rate on this part, so
-// beyond the exps only the last CTA's combine uses it).  It writes these and m_c
-// to scratch and bumps a counter; the CTA that sees the counter reach the grid
+// Knot representations (48 parameters): G CTAs split the n samples into
+// contiguous chunks of about 128.  Every CTA reads only its chunk's costs: their
+// minimum m_c over the finite ones, the weights w_k = exp(-(L_k - m_c)/lambda)
+// (0 if L_k is not finite) with the exponent and the exp in FP64, computed once
+// per sample into shared memory as FP32 pairs (about 48 significant bits), their
+// sum z_c and the sums S_c = sum_k w_k U_k (float-float pairs per lane, across
+// lanes and warps: FP64 runs at 1/64 of the FP32 rate on this part, so beyond
+// the exps only the last CTA's combine uses it).  It writes these and m_c to
+// scratch and bumps a counter; the CTA that sees the counter reach the grid
 // size - 1 (no waiting: it is simply the last to finish) takes L_min = min_c m_c
 // and scales chunk c by f_c = exp(-(m_c - L_min)/lambda) (FP64) -- Eq. 1's
 // weights factor as exp(-(L_k - L_min)/lambda) = w_k f_c -- so that
 // mu' = sum_c f_c S_c / sum_c f_c z_c.  The chunks are added in a fixed order and
 // tree, so the result does not depend on scheduling.  It writes mu', u0 = the
-// controls of step 0 (knot 0, or the first direct target), the shifted nominal
-// and the status, and re-arms the counter for the next launch.
+// controls of step 0 (knot 0), the shifted nominal and the status, and re-arms
+// the counter for the next launch.
+//
+// Direct targets (12 H parameters per sample, rows of kilobytes) take Eq. 1's
+// weights around the global minimum directly, in three launches: k_update_lmin
+// finds L_min over the finite costs (an atomic max on an order-reversed integer
+// key, so the result does not depend on scheduling); k_update_rows streams U
+// row by row -- CTA (c, y), two per SM, takes chunk c of the samples and column
+// tile y of the parameters, each thread one 16-byte group of every row, so a
+// warp reads 512 contiguous bytes per row -- with the weights
+// w_k = exp(-(L_k - L_min)/lambda) (FP64 exponent and exp); it adds the rows two
+// at a time in FP32, w_a u_a + w_b u_b by one product and one FMA, into
+// float-float sums, and writes its chunk's sums of its tile and, from tile 0,
+// z_c = sum w_k (float-float from the FP64 weights); k_update_combine adds the
+// chunks per column in float-float by a fixed tree (no factors: every chunk
+// shares the reference L_min) and its last CTA shifts.  Error of the two-row
+// FP32 step: at most 3 roundings of 2^-24 (the product, the FMA, the weight's
+// FP32 rounding) of sum_k w_k |u_kj|, so |mu'_j error| <= 1.8e-7 max_k |u_kj|.
 #include "kernels.h"
 
 namespace mppi {
@@ -101,33 +115,24 @@ __device__ __forceinline__ float block_min(float v, float* red) {
     return m;
 }
 
-// CTA b's chunk on the parameter tile starting at d0: its row of the tile's
-// scratch gets S_c of the tile's parameters, then z_c and m_c.  With PRE the
-// chunk's weights, z_c and m_c come from k_update_weights (a.wts, a.zm) instead
-// of being formed here (direct targets: every tile would repeat the FP64 exps).
-template <bool PRE>
-__device__ __forceinline__ void chunk_partials(const UpdateArgs& a, int b, int G, int d0, double* rows, UpdSmem& s) {
+// CTA b's chunk of the 48 knot parameters: its row of the scratch gets S_c of
+// the parameters, then z_c and m_c
+__device__ __forceinline__ void chunk_partials(const UpdateArgs& a, int b, int G, double* rows, UpdSmem& s) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int Dp = a.Dp;
     const int chunk = (a.n + G - 1) / G;
     const int k0 = b * chunk, k1 = min(a.n, k0 + chunk);
-    float m;
-    if (PRE) {
-        m = (float)__ldcg(a.zm + 2 * b + 1);
-    } else {
-        float lm = INFINITY;
-        for (int k = k0 + tid; k < k1; k += UPD_THREADS) {
-            const float l = __ldg(a.L + k);
-            if (finitef(l)) lm = fminf(lm, l);
-        }
-        m = block_min(lm, s.red);
+    float lm = INFINITY;
+    for (int k = k0 + tid; k < k1; k += UPD_THREADS) {
+        const float l = __ldg(a.L + k);
+        if (finitef(l)) lm = fminf(lm, l);
     }
+    const float m = block_min(lm, s.red);
     const bool okc = finitef(m);
     // sum_k w_k U_k: warp w takes samples ks + w, ks + w + 8, ... of each
-    // sub-chunk; lane i < 24 owns parameters d0 + 2i, d0 + 2i + 1 (Dp is even, so
-    // a pair never straddles the end)
-    const bool own = lane < UPD_TILE / 2 && d0 + 2 * lane < Dp;
-    const float2* u2 = reinterpret_cast<const float2*>(a.U + d0) + lane;
+    // sub-chunk; lane i < 24 owns parameters 2i, 2i + 1
+    const bool own = lane < UPD_TILE / 2;
+    const float2* u2 = reinterpret_cast<const float2*>(a.U) + lane;
     float zs = 0.f, ze = 0.f;
     float s0 = 0.f, s1 = 0.f, e0 = 0.f, e1 = 0.f;
     if (okc)
@@ -136,9 +141,7 @@ __device__ __forceinline__ void chunk_partials(const UpdateArgs& a, int b, int G
             // and exp in FP64, kept as pairs
             const int k = ks + tid;
             float2 wk = make_float2(0.f, 0.f);
-            if (PRE) {
-                if (k < k1) wk = __ldcg(a.wts + k);
-            } else if (k < k1) {
+            if (k < k1) {
                 const float l = __ldg(a.L + k);
                 if (finitef(l)) {
                     const double wd = exp(-((double)l - (double)m) * a.inv_lambda);
@@ -146,7 +149,7 @@ __device__ __forceinline__ void chunk_partials(const UpdateArgs& a, int b, int G
                     wk.y = (float)(wd - (double)wk.x);
                 }
             }
-            if (!PRE) ff_acc(zs, ze, wk.x, wk.y);
+            ff_acc(zs, ze, wk.x, wk.y);
             __syncthreads();  // the previous sub-chunk's weights are consumed
             s.w[tid] = wk;
             __syncthreads();
@@ -165,76 +168,22 @@ __device__ __forceinline__ void chunk_partials(const UpdateArgs& a, int b, int G
     __syncthreads();
     // the warps' pairs added in warp order; the row holds hi + lo as a double
     double* row = rows + (size_t)b * UPD_ROW;
-    if (tid < UPD_TILE && d0 + tid < Dp) {
+    if (tid < UPD_TILE) {
         float hi = s.part[0][tid].x, lo = s.part[0][tid].y;
         for (int w = 1; w < UPD_WARPS; w++) ff_acc(hi, lo, s.part[w][tid].x, s.part[w][tid].y);
         row[tid] = (double)hi + (double)lo;
     }
     if (tid == UPD_TILE) {
-        if (PRE) {
-            row[UPD_TILE] = __ldcg(a.zm + 2 * b);
-        } else {
-            float hi = s.z[0].x, lo = s.z[0].y;
-            for (int w = 1; w < UPD_WARPS; w++) ff_acc(hi, lo, s.z[w].x, s.z[w].y);
-            row[UPD_TILE] = (double)hi + (double)lo;
-        }
+        float hi = s.z[0].x, lo = s.z[0].y;
+        for (int w = 1; w < UPD_WARPS; w++) ff_acc(hi, lo, s.z[w].x, s.z[w].y);
+        row[UPD_TILE] = (double)hi + (double)lo;
     }
     if (tid == UPD_TILE + 1) row[UPD_TILE + 1] = (double)m;
 }
 
-// Direct targets, first pass: chunk b's cost minimum m_c, its samples' weights
-// exp(-(L_k - m_c) / lambda) (exponent and exp in FP64, kept as FP32 pairs) into
-// a.wts and z_c = their sum into a.zm -- once per sample, for every parameter
-// tile of the second pass
-__global__ void __launch_bounds__(UPD_THREADS) k_update_weights(UpdateArgs a) {
-    __shared__ float red[UPD_WARPS];
-    __shared__ float2 zw[UPD_WARPS];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, b = blockIdx.x, G = gridDim.x;
-    const int chunk = (a.n + G - 1) / G;
-    const int k0 = b * chunk, k1 = min(a.n, k0 + chunk);
-    float lm = INFINITY;
-    for (int k = k0 + tid; k < k1; k += UPD_THREADS) {
-        const float l = __ldg(a.L + k);
-        if (finitef(l)) lm = fminf(lm, l);
-    }
-    const float m = block_min(lm, red);
-    const bool okc = finitef(m);
-    float zs = 0.f, ze = 0.f;
-    for (int k = k0 + tid; k < k1; k += UPD_THREADS) {
-        const float l = __ldg(a.L + k);
-        float2 wk = make_float2(0.f, 0.f);
-        if (okc && finitef(l)) {
-            const double wd = exp(-((double)l - (double)m) * a.inv_lambda);
-            wk.x = (float)wd;
-            wk.y = (float)(wd - (double)wk.x);
-        }
-        a.wts[k] = wk;
-        ff_acc(zs, ze, wk.x, wk.y);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float v = __shfl_xor_sync(0xffffffffu, zs, o), ve = __shfl_xor_sync(0xffffffffu, ze, o);
-        ff_acc(zs, ze, v, ve);
-    }
-    if (lane == 0) zw[warp] = make_float2(zs, ze);
-    __syncthreads();
-    if (tid == 0) {
-        float hi = zw[0].x, lo = zw[0].y;
-        for (int w = 1; w < UPD_WARPS; w++) ff_acc(hi, lo, zw[w].x, zw[w].y);
-        a.zm[2 * b] = (double)hi + (double)lo;
-        a.zm[2 * b + 1] = (double)m;
-    }
-}
-
 // publish this CTA's writes and count it in: true in the last of `total` CTAs
 __device__ __forceinline__ bool count_in(unsigned* counter, unsigned total, UpdSmem& s) {
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s.last = (atomicAdd(counter, 1u) == total - 1);
-    __syncthreads();
-    if (!s.last) return false;
-    __threadfence();
-    return true;
+    return cta_count_in(counter, 1u, total, s.last);
 }
 
 // the last CTA of a tile: L_min over the G chunk minima of the tile's rows, the
@@ -298,7 +247,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_knots(UpdateArgs a) {
     __shared__ UpdSmem s;
     __shared__ float s_mu[D];
     const int tid = threadIdx.x, G = gridDim.x;
-    chunk_partials<false>(a, blockIdx.x, G, 0, a.part, s);
+    chunk_partials(a, blockIdx.x, G, a.part, s);
     if (!count_in(a.counter, (unsigned)G, s)) return;
 
     // last CTA: combine, apply, shift
@@ -334,7 +283,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_knots(UpdateArgs a) {
 __global__ void __launch_bounds__(UPD_THREADS) k_update_partial(UpdateArgs a) {
     __shared__ UpdSmem s;
     const int tid = threadIdx.x, G = gridDim.x;
-    chunk_partials<false>(a, blockIdx.x, G, 0, a.part, s);
+    chunk_partials(a, blockIdx.x, G, a.part, s);
     if (!count_in(a.counter, (unsigned)G, s)) return;
     const bool ok = combine_setup(a, G, a.part, s);
     {
@@ -366,46 +315,303 @@ __global__ void k_update_finalize(FinalizeArgs a) {
     for (int j = tid; j < D; j += blockDim.x) a.mu[j] = shifted_knot(s_mu, a.interp, a.H, a.ctrl_steps, j / NJ, j % NJ);
 }
 
-// Direct targets (12 H parameters): G x T CTAs, T = ceil(12 H / 48) parameter
-// tiles, each tile its own update: the last CTA of tile y (counter[1 + y])
-// combines the tile's 48 parameters from its G rows (every tile's rows carry
-// z_c and m_c, computed identically); the last tile to finish (counter[0])
-// applies the shift, which moves targets across tiles.
-__global__ void __launch_bounds__(UPD_THREADS) k_update_tiled(UpdateArgs a) {
-    __shared__ UpdSmem s;
-    const int tid = threadIdx.x, G = gridDim.x, T = gridDim.y, y = blockIdx.y;
-    const int Dp = a.Dp, d0 = y * UPD_TILE;
-    double* rows = a.part + (size_t)y * G * UPD_ROW;
-    chunk_partials<true>(a, blockIdx.x, G, d0, rows, s);
-    if (!count_in(a.counter + 1 + y, (unsigned)G, s)) return;
+// ---------------------------------------------------------------- direct targets
 
-    // last CTA of this tile: combine and apply its parameters
-    const bool ok = combine_setup(a, G, rows, s);
-    {
-        const int j = tid >> 2, q = tid & 3, d = d0 + j;
-        const double S = combine_param(G, rows, min(j, UPD_TILE - 1), q, s);
-        if (j < UPD_TILE && d < Dp && q == 0) {
-            const float mu_new = ok ? (float)(S / s.Z) : a.mu[d];  // every cost non-finite: keep the mean
-            a.mu_upd[d] = mu_new;
-            if (d < NJ) a.u0[d] = mu_new;  // the controls of step 0: the first direct target
+constexpr int ROW_GROUPS = 512;  // 16-byte parameter groups per column tile (threads per CTA at most)
+constexpr int ROW_SUB = 256;     // samples whose weights sit in shared memory at a time
+constexpr int ROW_NB = 8;        // rows whose loads a thread issues together
+constexpr int ROW_MAX_CHUNKS = 512;
+constexpr int CMB_THREADS = 512, CMB_WARPS = CMB_THREADS / 32;  // combine: 32 columns per CTA
+constexpr int CMB_NB = 20;       // chunk partials a combining lane loads per round trip (one round: G <= 320)
+static_assert(ROW_SUB % ROW_NB == 0, "a weight window holds whole batches");
+static_assert(ROW_MAX_CHUNKS <= CMB_THREADS, "the combine loads one chunk's weight sum per thread");
+
+static int row_tiles(int Dp) { return (Dp / 4 + ROW_GROUPS - 1) / ROW_GROUPS; }
+static int row_groups(int Dp) {  // groups per tile: the tiles split the row evenly
+    const int T = row_tiles(Dp);
+    return (Dp / 4 + T - 1) / T;
+}
+int update_direct_chunks_cap(int Dp) {
+    const int T = row_tiles(Dp), g = (1024 + T - 1) / T;
+    return g < 1 ? 1 : (g > ROW_MAX_CHUNKS ? ROW_MAX_CHUNKS : g);
+}
+size_t update_direct_part_doubles(int Dp) { return (size_t)update_direct_chunks_cap(Dp) * (Dp + 1); }
+
+// chunks of a direct-target update of n samples: about two CTAs per SM over the
+// chunks and column tiles, at least 16 samples per chunk
+static int update_direct_chunks(int n, int Dp, int sms) {
+    const int T = row_tiles(Dp);
+    int g = (2 * sms + T - 1) / T;
+    g = min(g, (n + 15) / 16);
+    g = min(g, update_direct_chunks_cap(Dp));
+    return g < 1 ? 1 : g;
+}
+
+// The minimum over finite costs as an integer key for atomicMax: the float's
+// bits made order-preserving as a signed integer (negative values have their
+// magnitude bits flipped), then reversed as INT_MAX - key (modulo 2^32), so 0
+// (the state between launches) means "no finite cost" -- no finite float maps
+// there.
+__device__ __forceinline__ unsigned lmin_key(float x) {
+    const int i = __float_as_int(x);
+    return 0x7fffffffu - (unsigned)(i >= 0 ? i : i ^ 0x7fffffff);
+}
+__device__ __forceinline__ float lmin_of_key(unsigned k) {
+    const int i = (int)(0x7fffffffu - k);
+    return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff);
+}
+
+// (s, e) += v: Knuth's TwoSum of s + v, its error into e
+__device__ __forceinline__ void ff_acc1(float& s, float& e, float v) {
+    const float t = __fadd_rn(s, v);
+    const float bp = __fsub_rn(t, s);
+    e = __fadd_rn(e, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp)));
+    s = t;
+}
+// (s, e) += w_a u_a + w_b u_b, the two products summed in FP32
+__device__ __forceinline__ void ff_madd2(float& s, float& e, float wa, float ua, float wb, float ub) {
+    ff_acc1(s, e, __fmaf_rn(wb, ub, __fmul_rn(wa, ua)));
+}
+__device__ __forceinline__ void ff_madd2_4(float (&s)[4], float (&e)[4], float wa, float4 a, float wb, float4 b) {
+    ff_madd2(s[0], e[0], wa, a.x, wb, b.x);
+    ff_madd2(s[1], e[1], wa, a.y, wb, b.y);
+    ff_madd2(s[2], e[2], wa, a.z, wb, b.z);
+    ff_madd2(s[3], e[3], wa, a.w, wb, b.w);
+}
+// pair sum a + b (float-float)
+__device__ __forceinline__ float2 ff_sum(float2 a, float2 b) {
+    ff_acc(a.x, a.y, b.x, b.y);
+    return a;
+}
+
+// minimum of v over the CTA's nw warps, returned to every thread
+__device__ __forceinline__ float block_min_n(float v, float* red, int nw) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();  // red is free
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    float m = red[0];
+    for (int w = 1; w < nw; w++) m = fminf(m, red[w]);
+    return m;
+}
+
+// Programmatic dependent launch: the next kernel on the stream may start once
+// every CTA of this one has called launch_dependents (or exited); a kernel
+// launched that way waits in grid_dependency_wait until its predecessor has
+// completed and its writes are visible.  Both are no-ops without the launch
+// attribute.
+__device__ __forceinline__ void launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// L_min over the finite costs into counter[1] (the reversed key; 0 between
+// launches): 4 costs per thread and round, loaded together
+__global__ void __launch_bounds__(256) k_update_lmin(UpdateArgs a) {
+    __shared__ float red[8];
+    launch_dependents();  // the rows kernel's CTAs may start their loads of U now
+    float lm = INFINITY;
+    for (int k = blockIdx.x * 1024 + threadIdx.x; k < a.n; k += gridDim.x * 1024) {
+        float l[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) l[q] = k + 256 * q < a.n ? __ldg(a.L + k + 256 * q) : INFINITY;
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (finitef(l[q])) lm = fminf(lm, l[q]);
+    }
+    lm = block_min_n(lm, red, 8);
+    if (threadIdx.x == 0 && finitef(lm)) atomicMax(a.counter + 1, lmin_key(lm));
+}
+
+// this thread's group of ROW_NB rows from row k (rows at or past k1 read nothing)
+__device__ __forceinline__ void load_rows(float4 (&ub)[ROW_NB], const float4* u4, int D4, int k, int k1) {
+#pragma unroll
+    for (int q = 0; q < ROW_NB; q++)
+        ub[q] = k + q < k1 ? __ldg(u4 + (size_t)(k + q) * D4) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// CTA (c, y): chunk c of the samples (contiguous, about n / G) against column
+// tile y (W groups of 4 parameters).  Thread t owns group y W + t of every row.
+// Its loads of the first ROW_NB rows go out before anything else; the weights
+// of ROW_SUB samples at a time (exponent and exp in FP64 around L_min, rounded
+// to FP32) sit in shared memory, and their float-float sum is kept.  Rows are
+// added two at a time (one product, one FMA) into float-float sums, in order,
+// ROW_NB rows' loads in flight.  Row c of the scratch (Dp + 1 float pairs) gets
+// the tile's sums and, from tile 0, the chunk's weight sum z_c.
+__global__ void __launch_bounds__(ROW_GROUPS) k_update_rows(UpdateArgs a, int W) {
+    __shared__ float s_w[ROW_SUB];
+    __shared__ float2 s_z[ROW_GROUPS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int c = blockIdx.x, G = gridDim.x, y = blockIdx.y;
+    const int Dp = a.Dp, D4 = Dp >> 2;
+    const int chunk = (a.n + G - 1) / G;
+    const int k0 = min(a.n, c * chunk), k1 = min(a.n, k0 + chunk);
+    const int g = y * W + tid;
+    const bool own = tid < W && g < D4;
+    const float4* u4 = reinterpret_cast<const float4*>(a.U) + g;
+    float4 ub[ROW_NB];
+    if (own) load_rows(ub, u4, D4, k0, k1);
+    grid_dependency_wait();  // L_min is known once k_update_lmin has completed
+    const unsigned key = __ldcg(a.counter + 1);
+    const bool ok = key != 0u;
+    const double m = ok ? (double)lmin_of_key(key) : 0.0;
+    float sv[4] = {0.f, 0.f, 0.f, 0.f}, ev[4] = {0.f, 0.f, 0.f, 0.f};
+    float zs = 0.f, ze = 0.f;
+    for (int kb = k0; kb < k1; kb += ROW_NB) {
+        const int ws = k0 + (kb - k0) / ROW_SUB * ROW_SUB;  // this weight window's first sample
+        if (kb == ws) {
+            __syncthreads();  // the previous window's weights are consumed
+            const int nk = min(ROW_SUB, k1 - ws);
+            for (int i = tid; i < nk; i += blockDim.x) {
+                const float l = __ldg(a.L + ws + i);
+                float wh = 0.f, wl = 0.f;
+                if (ok && finitef(l)) {
+                    const double wd = exp(-((double)l - m) * a.inv_lambda);
+                    wh = (float)wd;
+                    wl = (float)(wd - (double)wh);
+                }
+                s_w[i] = wh;
+                ff_acc(zs, ze, wh, wl);
+            }
+            __syncthreads();
+        }
+        if (own) {
+            if (kb != k0) load_rows(ub, u4, D4, kb, k1);
+            const float* w = s_w + (kb - ws);
+            if (kb + ROW_NB <= k1) {
+#pragma unroll
+                for (int q = 0; q < ROW_NB; q += 2) ff_madd2_4(sv, ev, w[q], ub[q], w[q + 1], ub[q + 1]);
+            } else {
+                const int nq = k1 - kb;  // 1 .. ROW_NB - 1; the rows past it loaded as zeros
+#pragma unroll
+                for (int q = 0; q < ROW_NB; q += 2)
+                    if (q < nq) ff_madd2_4(sv, ev, w[q], ub[q], q + 1 < nq ? w[q + 1] : 0.f, ub[q + 1]);
+            }
         }
     }
+    launch_dependents();  // the combine may be scheduled while the last rows finish
+    float2* row = reinterpret_cast<float2*>(a.part) + (size_t)c * (Dp + 1);
+    if (own) {
+#pragma unroll
+        for (int i = 0; i < 4; i++) row[4 * g + i] = make_float2(sv[i], ev[i]);
+    }
+    if (y != 0) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float v = __shfl_xor_sync(0xffffffffu, zs, o), ve = __shfl_xor_sync(0xffffffffu, ze, o);
+        ff_acc(zs, ze, v, ve);
+    }
+    if (lane == 0) s_z[warp] = make_float2(zs, ze);
+    __syncthreads();
     if (tid == 0) {
-        if (y == 0) {
-            if (ok && a.wsum) *a.wsum = s.Z;
-            if (a.status) *a.status = ok ? 0 : 4;
-        }
-        a.counter[1 + y] = 0u;  // re-arm for the next launch
+        float2 z = s_z[0];
+        for (int w = 1; w < nw; w++) z = ff_sum(z, s_z[w]);
+        row[Dp] = z;
     }
-    if (!count_in(a.counter, (unsigned)T, s)) return;
-    // the last tile: direct targets move ctrl_steps steps earlier, the last one
-    // held (every tile's mu_upd was published before its count)
-    for (int d = tid; d < Dp; d += UPD_THREADS) {
+}
+
+// q = S / Z for float-float S and Z > 0, rounded to FP32: the FP32 quotient of
+// the high parts, then one correction from the exact remainder S - q1 Z
+// (TwoProd by FMA) over Z's high part
+__device__ __forceinline__ float ff_div(float2 S, float2 Z) {
+    const float q1 = __fdiv_rn(S.x, Z.x);
+    const float ph = __fmul_rn(q1, Z.x), pl = __fmaf_rn(q1, Z.x, -ph);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(S.x, ph), pl), __fmaf_rn(-q1, Z.y, S.y));
+    return __fadd_rn(q1, __fdiv_rn(r, Z.x));
+}
+
+// The G chunk rows added per column in float-float: Z = sum_c z_c (chunk c by
+// thread c, then a fixed tree over lanes and warps) and, for the CTA's 32
+// columns, S_j = sum_c S_c[j] with warp w taking chunks c = w mod 16 (a fixed
+// pairwise tree over its chunks, then over the 16 warps); mu' = S / Z, u0 = the
+// first direct target, and the shift written straight from here: column
+// (t, i) of mu' is the shifted nominal's column (t - ctrl_steps, i), and the
+// last step's also fills the held steps past the end.  Pair arithmetic keeps
+// the dependency chains on the FP32 pipe (FP64 runs at 1/64 of its rate here).
+// With no finite cost (Z = 0, the same in every CTA) the previous mean is kept:
+// every CTA copies its columns of it, and the last to count in shifts it.  CTA 0
+// re-arms the L_min key (the rows kernel has read it).
+__global__ void __launch_bounds__(CMB_THREADS) k_update_combine(UpdateArgs a, int G) {
+    __shared__ float2 s_acc[CMB_WARPS][32];
+    __shared__ float2 s_zw[CMB_WARPS];
+    __shared__ int s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int Dp = a.Dp;
+    const size_t RW = (size_t)Dp + 1;
+    const float2* part = reinterpret_cast<const float2*>(a.part);
+    grid_dependency_wait();  // every chunk row is written
+    if (blockIdx.x == 0 && tid == 0) a.counter[1] = 0u;
+    const int j = blockIdx.x * 32 + lane, jj = min(j, Dp - 1);
+    const float2 zero = make_float2(0.f, 0.f);
+    float2 z = tid < G ? __ldcg(part + tid * RW + Dp) : zero;
+    float2 acc = zero;
+    for (int c0 = warp; c0 < G; c0 += CMB_WARPS * CMB_NB) {
+        float2 v[CMB_NB];
+#pragma unroll
+        for (int i = 0; i < CMB_NB; i++) {
+            const int c = c0 + CMB_WARPS * i;
+            v[i] = c < G ? __ldcg(part + c * RW + jj) : zero;
+        }
+#pragma unroll
+        for (int span = 1; span < CMB_NB; span *= 2)
+#pragma unroll
+            for (int i = 0; i + span < CMB_NB; i += 2 * span) v[i] = ff_sum(v[i], v[i + span]);
+        acc = ff_sum(acc, v[0]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        z = ff_sum(z, make_float2(__shfl_xor_sync(0xffffffffu, z.x, o), __shfl_xor_sync(0xffffffffu, z.y, o)));
+    if (lane == 0) s_zw[warp] = z;
+    s_acc[warp][lane] = acc;
+    __syncthreads();
+    // fixed trees over the 16 warps' sums (every warp forms Z; warp 0 the columns)
+    float2 Zv[CMB_WARPS];
+#pragma unroll
+    for (int w = 0; w < CMB_WARPS; w++) Zv[w] = s_zw[w];
+#pragma unroll
+    for (int span = 1; span < CMB_WARPS; span *= 2)
+#pragma unroll
+        for (int i = 0; i + span < CMB_WARPS; i += 2 * span) Zv[i] = ff_sum(Zv[i], Zv[i + span]);
+    const bool ok = Zv[0].x > 0.f;  // weights are >= 0: Z > 0 iff some cost is finite
+    if (ok) {
+        if (warp == 0) {
+            float2 Sv[CMB_WARPS];
+#pragma unroll
+            for (int w = 0; w < CMB_WARPS; w++) Sv[w] = s_acc[w][lane];
+#pragma unroll
+            for (int span = 1; span < CMB_WARPS; span *= 2)
+#pragma unroll
+                for (int i = 0; i + span < CMB_WARPS; i += 2 * span) Sv[i] = ff_sum(Sv[i], Sv[i + span]);
+            if (j < Dp) {
+                const float mu_new = ff_div(Sv[0], Zv[0]);
+                a.mu_upd[j] = mu_new;
+                if (j < NJ) a.u0[j] = mu_new;  // the controls of step 0: the first direct target
+                const int t = j / NJ, i = j % NJ, cs = a.ctrl_steps;
+                if (t - cs >= 0 && t < a.H - 1) a.mu[(t - cs) * NJ + i] = mu_new;
+                if (t == a.H - 1)
+                    for (int td = max(0, t - cs); td < a.H; td++) a.mu[td * NJ + i] = mu_new;
+            }
+            if (blockIdx.x == 0 && lane == 0) {
+                if (a.wsum) *a.wsum = (double)Zv[0].x + (double)Zv[0].y;
+                if (a.status) *a.status = 0;
+            }
+        }
+        return;
+    }
+    // no finite cost: keep the mean, then shift it once every CTA has read its columns
+    if (warp == 0 && j < Dp) {
+        const float mu_old = a.mu[j];
+        a.mu_upd[j] = mu_old;
+        if (j < NJ) a.u0[j] = mu_old;
+    }
+    if (blockIdx.x == 0 && tid == 0 && a.status) *a.status = 4;
+    if (!cta_count_in(a.counter, 1u, gridDim.x, s_last)) return;
+    for (int d = tid; d < Dp; d += CMB_THREADS) {
         const int t = d / NJ, i = d % NJ;
         const int src = min(t + a.ctrl_steps, a.H - 1);
         a.mu[d] = __ldcg(a.mu_upd + src * NJ + i);
     }
-    if (tid == 0) a.counter[0] = 0u;
+    if (tid == 0) a.counter[0] = 0u;  // re-arm for the next launch
 }
 
 int update_grid(int n) {
@@ -413,21 +619,36 @@ int update_grid(int n) {
     return g < 1 ? 1 : (g > UPDATE_MAX_CTAS ? UPDATE_MAX_CTAS : g);
 }
 
-// direct targets: chunks of ~128 samples (x T parameter tiles), as the knots
-static int update_grid_tiled(int n) {
-    int g = (n + 127) / 128;
-    return g < 1 ? 1 : (g > UPDATE_MAX_CTAS ? UPDATE_MAX_CTAS : g);
-}
-
 cudaError_t launch_update(const UpdateArgs& a, cudaStream_t st) {
-    if (a.Dp % 2 != 0 || a.Dp < D || (a.Dp > D && !a.mu_upd)) return cudaErrorInvalidValue;
-    if (a.Dp == D) {
+    const bool direct = a.interp == INTERP_DIRECT;
+    if (direct ? (a.Dp < 2 * NJ || a.Dp % NJ != 0 || !a.mu_upd || (reinterpret_cast<uintptr_t>(a.U) & 15u))
+               : a.Dp != D)
+        return cudaErrorInvalidValue;
+    if (!direct) {
         k_update_knots<<<update_grid(a.n), UPD_THREADS, 0, st>>>(a);
     } else {
-        if (!a.wts || !a.zm) return cudaErrorInvalidValue;
-        k_update_weights<<<update_grid_tiled(a.n), UPD_THREADS, 0, st>>>(a);
-        const dim3 grid(update_grid_tiled(a.n), (a.Dp + UPD_TILE - 1) / UPD_TILE);
-        k_update_tiled<<<grid, UPD_THREADS, 0, st>>>(a);
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return cudaErrorInvalidValue;
+        const int W = row_groups(a.Dp), G = update_direct_chunks(a.n, a.Dp, sms);
+        k_update_lmin<<<max(1, min(2 * sms, (a.n + 1023) / 1024)), 256, 0, st>>>(a);
+        // the rows and combine kernels as programmatic dependents of their predecessors
+        cudaLaunchAttribute pdl[1];
+        pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        pdl[0].val.programmaticStreamSerializationAllowed = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.stream = st;
+        cfg.attrs = pdl;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3(G, row_tiles(a.Dp));
+        cfg.blockDim = dim3((W + 31) / 32 * 32);
+        cudaError_t e = cudaLaunchKernelEx(&cfg, k_update_rows, a, W);
+        if (e != cudaSuccess) return e;
+        cfg.gridDim = dim3((a.Dp + 31) / 32);
+        cfg.blockDim = dim3(CMB_THREADS);
+        e = cudaLaunchKernelEx(&cfg, k_update_combine, a, G);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }

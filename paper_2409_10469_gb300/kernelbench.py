@@ -2,6 +2,9 @@
 and the update (mppi_update) of a controller at K samples, for the knot
 representations (48 parameters per sample) or direct targets (12 H), with the
 L2 flushed between calls (a 256 MB write) and CUDA events on the current stream.
+A spin kernel (about 100 us) runs ahead of the first event of each call, so the
+host's time to enqueue the call's kernels overlaps it and the events bracket
+device time only.
 
     python -m paper_2409_10469_gb300.kernelbench --K 16384 --H 100 --interp direct
 """
@@ -24,14 +27,16 @@ def run(K: int, H: int, interp: str = "direct", calls: int = 12, warmup: int = 3
     rng = np.random.default_rng(0)
     U = torch.tensor(rng.normal(0.5, 0.3, (K, D)).astype(np.float32)).cuda()
     L = torch.tensor((100 + 50 * rng.random(K)).astype(np.float32)).cuda()
-    mu, u0, U2 = torch.empty(D, device="cuda"), torch.empty(12, device="cuda"), torch.empty((K, D), device="cuda")
+    U2 = torch.empty((K, D), device="cuda")
     flush = torch.empty(64 << 20, device="cuda")
     t_upd, t_smp = [], []
     for s in range(warmup + calls):
-        for fn, out in ((lambda: ctl.update(L, U, n=K, mu_out=mu, u0_out=u0), t_upd),
+        # the update's kernels alone: its outputs stay in the handle (no copies)
+        for fn, out in ((lambda: ctl.update(L, U, n=K), t_upd),
                         (lambda: ctl.sample(s, out=U2), t_smp)):
             flush.fill_(float(s))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda._sleep(200000)
             e0.record()
             fn()
             e1.record()

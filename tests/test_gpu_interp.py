@@ -40,7 +40,8 @@ def nominal(m, mu48, rng=None):
     """a nominal of the representation's dimension around the 48 knots"""
     Dm = O.param_dim(m)
     mu = np.tile(mu48[:12], Dm // 12).astype(np.float32)
-    mu[:48] = mu48
+    n = min(48, Dm)
+    mu[:n] = mu48[:n]
     if rng is not None:
         mu += (0.03 * rng.standard_normal(Dm)).astype(np.float32)
     return mu
@@ -172,10 +173,12 @@ def test_batch_runs_knot_representations_and_rejects_direct():
 
 @pytest.mark.parametrize("mode", ["cubic", "direct"])
 def test_update_with_whole_chunks_non_finite(mode):
-    """The update kernel takes each chunk's cost minimum and rescales the chunks
+    """The update kernels take each chunk's cost minimum and rescale the chunks
     by exp(-(m_c - L_min)/lambda): chunks whose costs are all non-finite (m_c
-    infinite) must drop out, the chunk holding L_min must weigh 1.  K = 1000 is 8
-    chunks of 125; chunks 1 and 4 are all inf / NaN, chunk 6 holds the minimum."""
+    infinite) must drop out, the chunk holding L_min must weigh 1.  For the knots
+    K = 1000 is 8 chunks of 125; chunks 1 and 4 are all inf / NaN, chunk 6 holds
+    the minimum.  Direct targets chunk by 16 samples here, so the same ranges
+    cover several whole chunks each."""
     cfg = W.config_trot()
     K, H, lam = 1000, 50, 0.1
     ctl, m = ctl_for(cfg, K=K, H=H, lam=lam, interp=mode)
@@ -194,3 +197,36 @@ def test_update_with_whole_chunks_non_finite(mode):
     e = np.abs(mg - mu_o) / np.maximum(np.abs(mu_o), 1)
     assert e.max() <= 1e-6, (mode, e.max())
     assert np.array_equal(u0_g.cpu().numpy(), mg[:12])
+
+
+@pytest.mark.parametrize("K,H", [(64, 2), (64, 3), (300, 4), (5, 7), (2000, 300), (16384, 100)])
+def test_direct_update_sizes(K, H):
+    """Direct targets at the horizons where 12 H is below, at and far above the
+    48 knot parameters (H = 300: two column tiles of 450 groups of 4), with
+    fewer samples than a chunk's 16 and at the paper-scale K = 16384 (hundreds
+    of chunks): update, u0 and shift against the oracle <= 1e-6"""
+    cfg = W.config_trot()
+    lam = 0.1
+    ctl, m = ctl_for(cfg, K=K, H=H, lam=lam, interp="direct")
+    Dm = ctl.D
+    assert Dm == 12 * H
+    rng = np.random.default_rng(H)
+    mu = nominal(m, W.stand_mu(), rng)
+    ctl.set_nominal(mu)
+    U = (mu[None, :] + rng.normal(0, 0.3, (K, Dm))).astype(np.float32)
+    L = (100 + 8 * rng.random(K)).astype(np.float32)
+    mu_g = torch.empty(Dm, device="cuda")
+    u0_g = torch.empty(12, device="cuda")
+    assert ctl.update(dev(L), dev(U), n=K, mu_out=mu_g, u0_out=u0_g) == 0
+    _, mu_o, _ = O.update(L, U, lam, dim=Dm)
+    mg = mu_g.cpu().numpy()
+    e = np.abs(mg - mu_o) / np.maximum(np.abs(mu_o), 1)
+    assert e.max() <= 1e-6, e.max()
+    assert np.array_equal(u0_g.cpu().numpy(), mg[:12])
+    sh = O.shift(mg, H, m["ctrl_steps"], "direct")
+    assert np.array_equal(ctl.get_nominal(), sh.astype(np.float32))
+    # a second update on the same handle (the combine's counter re-armed)
+    L2 = L[::-1].copy()
+    assert ctl.update(dev(L2), dev(U), n=K, mu_out=mu_g) == 0
+    _, mu_o2, _ = O.update(L2, U, lam, dim=Dm)
+    assert (np.abs(mu_g.cpu().numpy() - mu_o2) / np.maximum(np.abs(mu_o2), 1)).max() <= 1e-6
