@@ -69,8 +69,8 @@ __device__ void block_update(const InstDesc& d, float* u0_row) {
     constexpr int ACTIVE = BLOCK / 12;  // groups processed at once (12 lanes each, four dims per lane)
     constexpr int GPT = (UPD_GROUPS + ACTIVE - 1) / ACTIVE;  // groups per thread
     __shared__ float s_min[W];
-    __shared__ double s_z[UPD_GROUPS];
-    __shared__ double s_part[UPD_GROUPS][D];
+    __shared__ float2 s_z[UPD_GROUPS];
+    __shared__ float2 s_part[UPD_GROUPS][D];
     __shared__ float s_mu[D];
     __shared__ float2 s_w[UPD_SUB];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -152,19 +152,20 @@ __device__ void block_update(const InstDesc& d, float* u0_row) {
         const int g = tid / 12 + gi * ACTIVE;
         if (!grp || g >= UPD_GROUPS) continue;
 #pragma unroll
-        for (int e = 0; e < 4; e++) s_part[g][4 * li + e] = (double)sh[gi][e] + (double)se[gi][e];
-        if (li == 0) s_z[g] = (double)zh[gi] + (double)ze[gi];
+        for (int e = 0; e < 4; e++) s_part[g][4 * li + e] = make_float2(sh[gi][e], se[gi][e]);
+        if (li == 0) s_z[g] = make_float2(zh[gi], ze[gi]);
     }
     __syncthreads();
     if (tid < D) {
         float mu_new;
         if (ok) {
-            double S = 0.0, Z = 0.0;
-            for (int q = 0; q < UPD_GROUPS; q++) {
-                S += s_part[q][tid];
-                Z += s_z[q];
+            // the groups' pairs added in order, float-float (FP32 pipe), then the quotient
+            float sh0 = s_part[0][tid].x, se0 = s_part[0][tid].y, zh0 = s_z[0].x, ze0 = s_z[0].y;
+            for (int q = 1; q < UPD_GROUPS; q++) {
+                bu_ff_add(sh0, se0, s_part[q][tid].x, s_part[q][tid].y);
+                bu_ff_add(zh0, ze0, s_z[q].x, s_z[q].y);
             }
-            mu_new = (float)(S / Z);
+            mu_new = ff_div(make_float2(sh0, se0), make_float2(zh0, ze0));
         } else {
             mu_new = __ldcg(d.mu + tid);
         }

@@ -101,6 +101,16 @@ __device__ __forceinline__ float shifted_knot(const float* mu, int interp, int H
     return (1.f - f) * mu[jj * NJ + i] + f * mu[(jj + 1) * NJ + i];
 }
 
+// q = S / Z for float-float S and Z > 0, rounded to FP32: the FP32 quotient of
+// the high parts, then one correction from the exact remainder S - q1 Z
+// (TwoProd by FMA) over Z's high part
+__device__ __forceinline__ float ff_div(float2 S, float2 Z) {
+    const float q1 = __fdiv_rn(S.x, Z.x);
+    const float ph = __fmul_rn(q1, Z.x), pl = __fmaf_rn(q1, Z.x, -ph);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(S.x, ph), pl), __fmaf_rn(-q1, Z.y, S.y));
+    return __fadd_rn(q1, __fdiv_rn(r, Z.x));
+}
+
 // Count this CTA in on a global counter after its global writes; returns, to
 // every thread, whether this CTA brought the count to `total` (it is the last
 // of the CTAs counted), in which case the counted CTAs' writes are visible to

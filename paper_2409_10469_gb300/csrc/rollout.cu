@@ -31,7 +31,7 @@ __device__ __forceinline__ bool fin_f(float x) { return fabsf(x) <= 3.402823466e
 // f_c = exp(-(m_c - L_min) / lambda), and for each of the 49 sums groups of
 // threads add f_c times the CTA partials over contiguous ranges of c, in four
 // interleaved accumulators each, all combined in a fixed order (32 partials
-// loaded per round trip); mu' = S / Z (FP64 division), u0, the status and the
+// loaded per round trip); mu' = S / Z (a float-float quotient), u0, the status and the
 // shifted nominal follow, and the counter is re-armed.  Every thread of the CTA
 // calls this (it synchronises the block).
 
@@ -171,10 +171,9 @@ __device__ __forceinline__ void fused_update(const RolloutArgs& a, float L, cons
         s_sum[0][d] = make_float2(hi, lo);
     }
     __syncthreads();
-    const double Z = (double)s_sum[0][D].x + (double)s_sum[0][D].y;
     for (int d = tid; d < D; d += B) {
-        // no finite cost: keep the mean
-        const float mu_new = ok ? (float)(((double)s_sum[0][d].x + (double)s_sum[0][d].y) / Z) : a.mu_w[d];
+        // no finite cost: keep the mean; the quotient of the pairs on the FP32 pipe
+        const float mu_new = ok ? ff_div(s_sum[0][d], s_sum[0][D]) : a.mu_w[d];
         s_mu[d] = mu_new;
         if (a.mu_upd) a.mu_upd[d] = mu_new;
         if (a.mu_host) a.mu_host[d] = mu_new;
@@ -184,7 +183,7 @@ __device__ __forceinline__ void fused_update(const RolloutArgs& a, float L, cons
         }
     }
     if (tid == 0) {
-        if (a.wsum && ok) *a.wsum = Z;
+        if (a.wsum && ok) *a.wsum = (double)s_sum[0][D].x + (double)s_sum[0][D].y;
         if (a.status) *a.status = ok ? 0 : 4;
         if (a.status_host) *a.status_host = ok ? 0 : 4;
         *a.counter = 0u;  // re-arm for the next launch (kernels on one stream are ordered)

@@ -95,11 +95,23 @@ struct UpdSmem {
     float2 z[UPD_WARPS];              // per-warp weight sums (hi, lo)
     float2 part[UPD_WARPS][UPD_TILE];  // per-warp parameter sums (hi, lo)
     float2 w[UPD_SUB];                 // a sub-chunk's weights (hi, lo)
-    double f[UPDATE_MAX_CTAS];  // the chunks' factors exp(-(m_c - L_min) / lambda)
-    double Z;
+    float2 f[UPDATE_MAX_CTAS];  // the chunks' factors exp(-(m_c - L_min) / lambda), from FP64, as pairs
+    float2 Z;
     float Lmin;  // the minimum over the chunks' cost minima (combine_setup)
     int last;
 };
+
+// float-float helpers of the combine: a + b, and the product of two pairs (the
+// high parts' rounding error by FMA, the cross terms; the lo * lo term is below
+// the pairs' precision)
+__device__ __forceinline__ float2 ff_sum(float2 a, float2 b) {
+    ff_acc(a.x, a.y, b.x, b.y);
+    return a;
+}
+__device__ __forceinline__ float2 ff_mul(float2 f, float2 v) {
+    const float p = __fmul_rn(f.x, v.x);
+    return make_float2(p, __fmaf_rn(f.x, v.y, __fmaf_rn(f.y, v.x, __fmaf_rn(f.x, v.x, -p))));
+}
 
 // minimum of v over the CTA, returned to every thread
 __device__ __forceinline__ float block_min(float v, float* red) {
@@ -166,19 +178,19 @@ __device__ __forceinline__ void chunk_partials(const UpdateArgs& a, int b, int G
         s.part[warp][2 * lane + 1] = make_float2(s1, e1);
     }
     __syncthreads();
-    // the warps' pairs added in warp order; the row holds hi + lo as a double
-    double* row = rows + (size_t)b * UPD_ROW;
+    // the warps' pairs added in warp order; the row holds (hi, lo) pairs
+    float2* row = reinterpret_cast<float2*>(rows) + (size_t)b * UPD_ROW;
     if (tid < UPD_TILE) {
-        float hi = s.part[0][tid].x, lo = s.part[0][tid].y;
-        for (int w = 1; w < UPD_WARPS; w++) ff_acc(hi, lo, s.part[w][tid].x, s.part[w][tid].y);
-        row[tid] = (double)hi + (double)lo;
+        float2 v = s.part[0][tid];
+        for (int w = 1; w < UPD_WARPS; w++) v = ff_sum(v, s.part[w][tid]);
+        row[tid] = v;
     }
     if (tid == UPD_TILE) {
-        float hi = s.z[0].x, lo = s.z[0].y;
-        for (int w = 1; w < UPD_WARPS; w++) ff_acc(hi, lo, s.z[w].x, s.z[w].y);
-        row[UPD_TILE] = (double)hi + (double)lo;
+        float2 v = s.z[0];
+        for (int w = 1; w < UPD_WARPS; w++) v = ff_sum(v, s.z[w]);
+        row[UPD_TILE] = v;
     }
-    if (tid == UPD_TILE + 1) row[UPD_TILE + 1] = (double)m;
+    if (tid == UPD_TILE + 1) row[UPD_TILE + 1] = make_float2(m, 0.f);
 }
 
 // publish this CTA's writes and count it in: true in the last of `total` CTAs
@@ -186,33 +198,37 @@ __device__ __forceinline__ bool count_in(unsigned* counter, unsigned total, UpdS
     return cta_count_in(counter, 1u, total, s.last);
 }
 
-// the last CTA of a tile: L_min over the G chunk minima of the tile's rows, the
-// factors f_c, and Z = sum_c f_c z_c (warp 0: lane j takes chunks j, j + 32, ...
-// in order, then a fixed xor tree).  Returns whether any cost is finite.
+// the last CTA: L_min over the G chunk minima, the factors f_c (FP64 exponent
+// and exp, kept as pairs), and Z = sum_c f_c z_c in float-float (warp 0: lane j
+// takes chunks j, j + 32, ..., then a fixed xor tree).  Returns whether any cost
+// is finite.  The sums stay on the FP32 pipe: FP64 runs at 1/64 of its rate on
+// this part, and its dependency chains cost more than the pairs' operations.
 __device__ __forceinline__ bool combine_setup(const UpdateArgs& a, int G, const double* rows, UpdSmem& s) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float mc = tid < G ? (float)__ldcg(rows + (size_t)tid * UPD_ROW + UPD_TILE + 1) : INFINITY;
+    const float2* row2 = reinterpret_cast<const float2*>(rows);
+    const float mc = tid < G ? __ldcg(row2 + (size_t)tid * UPD_ROW + UPD_TILE + 1).x : INFINITY;
     const float Lmin = block_min(mc, s.red);
     const bool ok = finitef(Lmin);
     if (tid == 0) s.Lmin = Lmin;
-    if (tid < G) s.f[tid] = (ok && finitef(mc)) ? exp(-((double)mc - (double)Lmin) * a.inv_lambda) : 0.0;
+    if (tid < G) {
+        const double f = (ok && finitef(mc)) ? exp(-((double)mc - (double)Lmin) * a.inv_lambda) : 0.0;
+        const float fh = (float)f;
+        s.f[tid] = make_float2(fh, (float)(f - (double)fh));
+    }
     __syncthreads();
     if (warp == 0) {
         constexpr int NQ = UPDATE_MAX_CTAS / 32;
-        double v[NQ];
+        float2 v[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
             const int c = lane + 32 * q;
-            v[q] = c < G ? __ldcg(rows + (size_t)c * UPD_ROW + UPD_TILE) : 0.0;
+            v[q] = c < G ? ff_mul(s.f[c], __ldcg(row2 + (size_t)c * UPD_ROW + UPD_TILE)) : make_float2(0.f, 0.f);
         }
-        double z = 0.0;
+        float2 z = ff_sum(ff_sum(v[0], v[1]), ff_sum(v[2], v[3]));
+        static_assert(NQ == 4, "the tree above adds four chunks per lane");
 #pragma unroll
-        for (int q = 0; q < NQ; q++) {
-            const int c = lane + 32 * q;
-            if (c < G) z = fma(s.f[c], v[q], z);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+        for (int o = 16; o > 0; o >>= 1)
+            z = ff_sum(z, make_float2(__shfl_xor_sync(0xffffffffu, z.x, o), __shfl_xor_sync(0xffffffffu, z.y, o)));
         if (lane == 0) s.Z = z;
     }
     __syncthreads();
@@ -220,25 +236,33 @@ __device__ __forceinline__ bool combine_setup(const UpdateArgs& a, int G, const 
 }
 
 // S_j = sum_c f_c S_c[j] for tile parameter j by the 4 lanes q of a quad (chunks
-// c = q mod 4 in order, UPD_NB loads per round trip), added over the quad by a
-// fixed xor tree; every lane of the quad returns it.  The whole warp calls it.
-__device__ __forceinline__ double combine_param(int G, const double* rows, int j, int q, const UpdSmem& s) {
-    double acc = 0.0;
+// c = q mod 4, UPD_NB loads per round trip, each round's products added by a
+// fixed pairwise tree, the rounds in order), added over the quad by a fixed xor
+// tree, float-float throughout; every lane of the quad returns it.  The whole
+// warp calls it.
+__device__ __forceinline__ float2 combine_param(int G, const double* rows, int j, int q, const UpdSmem& s) {
+    const float2* row2 = reinterpret_cast<const float2*>(rows);
+    float2 acc = make_float2(0.f, 0.f);
     for (int c0 = q; c0 < G; c0 += 4 * UPD_NB) {
-        double v[UPD_NB];
+        float2 v[UPD_NB];
 #pragma unroll
         for (int i = 0; i < UPD_NB; i++) {
             const int c = c0 + 4 * i;
-            v[i] = c < G ? __ldcg(rows + (size_t)c * UPD_ROW + j) : 0.0;
+            v[i] = c < G ? __ldcg(row2 + (size_t)c * UPD_ROW + j) : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int i = 0; i < UPD_NB; i++) {
             const int c = c0 + 4 * i;
-            if (c < G) acc = fma(s.f[c], v[i], acc);
+            v[i] = c < G ? ff_mul(s.f[c], v[i]) : make_float2(0.f, 0.f);
         }
+#pragma unroll
+        for (int span = 1; span < UPD_NB; span *= 2)
+#pragma unroll
+            for (int i = 0; i + span < UPD_NB; i += 2 * span) v[i] = ff_sum(v[i], v[i + span]);
+        acc = ff_sum(acc, v[0]);
     }
-    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc = ff_sum(acc, make_float2(__shfl_xor_sync(0xffffffffu, acc.x, 1), __shfl_xor_sync(0xffffffffu, acc.y, 1)));
+    acc = ff_sum(acc, make_float2(__shfl_xor_sync(0xffffffffu, acc.x, 2), __shfl_xor_sync(0xffffffffu, acc.y, 2)));
     return acc;
 }
 
@@ -254,17 +278,17 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_knots(UpdateArgs a) {
     const bool ok = combine_setup(a, G, a.part, s);
     {
         const int j = tid >> 2, q = tid & 3;  // 64 quads, 48 parameters
-        const double S = combine_param(G, a.part, min(j, D - 1), q, s);
+        const float2 S = combine_param(G, a.part, min(j, D - 1), q, s);
         if (j < D && q == 0) {
             // every cost non-finite: keep the previous mean
-            const float mu_new = ok ? (float)(S / s.Z) : a.mu[j];
+            const float mu_new = ok ? ff_div(S, s.Z) : a.mu[j];
             s_mu[j] = mu_new;
             if (a.mu_upd) a.mu_upd[j] = mu_new;
             if (j < NJ) a.u0[j] = mu_new;  // the spline at tau = 0 is knot 0
         }
     }
     if (tid == 0) {
-        if (ok && a.wsum) *a.wsum = s.Z;
+        if (ok && a.wsum) *a.wsum = (double)s.Z.x + (double)s.Z.y;
         if (a.status) *a.status = ok ? 0 : 4;
         *a.counter = 0u;  // re-arm for the next launch (kernels on one stream are ordered)
     }
@@ -288,12 +312,12 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_partial(UpdateArgs a) {
     const bool ok = combine_setup(a, G, a.part, s);
     {
         const int j = tid >> 2, q = tid & 3;
-        const double S = combine_param(G, a.part, min(j, D - 1), q, s);
-        if (j < D && q == 0) a.partial_out[2 + j] = ok ? S : 0.0;
+        const float2 S = combine_param(G, a.part, min(j, D - 1), q, s);
+        if (j < D && q == 0) a.partial_out[2 + j] = ok ? (double)S.x + (double)S.y : 0.0;
     }
     if (tid == 0) {
         a.partial_out[0] = (double)s.Lmin;
-        a.partial_out[1] = ok ? s.Z : 0.0;
+        a.partial_out[1] = ok ? (double)s.Z.x + (double)s.Z.y : 0.0;
         *a.counter = 0u;  // re-arm for the next launch
     }
 }
@@ -377,11 +401,6 @@ __device__ __forceinline__ void ff_madd2_4(float (&s)[4], float (&e)[4], float w
     ff_madd2(s[1], e[1], wa, a.y, wb, b.y);
     ff_madd2(s[2], e[2], wa, a.z, wb, b.z);
     ff_madd2(s[3], e[3], wa, a.w, wb, b.w);
-}
-// pair sum a + b (float-float)
-__device__ __forceinline__ float2 ff_sum(float2 a, float2 b) {
-    ff_acc(a.x, a.y, b.x, b.y);
-    return a;
 }
 
 // minimum of v over the CTA's nw warps, returned to every thread
@@ -508,16 +527,6 @@ __global__ void __launch_bounds__(ROW_GROUPS) k_update_rows(UpdateArgs a, int W)
         for (int w = 1; w < nw; w++) z = ff_sum(z, s_z[w]);
         row[Dp] = z;
     }
-}
-
-// q = S / Z for float-float S and Z > 0, rounded to FP32: the FP32 quotient of
-// the high parts, then one correction from the exact remainder S - q1 Z
-// (TwoProd by FMA) over Z's high part
-__device__ __forceinline__ float ff_div(float2 S, float2 Z) {
-    const float q1 = __fdiv_rn(S.x, Z.x);
-    const float ph = __fmul_rn(q1, Z.x), pl = __fmaf_rn(q1, Z.x, -ph);
-    const float r = __fadd_rn(__fsub_rn(__fsub_rn(S.x, ph), pl), __fmaf_rn(-q1, Z.y, S.y));
-    return __fadd_rn(q1, __fdiv_rn(r, Z.x));
 }
 
 // The G chunk rows added per column in float-float: Z = sum_c z_c (chunk c by
