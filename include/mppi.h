@@ -167,7 +167,8 @@ mppi_status mppi_rollouts(mppi_handle h, const float* x0, int x0_per_sample, con
                           int n, double t0, float* L_out, float* traj_out);
 
 /* Eq. 1 + Eq. 2 + apply + shift: weights exp(-(L - L_min)/lambda) over finite
- * costs (normaliser accumulated in FP64), mu' = sum w U / sum w, u0 = mu'[knot 0],
+ * costs (exponent and exp in FP64, the sums in compensated float-float pairs),
+ * mu' = sum w U / sum w, u0 = mu'[knot 0] (the first target for DIRECT),
  * then the nominal becomes shifted(mu').  L (float[n]) and U (float[n][48]) may be
  * NULL for the handle's own buffers.  mu_out (float[48], the updated mean before
  * the shift), u0_out (float[12]) optional.  Returns NONFINITE and keeps mu when
@@ -361,7 +362,7 @@ mppi_status mppi_set_proposal(mppi_handle h, const float* mu_prop);
  * finite), sums them over ranks (an all-reduce(sum) of 49 doubles) and calls
  * mppi_step_finalize with the sums: every rank then holds the same mu', u0 and
  * shifted nominal -- those of mppi_step on all K samples, up to the order of
- * the FP64 sums.  Knot representations only (ARG for DIRECT).
+ * the sums.  Knot representations only (ARG for DIRECT).
  * mppi_step_partial: x0 float[nx] host or device; the step's samples k0 ..
  * k0 + n - 1 (0 <= k0, 1 <= n, k0 + n <= K) are drawn, rolled out and weighted
  * around their own finite-cost minimum m; part_out double[MPPI_SHARD_PARTIAL]

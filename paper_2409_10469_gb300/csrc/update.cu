@@ -8,16 +8,16 @@
 // (0 if L_k is not finite) with the exponent and the exp in FP64, computed once
 // per sample into shared memory as FP32 pairs (about 48 significant bits), their
 // sum z_c and the sums S_c = sum_k w_k U_k (float-float pairs per lane, across
-// lanes and warps: FP64 runs at 1/64 of the FP32 rate on this part, so beyond
-// the exps only the last CTA's combine uses it).  It writes these and m_c to
-// scratch and bumps a counter; the CTA that sees the counter reach the grid
-// size - 1 (no waiting: it is simply the last to finish) takes L_min = min_c m_c
-// and scales chunk c by f_c = exp(-(m_c - L_min)/lambda) (FP64) -- Eq. 1's
-// weights factor as exp(-(L_k - L_min)/lambda) = w_k f_c -- so that
-// mu' = sum_c f_c S_c / sum_c f_c z_c.  The chunks are added in a fixed order and
-// tree, so the result does not depend on scheduling.  It writes mu', u0 = the
-// controls of step 0 (knot 0), the shifted nominal and the status, and re-arms
-// the counter for the next launch.
+// lanes and warps: FP64 runs at 1/64 of the FP32 rate on this part, so only the
+// exps use it).  It writes these pairs and m_c to scratch and bumps a counter;
+// the CTA that sees the counter reach the grid size - 1 (no waiting: it is
+// simply the last to finish) takes L_min = min_c m_c and scales chunk c by
+// f_c = exp(-(m_c - L_min)/lambda) (FP64, kept as a pair) -- Eq. 1's weights
+// factor as exp(-(L_k - L_min)/lambda) = w_k f_c -- so that
+// mu' = sum_c f_c S_c / sum_c f_c z_c, the sums and the quotient in float-float.
+// The chunks are added in a fixed order and tree, so the result does not depend
+// on scheduling.  It writes mu', u0 = the controls of step 0 (knot 0), the
+// shifted nominal and the status, and re-arms the counter for the next launch.
 //
 // Direct targets (12 H parameters per sample, rows of kilobytes) take Eq. 1's
 // weights around the global minimum directly, in three launches: k_update_lmin

@@ -314,7 +314,9 @@ def test_rollout_cost_within_fp64_sensitivity():
 def test_update_parity():
     cfg = W.config_trot()
     rng = np.random.default_rng(3)
-    for K, lam, scale in [(4096, 0.1, 5.0), (1000, 1.0, 50.0), (7, 1e6, 3.0), (513, 0.01, 0.05)]:
+    # 40000 and 65536: chunks of 313 and 512 samples on the 128-CTA grid (two weight windows each)
+    for K, lam, scale in [(4096, 0.1, 5.0), (1000, 1.0, 50.0), (7, 1e6, 3.0), (513, 0.01, 0.05),
+                          (40000, 0.1, 5.0), (65536, 0.05, 20.0)]:
         ctl, m = ctl_for(cfg, K=K, lam=lam)
         U = (np.tile(W.stand_mu(), (K, 1)) + rng.normal(0, 0.3, (K, 48))).astype(np.float32)
         L = (100 + scale * rng.random(K)).astype(np.float32)
