@@ -57,6 +57,7 @@ __device__ __forceinline__ void ff_acc(float& s, float& e, float v, float ve) {
 }
 
 constexpr int UPD_SUB = UPD_THREADS;  // samples whose weights sit in shared memory at a time
+constexpr int UPD_PF = 16;            // a warp's samples whose loads go out before the weights are known
 
 // One warp's share of a sub-chunk: samples k = kb, kb + UPD_WARPS, ... < ke, the
 // lane's parameter pair u2[k * row2] times the weight pair w[k - ks] (the
@@ -134,6 +135,19 @@ __device__ __forceinline__ void chunk_partials(const UpdateArgs& a, int b, int G
     const int Dp = a.Dp;
     const int chunk = (a.n + G - 1) / G;
     const int k0 = b * chunk, k1 = min(a.n, k0 + chunk);
+    // sum_k w_k U_k: warp w takes samples ks + w, ks + w + 8, ... of each
+    // sub-chunk; lane i < 24 owns parameters 2i, 2i + 1.  The loads of the
+    // warp's first UPD_PF samples go out first: they depend on neither the
+    // costs' minimum nor the weights.
+    const bool own = lane < UPD_TILE / 2;
+    const float2* u2 = reinterpret_cast<const float2*>(a.U) + lane;
+    const int ke0 = min(k1, k0 + UPD_SUB);
+    float2 pf[UPD_PF];
+#pragma unroll
+    for (int q = 0; q < UPD_PF; q++) {
+        const int k = k0 + warp + q * UPD_WARPS;
+        pf[q] = own && k < ke0 ? __ldg(u2 + (size_t)k * (Dp / 2)) : make_float2(0.f, 0.f);
+    }
     float lm = INFINITY;
     for (int k = k0 + tid; k < k1; k += UPD_THREADS) {
         const float l = __ldg(a.L + k);
@@ -141,10 +155,6 @@ __device__ __forceinline__ void chunk_partials(const UpdateArgs& a, int b, int G
     }
     const float m = block_min(lm, s.red);
     const bool okc = finitef(m);
-    // sum_k w_k U_k: warp w takes samples ks + w, ks + w + 8, ... of each
-    // sub-chunk; lane i < 24 owns parameters 2i, 2i + 1
-    const bool own = lane < UPD_TILE / 2;
-    const float2* u2 = reinterpret_cast<const float2*>(a.U) + lane;
     float zs = 0.f, ze = 0.f;
     float s0 = 0.f, s1 = 0.f, e0 = 0.f, e1 = 0.f;
     if (okc)
@@ -165,7 +175,22 @@ __device__ __forceinline__ void chunk_partials(const UpdateArgs& a, int b, int G
             __syncthreads();  // the previous sub-chunk's weights are consumed
             s.w[tid] = wk;
             __syncthreads();
-            if (own) sum_chunk(s.w, ks, u2, Dp / 2, ks + warp, min(k1, ks + UPD_SUB), s0, s1, e0, e1);
+            if (own) {
+                int kb = ks + warp;
+                if (ks == k0) {  // the prefetched samples, in the same order as the loop below
+#pragma unroll
+                    for (int q = 0; q < UPD_PF; q++) {
+                        const int k = k0 + warp + q * UPD_WARPS;
+                        if (k >= ke0) break;
+                        const float2 wk = s.w[k - ks];
+                        const float p0 = wk.x * pf[q].x, p1 = wk.x * pf[q].y;
+                        ff_acc(s0, e0, p0, fmaf(wk.y, pf[q].x, fmaf(wk.x, pf[q].x, -p0)));
+                        ff_acc(s1, e1, p1, fmaf(wk.y, pf[q].y, fmaf(wk.x, pf[q].y, -p1)));
+                    }
+                    kb = k0 + warp + UPD_PF * UPD_WARPS;
+                }
+                sum_chunk(s.w, ks, u2, Dp / 2, kb, min(k1, ks + UPD_SUB), s0, s1, e0, e1);
+            }
         }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -206,6 +231,14 @@ __device__ __forceinline__ bool count_in(unsigned* counter, unsigned total, UpdS
 __device__ __forceinline__ bool combine_setup(const UpdateArgs& a, int G, const double* rows, UpdSmem& s) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float2* row2 = reinterpret_cast<const float2*>(rows);
+    constexpr int NQ = UPDATE_MAX_CTAS / 32;
+    float2 zv[NQ];  // warp 0: the weight sums of chunks lane, lane + 32, ..., loaded with the minima
+    if (warp == 0)
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            const int c = lane + 32 * q;
+            zv[q] = c < G ? __ldcg(row2 + (size_t)c * UPD_ROW + UPD_TILE) : make_float2(0.f, 0.f);
+        }
     const float mc = tid < G ? __ldcg(row2 + (size_t)tid * UPD_ROW + UPD_TILE + 1).x : INFINITY;
     const float Lmin = block_min(mc, s.red);
     const bool ok = finitef(Lmin);
@@ -217,12 +250,11 @@ __device__ __forceinline__ bool combine_setup(const UpdateArgs& a, int G, const 
     }
     __syncthreads();
     if (warp == 0) {
-        constexpr int NQ = UPDATE_MAX_CTAS / 32;
         float2 v[NQ];
 #pragma unroll
         for (int q = 0; q < NQ; q++) {
             const int c = lane + 32 * q;
-            v[q] = c < G ? ff_mul(s.f[c], __ldcg(row2 + (size_t)c * UPD_ROW + UPD_TILE)) : make_float2(0.f, 0.f);
+            v[q] = c < G ? ff_mul(s.f[c], zv[q]) : make_float2(0.f, 0.f);
         }
         float2 z = ff_sum(ff_sum(v[0], v[1]), ff_sum(v[2], v[3]));
         static_assert(NQ == 4, "the tree above adds four chunks per lane");
@@ -235,20 +267,33 @@ __device__ __forceinline__ bool combine_setup(const UpdateArgs& a, int G, const 
     return ok;
 }
 
-// S_j = sum_c f_c S_c[j] for tile parameter j by the 4 lanes q of a quad (chunks
-// c = q mod 4, UPD_NB loads per round trip, each round's products added by a
-// fixed pairwise tree, the rounds in order), added over the quad by a fixed xor
-// tree, float-float throughout; every lane of the quad returns it.  The whole
-// warp calls it.
-__device__ __forceinline__ float2 combine_param(int G, const double* rows, int j, int q, const UpdSmem& s) {
+// one round of a quad lane's chunk partials for parameter j: chunks c0, c0 + 4,
+// ..., UPD_NB of them (zero past G)
+__device__ __forceinline__ void load_round(float2 (&v)[UPD_NB], int G, const double* rows, int j, int c0) {
     const float2* row2 = reinterpret_cast<const float2*>(rows);
+#pragma unroll
+    for (int i = 0; i < UPD_NB; i++) {
+        const int c = c0 + 4 * i;
+        v[i] = c < G ? __ldcg(row2 + (size_t)c * UPD_ROW + j) : make_float2(0.f, 0.f);
+    }
+}
+
+// S_j = sum_c f_c S_c[j] for tile parameter j by the 4 lanes q of a quad (chunks
+// c = q mod 4, UPD_NB per round, each round's products added by a fixed pairwise
+// tree, the rounds in order), added over the quad by a fixed xor tree,
+// float-float throughout; every lane of the quad returns it.  v0 holds the first
+// round (load_round(.., q)), loaded before the factors were formed.  The whole
+// warp calls it.
+__device__ __forceinline__ float2 combine_param(int G, const double* rows, int j, int q, const UpdSmem& s,
+                                                const float2 (&v0)[UPD_NB]) {
     float2 acc = make_float2(0.f, 0.f);
     for (int c0 = q; c0 < G; c0 += 4 * UPD_NB) {
         float2 v[UPD_NB];
+        if (c0 == q) {
 #pragma unroll
-        for (int i = 0; i < UPD_NB; i++) {
-            const int c = c0 + 4 * i;
-            v[i] = c < G ? __ldcg(row2 + (size_t)c * UPD_ROW + j) : make_float2(0.f, 0.f);
+            for (int i = 0; i < UPD_NB; i++) v[i] = v0[i];
+        } else {
+            load_round(v, G, rows, j, c0);
         }
 #pragma unroll
         for (int i = 0; i < UPD_NB; i++) {
@@ -274,11 +319,14 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_knots(UpdateArgs a) {
     chunk_partials(a, blockIdx.x, G, a.part, s);
     if (!count_in(a.counter, (unsigned)G, s)) return;
 
-    // last CTA: combine, apply, shift
+    // last CTA: combine, apply, shift (the first round of partials loaded
+    // before the factors are formed)
+    const int j = tid >> 2, q = tid & 3;  // 64 quads, 48 parameters
+    float2 v0[UPD_NB];
+    load_round(v0, G, a.part, min(j, D - 1), q);
     const bool ok = combine_setup(a, G, a.part, s);
     {
-        const int j = tid >> 2, q = tid & 3;  // 64 quads, 48 parameters
-        const float2 S = combine_param(G, a.part, min(j, D - 1), q, s);
+        const float2 S = combine_param(G, a.part, min(j, D - 1), q, s, v0);
         if (j < D && q == 0) {
             // every cost non-finite: keep the previous mean
             const float mu_new = ok ? ff_div(S, s.Z) : a.mu[j];
@@ -309,10 +357,12 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update_partial(UpdateArgs a) {
     const int tid = threadIdx.x, G = gridDim.x;
     chunk_partials(a, blockIdx.x, G, a.part, s);
     if (!count_in(a.counter, (unsigned)G, s)) return;
+    const int j = tid >> 2, q = tid & 3;
+    float2 v0[UPD_NB];
+    load_round(v0, G, a.part, min(j, D - 1), q);
     const bool ok = combine_setup(a, G, a.part, s);
     {
-        const int j = tid >> 2, q = tid & 3;
-        const float2 S = combine_param(G, a.part, min(j, D - 1), q, s);
+        const float2 S = combine_param(G, a.part, min(j, D - 1), q, s, v0);
         if (j < D && q == 0) a.partial_out[2 + j] = ok ? (double)S.x + (double)S.y : 0.0;
     }
     if (tid == 0) {
