@@ -43,13 +43,15 @@ def time_avg_cost(states, controls, cfgs):
     return np.array(out)
 
 
-def point(E, K=256, H=60, lam=None, ctrl_steps=None, seed=5, seconds=SECONDS):
+def point(E, K=256, H=60, lam=None, ctrl_steps=None, dt=None, seed=5, seconds=SECONDS):
     def make(e):
         cfg = W.config_trot(K=K, H=H)
         if lam is not None:
             cfg.mppi["lam"] = lam
         if ctrl_steps is not None:
             cfg.mppi["ctrl_steps"] = ctrl_steps
+        if dt is not None:
+            cfg.mppi["dt"] = dt
         return cfg
     cfg0 = make(0)
     steps = int(round(seconds / (cfg0.mppi["ctrl_steps"] * cfg0.mppi["dt"])))
@@ -77,6 +79,8 @@ def test_hyperparameter_sweeps_full():
 
     for cs in (20, 10, 4, 2, 1):                  # 10, 20, 50, 100, 200 Hz at dt = 0.005
         rec("rate_hz", round(1.0 / (cs * 0.005)), point(E, ctrl_steps=cs))
+    # 250 Hz: one control step per dt step of 4 ms, H = 75 keeping the 0.3 s horizon
+    rec("rate_hz", 250, point(E, ctrl_steps=1, dt=0.004, H=75))
     for lam in (0.005, 0.01, 0.03, 0.1, 0.3, 1.0):
         rec("lambda", lam, point(E, lam=lam))
     for H in (5, 10, 20, 40, 60, 100):
