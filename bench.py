@@ -357,10 +357,11 @@ def proposal_form(flush, steps=200, warmup=10):
 def direct_form(flush, peaks, steps=60, warmup=5):
     """Direct targets (the paper's sampling ablation, Sec. IV-E): the same trot
     workload at K = 4096, H = 100 with 12 H = 1200 sampled parameters per
-    sample instead of 48 knots.  The step is three kernels (sampling, rollouts,
-    update), each timed by the library's CUDA events on the stream
+    sample instead of 48 knots.  The step is three stages (sampling, rollouts,
+    and the update's three launches: L_min, the row-streaming sums, the
+    combine), each timed by the library's CUDA events on the stream
     (mppi_set_timing); L2 flushed between steps.  The sampler writes and the
-    update reads 19.7 MB per step, so these two are HBM kernels."""
+    update reads 19.7 MB per step, so these two are HBM stages."""
     import torch
     from paper_2409_10469_gb300 import _mppi, flops as F, workloads as W
     K, H = K_BENCH, H_BENCH
@@ -537,7 +538,7 @@ def run_ours(args):
         "roofline_full_occupancy": full_occ,
         # the learned-proposal form (K = 2048, half the samples around the network's mean)
         "proposal_form": prop,
-        # direct targets (12 H sampled parameters per sample): three kernels per step
+        # direct targets (12 H sampled parameters per sample): sampler, rollouts, a three-launch update
         "direct_form": direct,
         # many controllers in one persistent launch per step (16 instances, uneven K and H)
         "multi_instance": multi16,

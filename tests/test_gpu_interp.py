@@ -230,3 +230,20 @@ def test_direct_update_sizes(K, H):
     assert ctl.update(dev(L2), dev(U), n=K, mu_out=mu_g) == 0
     _, mu_o2, _ = O.update(L2, U, lam, dim=Dm)
     assert (np.abs(mu_g.cpu().numpy() - mu_o2) / np.maximum(np.abs(mu_o2), 1)).max() <= 1e-6
+
+
+def test_direct_update_more_samples_than_k():
+    """Device costs and targets of more samples than the handle's K: the row kernel's
+    chunk count is capped independently of n, so the update takes any n"""
+    cfg = W.config_trot()
+    ctl, m = ctl_for(cfg, K=64, H=7, lam=0.2, interp="direct")
+    n = 5000
+    rng = np.random.default_rng(77)
+    mu = nominal(m, W.stand_mu(), rng)
+    ctl.set_nominal(mu)
+    U = (mu[None, :] + rng.normal(0, 0.3, (n, ctl.D))).astype(np.float32)
+    L = (50 + 4 * rng.random(n)).astype(np.float32)
+    mu_g = torch.empty(ctl.D, device="cuda")
+    assert ctl.update(dev(L), dev(U), n=n, mu_out=mu_g) == 0
+    _, mu_o, _ = O.update(L, U, 0.2, dim=ctl.D)
+    assert (np.abs(mu_g.cpu().numpy() - mu_o) / np.maximum(np.abs(mu_o), 1)).max() <= 1e-6
