@@ -199,7 +199,7 @@ def test_update_with_whole_chunks_non_finite(mode):
     assert np.array_equal(u0_g.cpu().numpy(), mg[:12])
 
 
-@pytest.mark.parametrize("K,H", [(64, 2), (64, 3), (300, 4), (5, 7), (2000, 300), (16384, 100)])
+@pytest.mark.parametrize("K,H", [(1, 3), (64, 2), (64, 3), (300, 4), (5, 7), (2000, 300), (16384, 100)])
 def test_direct_update_sizes(K, H):
     """Direct targets at the horizons where 12 H is below, at and far above the
     48 knot parameters (H = 300: two column tiles of 450 groups of 4), with

@@ -519,6 +519,45 @@ def test_full_size_sampled_parity():
     assert rel.max() <= 1e-5, rel.max()
 
 
+def test_largest_step_unfused_update():
+    """the control step at K = 65536, H = 100: 2048 CTAs, past the fused update's
+    limit, so the update kernel follows the rollouts.  Every knot of the step is
+    the oracle's Philox sample, mu' is the oracle's Eq. 1 / Eq. 2 on the step's
+    own knots and costs (<= 1e-6), and 6 sampled rollouts' costs equal the oracle's
+    stage costs along their GPU trajectories (<= 1e-5)"""
+    K = 65536
+    cfg = W.config_trot(K=K, H=100)
+    ctl, m = ctl_for(cfg)
+    ctl.set_nominal(cfg.mu0)
+    u0, mu = np.zeros(12, np.float32), np.zeros(48, np.float32)
+    assert ctl.step(cfg.x0.astype(np.float32), 7, u0_out=u0, mu_out=mu) == 0
+    assert ctl.launch_count() == 2
+    Ug, Lg = ctl.last_samples()
+    assert np.array_equal(Ug.view(np.uint32), O.sample(m, cfg.mu0, 7).view(np.uint32))
+    _, mu_o, _ = O.update(Lg, Ug, m["lam"])
+    assert np.abs(mu - mu_o).max() <= 1e-6 * max(1.0, np.abs(mu_o).max())
+    assert np.array_equal(u0, mu[:12])
+    idx = np.r_[0, K - 1, np.random.default_rng(1).choice(np.arange(1, K - 1), 4, replace=False)]
+    x0 = cfg.x0.astype(np.float32)
+    t0 = 7 * m["ctrl_steps"] * m["dt"]
+    ctl2, _ = ctl_for(cfg, K=len(idx))
+    traj = torch.empty((len(idx), 101, 37), device="cuda")
+    L2 = torch.empty(len(idx), device="cuda")
+    ctl2.rollouts(dev(x0), U=dev(Ug[idx]), n=len(idx), t0=t0, L_out=L2, traj_out=traj)
+    assert np.array_equal(L2.cpu().numpy(), Lg[idx])   # the same rollouts as inside the step
+    tg = traj.cpu().numpy().astype(np.float64)
+    world = O.World(cfg.robot)
+    ut = np.array([[O.spline_eval(Ug[k], t / 99) for t in range(100)] for k in idx])
+    tabs = t0 + np.arange(100) * m["dt"]
+    n = len(idx)
+    sc = O.stage_costs(world, cfg.cost, tg[:, :100].reshape(-1, 37), ut.reshape(-1, 12),
+                       np.tile(tabs, n)).reshape(n, 100).sum(1) + O.stage_costs(world, cfg.cost, tg[:, 100])
+    rel = np.abs(L2.cpu().numpy() - sc) / np.maximum(np.abs(sc), 1)
+    assert rel.max() <= 1e-5, rel.max()
+    ctl.close()
+    ctl2.close()
+
+
 def test_step_outputs_same_bits_on_host_and_device():
     """Host-bound outputs of the control step are written by its kernel into the
     handle's pinned, device-mapped mailbox; device-bound ones are copied on the
