@@ -488,6 +488,30 @@ def test_edge_cases():
         _mppi.Controller(cfg.robot, cfg.cost, bad)
 
 
+@pytest.mark.parametrize("mode", ["k1", "sigma0"])
+def test_step_degenerate_cases(mode):
+    """the method's degenerate cases through the whole control step: K = 1 keeps
+    only the nominal sample, and sigma = 0 makes every sample the nominal; either
+    way mu' is the nominal itself (bit for bit: one weight of 1, or equal weights
+    of equal knots) and the new nominal is its shift"""
+    cfg = W.config_trot(K=1 if mode == "k1" else 300, H=40)
+    m = dict(cfg.mppi)
+    if mode == "sigma0":
+        m["sigma"] = [0.0] * 48
+    ctl = _mppi.Controller(cfg.robot, cfg.cost, m)
+    mu0 = cfg.mu0.astype(np.float32)
+    ctl.set_nominal(mu0)
+    u0, mu = np.zeros(12, np.float32), np.zeros(48, np.float32)
+    assert ctl.step(cfg.x0.astype(np.float32), 2, u0_out=u0, mu_out=mu) == 0
+    assert np.abs(mu - mu0).max() <= 1e-6 * max(1.0, np.abs(mu0).max())
+    if mode == "k1":
+        assert np.array_equal(mu, mu0)
+    assert np.array_equal(u0, mu[:12])
+    sh = O.shift(mu, m["H"], m["ctrl_steps"])
+    assert np.abs(ctl.get_nominal() - sh).max() <= 1e-6 * max(1.0, np.abs(sh).max())
+    ctl.close()
+
+
 def test_full_size_sampled_parity():
     """trot K=4096 H=100 (the bench's step): every knot bit-exact; the costs of
     24 sampled rollouts checked teacher-forced along their GPU trajectories"""
