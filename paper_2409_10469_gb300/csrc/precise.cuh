@@ -93,8 +93,12 @@ constexpr float TRIG_INV_STEP = 81.4873275756836f;
 // with |d| <= pi / TRIG_N (the dropped d^4/24, d^5/120 terms are below 1e-10).
 // Returned as pairs (table value, its low part plus the Taylor term).
 __device__ __forceinline__ void sincos_pair(float xh, float xl, F2& s, F2& c) {
-    const float jf = rintf(xh * TRIG_INV_STEP);
-    const int j = (int)jf & (TRIG_N - 1);
+    // the nearest table point j = rint(xh / step) by the 1.5 * 2^23 shift (|xh / step| < 2^22):
+    // one FMA and one subtraction, no conversion instructions; the low bits of the
+    // shifted value are j modulo the table size
+    const float y = __fmaf_rn(xh, TRIG_INV_STEP, 12582912.0f);
+    const float jf = __fsub_rn(y, 12582912.0f);
+    const int j = __float_as_int(y) & (TRIG_N - 1);
     const float t = __fmaf_rn(-jf, TRIG_STEP_HI, xh);
     const float d = __fadd_rn(t, __fmaf_rn(-jf, TRIG_STEP_LO, xl));
     const float4 T = __ldg(g_trig + j);  // cos hi, cos lo, sin hi, sin lo
