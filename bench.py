@@ -37,7 +37,7 @@ METRIC = "rollout-steps/s (MPPI step, K=4096, H=100)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture) of
 # one k_rollout launch on this workload, valid only for the kernel sources whose
 # SHA-256 prefix is given; reported as null once those sources change.
-ROLLOUT_TRAFFIC = {"bytes": 105984, "sources_sha256": "6ef049d021c2ff59"}
+ROLLOUT_TRAFFIC = {"bytes": 110336, "sources_sha256": "156984b6b80e5838"}
 ROLLOUT_SOURCES = ("rollout.cu", "rollout.cuh", "common.cuh", "noise.cuh", "kernels.h", "precise.cuh")
 
 

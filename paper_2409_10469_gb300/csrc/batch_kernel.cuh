@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 1 : (BLOCK == 128 ? BATC
     k_batch(const __grid_constant__ BatchArgs a) {
     __shared__ InstDesc sd;
     __shared__ int s_item, s_last;
+    trig_to_shared();
     const int tid = threadIdx.x, leg = tid & 3, r = tid >> 2;
     const int n_items = *a.n_items;
     for (;;) {

@@ -92,6 +92,16 @@ constexpr float TRIG_INV_STEP = 81.4873275756836f;
 //   cos(a_j + d) = C - (S d + C d^2/2 - S d^3/6),
 // with |d| <= pi / TRIG_N (the dropped d^4/24, d^5/120 terms are below 1e-10).
 // Returned as pairs (table value, its low part plus the Taylor term).
+// The table in shared memory: every kernel that runs sub-steps copies it there
+// once at its start (trig_to_shared, which synchronises the block), so each
+// table read on the sub-step's dependency chain is a shared load rather than
+// an L1 hit.
+__shared__ float4 s_trig[TRIG_N];
+__device__ __forceinline__ void trig_to_shared() {
+    for (int i = threadIdx.x; i < TRIG_N; i += blockDim.x) s_trig[i] = g_trig[i];
+    __syncthreads();
+}
+
 __device__ __forceinline__ void sincos_pair(float xh, float xl, F2& s, F2& c) {
     // the nearest table point j = rint(xh / step) by the 1.5 * 2^23 shift (|xh / step| < 2^22):
     // one FMA and one subtraction, no conversion instructions; the low bits of the
@@ -101,7 +111,7 @@ __device__ __forceinline__ void sincos_pair(float xh, float xl, F2& s, F2& c) {
     const int j = __float_as_int(y) & (TRIG_N - 1);
     const float t = __fmaf_rn(-jf, TRIG_STEP_HI, xh);
     const float d = __fadd_rn(t, __fmaf_rn(-jf, TRIG_STEP_LO, xl));
-    const float4 T = __ldg(g_trig + j);  // cos hi, cos lo, sin hi, sin lo
+    const float4 T = s_trig[j];  // cos hi, cos lo, sin hi, sin lo
     const float hd2 = __fmul_rn(0.5f, __fmul_rn(d, d));
     const float d3 = __fmul_rn(__fmul_rn(hd2, d), 1.f / 3.f);
     s.h = T.z;

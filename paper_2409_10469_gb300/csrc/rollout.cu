@@ -195,6 +195,7 @@ __device__ __forceinline__ void fused_update(const RolloutArgs& a, float L, cons
 
 template <int TERR, bool BOX, bool DIRECT>
 __global__ void __launch_bounds__(256, 1) k_rollout(RolloutArgs a) {
+    trig_to_shared();
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int k = gt >> 2, leg = gt & 3;
     const bool valid = k < a.n;
