@@ -126,7 +126,7 @@ static void derive_model(const mppi_model_t& p, double h, DevModel& d) {
     d.hf_cell = (float)p.hf_cell;
     d.hf_inv_cell = p.hf_cell > 0 ? (float)(1.0 / p.hf_cell) : 0.f;
     d.hf_x0 = (float)p.hf_x0; d.hf_y0 = (float)p.hf_y0;
-    d.n_sbox = p.n_static_boxes;  // boxes themselves go to a device buffer (mppi_create)
+    d.n_sbox = p.n_static_boxes;  // the boxes themselves are filled in by mppi_create
     d.has_box = p.has_box;
     if (p.has_box) {
         d.box_m = (float)p.box_mass;
@@ -320,9 +320,7 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
                 boxes[6 * i + k] = (float)model->sbox_lo[i][k];
                 boxes[6 * i + 3 + k] = (float)model->sbox_hi[i][k];
             }
-        ok = al((void**)&h->d_sbox, sizeof(boxes)) &&
-             cudaMemcpy(h->d_sbox, boxes, sizeof(boxes), cudaMemcpyHostToDevice) == cudaSuccess;
-        h->dm.sbox = h->d_sbox;
+        memcpy(h->dm.sbox, boxes, sizeof(boxes));
         std::vector<float> heights;
         if (ok && model->terrain == 1) {
             heights.resize((size_t)model->hf_nx * model->hf_ny);
@@ -363,7 +361,7 @@ extern "C" mppi_status mppi_destroy(mppi_handle h) {
     else cudaDeviceSynchronize();
     void* bufs[] = {h->d_mu,  h->d_mu_prop, h->d_mu_upd, h->d_U,    h->d_L,    h->d_x0,
                     h->d_u0,  h->d_hf,      h->d_status, h->d_wsum, h->d_part, h->d_counter,
-                    h->d_sbox, h->d_B,      h->d_shard};
+                    h->d_B,      h->d_shard};
     for (void* p : bufs)
         if (p) cudaFree(p);
     if (h->h_box) cudaFreeHost(h->h_box);

@@ -60,7 +60,7 @@ struct DevModel {
     float hf_cell, hf_inv_cell, hf_x0, hf_y0;
     const float* hf;                  // device heights [ny][nx]
     int n_sbox;
-    const float* sbox;                // device [n_sbox][6]: lo xyz, hi xyz
+    float sbox[MAX_SBOX * 6];         // [n_sbox][6]: lo xyz, hi xyz, by value (kernel parameters)
     int has_box;
     float box_m, box_inv_m, box_half[3], box_Ic[3], box_inv_Ic[3], box_cr;
     int nx;

@@ -25,7 +25,7 @@ struct mppi_handle_s {
     int nx = mppi::NX_ROBOT;
     int D = mppi::D;  // parameters per sample: 48, or 12 H for direct targets
     float *d_mu = nullptr, *d_mu_prop = nullptr, *d_mu_upd = nullptr, *d_U = nullptr, *d_L = nullptr;
-    float *d_x0 = nullptr, *d_u0 = nullptr, *d_hf = nullptr, *d_sbox = nullptr;
+    float *d_x0 = nullptr, *d_u0 = nullptr, *d_hf = nullptr;
     float* d_B = nullptr;  // [H][4] knot weights of each dt step (16-B aligned rows)
     int* d_status = nullptr;
     // pinned, device-mapped mailbox: u0 [12], mu' [48], status; the control

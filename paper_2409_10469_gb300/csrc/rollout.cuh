@@ -252,8 +252,8 @@ __device__ __forceinline__ void sphere_env(const DevModel& m, float3 xw, F2 xp, 
     for (int b = 0; b < m.n_sbox; b++) {
         float3 nn; float pb;
         const float* bx = m.sbox + 6 * b;
-        const float3 lo = f3(__ldg(bx), __ldg(bx + 1), __ldg(bx + 2));
-        const float3 hi = f3(__ldg(bx + 3), __ldg(bx + 4), __ldg(bx + 5));
+        const float3 lo = f3(bx[0], bx[1], bx[2]);
+        const float3 hi = f3(bx[3], bx[4], bx[5]);
         if (on && sphere_aabb(xw, r, lo, hi, nn, pb, f3(xn.l, yn.l, zn.l)))
             contact_wrench<SG>(m, pb, toBody(nn), cb, r, w, v, torque, force);
     }
@@ -268,8 +268,7 @@ __device__ __forceinline__ float ground_under(const DevModel& m, float x, float 
     ground(m, x, y, h, hx, hy);
     for (int b = 0; b < m.n_sbox; b++) {
         const float* bx = m.sbox + 6 * b;
-        if (x >= __ldg(bx) && x <= __ldg(bx + 3) && y >= __ldg(bx + 1) && y <= __ldg(bx + 4))
-            h = fmaxf(h, __ldg(bx + 5));
+        if (x >= bx[0] && x <= bx[3] && y >= bx[1] && y <= bx[4]) h = fmaxf(h, bx[5]);
     }
     return h;
 }
