@@ -37,7 +37,7 @@ METRIC = "rollout-steps/s (MPPI step, K=4096, H=100)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture) of
 # one k_rollout launch on this workload, valid only for the kernel sources whose
 # SHA-256 prefix is given; reported as null once those sources change.
-ROLLOUT_TRAFFIC = {"bytes": 110336, "sources_sha256": "156984b6b80e5838"}
+ROLLOUT_TRAFFIC = {"bytes": 107520, "sources_sha256": "794fd5c460e574f9"}
 ROLLOUT_SOURCES = ("rollout.cu", "rollout.cuh", "common.cuh", "noise.cuh", "kernels.h", "precise.cuh")
 
 
@@ -491,13 +491,15 @@ def run_ours(args):
     x0_h = torch.tensor(cfg.x0, dtype=torch.float32).pin_memory()
     u0_h = torch.empty(12, dtype=torch.float32).pin_memory()
     e2e = []
-    for s in range(max(8, min(args.steps, 64))):
+    n_e2e = max(8, min(args.steps, 64))
+    for s in range(3 + n_e2e):  # the first 3 calls warm the host buffers' path up, untimed
         with torch.cuda.stream(stream):
             flush.fill_(float(s))
         stream.synchronize()
         t = time.perf_counter()
         ctl.step(x0_h, 10000 + s, u0_out=u0_h)
-        e2e.append(time.perf_counter() - t)
+        if s >= 3:
+            e2e.append(time.perf_counter() - t)
     e2e_ms = float(np.mean(e2e)) * 1e3
     sampler.stop()
     clocks = sampler.summary()
