@@ -16,7 +16,11 @@
  *   - Pointers may be host or device memory: the library asks
  *     cudaPointerGetAttributes and copies host buffers through its own pinned
  *     staging.  The caller owns every pointer it passes; the handle owns its
- *     device workspace.  Device buffers must be on the handle's device.
+ *     device workspace.  Calls run on the current device, which must be the
+ *     one the handle (batch, network, server) was created on, and device
+ *     buffers must be memory of that device or managed memory: another GPU's
+ *     memory, or a call made while another device is current, returns
+ *     MPPI_ERR_ARG before anything is copied or launched.
  *   - Work is enqueued on the handle's stream (given at creation; NULL = the
  *     legacy default stream).  A call returns once its work is enqueued, except
  *     that results written to HOST memory are complete on return (the call
@@ -279,16 +283,17 @@ mppi_status mppi_server_create(size_t budget_bytes, int max_robots, int max_samp
 mppi_status mppi_server_destroy(mppi_server s);
 const char* mppi_server_last_error(mppi_server s);
 /* Register a robot (its handle must outlive the server).  ARG if one of its
- * solves alone exceeds the budget. */
+ * solves alone exceeds the budget, or if the handle was created on another
+ * device than the server. */
 mppi_status mppi_server_add_robot(mppi_server s, mppi_handle h, int* robot_id);
 /* Queue one control step of `robot` from host state x0 (float[nx]) at control
  * index `step`.  BUSY if the robot already has a request queued or in flight;
- * NONFINITE if x0 is not finite. */
+ * NONFINITE if x0 is not finite; ARG if x0 is device memory. */
 mppi_status mppi_server_submit(mppi_server s, int robot, const float* x0, uint32_t step);
 /* Retire finished launches, admit and launch queued requests. */
 mppi_status mppi_server_tick(mppi_server s, int* completed);
-/* ready = 1 and the control (float[12]) and submit-to-completion latency when a
- * new result is waiting; ready = 0 otherwise. */
+/* ready = 1 and the control (float[12], host memory) and submit-to-completion
+ * latency when a new result is waiting; ready = 0 otherwise. */
 mppi_status mppi_server_poll(mppi_server s, int robot, float* u0_out, double* latency_s, int* ready);
 mppi_status mppi_server_stats(mppi_server s, mppi_server_stats_t* out);
 mppi_status mppi_server_reset_stats(mppi_server s);

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "handle.h"
+#include "memkind.h"
 
 using namespace mppi;
 
@@ -35,17 +36,26 @@ static mppi_status cuda_fail(mppi_handle h, cudaError_t e, const char* where) {
         if (e_ != cudaSuccess) return cuda_fail(h, e_, #call);    \
     } while (0)
 
-// true when p is device (or managed) memory; host (pageable or pinned) -> false
-static bool is_device(const void* p) {
-    if (!p) return false;
-    cudaPointerAttributes at;
-    cudaError_t e = cudaPointerGetAttributes(&at, p);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+// true when p is memory of the current device (or managed memory); host memory
+// (pageable or pinned) -> false.  Another GPU's memory never reaches here: every
+// entry point rejects it first (local_call).
+static bool is_device(const void* p) { return is_local(p); }
+
+// The checks every call taking buffers makes before its first copy or launch:
+// the handle's device is the current one (its workspace lives there), and no
+// buffer is device memory of another GPU.
+static mppi_status local_call(mppi_handle h, std::initializer_list<const void*> bufs) {
+    const int dev = current_device();
+    if (dev < 0) return fail(h, MPPI_ERR_CUDA, "cudaGetDevice failed");
+    if (dev != h->device) return fail(h, MPPI_ERR_ARG, "the handle's device is not the current device");
+    if (any_foreign(dev, bufs)) return fail(h, MPPI_ERR_ARG, "a buffer is memory of another GPU");
+    return MPPI_OK;
 }
+#define LOCAL_CALL(...)                                              \
+    do {                                                             \
+        const mppi_status s_ = local_call(h, {__VA_ARGS__});         \
+        if (s_ != MPPI_OK) return s_;                                \
+    } while (0)
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -273,6 +283,7 @@ extern "C" mppi_status mppi_create(const mppi_model_t* model, const mppi_cost_t*
     if (model->n_static_boxes < 0 || model->n_static_boxes > MAX_SBOX) return MPPI_ERR_ARG;
     if (model->n_trunk_spheres < 0 || model->n_trunk_spheres > 4) return MPPI_ERR_ARG;
     if (cost->gait < 0 || cost->gait > 2 || (cost->gait == 2 && !(cost->raibert_len > 0))) return MPPI_ERR_ARG;
+    if (model->terrain == 1 && mem_kind(model->hf, current_device()) == Mem::FOREIGN) return MPPI_ERR_ARG;
 
     mppi_handle h = new mppi_handle_s();
     h->model_in = *model;
@@ -379,6 +390,7 @@ extern "C" int mppi_param_dim(mppi_handle h) { return h ? h->D : 0; }
 
 extern "C" mppi_status mppi_set_nominal(mppi_handle h, const float* mu) {
     if (!h || !mu) return fail(h, MPPI_ERR_ARG, "null argument");
+    LOCAL_CALL(mu);
     cudaMemcpyKind kind = is_device(mu) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     CK(cudaMemcpyAsync(h->d_mu, mu, (size_t)h->D * sizeof(float), kind, h->stream));
     if (kind == cudaMemcpyHostToDevice) CK(cudaStreamSynchronize(h->stream));
@@ -387,6 +399,7 @@ extern "C" mppi_status mppi_set_nominal(mppi_handle h, const float* mu) {
 
 extern "C" mppi_status mppi_get_nominal(mppi_handle h, float* mu_out) {
     if (!h || !mu_out) return fail(h, MPPI_ERR_ARG, "null argument");
+    LOCAL_CALL(mu_out);
     bool dev = is_device(mu_out);
     CK(cudaMemcpyAsync(mu_out, h->d_mu, (size_t)h->D * sizeof(float),
                        dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
@@ -396,6 +409,7 @@ extern "C" mppi_status mppi_get_nominal(mppi_handle h, float* mu_out) {
 
 extern "C" mppi_status mppi_get_samples(mppi_handle h, float* U_out, float* L_out) {
     if (!h) return fail(h, MPPI_ERR_ARG, "null argument");
+    LOCAL_CALL(U_out, L_out);
     const size_t K = (size_t)h->cfg.K;
     bool host = false;
     if (U_out) {
@@ -447,6 +461,7 @@ static mppi_status do_sample(mppi_handle h, uint32_t step, const float* mu_prop,
 
 extern "C" mppi_status mppi_sample(mppi_handle h, uint32_t step, const float* mu_prop, float* U_out) {
     if (!h) return MPPI_ERR_ARG;
+    LOCAL_CALL(mu_prop, U_out);
     bool host_out = U_out && !is_device(U_out);
     if (U_out && !host_out && !aligned16(U_out)) return fail(h, MPPI_ERR_ARG, "U_out must be 16-byte aligned");
     float* dst = (U_out && !host_out) ? U_out : h->d_U;
@@ -514,6 +529,7 @@ static int rollout_block(mppi_handle h) { return rollout_block_cfg(h->cfg); }
 extern "C" mppi_status mppi_rollouts(mppi_handle h, const float* x0, int x0_per_sample, const float* U, int n,
                                      double t0, float* L_out, float* traj_out) {
     if (!h || !x0 || n < 0) return fail(h, MPPI_ERR_ARG, "bad argument");
+    LOCAL_CALL(x0, U, L_out, traj_out);
     const int nx = h->nx;
     const bool per = x0_per_sample != 0;
     if (!U && n > h->cfg.K) return fail(h, MPPI_ERR_ARG, "n exceeds K for the handle's own samples");
@@ -641,6 +657,7 @@ static mppi_status finish_outputs(mppi_handle h, float* u0_out, float* mu_out) {
 extern "C" mppi_status mppi_update(mppi_handle h, const float* L, const float* U, int n, float* mu_out,
                                    float* u0_out) {
     if (!h || n < 0) return fail(h, MPPI_ERR_ARG, "bad argument");
+    LOCAL_CALL(L, U, mu_out, u0_out);
     const float* dL = h->d_L;
     const float* dU = h->d_U;
     if ((!L || !U) && n > h->cfg.K) return fail(h, MPPI_ERR_ARG, "n exceeds K");
@@ -665,6 +682,7 @@ extern "C" mppi_status mppi_update(mppi_handle h, const float* L, const float* U
 
 extern "C" mppi_status mppi_step(mppi_handle h, const float* x0, uint32_t step, float* u0_out, float* mu_out) {
     if (!h || !x0) return fail(h, MPPI_ERR_ARG, "null argument");
+    LOCAL_CALL(x0, u0_out, mu_out);
     const int nx = h->nx;
     const float* dx0;
     if (is_device(x0)) {
@@ -729,6 +747,7 @@ extern "C" mppi_status mppi_step(mppi_handle h, const float* x0, uint32_t step, 
 extern "C" mppi_status mppi_step_partial(mppi_handle h, const float* x0, uint32_t step, int k0, int n,
                                          double* part_out) {
     if (!h || !x0 || !part_out) return fail(h, MPPI_ERR_ARG, "null argument");
+    LOCAL_CALL(x0, part_out);
     if (h->cfg.interp == MPPI_INTERP_DIRECT) return fail(h, MPPI_ERR_ARG, "sharded steps take the knot forms");
     if (k0 < 0 || n < 1 || (long)k0 + n > h->cfg.K) return fail(h, MPPI_ERR_ARG, "sample range outside 0..K");
     const float* dx0;
@@ -779,6 +798,7 @@ extern "C" mppi_status mppi_step_partial(mppi_handle h, const float* x0, uint32_
 
 extern "C" mppi_status mppi_step_finalize(mppi_handle h, const double* sums, float* u0_out, float* mu_out) {
     if (!h || !sums) return fail(h, MPPI_ERR_ARG, "null argument");
+    LOCAL_CALL(sums, u0_out, mu_out);
     if (h->cfg.interp == MPPI_INTERP_DIRECT) return fail(h, MPPI_ERR_ARG, "sharded steps take the knot forms");
     const double* ds = h->d_shard + 64;
     if (is_device(sums)) {
@@ -804,6 +824,8 @@ extern "C" mppi_status mppi_step_finalize(mppi_handle h, const double* sums, flo
 extern "C" mppi_status mppi_step_proposal(mppi_handle h, mppi_mlp net, const float* x0, uint32_t step, float* u0_out,
                                           float* mu_out) {
     if (!h || !net || !x0) return fail(h, MPPI_ERR_ARG, "null argument");
+    LOCAL_CALL(x0, u0_out, mu_out);
+    if (mppi_mlp_device(net) != h->device) return fail(h, MPPI_ERR_ARG, "the network lives on another device");
     if (h->cfg.n_prop < 1) return fail(h, MPPI_ERR_ARG, "the handle was created with n_prop = 0");
     if (h->cfg.interp == MPPI_INTERP_DIRECT) return fail(h, MPPI_ERR_ARG, "the proposal is a knot mean");
     const int nx = h->nx;

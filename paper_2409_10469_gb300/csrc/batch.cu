@@ -35,6 +35,7 @@
 #include "batch.cuh"
 #include "batch_kernel.cuh"
 #include "handle.h"
+#include "memkind.h"
 
 using namespace mppi;
 
@@ -110,6 +111,7 @@ struct mppi_batch_s {
     float *h_x0s = nullptr, *h_u0s = nullptr;  // pinned
     cudaGraphExec_t exec = nullptr;
     int graph_block = 0, graph_bpsm = 0;
+    int device = 0;  // every handle's and the batch's buffers live here
     uint64_t launches = 0;
     std::string err;
 };
@@ -124,13 +126,16 @@ static mppi_status bfail(mppi_batch b, mppi_status s, const std::string& m) {
         if (e_ != cudaSuccess) return bfail(b, MPPI_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
     } while (0)
 
-static bool dev_ptr(const void* p) {
-    cudaPointerAttributes at;
-    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+// memory of the current device (or managed memory)
+static bool dev_ptr(const void* p) { return is_local(p); }
+
+// the batch's device is the current one and no buffer is another GPU's memory
+static mppi_status local_call(mppi_batch b, std::initializer_list<const void*> bufs) {
+    const int dev = current_device();
+    if (dev < 0) return bfail(b, MPPI_ERR_CUDA, "cudaGetDevice failed");
+    if (dev != b->device) return bfail(b, MPPI_ERR_ARG, "the batch's device is not the current device");
+    if (any_foreign(dev, bufs)) return bfail(b, MPPI_ERR_ARG, "a buffer is memory of another GPU");
+    return MPPI_OK;
 }
 
 InstDesc mppi::make_desc(const mppi_handle_s* h) {
@@ -255,13 +260,14 @@ extern "C" mppi_status mppi_batch_create(const mppi_handle* hs, int n, void* str
     mppi_batch b = new mppi_batch_s();
     b->n = n;
     b->stream = (cudaStream_t)stream;
-    int dev = 0;
-    cudaGetDevice(&dev);
+    const int dev = current_device();
+    b->device = dev;
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
     std::vector<InstDesc> descs;
     int max_items = 0;
     for (int i = 0; i < n; i++) {
-        if (!hs[i] || hs[i]->cfg.interp == MPPI_INTERP_DIRECT) {  // batches run the knot representations
+        // batches run the knot representations of handles on the current device
+        if (!hs[i] || hs[i]->cfg.interp == MPPI_INTERP_DIRECT || hs[i]->device != dev) {
             delete b;
             return MPPI_ERR_ARG;
         }
@@ -356,7 +362,9 @@ static mppi_status stage_inputs(mppi_batch b, const float* x0s, const uint32_t* 
 extern "C" mppi_status mppi_batch_step(mppi_batch b, const int* active, const float* x0s, const uint32_t* steps,
                                        float* u0s) {
     if (!b) return MPPI_ERR_ARG;
-    mppi_status s = stage_inputs(b, x0s, steps);
+    mppi_status s = local_call(b, {x0s, u0s});
+    if (s != MPPI_OK) return s;
+    s = stage_inputs(b, x0s, steps);
     if (s != MPPI_OK) return s;
     // the previous graph launch may still read the pinned work list: order the rewrite after it
     BCK(cudaStreamSynchronize(b->stream));
@@ -384,7 +392,9 @@ extern "C" mppi_status mppi_batch_step(mppi_batch b, const int* active, const fl
 extern "C" mppi_status mppi_batch_autotune(mppi_batch b, const float* x0s, int trials, int* block_out,
                                            int* bpsm_out, float* best_ms_out) {
     if (!b || trials < 1) return MPPI_ERR_ARG;
-    mppi_status s = stage_inputs(b, x0s, nullptr);
+    mppi_status s = local_call(b, {x0s});
+    if (s != MPPI_OK) return s;
+    s = stage_inputs(b, x0s, nullptr);
     if (s != MPPI_OK) return s;
     // every candidate starts from the same nominals: save them, restore after each trial
     std::vector<float*> saved(b->n, nullptr);
@@ -458,6 +468,8 @@ extern "C" mppi_status mppi_batch_shared_model(mppi_batch b, int* shared) {
 
 extern "C" mppi_status mppi_batch_get_means(mppi_batch b, float* mu_upds, float* nominals) {
     if (!b) return MPPI_ERR_ARG;
+    const mppi_status s = local_call(b, {mu_upds, nominals});
+    if (s != MPPI_OK) return s;
     const bool hu = mu_upds && !dev_ptr(mu_upds), hn = nominals && !dev_ptr(nominals);
     for (int i = 0; i < b->n; i++) {
         if (mu_upds)

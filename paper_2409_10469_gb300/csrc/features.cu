@@ -4,6 +4,7 @@
 
 #include "features.cuh"
 #include "handle.h"
+#include "memkind.h"
 
 namespace mppi {
 
@@ -24,13 +25,21 @@ __global__ void k_features(FeatArgs a) {
 
 using namespace mppi;
 
-static bool fdev(const void* p) {
-    cudaPointerAttributes at;
-    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
+// memory of the current device (or managed memory)
+static bool fdev(const void* p) { return is_local(p); }
+
+// the handle's device is the current one and no buffer is another GPU's memory
+static bool local_call(mppi_handle h, std::initializer_list<const void*> bufs) {
+    const int dev = current_device();
+    if (dev != h->device) {
+        h->err = "the handle's device is not the current device";
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (any_foreign(dev, bufs)) {
+        h->err = "a buffer is memory of another GPU";
+        return false;
+    }
+    return true;
 }
 
 // what the features take besides the state, for this handle at control index `step`
@@ -63,6 +72,7 @@ static cudaError_t launch_features(mppi_handle h, const float* dX, int n, uint32
 
 extern "C" mppi_status mppi_features(mppi_handle h, const float* X, int n, uint32_t step, float* F) {
     if (!h || !X || !F || n < 1) return MPPI_ERR_ARG;
+    if (!local_call(h, {X, F})) return MPPI_ERR_ARG;
     const int nx = h->nx;
     cudaStream_t st = h->stream;
     float *dX = nullptr, *dF = nullptr;
@@ -92,6 +102,7 @@ extern "C" mppi_status mppi_set_proposal(mppi_handle h, const float* mu_prop) {
         h->err = "the handle was created with n_prop = 0";
         return MPPI_ERR_ARG;
     }
+    if (!local_call(h, {mu_prop})) return MPPI_ERR_ARG;
     const cudaMemcpyKind k = fdev(mu_prop) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (cudaMemcpyAsync(h->d_mu_prop, mu_prop, D * sizeof(float), k, h->stream) != cudaSuccess) return MPPI_ERR_CUDA;
     if (k == cudaMemcpyHostToDevice && cudaStreamSynchronize(h->stream) != cudaSuccess) return MPPI_ERR_CUDA;

@@ -48,6 +48,8 @@ struct mppi_handle_s {
 // internal launchers shared by the units (no host synchronisation)
 // what the proposal network's features take besides the state, for this handle at control index `step`
 mppi::FeatParams mppi_feature_params(mppi_handle h, uint32_t step);
+// the device the network's buffers live on
+int mppi_mlp_device(mppi_mlp net);
 // the network's small-batch forward: n <= 128 device rows dX [n][62] -> dY [n][48]
 cudaError_t mppi_mlp_forward_small_dev(mppi_mlp net, const float* dX, int n, float* dY, cudaStream_t st);
 // the same on the features (features.cuh) of n device states dS (row stride lds),

@@ -32,6 +32,7 @@
 #include "../../include/mppi.h"
 #include "gemm.h"
 #include "handle.h"
+#include "memkind.h"
 #include "tc.cuh"
 
 using namespace mppi;
@@ -585,6 +586,7 @@ struct mppi_mlp_s {
     float* d_cpart = nullptr;                 // bias-gradient partial column sums [COLSUM_SPLIT][256]
     __nv_bfloat16** d_wbtp = nullptr;
     int step = 0;
+    int device = 0;  // the network's buffers live here
     std::string err;
 };
 
@@ -598,19 +600,30 @@ static mppi_status mfail(mppi_mlp n, mppi_status s, const std::string& m) {
         if (e_ != cudaSuccess) return mfail(net, MPPI_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
     } while (0)
 
-static bool mdev(const void* p) {
-    cudaPointerAttributes at;
-    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+// memory of the current device (or managed memory)
+static bool mdev(const void* p) { return is_local(p); }
+
+// the network's device is the current one and no buffer is another GPU's memory
+static mppi_status local_call(mppi_mlp net, std::initializer_list<const void*> bufs) {
+    const int dev = current_device();
+    if (dev < 0) return mfail(net, MPPI_ERR_CUDA, "cudaGetDevice failed");
+    if (dev != net->device) return mfail(net, MPPI_ERR_ARG, "the network's device is not the current device");
+    if (any_foreign(dev, bufs)) return mfail(net, MPPI_ERR_ARG, "a buffer is memory of another GPU");
+    return MPPI_OK;
 }
+#define MLP_LOCAL_CALL(...)                                              \
+    do {                                                                 \
+        const mppi_status s_ = local_call(net, {__VA_ARGS__});           \
+        if (s_ != MPPI_OK) return s_;                                    \
+    } while (0)
+
+int mppi_mlp_device(mppi_mlp net) { return net->device; }
 
 extern "C" mppi_status mppi_mlp_create(int max_batch, mppi_mlp* out) {
     if (!out || max_batch < 1) return MPPI_ERR_ARG;
     mppi_mlp net = new mppi_mlp_s();
     net->max_batch = max_batch;
+    net->device = current_device();
     long o = 0;
     for (int l = 0; l < NL; l++) {
         net->wofs[l] = o;
@@ -716,6 +729,7 @@ static mppi_status refresh_bf16(mppi_mlp net, cudaStream_t st) {
 
 extern "C" mppi_status mppi_mlp_set_params(mppi_mlp net, const float* params, void* stream) {
     if (!net || !params) return MPPI_ERR_ARG;
+    MLP_LOCAL_CALL(params);
     cudaStream_t st = (cudaStream_t)stream;
     MCK(cudaMemcpyAsync(net->d_p, params, net->nparam * 4, mdev(params) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                         st));
@@ -730,6 +744,7 @@ extern "C" mppi_status mppi_mlp_set_params(mppi_mlp net, const float* params, vo
 
 extern "C" mppi_status mppi_mlp_get_params(mppi_mlp net, float* params, void* stream) {
     if (!net || !params) return MPPI_ERR_ARG;
+    MLP_LOCAL_CALL(params);
     cudaStream_t st = (cudaStream_t)stream;
     const bool dev = mdev(params);
     MCK(cudaMemcpyAsync(params, net->d_p, net->nparam * 4, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
@@ -851,6 +866,7 @@ cudaError_t mppi_mlp_forward_states_dev(mppi_mlp net, const float* dS, int lds, 
 
 extern "C" mppi_status mppi_mlp_forward(mppi_mlp net, const float* X, int B, float* Y, void* stream) {
     if (!net || !X || !Y || B < 1 || B > net->max_batch) return MPPI_ERR_ARG;
+    MLP_LOCAL_CALL(X, Y);
     cudaStream_t st = (cudaStream_t)stream;
     if (B <= SMALL_BATCH) {
         // a few samples: the fused CUDA-core forward (one launch)
@@ -880,6 +896,7 @@ extern "C" mppi_status mppi_mlp_forward(mppi_mlp net, const float* X, int B, flo
 extern "C" mppi_status mppi_mlp_train_step(mppi_mlp net, const float* X, const float* T, int B, float lr,
                                            float weight_decay, float* loss_out, float* grad_out, void* stream) {
     if (!net || !X || !T || B < 1 || B > net->max_batch) return MPPI_ERR_ARG;
+    MLP_LOCAL_CALL(X, T, loss_out, grad_out);
     cudaStream_t st = (cudaStream_t)stream;
     mppi_status s = stage_x(net, X, B, st, true);
     if (s == MPPI_OK) s = forward_bf16(net, B, st, true);

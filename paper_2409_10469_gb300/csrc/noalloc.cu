@@ -26,6 +26,7 @@
 
 #include "../../include/mppi.h"
 #include "kernels.h"
+#include "memkind.h"
 
 using namespace mppi;
 
@@ -46,15 +47,7 @@ void* g_addr[MAX_DEVICES] = {nullptr};
 // device memory of GPU `dev` (or managed memory): the kernels run on the current
 // device, so a buffer on another GPU is rejected instead of being reached
 // through a peer mapping that may not exist
-bool on_device(const void* p, int dev) {
-    cudaPointerAttributes at;
-    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    if (at.type == cudaMemoryTypeManaged) return true;
-    return at.type == cudaMemoryTypeDevice && at.device == dev;
-}
+bool on_device(const void* p, int dev) { return mem_kind(p, dev) == Mem::LOCAL; }
 
 }  // namespace
 

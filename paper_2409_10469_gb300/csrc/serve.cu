@@ -35,6 +35,7 @@
 
 #include "batch.cuh"
 #include "handle.h"
+#include "memkind.h"
 
 using namespace mppi;
 
@@ -129,6 +130,7 @@ struct mppi_server_s {
     std::deque<Request> queue;
     Launch L[2];
     int block = 128, bpsm = 2, sms = 0;
+    int device = 0;  // the robots' handles and the server's buffers live here
     uint64_t submitted = 0, completed = 0, launches = 0, busy_rejects = 0;
     double rollout_steps = 0;
     std::vector<double> lat;
@@ -152,8 +154,8 @@ extern "C" mppi_status mppi_server_create(size_t budget_bytes, int max_robots, i
     s->max_robots = max_robots;
     // enough work items for max_robots solves of max_samples at 16 rollouts per item
     s->max_items = max_robots * ((max_samples + 15) / 16);
-    int dev = 0;
-    cudaGetDevice(&dev);
+    const int dev = current_device();
+    s->device = dev;
     cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
     s->bpsm = std::max(1, std::min(2, max_blocks_per_sm(s->block)));
     bool ok = cudaMalloc((void**)&s->d_pool, budget_bytes) == cudaSuccess;
@@ -209,6 +211,7 @@ extern "C" const char* mppi_server_last_error(mppi_server s) { return s ? s->err
 extern "C" mppi_status mppi_server_add_robot(mppi_server s, mppi_handle h, int* robot_id) {
     if (!s || !h || !robot_id) return MPPI_ERR_ARG;
     if (h->cfg.interp == MPPI_INTERP_DIRECT) return sfail(s, MPPI_ERR_ARG, "served robots use a knot representation");
+    if (h->device != s->device) return sfail(s, MPPI_ERR_ARG, "the handle lives on another device than the server");
     if ((int)s->robots.size() >= s->max_robots) return sfail(s, MPPI_ERR_ARG, "max_robots reached");
     if (h->cfg.K > (s->max_items / s->max_robots) * 16) return sfail(s, MPPI_ERR_ARG, "K above max_samples");
     Robot r;
@@ -224,6 +227,7 @@ extern "C" mppi_status mppi_server_add_robot(mppi_server s, mppi_handle h, int* 
 
 extern "C" mppi_status mppi_server_submit(mppi_server s, int robot, const float* x0, uint32_t step) {
     if (!s || !x0 || robot < 0 || robot >= (int)s->robots.size()) return MPPI_ERR_ARG;
+    if (!host_accessible(x0)) return sfail(s, MPPI_ERR_ARG, "x0 must be host memory");
     Robot& r = s->robots[robot];
     if (r.outstanding) {
         s->busy_rejects++;
@@ -363,6 +367,7 @@ extern "C" mppi_status mppi_server_tick(mppi_server s, int* completed_out) {
 
 extern "C" mppi_status mppi_server_poll(mppi_server s, int robot, float* u0_out, double* latency_s, int* ready) {
     if (!s || robot < 0 || robot >= (int)s->robots.size() || !ready) return MPPI_ERR_ARG;
+    if (u0_out && !host_accessible(u0_out)) return sfail(s, MPPI_ERR_ARG, "u0_out must be host memory");
     Robot& r = s->robots[robot];
     *ready = r.ready ? 1 : 0;
     if (r.ready) {

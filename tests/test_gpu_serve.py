@@ -173,3 +173,22 @@ def test_serving_loop_small():
                     warmup=0.05)
     assert out["requests"] > 0 and out["latency_ms"]["p99"] is not None
     assert out["pool_peak_bytes"] <= out["budget_bytes"]
+
+
+def test_device_buffers_refused_where_host_memory_is_read():
+    """The server reads x0 and writes u0 on the host: device memory there is an
+    argument error, returned before anything is read or written."""
+    import ctypes as C
+    srv = _mppi.Server(32 << 20, 1, 512)
+    c, cfg = robot("stand", 512, 50, inst=1)
+    r = srv.add_robot(c)
+    x_dev = torch.tensor(cfg.x0, dtype=torch.float32, device="cuda")
+    u_dev = torch.zeros(12, device="cuda")
+    L = _mppi.lib()
+    assert L.mppi_server_submit(srv.s, r, C.c_void_p(x_dev.data_ptr()), 0) == _mppi.MPPI_ERR_ARG
+    assert srv.submit(r, cfg.x0, 0) == _mppi.MPPI_OK
+    srv.drain()
+    lat, ready = C.c_double(), C.c_int()
+    assert L.mppi_server_poll(srv.s, r, C.c_void_p(u_dev.data_ptr()), C.byref(lat),
+                              C.byref(ready)) == _mppi.MPPI_ERR_ARG
+    assert srv.poll(r) is not None  # the result is still waiting after the refused poll
