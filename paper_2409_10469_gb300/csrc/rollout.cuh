@@ -13,10 +13,10 @@
 // solves the 6x6 trunk system itself, so the replicated trunk state never
 // diverges between lanes.
 //
-// Precision: the contact spheres' heights are evaluated as FP32 pairs
-// (precise.cuh) from joint angles and trunk / box positions that carry an FP32
-// compensation term (the rounding error of every sub-step's position update)
-// through a dt step; at the end of each dt step the state is rounded to FP32,
+// Precision: the contact spheres' heights (and, against the free box, their
+// positions in the box frame) are evaluated as FP32 pairs (precise.cuh) from
+// joint angles and trunk / box positions that carry an FP32 compensation term
+// (the rounding error of every sub-step's position update) through a dt step; at the end of each dt step the state is rounded to FP32,
 // the granularity of every output (trajectories, costs).  The rest of the
 // sub-step is plain FP32.
 #pragma once
@@ -185,21 +185,41 @@ struct BoxKin {
     float3 p;
     float R[3][3];
     float3 w, v;
+    F2 rz[3];   // row 2 of R as pairs (the corner spheres' heights)
 };
 
 // robot sphere (world centre xw, radius r, centre cb in its body) against the
 // free box (oriented box in its own frame): equal and opposite forces at the
 // sphere's deepest point, from the relative velocity of the two body points.
-// The robot's share goes to (torque, force) with sign SG, the box's to (bt, bf).
-template <int SG, typename Frame>
-__device__ __forceinline__ void sphere_vs_box(const DevModel& m, const BoxKin& B, float3 xw, float r, float3 cb,
-                                              float3 w, float3 v, const Frame& F, float3& torque, float3& force,
-                                              float3& bt, float3& bf, bool on = true) {
-    const float3 xl = mulRT(B.R, xw - B.p);
+// An FP32 test first drops the spheres that cannot reach the box (its error,
+// ~1e-6 m, is far inside the 1e-4 m margin); a sphere within reach enters the
+// box frame as pairs, R^T (x - p) with the centre (pos(): its world position as
+// pairs), the box's position and the rows of R as pairs -- a difference of
+// ~0.5 m terms, as for the ground: FP32 would leave ~3e-8 m on the depth.  The
+// robot's share goes to (torque, force) with sign SG, the box's to (bt, bf).
+template <int SG, typename Frame, typename PairPos>
+__device__ __forceinline__ void sphere_vs_box(const DevModel& m, const BoxKin& B, const BoxState& Bx, float3 xw,
+                                              float r, float3 cb, float3 w, float3 v, const Frame& F,
+                                              float3& torque, float3& force, float3& bt, float3& bf,
+                                              const PairPos& pos, bool on = true) {
     const float3 hb = f3(m.box_half[0], m.box_half[1], m.box_half[2]);
+    const float3 x32 = mulRT(B.R, xw - B.p);
+    const float reach = r + 1e-4f;
+    if (!on || fabsf(x32.x) > hb.x + reach || fabsf(x32.y) > hb.y + reach || fabsf(x32.z) > hb.z + reach) return;
+    F2 xp, yp, zp;
+    pos(xp, yp, zp);
+    F2 brx[3], bry[3];
+    quat_rows01(Bx.quat, Bx.quatl, brx, bry);
+    const F2 dx = f2_sub(xp, F2{Bx.p[0], Bx.pl[0]}), dy = f2_sub(yp, F2{Bx.p[1], Bx.pl[1]});
+    const F2 dz = f2_sub(zp, F2{Bx.p[2], Bx.pl[2]});
+    F2 xq[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+        xq[k] = f2_norm(f2_add(f2_add(f2_mul(brx[k], dx), f2_mul(bry[k], dy)), f2_mul(B.rz[k], dz)));
+    const float3 xl = f3(xq[0].h, xq[1].h, xq[2].h);
     float3 nl;
     float pen;
-    if (!on || !sphere_aabb(xl, r, -hb, hb, nl, pen)) return;
+    if (!sphere_aabb(xl, r, -hb, hb, nl, pen, f3(xq[0].l, xq[1].l, xq[2].l))) return;
     const float3 nw = mulR(B.R, nl);
     const float3 nb = F(nw);
     const float3 pc_b = cb - r * nb;                      // contact point, robot body frame
@@ -388,14 +408,15 @@ __device__ __forceinline__ LegGeom leg_geom(const DevModel& m, int leg) {
     return g;
 }
 
-// p += h dp with the height's rounding error (and, over terrain, the horizontal
-// ones: the heightfield and the static boxes are looked up at x, y) kept in pl
-template <int TERR>
+// p += h dp with the height's rounding error (and, over terrain or with the
+// free box, the horizontal ones: the heightfield and the static boxes are looked
+// up at x, y, and robot spheres meet the box sideways) kept in pl
+template <bool XY>
 __device__ __forceinline__ void advance_pos(float p[3], float pl[3], float3 dp, float h) {
     const float d[3] = {dp.x, dp.y, dp.z};
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        if (TERR == 0 && k < 2) {
+        if (!XY && k < 2) {
             p[k] = fmaf(h, d[k], p[k]);
             continue;
         }
@@ -447,6 +468,7 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, const LegGeo
         quat_R(Bx.quat, BK.R);
         BK.w = Bx.w;
         BK.v = Bx.v;
+        quat_row2(Bx.quat, Bx.quatl, BK.rz[0], BK.rz[1], BK.rz[2]);
     }
 
     // ---- leg kinematics: joint transforms, body velocities, velocity products.
@@ -469,7 +491,8 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, const LegGeo
     F2 rz0, rz1, rz2;
     quat_row2(T.quat, T.quatl, rz0, rz1, rz2);
     const F2 pz_t = {T.p[2], T.pl[2]};
-    // over terrain the spheres' horizontal positions as pairs too (rows 0 and 1)
+    // over terrain the spheres' horizontal positions as pairs too (rows 0 and 1;
+    // against the free box they are formed only for spheres within its reach)
     F2 rx[3], ry[3];
     if (TERR != 0) quat_rows01(T.quat, T.quatl, rx, ry);
     const F2 px_t = {T.p[0], T.pl[0]}, py_t = {T.p[1], T.pl[1]};
@@ -518,7 +541,21 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, const LegGeo
         const CalfFrame toCalf = {R0[0][0], R0[0][1], R0[0][2], R0[1][0], R0[1][1], R0[1][2],
                                   R0[2][0], R0[2][1], R0[2][2], c0, s0, c1, s1, c2, s2};
         sphere_env<TERR, -1>(m, xw, xpw, ypw, zw, m.foot_r, foot, wc, vc, toCalf, pa_n, pa_f);
-        if (BOX) sphere_vs_box<-1>(m, BK, xw, m.foot_r, foot, wc, vc, toCalf, pa_n, pa_f, bx_t, bx_f);
+        if (BOX) {
+            const auto foot_pos = [&](F2& X, F2& Y, F2& Z) {
+                if (TERR != 0) {
+                    X = xpw;
+                    Y = ypw;
+                } else {
+                    F2 qx[3], qy[3];
+                    quat_rows01(T.quat, T.quatl, qx, qy);
+                    X = f2_add(f2_add(px_t, f2_mul(qx[0], px)), f2_add(f2_mul(qx[1], py), f2_mul(qx[2], pz)));
+                    Y = f2_add(f2_add(py_t, f2_mul(qy[0], px)), f2_add(f2_mul(qy[1], py), f2_mul(qy[2], pz)));
+                }
+                Z = zw;
+            };
+            sphere_vs_box<-1>(m, BK, Bx, xw, m.foot_r, foot, wc, vc, toCalf, pa_n, pa_f, bx_t, bx_f, foot_pos);
+        }
     }
     // the calf's articulated inertia after projection is a model constant
     const float D2inv = m.calf_D_inv;
@@ -572,14 +609,27 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, const LegGeo
         const TrunkFrame toTrunk = {R0[0][0], R0[0][1], R0[0][2], R0[1][0], R0[1][1], R0[1][2],
                                     R0[2][0], R0[2][1], R0[2][2]};
         sphere_env<TERR, -1>(m, xw, xpw, ypw, zw, m.tsph_r, cb, T.w, T.v, toTrunk, pa_n, pa_f, on);
-        if (BOX) sphere_vs_box<-1>(m, BK, xw, m.tsph_r, cb, T.w, T.v, toTrunk, pa_n, pa_f, bx_t, bx_f, on);
+        if (BOX) {
+            const auto tsph_pos = [&](F2& X, F2& Y, F2& Z) {
+                if (TERR != 0) {
+                    X = xpw;
+                    Y = ypw;
+                } else {
+                    F2 qx[3], qy[3];
+                    quat_rows01(T.quat, T.quatl, qx, qy);
+                    X = f2_add(px_t, f2_mulf(qx[0], tx));
+                    Y = f2_add(py_t, f2_mulf(qy[0], tx));
+                }
+                Z = zw;
+            };
+            sphere_vs_box<-1>(m, BK, Bx, xw, m.tsph_r, cb, T.w, T.v, toTrunk, pa_n, pa_f, bx_t, bx_f, tsph_pos, on);
+        }
     }
     // ---- the box's 8 corner spheres against the static environment, 2 per lane
     if (BOX) {
         const TrunkFrame toBox = {BK.R[0][0], BK.R[0][1], BK.R[0][2], BK.R[1][0], BK.R[1][1], BK.R[1][2],
                                   BK.R[2][0], BK.R[2][1], BK.R[2][2]};
-        F2 bz0, bz1, bz2;
-        quat_row2(Bx.quat, Bx.quatl, bz0, bz1, bz2);
+        const F2 bz0 = BK.rz[0], bz1 = BK.rz[1], bz2 = BK.rz[2];
 #pragma unroll
         for (int cc = 0; cc < 2; cc++) {
             const int cn = 2 * leg + cc;
@@ -705,7 +755,7 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, const LegGeo
     T.v = f3(fmaf(h, av.x, fmaf(hg, R0[2][0], T.v.x)), fmaf(h, av.y, fmaf(hg, R0[2][1], T.v.y)),
              fmaf(h, av.z, fmaf(hg, R0[2][2], T.v.z)));
     const float3 dp = mulR(R0, T.v);
-    advance_pos<TERR>(T.p, T.pl, dp, h);
+    advance_pos<TERR != 0 || BOX>(T.p, T.pl, dp, h);
     quat_integrate_pair(T.quat, T.quatl, T.qc, T.w, h);
     if (BOX) {
         // Newton-Euler of the box about its centre (principal axes), from the summed wrench
@@ -720,7 +770,7 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, const LegGeo
         Bx.w = Bx.w + h * aw_b;
         Bx.v = Bx.v + h * av_b;
         const float3 dpb = mulR(BK.R, Bx.v);
-        advance_pos<TERR>(Bx.p, Bx.pl, dpb, h);
+        advance_pos<true>(Bx.p, Bx.pl, dpb, h);
         quat_integrate_pair(Bx.quat, Bx.quatl, Bx.qc, Bx.w, h);
     }
 }

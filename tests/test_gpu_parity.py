@@ -212,7 +212,8 @@ def teacher_forced(cfg, K, H, t0=0.0):
 def test_rollout_teacher_forced(which):
     """every dt step of every GPU rollout matches the oracle stepped from the same
     FP32 state within 1e-5 per block (state_parity's conditioning exception for
-    at most 1% of steps), but for robot-box contacts (see below); the GPU's
+    at most 1% of steps), robot-box contacts of the push task included (their
+    depths are formed from pair positions in the box frame); the GPU's
     accumulated cost matches the oracle's L_walk evaluated along the GPU
     trajectory (<= 1e-5: the cost arithmetic alone)"""
     if which == "stand":
@@ -225,24 +226,18 @@ def test_rollout_teacher_forced(which):
         cfg, K, H, t0 = W.config_push(), 40, 100, 0.0
     (e_gpu, S, X), cost_rel = teacher_forced(cfg, K, H, t0)
     assert cost_rel.max() <= 1e-5, cost_rel.max()
-    if which != "push":
-        bad, n_exc = state_parity(e_gpu, S)
-        assert not bad, (bad, n_exc)
-        return
-    # A robot sphere against the free box is still evaluated from FP32 positions
-    # (the box's orientation would be needed as pairs too): steps with such a
-    # contact are held to 5e-5 and counted; every other push step meets the rule.
-    n = len(X)
-    world = O.World(cfg.robot)
-    away = X.copy()
-    away[:, 37:40] = (50.0, 50.0, 0.21)
-    touch = np.array([np.abs(O.contact_fext(world, X[i])[0] - O.contact_fext(world, away[i])[0]).max() > 0
-                      for i in range(n)])
-    keep = ~touch
-    bad, n_exc = state_parity({k: v[keep] for k, v in e_gpu.items()}, {k: v[keep] for k, v in S.items()})
+    if which == "push":
+        # the steps with a robot-box contact must be among those checked
+        world = O.World(cfg.robot)
+        away = X.copy()
+        away[:, 37:40] = (50.0, 50.0, 0.21)
+        touch = np.array([np.abs(O.contact_fext(world, X[i])[0] - O.contact_fext(world, away[i])[0]).max() > 0
+                          for i in range(len(X))])
+        assert touch.sum() >= 10, touch.sum()
+        print("push: %d of %d steps with a robot-box contact, worst block error there %.2e"
+              % (touch.sum(), len(X), max(float(v[touch].max()) for v in e_gpu.values())))
+    bad, n_exc = state_parity(e_gpu, S)
     assert not bad, (bad, n_exc)
-    worst_touch = max((float(v[touch].max()) for v in e_gpu.values()), default=0.0) if touch.any() else 0.0
-    assert worst_touch <= 5e-5, worst_touch
 
 
 @pytest.mark.parametrize("which", ["stand", "trot", "terrain", "push"])
