@@ -427,7 +427,7 @@ def multi_instance(peak, steps=20):
             "rollout_steps_per_batch_step": r["rollout_steps_per_batch_step"],
             "rollout_steps_per_s": r["best_rollout_steps_per_s"],
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                         "kernel": "k_batch<128, true> (one model and cost: parameter-bank form)", "flops_per_launch": fl}}
+                         "kernel": "k_batch<128, UNI_TERRAIN> (one model and cost: parameter-bank form)", "flops_per_launch": fl}}
 
 
 def run_ours(args):

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmppi_gb300.so")
-SOURCES = ["api.cu", "sample.cu", "rollout.cu", "update.cu", "noalloc.cu", "batch.cu", "batch_uni.cu", "serve.cu", "mlp.cu", "gemm.cu", "features.cu"]
+SOURCES = ["api.cu", "sample.cu", "rollout.cu", "update.cu", "noalloc.cu", "batch.cu", "batch_uni.cu", "batch_uni_box.cu", "serve.cu", "mlp.cu", "gemm.cu", "features.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include"), "-I" + BUILD]

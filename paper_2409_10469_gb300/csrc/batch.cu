@@ -41,14 +41,26 @@ using namespace mppi;
 
 namespace mppi {
 
-// the uniform-model kernels are compiled in batch_uni.cu
-extern template cudaError_t launch_k_batch<64, true>(const BatchArgs&, int, cudaStream_t);
-extern template cudaError_t launch_k_batch<128, true>(const BatchArgs&, int, cudaStream_t);
-extern template cudaError_t launch_k_batch<256, true>(const BatchArgs&, int, cudaStream_t);
+// the shared-model kernels are compiled in batch_uni.cu (no box) and batch_uni_box.cu
+#define MPPI_UNI_EXTERN(B)                                                                  \
+    extern template cudaError_t launch_k_batch<B, UNI_FLAT>(const BatchArgs&, int, cudaStream_t);    \
+    extern template cudaError_t launch_k_batch<B, UNI_TERRAIN>(const BatchArgs&, int, cudaStream_t); \
+    extern template cudaError_t launch_k_batch<B, UNI_FLAT_BOX>(const BatchArgs&, int, cudaStream_t); \
+    extern template cudaError_t launch_k_batch<B, UNI_TERRAIN_BOX>(const BatchArgs&, int, cudaStream_t);
+MPPI_UNI_EXTERN(64)
+MPPI_UNI_EXTERN(128)
+MPPI_UNI_EXTERN(256)
+#undef MPPI_UNI_EXTERN
 
 template <int BLOCK>
 static cudaError_t launch_batch_t(const BatchArgs& a, int grid, cudaStream_t st) {
-    return a.uniform ? launch_k_batch<BLOCK, true>(a, grid, st) : launch_k_batch<BLOCK, false>(a, grid, st);
+    if (!a.uniform) return launch_k_batch<BLOCK, UNI_NONE>(a, grid, st);
+    switch (uni_kind(a.model)) {
+        case UNI_FLAT: return launch_k_batch<BLOCK, UNI_FLAT>(a, grid, st);
+        case UNI_TERRAIN: return launch_k_batch<BLOCK, UNI_TERRAIN>(a, grid, st);
+        case UNI_FLAT_BOX: return launch_k_batch<BLOCK, UNI_FLAT_BOX>(a, grid, st);
+        default: return launch_k_batch<BLOCK, UNI_TERRAIN_BOX>(a, grid, st);
+    }
 }
 
 void set_uniform(BatchArgs& a, const InstDesc* d, int n) {
@@ -76,10 +88,10 @@ cudaError_t launch_batch(const BatchArgs& a, int block, int grid, cudaStream_t s
 int max_blocks_per_sm(int block) {
     int n = 0;
     cudaError_t e = cudaErrorInvalidValue;
-    // (both variants have the same launch bounds)
-    if (block == 64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<64, false>, 64, 0);
-    if (block == 128) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<128, false>, 128, 0);
-    if (block == 256) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<256, false>, 256, 0);
+    // (every variant has the same launch bounds)
+    if (block == 64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<64, UNI_NONE>, 64, 0);
+    if (block == 128) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<128, UNI_NONE>, 128, 0);
+    if (block == 256) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch<256, UNI_NONE>, 256, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;

@@ -181,10 +181,27 @@ __device__ void block_update(const InstDesc& d, float* u0_row) {
     if (tid < D) d.mu[tid] = shifted_knot(s_mu, d.interp, d.H, d.ctrl_steps, tid / NJ, tid % NJ);
 }
 
+// Kernel variants: UNI_NONE reads each item's model and cost from its
+// descriptor; the UNI_* forms serve launches whose instances share one model
+// and cost (the launch parameters), one per terrain / box combination, so each
+// holds only the rollout code its model runs.
+enum : int { UNI_NONE = 0, UNI_FLAT = 1, UNI_TERRAIN = 2, UNI_FLAT_BOX = 3, UNI_TERRAIN_BOX = 4 };
+
+// the shared-model variant for a model
+inline int uni_kind(const DevModel& m) {
+    const bool terr = m.terrain != 0 || m.n_sbox > 0;
+    return m.has_box ? (terr ? UNI_TERRAIN_BOX : UNI_FLAT_BOX) : (terr ? UNI_TERRAIN : UNI_FLAT);
+}
+
 // one item's rollouts on the terrain / box variant its model needs
+template <int UNI>
 __device__ __forceinline__ float rollout_item(const DevModel& m, const DevCost& c, const HorizonArgs& hz,
                                               const float* x0, const float (&Uk)[NKNOT][3], int leg, int k,
                                               bool valid) {
+    if (UNI == UNI_FLAT) return rollout_lane<0, false>(m, c, hz, x0, Uk, nullptr, leg, k, valid, nullptr);
+    if (UNI == UNI_TERRAIN) return rollout_lane<1, false>(m, c, hz, x0, Uk, nullptr, leg, k, valid, nullptr);
+    if (UNI == UNI_FLAT_BOX) return rollout_lane<0, true>(m, c, hz, x0, Uk, nullptr, leg, k, valid, nullptr);
+    if (UNI == UNI_TERRAIN_BOX) return rollout_lane<1, true>(m, c, hz, x0, Uk, nullptr, leg, k, valid, nullptr);
     if (m.terrain != 0 || m.n_sbox > 0)
         return m.has_box ? rollout_lane<1, true>(m, c, hz, x0, Uk, nullptr, leg, k, valid, nullptr)
                          : rollout_lane<1, false>(m, c, hz, x0, Uk, nullptr, leg, k, valid, nullptr);
@@ -198,8 +215,8 @@ __device__ __forceinline__ float rollout_item(const DevModel& m, const DevCost& 
 #define BATCH_BLOCKS_128 3
 #endif
 
-// UNI: every instance has the launch's model and cost (a.model, a.cost)
-template <int BLOCK, bool UNI>
+// UNI != UNI_NONE: every instance has the launch's model and cost (a.model, a.cost)
+template <int BLOCK, int UNI>
 __global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 1 : (BLOCK == 128 ? BATCH_BLOCKS_128 : 384 / BLOCK))
     k_batch(const __grid_constant__ BatchArgs a) {
     __shared__ InstDesc sd;
@@ -230,8 +247,8 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 1 : (BLOCK == 128 ? BATC
                                                                           : (float)t0d;
         const HorizonArgs hz = {sd.H, sd.n_sub, sd.nx, sd.h, sd.dt, sd.inv_Hm1, t0, sd.arm, sd.interp, sd.Bt};
         const float* x0 = a.x0s + (size_t)w.inst * NX_BOX;
-        const float L = UNI ? rollout_item(a.model, a.cost, hz, x0, Uk, leg, k, valid)
-                            : rollout_item(sd.model, sd.cost, hz, x0, Uk, leg, k, valid);
+        const float L = UNI != UNI_NONE ? rollout_item<UNI>(a.model, a.cost, hz, x0, Uk, leg, k, valid)
+                                        : rollout_item<UNI>(sd.model, sd.cost, hz, x0, Uk, leg, k, valid);
         if (valid && leg == 0) sd.L[k] = L;
         if (cta_count_in(a.done + w.inst, (unsigned)w.n, (unsigned)sd.K, s_last)) {
             block_update<BLOCK>(sd, a.u0s + (size_t)w.inst * NJ);
@@ -241,7 +258,7 @@ __global__ void __launch_bounds__(BLOCK, BLOCK == 256 ? 1 : (BLOCK == 128 ? BATC
     }
 }
 
-template <int BLOCK, bool UNI>
+template <int BLOCK, int UNI>
 cudaError_t launch_k_batch(const BatchArgs& a, int grid, cudaStream_t st) {
     k_batch<BLOCK, UNI><<<grid, BLOCK, 0, st>>>(a);
     return cudaGetLastError();
