@@ -126,16 +126,33 @@ def test_shared_model_batch_matches_single_instance_steps():
     assert not mixed.shared_model()
 
 
-def test_batch_alone_equals_mixed_bit_exact():
-    """a one-instance batch takes the parameter-bank kernel, the mixed batch the
-    general one: the same instance's results are bit-identical"""
-    cfg = W.config_trot()
+def push_on_steps():
+    """the push task on a model that also has a static box (out of the robot's
+    reach): the free box and the static-environment code in one model"""
+    cfg = W.config_push()
+    rb = W.robot(box=True, static_boxes=[((2.5, -0.5, -0.2), (3.0, 0.5, 0.1))])
+    return W.Workload("push_static_box", rb, cfg.cost, cfg.mppi, cfg.x0, cfg.mu0, cfg.steps)
+
+
+ALONE = {"trot": W.config_trot, "terrain": W.config_terrain, "push": W.config_push,
+         "push_static_box": push_on_steps}
+
+
+@pytest.mark.parametrize("task", list(ALONE))
+def test_batch_alone_equals_mixed_bit_exact(task):
+    """a one-instance batch takes the parameter-bank kernel of its model's
+    terrain / free-box variant (flat, terrain, free box, free box with a static
+    box), the mixed batch the general one: the same instance's results are
+    bit-identical"""
+    cfg = ALONE[task]()
     alone, _ = make(cfg, 256, 50, seed=7, inst=3)
     b1 = _mppi.Batch([alone])
+    assert b1.shared_model()
     twin, _ = make(cfg, 256, 50, seed=7, inst=3)
     others = [make(W.config_terrain(), 512, 150, inst=9)[0], make(W.config_stand(), 1024, 100, inst=4)[0],
               make(W.config_push(), 128, 100, inst=5)[0]]
     b2 = _mppi.Batch([others[0], twin, others[1], others[2]])
+    assert not b2.shared_model()
     x0 = x0_row(cfg)
     x0s = np.stack([x0_row(W.config_terrain()), x0, x0_row(W.config_stand()), x0_row(W.config_push())])
     for step in range(3):
