@@ -38,7 +38,7 @@ METRIC = "rollout-steps/s (MPPI step, K=4096, H=100)"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture) of
 # one k_rollout launch on this workload, valid only for the kernel sources whose
 # SHA-256 prefix is given; reported as null once those sources change.
-ROLLOUT_TRAFFIC = {"bytes": 171008, "sources_sha256": "09ed80acc52e28a0"}
+ROLLOUT_TRAFFIC = {"bytes": 106240, "sources_sha256": "6d12a4c3579f2422"}
 ROLLOUT_SOURCES = ("rollout.cu", "rollout.cuh", "common.cuh", "noise.cuh", "kernels.h", "precise.cuh")
 
 

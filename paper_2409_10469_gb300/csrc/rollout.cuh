@@ -9,9 +9,9 @@
 // Mapping: one rollout = 4 consecutive lanes, one lane per leg.  Each lane runs
 // its leg's 3-body chain of every ABA pass in registers; the legs meet only at
 // the trunk, whose articulated inertia (21 numbers) and bias force (6) are summed
-// with two xor-shuffle rounds.  Every lane then holds bit-identical trunk sums and
-// solves the 6x6 trunk system itself, so the replicated trunk state never
-// diverges between lanes.
+// with two xor-shuffle rounds (two values per packed addition).  Every lane then
+// holds bit-identical trunk sums and solves the 6x6 trunk system itself, so the
+// replicated trunk state never diverges between lanes.
 //
 // Precision: the contact spheres' heights (and, against the free box, their
 // positions in the box frame) are evaluated as FP32 pairs (precise.cuh) from
@@ -43,6 +43,17 @@ __device__ __forceinline__ float xsum4(float v) {
     v += __shfl_xor_sync(0xffffffffu, v, 1);
     v += __shfl_xor_sync(0xffffffffu, v, 2);
     return v;
+}
+
+// xsum4 of two values at once: each round adds both by one packed FP32
+// addition (two IEEE additions, each rounded as xsum4's), so a and b come out
+// bit-identical to xsum4(a), xsum4(b) in half the add instructions
+__device__ __forceinline__ void xsum4_pair(float& a, float& b) {
+    float2 v = make_float2(a, b);
+    v = __fadd2_rn(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, 1), __shfl_xor_sync(0xffffffffu, v.y, 1)));
+    v = __fadd2_rn(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, 2), __shfl_xor_sync(0xffffffffu, v.y, 2)));
+    a = v.x;
+    b = v.y;
 }
 
 // ---------------------------------------------------------------- terrain
@@ -644,31 +655,51 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, const LegGeo
         }
     }
 
-    // ---- trunk: sum the 4 legs' contributions, add the trunk's own terms
+    // ---- trunk: sum the 4 legs' contributions (27 values: 13 packed pairs and
+    // one single), add the trunk's own terms
     float Mt[6][6], bt[6];
+    float3 sn, sf;   // the legs' bias terms less the lanes' trunk-sphere wrenches, summed
+    {
+        float v[27];
 #pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = i; j < 3; j++) {
-            Mt[i][j] = xsum4(IA.A[sidx(i, j)]);
-            Mt[3 + i][3 + j] = xsum4(IA.C[sidx(i, j)]);
+        for (int i = 0; i < 6; i++) {
+            v[i] = IA.A[i];
+            v[6 + i] = IA.C[i];
         }
 #pragma unroll
-    for (int i = 0; i < 3; i++)
+        for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) Mt[i][3 + j] = xsum4(IA.B[i][j]);
+            for (int j = 0; j < 3; j++) v[12 + 3 * i + j] = IA.B[i][j];
+        v[21] = pa_n.x; v[22] = pa_n.y; v[23] = pa_n.z;
+        v[24] = pa_f.x; v[25] = pa_f.y; v[26] = pa_f.z;
+#pragma unroll
+        for (int q = 0; q < 13; q++) xsum4_pair(v[2 * q], v[2 * q + 1]);
+        v[26] = xsum4(v[26]);
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = i; j < 3; j++) {
+                Mt[i][j] = v[sidx(i, j)];
+                Mt[3 + i][3 + j] = v[6 + sidx(i, j)];
+            }
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int j = 0; j < 3; j++) Mt[i][3 + j] = v[12 + 3 * i + j];
+        sn = f3(v[21], v[22], v[23]);
+        sf = f3(v[24], v[25], v[26]);
+    }
 #pragma unroll
     for (int i = 0; i < 3; i++) {
         Mt[i][i] += m.tr_Ic[i];
         Mt[3 + i][3 + i] += m.tr_m;
     }
     {
-        // per-lane terms (leg bias less this lane's trunk-sphere wrench) summed
-        // over the 4 lanes, then the trunk's own bias v x* I v once
+        // the trunk's own bias v x* I v, once, on the summed terms
         const float3 Iw = f3(m.tr_Ic[0] * T.w.x, m.tr_Ic[1] * T.w.y, m.tr_Ic[2] * T.w.z);
-        const float3 bn = cross_acc(T.w, Iw, f3(xsum4(pa_n.x), xsum4(pa_n.y), xsum4(pa_n.z)));
+        const float3 bn = cross_acc(T.w, Iw, sn);
         const float3 mv = m.tr_m * T.v;
-        const float3 bf = cross_acc(T.w, mv, f3(xsum4(pa_f.x), xsum4(pa_f.y), xsum4(pa_f.z)));
+        const float3 bf = cross_acc(T.w, mv, sf);
         bt[0] = bn.x; bt[1] = bn.y; bt[2] = bn.z;
         bt[3] = bf.x; bt[4] = bf.y; bt[5] = bf.z;
     }
@@ -759,8 +790,10 @@ __device__ __forceinline__ void substep(const DevModel& m, int leg, const LegGeo
     quat_integrate_pair(T.quat, T.quatl, T.qc, T.w, h);
     if (BOX) {
         // Newton-Euler of the box about its centre (principal axes), from the summed wrench
-        const float3 tb = f3(xsum4(bx_t.x), xsum4(bx_t.y), xsum4(bx_t.z));
-        const float3 fb = f3(xsum4(bx_f.x), xsum4(bx_f.y), xsum4(bx_f.z));
+        float3 tb = bx_t, fb = bx_f;
+        xsum4_pair(tb.x, tb.y);
+        xsum4_pair(tb.z, fb.x);
+        xsum4_pair(fb.y, fb.z);
         const float3 Iw = f3(m.box_Ic[0] * BK.w.x, m.box_Ic[1] * BK.w.y, m.box_Ic[2] * BK.w.z);
         const float3 wxIw = cross3(BK.w, Iw), wxv = cross3(BK.w, BK.v);
         const float3 aw_b = f3((tb.x - wxIw.x) * m.box_inv_Ic[0], (tb.y - wxIw.y) * m.box_inv_Ic[1],
