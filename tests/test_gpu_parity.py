@@ -171,6 +171,8 @@ def test_one_step_state_parity(which):
     assert np.array_equal(tg[:, 0], X)
     e_gpu = rel_block(tg[:, 1].astype(np.float64), ref)
     bad, n_exc = state_parity(e_gpu, fp32_conditioning(step, X64, ref))
+    print("one-step %s: worst block %.2e, %d of %d states excepted" %
+          (which, max(float(v.max()) for v in e_gpu.values()), n_exc, n))
     assert not bad, (bad, n_exc)
 
 
@@ -237,13 +239,17 @@ def test_rollout_teacher_forced(which):
         print("push: %d of %d steps with a robot-box contact, worst block error there %.2e"
               % (touch.sum(), len(X), max(float(v[touch].max()) for v in e_gpu.values())))
     bad, n_exc = state_parity(e_gpu, S)
+    print("teacher-forced %s: worst block %.2e, %d of %d steps excepted, cost %.2e" %
+          (which, max(float(v.max()) for v in e_gpu.values()), n_exc, len(X), cost_rel.max()))
     assert not bad, (bad, n_exc)
 
 
 @pytest.mark.parametrize("which", ["stand", "trot", "terrain", "push"])
 def test_rollout_cost_parity(which):
     """full-horizon rollout cost (the stated 1e-3 bound): <= 1e-3 relative for every
-    sample, on the model spec's well-conditioned sub-step"""
+    sample on flat ground, over the heightfield and with the free box (the contact
+    depths are pair-precise; the heightfield's slope still jumps at cell edges,
+    which makes the terrain samples the closest, ~9e-4)"""
     if which == "stand":
         cfg, K, H, t0 = W.config_stand(), 100, 50, 0.0
     elif which == "trot":
@@ -265,20 +271,9 @@ def test_rollout_cost_parity(which):
     Lo = O.rollouts(world, cfg.cost, m, t0, x0d, U.cpu().numpy())
     rel = np.abs(Lg - Lo) / np.maximum(np.abs(Lo), 1.0)
     assert np.all(np.isfinite(Lg))
-    if which in ("stand", "trot"):
-        assert rel.max() <= 1e-3, (rel.max(), np.percentile(rel, 99))
-    else:
-        # a bilinear heightfield's slope jumps at cell edges, a box's normal jumps
-        # at its edges: a rollout that crosses one at the wrong moment is not
-        # determined to 1e-3 even in FP64; bound every sample by max(1e-3, 3x its
-        # own FP64 sensitivity)
-        sens = np.zeros(K)
-        for sd in range(2):
-            xp = x0d * (1 + 1e-7 * np.random.default_rng(sd).standard_normal(x0d.shape))
-            Lp = O.rollouts(world, cfg.cost, m, t0, xp, U.cpu().numpy())
-            sens = np.maximum(sens, np.abs(Lp - Lo) / np.maximum(np.abs(Lo), 1.0))
-        assert np.percentile(rel, 95) <= 1e-3
-        assert np.all(rel <= np.maximum(1e-3, 3 * sens)), (rel.max(), sens[rel.argmax()])
+    print("full-horizon cost %s K=%d: max %.2e, p95 %.2e, above 1e-3: %d" %
+          (which, K, rel.max(), np.percentile(rel, 95), int(np.sum(rel > 1e-3))))
+    assert rel.max() <= 1e-3, (rel.max(), np.percentile(rel, 99))
 
 
 def test_rollout_cost_within_fp64_sensitivity():
